@@ -1,0 +1,162 @@
+/*
+ * vlasov.h -- C ABI of libvlasov, the GB300 (sm_103a) hot path of the split 6D
+ * Vlasov solver for relic neutrinos (Yoshikawa, Tanaka & Yoshida, SC'21).
+ *
+ * The library advances the neutrino distribution function f(x, u) on a
+ * uniform 6D grid with the directionally split scheme of Eq. (5): three 1D
+ * position advections, Eq. (3), and three 1D velocity advections, Eq. (4),
+ * each done by SL-MPP5 (Sec. 4.2: conservative semi-Lagrangian flux, one
+ * flux evaluation per step, monotonicity- and positivity-preserving
+ * constraints), and reduces f to the density rho_nu(x) = int f d^3u that feeds
+ * the Poisson equation, Eq. (2).
+ *
+ * Conventions for every entry point
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *   - The caller owns every buffer it passes (f, scale, phi, rho, lambda).
+ *     The library owns only its scratch, allocated in vlasov_init and freed by
+ *     vlasov_destroy.
+ *   - All GPU work is queued on the context's stream and is asynchronous
+ *     unless the entry point says it synchronises.
+ *   - Return value 0 = success, a negative VLASOV_E* code on failure; the
+ *     message is available from vlasov_last_error().  No C++ exception and
+ *     no device trap crosses this boundary.  Errors detected on the device
+ *     (a velocity Courant number >= 1, a NaN, a bounded wait that ran out)
+ *     are sticky in a device word and are returned by vlasov_status().
+ *
+ * Grid and layout
+ *   f is one array f[ix][iy][iz][jx][jy][jz] with jz fastest (Listing 1 keeps
+ *   each spatial cell's velocity cube contiguous with u_z innermost).
+ *   Spatial cell centres x_i = (i + 1/2) L / n, periodic on 0 <= x < L
+ *   (Sec. 4.1.3).  Velocity cell centres u_j = -V + (j + 1/2) du, du = 2V/n_u,
+ *   on -V <= u < V; the outer velocity faces carry no flux.
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VLASOV_OK 0
+#define VLASOV_EINVAL (-1)   /* bad argument: axis, size, null or misaligned pointer */
+#define VLASOV_ECFL (-2)     /* a velocity-sweep Courant number |nu| >= 1           */
+#define VLASOV_ECUDA (-3)    /* a CUDA runtime call failed                            */
+#define VLASOV_ENAN (-4)     /* a sweep produced a NaN/Inf or a negative line sum     */
+#define VLASOV_ETIMEOUT (-5) /* a bounded device wait ran out (kernel returned early) */
+#define VLASOV_ENOMEM (-6)   /* scratch allocation failed                             */
+
+/* storage type of f */
+#define VLASOV_F64 0
+#define VLASOV_F32 1
+#define VLASOV_BF16 2
+#define VLASOV_F16 3
+
+typedef struct vlasov_ctx vlasov_ctx; /* opaque, owned by the library */
+
+typedef struct {
+    int nx, ny, nz;    /* spatial cells (each >= 4, <= 256)                    */
+    int nux, nuy, nuz; /* velocity cells (each >= 4, <= 256, multiple of 4)    */
+    double L;          /* box side                                              */
+    double V;          /* velocity half-extent: -V <= u < V                     */
+    int dtype;         /* VLASOV_F64 / F32 (BF16 / F16 reserved for the codec)  */
+} vlasov_grid;
+
+/*
+ * Create a context for the grid g and the caller's distribution function
+ * f_dev (nx*ny*nz*nux*nuy*nuz elements of g->dtype, 16-byte aligned).
+ * scale_dev must be NULL for F64/F32.  stream is a cudaStream_t (NULL = the
+ * legacy default stream).  Allocates the library's scratch on the current
+ * device.  On success *out receives the context.
+ */
+int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev,
+                void *stream);
+
+/* Free the scratch and the context (synchronises the stream).  NULL is a no-op. */
+void vlasov_destroy(vlasov_ctx *ctx);
+
+/* Queue all later work of ctx on this cudaStream_t. */
+int vlasov_set_stream(vlasov_ctx *ctx, void *stream);
+
+/*
+ * One directional sweep D_axis(dt) of f in place (Eq. 3 for axis 0..2 =
+ * x, y, z; Eq. 4 for axis 3..5 = u_x, u_y, u_z).
+ *   Position sweep i: Courant number nu_j = u_j dt / (a^2 dx_i) for each
+ *   velocity column j (any magnitude: whole-cell shifts are exact);
+ *   phi_dev is ignored.
+ *   Velocity sweep i: nu(x) = -g_i(x) dt / du_i, g_i the periodic 4th-order
+ *   central difference of phi_dev (nx*ny*nz FP32, C order).  |nu| must be < 1
+ *   in every cell; a cell that breaks it is left unchanged and VLASOV_ECFL is
+ *   raised through vlasov_status().  a is ignored.
+ */
+int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *phi_dev);
+
+/*
+ * rho_nu(x) = du_x du_y du_z * sum over the velocity cube of f (Sec. 4.1.3),
+ * written to rho_dev (nx*ny*nz FP64).  Each cell sum is formed from
+ * compensated FP32 partial sums combined in FP64.  If mass_host is non-NULL
+ * the call synchronises and stores dx dy dz * sum_x rho_nu there.
+ */
+int vlasov_moment(vlasov_ctx *ctx, double *rho_dev, double *mass_host);
+
+/*
+ * Eq. (2): solve nabla^2 phi = four_pi_G a^2 (rho - mean rho) on the periodic
+ * spatial grid by a discrete Fourier transform (continuous |k|^2 =
+ * (2 pi n / L)^2, the k = 0 mode set to zero).  rho = rho_dev + rho_bg_dev
+ * (rho_bg_dev may be NULL), both nx*ny*nz FP64.  phi_dev receives FP32.
+ */
+int vlasov_poisson(vlasov_ctx *ctx, const double *rho_dev, const double *rho_bg_dev, double a,
+                   double four_pi_G, float *phi_dev);
+
+/*
+ * One time step of Eq. (5), operators applied right to left:
+ *   kick  D_ux, D_uy, D_uz (dt/2) with phi_n,
+ *   drift D_z, D_y, D_x (dt) at scale factor a_half,
+ *   kick  D_ux, D_uy, D_uz (dt/2) with phi_next if non-NULL, else phi_n.
+ * If phi_next_dev is non-NULL the step is self-consistent: after the drift
+ * rho_nu + rho_bg_dev (FP64, may be NULL) is turned into phi_next by
+ * vlasov_poisson at a_full.  rho_nu_dev (FP64, may be NULL) receives the
+ * post-drift moment.
+ */
+int vlasov_step(vlasov_ctx *ctx, double dt, double a_half, double a_full, const float *phi_n_dev,
+                const double *rho_bg_dev, double four_pi_G, float *phi_next_dev,
+                double *rho_nu_dev);
+
+/*
+ * Copy the whole distribution function between a caller's host buffer
+ * (nx*ny*nz*nux*nuy*nuz elements of the storage type; pinned memory makes the
+ * copy asynchronous) and the context's device array f, on the context stream.
+ * The host buffer must stay valid until the stream reaches the copy.
+ */
+int vlasov_upload(vlasov_ctx *ctx, const void *f_host);
+int vlasov_download(vlasov_ctx *ctx, void *f_host);
+
+/*
+ * Per-part timers (the paper times each part of a step, Sec. 5.1).  While
+ * enabled, every kernel the library queues is bracketed by two CUDA events on
+ * the context stream.  vlasov_read_timers synchronises the stream and, for each
+ * kind k < nkinds, writes the summed event time in ms to ms[k] (may be NULL)
+ * and the number of kernel launches to launches[k] (counted whether or not
+ * timers are enabled), then resets both.
+ */
+#define VLASOV_T_SWEEP_X 0 /* kinds 0..5: sweeps along x, y, z, u_x, u_y, u_z */
+#define VLASOV_T_MOMENT 6
+#define VLASOV_T_POISSON 7
+#define VLASOV_T_COEF 8 /* velocity-sweep constants (potential gradient)      */
+#define VLASOV_T_MASS 9
+#define VLASOV_T_KINDS 10
+int vlasov_enable_timers(vlasov_ctx *ctx, int on);
+int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
+
+/*
+ * Synchronise the stream, read and clear the device error word.  Returns 0 or
+ * the first of VLASOV_ETIMEOUT, VLASOV_ENAN, VLASOV_ECFL that was raised.
+ */
+int vlasov_status(vlasov_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed vlasov_init when ctx is NULL). */
+const char *vlasov_last_error(const vlasov_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLASOV_H */

@@ -1,0 +1,229 @@
+"""Thin Python binding of libvlasov's C ABI (include/vlasov.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  There is no CPU fallback:
+if the compiled library is missing, loading raises.
+
+Low level: ``vlasov_init``, ``vlasov_sweep``, ``vlasov_moment``, ``vlasov_poisson``,
+``vlasov_step``, ``vlasov_status``, ``vlasov_last_error``, ``vlasov_destroy`` with the
+C names and raw pointers.  High level: :class:`Vlasov`, a context bound to one 6D
+torch tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+AXES = {"x": 0, "y": 1, "z": 2, "ux": 3, "uy": 4, "uz": 5}
+
+OK, EINVAL, ECFL, ECUDA, ENAN, ETIMEOUT, ENOMEM = 0, -1, -2, -3, -4, -5, -6
+_NAMES = {EINVAL: "EINVAL", ECFL: "ECFL", ECUDA: "ECUDA", ENAN: "ENAN", ETIMEOUT: "ETIMEOUT",
+          ENOMEM: "ENOMEM"}
+
+
+class VlasovError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "E?"), code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nux", ctypes.c_int), ("nuy", ctypes.c_int), ("nuz", ctypes.c_int),
+                ("L", ctypes.c_double), ("V", ctypes.c_double), ("dtype", ctypes.c_int)]
+
+
+_VP = ctypes.c_void_p
+_lib = None
+
+SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep", "vlasov_moment",
+           "vlasov_poisson", "vlasov_step", "vlasov_status", "vlasov_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libvlasov.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libvlasov.so is not built (run __graft_entry__.build())")
+        _build.build()
+    L = ctypes.CDLL(path)
+    L.vlasov_init.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Grid), _VP, _VP, _VP]
+    L.vlasov_init.restype = ctypes.c_int
+    L.vlasov_destroy.argtypes = [_VP]
+    L.vlasov_destroy.restype = None
+    L.vlasov_set_stream.argtypes = [_VP, _VP]
+    L.vlasov_set_stream.restype = ctypes.c_int
+    L.vlasov_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP]
+    L.vlasov_sweep.restype = ctypes.c_int
+    L.vlasov_moment.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_double)]
+    L.vlasov_moment.restype = ctypes.c_int
+    L.vlasov_poisson.argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP]
+    L.vlasov_poisson.restype = ctypes.c_int
+    L.vlasov_step.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                              ctypes.c_double, _VP, _VP]
+    L.vlasov_step.restype = ctypes.c_int
+    L.vlasov_status.argtypes = [_VP]
+    L.vlasov_status.restype = ctypes.c_int
+    L.vlasov_last_error.argtypes = [_VP]
+    L.vlasov_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# C names, raw pointers (ints or None)
+# ---------------------------------------------------------------------------
+
+def vlasov_last_error(ctx) -> str:
+    return load().vlasov_last_error(ctx).decode(errors="replace")
+
+
+def _check(ctx, rc):
+    if rc != OK:
+        raise VlasovError(rc, vlasov_last_error(ctx))
+    return rc
+
+
+def vlasov_init(grid: Grid, f_ptr: int, scale_ptr, stream: int):
+    ctx = _VP()
+    rc = load().vlasov_init(ctypes.byref(ctx), ctypes.byref(grid), f_ptr, scale_ptr, stream)
+    _check(None, rc)
+    return ctx.value
+
+
+def vlasov_destroy(ctx) -> None:
+    load().vlasov_destroy(ctx)
+
+
+def vlasov_set_stream(ctx, stream: int):
+    return _check(ctx, load().vlasov_set_stream(ctx, stream))
+
+
+def vlasov_sweep(ctx, axis: int, dt: float, a: float, phi_ptr):
+    return _check(ctx, load().vlasov_sweep(ctx, axis, dt, a, phi_ptr))
+
+
+def vlasov_moment(ctx, rho_ptr: int, want_mass: bool = False):
+    m = ctypes.c_double(0.0)
+    _check(ctx, load().vlasov_moment(ctx, rho_ptr, ctypes.byref(m) if want_mass else None))
+    return m.value if want_mass else None
+
+
+def vlasov_poisson(ctx, rho_ptr, rho_bg_ptr, a: float, four_pi_G: float, phi_ptr):
+    return _check(ctx, load().vlasov_poisson(ctx, rho_ptr, rho_bg_ptr, a, four_pi_G, phi_ptr))
+
+
+def vlasov_step(ctx, dt, a_half, a_full, phi_n_ptr, rho_bg_ptr, four_pi_G, phi_next_ptr,
+                rho_nu_ptr):
+    return _check(ctx, load().vlasov_step(ctx, dt, a_half, a_full, phi_n_ptr, rho_bg_ptr,
+                                          four_pi_G, phi_next_ptr, rho_nu_ptr))
+
+
+def vlasov_status(ctx):
+    return _check(ctx, load().vlasov_status(ctx))
+
+
+# ---------------------------------------------------------------------------
+# context bound to a torch tensor
+# ---------------------------------------------------------------------------
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Vlasov:
+    """A libvlasov context over the 6D CUDA tensor ``f`` [nx,ny,nz,nux,nuy,nuz].
+
+    The tensor is updated in place by every sweep; the context keeps a reference.
+    Work is queued on the torch stream current at each call.
+    """
+
+    def __init__(self, f, L: float = 1.0, V: float = 5.0):
+        import torch
+        if not f.is_cuda or f.dim() != 6 or not f.is_contiguous():
+            raise ValueError("f must be a contiguous 6D CUDA tensor")
+        dt = {torch.float64: F64, torch.float32: F32}.get(f.dtype)
+        if dt is None:
+            raise ValueError("f must be float32 or float64")
+        self.f = f
+        self.torch = torch
+        g = Grid()
+        g.nx, g.ny, g.nz, g.nux, g.nuy, g.nuz = f.shape
+        g.L, g.V, g.dtype = L, V, dt
+        self.grid = g
+        self.shape = tuple(f.shape)
+        with torch.cuda.device(f.device):
+            self._stream = torch.cuda.current_stream(f.device).cuda_stream
+            self.ctx = vlasov_init(g, f.data_ptr(), None, self._stream)
+
+    # keep the context on the caller's current stream
+    def _sync_stream(self):
+        s = self.torch.cuda.current_stream(self.f.device).cuda_stream
+        if s != self._stream:
+            vlasov_set_stream(self.ctx, s)
+            self._stream = s
+
+    def _field(self, t, dtype):
+        if t is None:
+            return None
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype or \
+                tuple(t.shape) != self.shape[:3]:
+            raise ValueError("spatial field must be a contiguous %s CUDA tensor of shape %s"
+                             % (dtype, self.shape[:3]))
+        return t
+
+    def sweep(self, axis, dt: float, a: float = 1.0, phi=None):
+        ax = AXES[axis] if isinstance(axis, str) else int(axis)
+        self._sync_stream()
+        phi = self._field(phi, self.torch.float32)
+        vlasov_sweep(self.ctx, ax, dt, a, _ptr(phi))
+
+    def moment(self, rho=None, mass: bool = False):
+        self._sync_stream()
+        if rho is None:
+            rho = self.torch.empty(self.shape[:3], dtype=self.torch.float64, device=self.f.device)
+        self._field(rho, self.torch.float64)
+        m = vlasov_moment(self.ctx, rho.data_ptr(), mass)
+        return (rho, m) if mass else rho
+
+    def poisson(self, rho, a: float, four_pi_G: float = 1.0, rho_bg=None, phi=None):
+        self._sync_stream()
+        if phi is None:
+            phi = self.torch.empty(self.shape[:3], dtype=self.torch.float32, device=self.f.device)
+        vlasov_poisson(self.ctx, _ptr(self._field(rho, self.torch.float64)),
+                       _ptr(self._field(rho_bg, self.torch.float64)), a, four_pi_G,
+                       _ptr(self._field(phi, self.torch.float32)))
+        return phi
+
+    def step(self, dt: float, a_half: float, a_full: float, phi_n, rho_bg=None,
+             four_pi_G: float = 1.0, phi_next=None, rho_nu=None):
+        self._sync_stream()
+        vlasov_step(self.ctx, dt, a_half, a_full, _ptr(self._field(phi_n, self.torch.float32)),
+                    _ptr(self._field(rho_bg, self.torch.float64)), four_pi_G,
+                    _ptr(self._field(phi_next, self.torch.float32)),
+                    _ptr(self._field(rho_nu, self.torch.float64)))
+
+    def status(self):
+        return vlasov_status(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            vlasov_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

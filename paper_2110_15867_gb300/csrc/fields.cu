@@ -1,0 +1,266 @@
+// fields.cu -- the small spatial-grid kernels around the sweeps
+// (Yoshikawa, Tanaka & Yoshida, SC'21):
+//   * velocity-sweep coefficients: g_i = d phi / d x_i by the periodic
+//     4th-order central difference (the "differentiating" of the PM potential,
+//     Sec. 4.1.2) and the Courant number nu = -g_i dt / du of Eq. (4);
+//   * the density moment rho_nu(x) = int f d^3u (Sec. 4.1.3: every spatial
+//     cell holds its whole velocity cube, so the moment needs no exchange);
+//   * the total mass (compensated FP64);
+//   * the periodic Poisson solve of Eq. (2) by discrete Fourier transform
+//     (the convolution method of Sec. 4.1.2 on one GPU).
+#include "vk_common.cuh"
+
+namespace vk {
+
+// ----------------------------------------------------------------------------
+// velocity-sweep coefficients
+// ----------------------------------------------------------------------------
+
+template <typename C>
+__global__ void velocity_coef_kernel(GridDims g, const float *__restrict__ phi, double dt, int mask,
+                                     LineCoefT<C> *cx, LineCoefT<C> *cy, LineCoefT<C> *cz, unsigned *err)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int iz = int(c % g.n[2]);
+        const int iy = int((c / g.n[2]) % g.n[1]);
+        const int ix = int(c / ((long long)g.n[2] * g.n[1]));
+        const int idx[3] = {ix, iy, iz};
+        LineCoefT<C> *outs[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+            if (!(mask & (1 << d))) continue;
+            double v[5];
+            for (int o = -2; o <= 2; ++o) {
+                int q[3] = {idx[0], idx[1], idx[2]};
+                q[d] = (q[d] + o + 2 * g.n[d]) % g.n[d];
+                v[o + 2] = (double)phi[((long long)q[0] * g.n[1] + q[1]) * g.n[2] + q[2]];
+            }
+            const double h = g.L / g.n[d];
+            const double grad = (8.0 * (v[3] - v[1]) - (v[4] - v[0])) / (12.0 * h);
+            const double du = 2.0 * g.V / g.nu[d];
+            const double nu = -grad * dt / du;
+            LineCoefT<C> k = make_line_coef<C>(nu);
+            if (!(fabs(nu) < 1.0)) { // also catches NaN
+                k.nd = -1;
+                atomicOr(err, ERR_CFL);
+            }
+            outs[d][c] = k;
+        }
+    }
+}
+
+cudaError_t launch_velocity_coef(const GridDims &g, const float *phi, double dt, int mask, void *coef_x,
+                                 void *coef_y, void *coef_z, int dtype, unsigned *err, cudaStream_t st)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int threads = 256;
+    const int blocks = int((ncell + threads - 1) / threads < 4096 ? (ncell + threads - 1) / threads : 4096);
+    if (dtype == 0)
+        velocity_coef_kernel<double><<<blocks, threads, 0, st>>>(
+            g, phi, dt, mask, (LineCoefT<double> *)coef_x, (LineCoefT<double> *)coef_y,
+            (LineCoefT<double> *)coef_z, err);
+    else
+        velocity_coef_kernel<float><<<blocks, threads, 0, st>>>(
+            g, phi, dt, mask, (LineCoefT<float> *)coef_x, (LineCoefT<float> *)coef_y,
+            (LineCoefT<float> *)coef_z, err);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// moment
+// ----------------------------------------------------------------------------
+
+// Neumaier step in the working precision: (s, c) accumulates x exactly up to
+// the second-order term; s + c is formed only in FP64.
+__device__ __forceinline__ void neumaier(float &s, float &c, float x)
+{
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One CTA per spatial cell (grid-stride): FP32 compensated partial sums over
+// 16-byte vectors, combined in FP64 across the CTA in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) moment_kernel(GridDims g, const T *__restrict__ f, double *rho)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long cube = (long long)g.nu[0] * g.nu[1] * g.nu[2];
+    const double du3 = (2.0 * g.V / g.nu[0]) * (2.0 * g.V / g.nu[1]) * (2.0 * g.V / g.nu[2]);
+    __shared__ double part[8];
+    for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const T *q = f + c * cube;
+        double tot;
+        if (sizeof(T) == 8) {
+            double s = 0.0, e = 0.0;
+            for (long long k = threadIdx.x; k < cube; k += blockDim.x) {
+                const double x = (double)q[k];
+                const double t = s + x;
+                e += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+                s = t;
+            }
+            tot = s + e;
+        } else {
+            float s = 0.f, e = 0.f;
+            const float4 *q4 = reinterpret_cast<const float4 *>(q);
+            const long long n4 = cube / 4;
+            for (long long k = threadIdx.x; k < n4; k += blockDim.x) {
+                const float4 v = q4[k];
+                neumaier(s, e, v.x);
+                neumaier(s, e, v.y);
+                neumaier(s, e, v.z);
+                neumaier(s, e, v.w);
+            }
+            tot = (double)s + (double)e;
+        }
+        tot = warp_sum_d(tot);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = tot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double r = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += part[w];
+            rho[c] = du3 * r;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *rho, cudaStream_t st,
+                          int sm_count)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long blocks = ncell < (long long)sm_count * 8 ? ncell : (long long)sm_count * 8;
+    if (dtype == 0)
+        moment_kernel<double><<<int(blocks), 256, 0, st>>>(g, (const double *)f, rho);
+    else
+        moment_kernel<float><<<int(blocks), 256, 0, st>>>(g, (const float *)f, rho);
+    return cudaGetLastError();
+}
+
+// dx dy dz * sum rho, Neumaier in FP64 per thread, fixed-order combine
+__global__ void __launch_bounds__(1024) mass_kernel(GridDims g, const double *__restrict__ rho, double *out)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    double s = 0.0, e = 0.0;
+    for (long long k = threadIdx.x; k < ncell; k += blockDim.x) {
+        const double x = rho[k];
+        const double t = s + x;
+        e += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __shared__ double ps[1024], pe[1024];
+    ps[threadIdx.x] = s;
+    pe[threadIdx.x] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, E = 0.0;
+        for (unsigned i = 0; i < blockDim.x; ++i) {
+            const double x = ps[i];
+            const double t = S + x;
+            E += (fabs(S) >= fabs(x)) ? ((S - t) + x) : ((x - t) + S);
+            S = t;
+            E += pe[i];
+        }
+        *out = (S + E) * (g.L / g.n[0]) * (g.L / g.n[1]) * (g.L / g.n[2]);
+    }
+}
+
+cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st)
+{
+    mass_kernel<<<1, 1024, 0, st>>>(g, rho, out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Poisson, Eq. (2)
+// ----------------------------------------------------------------------------
+
+__global__ void poisson_load_kernel(long long n, const double *__restrict__ rho, const double *__restrict__ bg,
+                                    double2 *z)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[i] = make_double2(rho[i] + (bg ? bg[i] : 0.0), 0.0);
+}
+
+// DFT along dimension d: out[.., k, ..] = sum_m in[.., m, ..] e^{sign 2 pi i k m / n_d}
+__global__ void dft_axis_kernel(GridDims g, int d, int sign, const double2 *__restrict__ in, double2 *out,
+                                const double2 *__restrict__ tw)
+{
+    const long long n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    const long long total = n0 * n1 * n2;
+    const long long st[3] = {n1 * n2, n2, 1};
+    const int nd = g.n[d];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long id[3] = {i / st[0], (i / st[1]) % n1, i % n2};
+        const int k = int(id[d]);
+        const long long base = i - id[d] * st[d];
+        double sr = 0.0, si = 0.0;
+        int q = 0; // (k m) mod nd
+        for (int m = 0; m < nd; ++m) {
+            const double2 x = in[base + m * st[d]];
+            const double2 w = tw[q];
+            const double wi = sign * w.y;
+            sr += x.x * w.x - x.y * wi;
+            si += x.x * wi + x.y * w.x;
+            q += k;
+            if (q >= nd) q -= nd;
+        }
+        out[i] = make_double2(sr, si);
+    }
+}
+
+__global__ void poisson_scale_kernel(GridDims g, double2 *z, double fac)
+{
+    const long long n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    const long long total = n0 * n1 * n2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long id[3] = {i / (n1 * n2), (i / n2) % n1, i % n2};
+        double k2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const long long nd = g.n[d];
+            const long long w = id[d] < (nd + 1) / 2 ? id[d] : id[d] - nd; // integer wave number
+            const double k = 2.0 * M_PI * (double)w / g.L;
+            k2 += k * k;
+        }
+        const double s = (k2 == 0.0) ? 0.0 : -fac / k2;
+        z[i] = make_double2(z[i].x * s, z[i].y * s);
+    }
+}
+
+__global__ void poisson_store_kernel(long long n, const double2 *__restrict__ z, float *phi)
+{
+    const double inv = 1.0 / (double)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        phi[i] = (float)(z[i].x * inv);
+}
+
+cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const double *rho, const double *bg,
+                           double a, double four_pi_G, float *phi, cudaStream_t st)
+{
+    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 8192 ? (n + threads - 1) / threads : 8192);
+    poisson_load_kernel<<<blocks, threads, 0, st>>>(n, rho, bg, ps.z0);
+    double2 *a0 = ps.z0, *a1 = ps.z1;
+    for (int d = 2; d >= 0; --d) {
+        dft_axis_kernel<<<blocks, threads, 0, st>>>(g, d, -1, a0, a1, ps.tw[d]);
+        double2 *t = a0; a0 = a1; a1 = t;
+    }
+    poisson_scale_kernel<<<blocks, threads, 0, st>>>(g, a0, four_pi_G * a * a);
+    for (int d = 0; d < 3; ++d) {
+        dft_axis_kernel<<<blocks, threads, 0, st>>>(g, d, +1, a0, a1, ps.tw[d]);
+        double2 *t = a0; a0 = a1; a1 = t;
+    }
+    poisson_store_kernel<<<blocks, threads, 0, st>>>(n, a0, phi);
+    return cudaGetLastError();
+}
+
+} // namespace vk

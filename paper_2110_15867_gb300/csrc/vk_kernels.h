@@ -1,0 +1,145 @@
+// vk_kernels.h -- internal interface between the C ABI (vlasov_api.cu) and the
+// kernel translation units of libvlasov.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace vk {
+
+// sticky error bits of the device error word
+enum : unsigned { ERR_CFL = 1u, ERR_NAN = 2u, ERR_TIMEOUT = 4u };
+
+constexpr int kMaxVel = 128;       // largest velocity-axis length a position table holds
+constexpr int kConsumers = 256;    // consumer threads per CTA (8 warps)
+constexpr int kProducer = 32;      // one producer warp (lane 0 drives the TMA engine)
+
+// Per-line SL-MPP5 constants, see LineCoef in the kernels.  C = float for
+// FP32 / 16-bit storage, double for FP64 storage.
+// nd = 2 N + (dir < 0), or -1: leave the line untouched (Courant number out of range).
+template <typename C> struct LineCoefT {
+    C w[5];
+    C s;
+    C alpha;
+    int nd;
+    int pad;
+};
+
+// Weights of the mean over the departure interval, fbar = sum_m W_m(s) c_{j-2+m},
+// W_m(s) = K1_m + K2_m s + K3_m s^2 + K4_m s^3 + K5_m s^4.  They come from
+// expanding, in powers of s, the exact integral over [x_{j+1/2} - s dx,
+// x_{j+1/2}] of the quintic that interpolates the primitive function at the six
+// faces j-5/2 .. j+5/2, divided by s (K1 is the classic fifth-order face value).
+__host__ __device__ inline void sl5_weights(double s, double w[5])
+{
+    const double K1[5] = {1.0 / 30, -13.0 / 60, 47.0 / 60, 9.0 / 20, -1.0 / 20};
+    const double K2[5] = {0.0, -1.0 / 24, 5.0 / 8, -5.0 / 8, 1.0 / 24};
+    const double K3[5] = {-1.0 / 24, 1.0 / 4, -1.0 / 3, 1.0 / 12, 1.0 / 24};
+    const double K4[5] = {0.0, 1.0 / 24, -1.0 / 8, 1.0 / 8, -1.0 / 24};
+    const double K5[5] = {1.0 / 120, -1.0 / 30, 1.0 / 20, -1.0 / 30, 1.0 / 120};
+    for (int m = 0; m < 5; ++m) w[m] = K1[m] + s * (K2[m] + s * (K3[m] + s * (K4[m] + s * K5[m])));
+}
+
+// Constants of a line with signed Courant number nu.
+template <typename C> __host__ __device__ inline LineCoefT<C> make_line_coef(double nu)
+{
+    LineCoefT<C> k;
+    const int neg = nu < 0.0;
+    const double a = neg ? -nu : nu;
+    const double Nf = floor(a);
+    const double s = a - Nf;
+    double w[5];
+    sl5_weights(s, w);
+    for (int m = 0; m < 5; ++m) k.w[m] = (C)w[m];
+    k.s = (C)s;
+    // Suresh-Huynh alpha tied to the departure fraction: a monotone update needs
+    // s (1 + alpha) <= 1; capped where s -> 0 (the flux then vanishes anyway).
+    const double alpha = s > 0.0 ? (1.0 - s) / s : 1e6;
+    k.alpha = (C)(alpha > 1e6 ? 1e6 : alpha);
+    k.nd = (int)(2.0 * Nf) + neg;
+    k.pad = 0;
+    return k;
+}
+
+// ----------------------------------------------------------------------------
+// strided sweep (axes x, y, z, u_x, u_y)
+// ----------------------------------------------------------------------------
+// f viewed as [O][L][I] (outer, swept, inner).  A tile is the TMA box
+// {W inner, L swept, P outer}; each consumer thread owns one (inner, outer)
+// column and marches it along the swept axis.
+template <typename C> struct StridedArgs {
+    int L, W, P, stages;
+    int tiles_inner;
+    int periodic;
+    long long n_inner, n_outer;
+    long long num_tiles;
+    // position sweeps: j = (inner / vstride) % nvel indexes table
+    long long vstride;
+    int nvel;
+    int coef_mode; // 0 = position table, 1 = per-cell array
+    // velocity sweeps: cell = outer / outer_per_cell indexes cell_coef
+    long long outer_per_cell;
+    const LineCoefT<C> *cell_coef;
+    unsigned *err;
+    LineCoefT<C> table[kMaxVel];
+};
+
+// ----------------------------------------------------------------------------
+// contiguous sweep (axis u_z): rows of nuz cells
+// ----------------------------------------------------------------------------
+template <typename C> struct ContigArgs {
+    int L;      // nuz
+    int R;      // rows per tile (= consumer threads)
+    int stages;
+    long long rows;
+    long long num_tiles;
+    long long rows_per_cell;
+    const LineCoefT<C> *cell_coef;
+    unsigned *err;
+};
+
+// host launchers (return cudaGetLastError() of the launch)
+cudaError_t launch_strided_f32(const CUtensorMap &map, const StridedArgs<float> &a, int grid,
+                               size_t smem, cudaStream_t st);
+cudaError_t launch_strided_f64(const CUtensorMap &map, const StridedArgs<double> &a, int grid,
+                               size_t smem, cudaStream_t st);
+cudaError_t launch_contig_f32(const CUtensorMap &map, const ContigArgs<float> &a, int grid,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_contig_f64(const CUtensorMap &map, const ContigArgs<double> &a, int grid,
+                              size_t smem, cudaStream_t st);
+// largest resident CTAs per SM for a launcher's kernel with this dynamic smem
+int occupancy_strided(int dtype, int periodic, size_t smem);
+int occupancy_contig(int dtype, size_t smem);
+
+// ----------------------------------------------------------------------------
+// fields: velocity-sweep coefficients, moment, Poisson
+// ----------------------------------------------------------------------------
+struct GridDims {
+    int n[3];
+    int nu[3];
+    double L, V;
+};
+
+// For each axis d with bit d set in mask: coef[d][cell] for a velocity sweep
+// of length dt from the 4th-order gradient of phi (FP32, nx*ny*nz).
+cudaError_t launch_velocity_coef(const GridDims &g, const float *phi, double dt, int mask,
+                                 void *coef_x, void *coef_y, void *coef_z, int dtype, unsigned *err,
+                                 cudaStream_t st);
+
+cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *rho, cudaStream_t st,
+                          int sm_count);
+// mass = dx dy dz * sum rho (FP64, compensated) written to out (device)
+cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st);
+
+// scratch of the spectral solve: 2 complex buffers of nx*ny*nz and twiddles
+struct PoissonScratch {
+    double2 *z0, *z1;
+    double2 *tw[3]; // tw[d][q] = (cos, sin)(2 pi q / n_d)
+};
+cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const double *rho,
+                           const double *rho_bg, double a, double four_pi_G, float *phi,
+                           cudaStream_t st);
+
+} // namespace vk

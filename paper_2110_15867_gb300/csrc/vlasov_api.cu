@@ -1,0 +1,521 @@
+// vlasov_api.cu -- host side of the C ABI declared in include/vlasov.h.
+//
+// Owns the context: argument checks, the TMA tensor maps of f for each sweep
+// axis, the tile / pipeline geometry, the scratch buffers, and the order of
+// the kernels of one split step (Eq. 5 of Yoshikawa, Tanaka & Yoshida, SC'21).
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/vlasov.h"
+#include "vk_kernels.h"
+
+using namespace vk;
+
+namespace {
+
+thread_local char g_init_error[256] = "";
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+struct AxisPlan {
+    CUtensorMap map;
+    int L, W, P, stages, grid;
+    long long n_inner, n_outer, num_tiles;
+    int tiles_inner;
+    size_t smem;
+};
+
+} // namespace
+
+struct vlasov_ctx {
+    vlasov_grid g;
+    GridDims gd;
+    void *f;
+    cudaStream_t stream;
+    size_t es;
+    int sm_count;
+    long long ncell; // spatial cells
+    AxisPlan plan[6];
+    // scratch
+    unsigned *d_err;
+    void *d_coef[3];
+    double *d_rho;
+    double *d_mass;
+    PoissonScratch ps;
+    char msg[256];
+    // per-part timers
+    bool timers_on;
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double acc_ms[VLASOV_T_KINDS];
+    long long launches[VLASOV_T_KINDS];
+};
+
+// Bracket the kernels queued between construction and destruction with events
+// (when timers are on) and count them.
+struct PartTimer {
+    vlasov_ctx *c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    PartTimer(vlasov_ctx *c_, int kind_, int nlaunch) : c(c_), kind(kind_)
+    {
+        c->launches[kind] += nlaunch;
+        if (!c->timers_on) return;
+        a = take();
+        cudaEventRecord(a, c->stream);
+    }
+    cudaEvent_t take()
+    {
+        cudaEvent_t e = nullptr;
+        if (!c->pool.empty()) { e = c->pool.back(); c->pool.pop_back(); }
+        else cudaEventCreate(&e);
+        return e;
+    }
+    ~PartTimer()
+    {
+        if (!a) return;
+        cudaEvent_t b = take();
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({kind, a, b});
+    }
+};
+
+static int fail(vlasov_ctx *c, int code, const char *fmt, ...)
+{
+    char *dst = c ? c->msg : g_init_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(vlasov_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, VLASOV_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define VK_CUDA(ctx, call)                                                                                  \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);                                          \
+    } while (0)
+
+static CUtensorMapDataType tmap_type(int dtype)
+{
+    switch (dtype) {
+    case VLASOV_F64: return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    case VLASOV_F32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    case VLASOV_BF16: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    }
+}
+
+static int plan_axes(vlasov_ctx *c)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return fail(c, VLASOV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const long long d6[6] = {c->g.nx, c->g.ny, c->g.nz, c->g.nux, c->g.nuy, c->g.nuz};
+    const size_t es = c->es;
+    const size_t kSmemBudget = 200 * 1024;
+    for (int ax = 0; ax < 6; ++ax) {
+        AxisPlan &p = c->plan[ax];
+        p.L = int(d6[ax]);
+        long long I = 1, O = 1;
+        for (int k = ax + 1; k < 6; ++k) I *= d6[k];
+        for (int k = 0; k < ax; ++k) O *= d6[k];
+        p.n_inner = I;
+        p.n_outer = O;
+        CUresult r;
+        if (ax < 5) {
+            int W, P;
+            if (I >= kConsumers) { W = kConsumers; P = 1; }
+            else { W = int(I); P = kConsumers / W; if (P > O) P = int(O); }
+            while ((size_t)W * p.L * P * es > 96 * 1024 && W * P > 32) {
+                if (P > 1) P = (P + 1) / 2;
+                else W /= 2;
+            }
+            p.W = W;
+            p.P = P;
+            p.tiles_inner = int((I + W - 1) / W);
+            p.num_tiles = (long long)p.tiles_inner * ((O + P - 1) / P);
+            const size_t tile = ((size_t)W * p.L * P * es + 127) & ~size_t(127);
+            const size_t tab = ax < 3 ? ((sizeof(LineCoefT<double>) * kMaxVel + 127) & ~size_t(127)) : 0;
+            int S = int((kSmemBudget - 128 - tab) / tile);
+            S = S < 2 ? 2 : (S > 4 ? 4 : S);
+            p.stages = S;
+            p.smem = 128 + tab + (size_t)S * tile;
+            const cuuint64_t gdim[3] = {(cuuint64_t)I, (cuuint64_t)p.L, (cuuint64_t)O};
+            const cuuint64_t gstr[2] = {(cuuint64_t)(I * es), (cuuint64_t)(I * p.L * es)};
+            const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)p.L, (cuuint32_t)P};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            r = enc(&p.map, tmap_type(c->g.dtype), 3, c->f, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            const int occ = occupancy_strided(c->g.dtype == VLASOV_F64 ? 0 : 1, ax < 3, p.smem);
+            if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a CTA does not fit (%zu B shared memory)", ax, p.smem);
+            p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
+        } else {
+            const long long rows = O * 1; // one row per (cell, jx, jy)
+            p.W = p.L;
+            p.P = kConsumers; // rows per tile
+            p.n_outer = rows;
+            p.num_tiles = (rows + kConsumers - 1) / kConsumers;
+            p.tiles_inner = 1;
+            const size_t ces = c->g.dtype == VLASOV_F64 ? 8 : 4;
+            const size_t tile = ((size_t)p.L * kConsumers * es + 127) & ~size_t(127);
+            const size_t bbuf = (size_t)p.L * (kConsumers + 1) * ces;
+            int S = int((kSmemBudget - 128 - bbuf) / tile);
+            S = S < 2 ? 2 : (S > 4 ? 4 : S);
+            p.stages = S;
+            p.smem = 128 + (size_t)S * tile + bbuf;
+            const cuuint64_t gdim[2] = {(cuuint64_t)p.L, (cuuint64_t)rows};
+            const cuuint64_t gstr[1] = {(cuuint64_t)(p.L * es)};
+            const cuuint32_t box[2] = {(cuuint32_t)p.L, (cuuint32_t)kConsumers};
+            const cuuint32_t estr[2] = {1, 1};
+            r = enc(&p.map, tmap_type(c->g.dtype), 2, c->f, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            const int occ = occupancy_contig(c->g.dtype == VLASOV_F64 ? 0 : 1, p.smem);
+            if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis 5: a CTA does not fit (%zu B shared memory)", p.smem);
+            p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
+        }
+        if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: cuTensorMapEncodeTiled failed (%d)", ax, int(r));
+    }
+    return VLASOV_OK;
+}
+
+static void free_scratch(vlasov_ctx *c)
+{
+    cudaFree(c->d_err);
+    for (int d = 0; d < 3; ++d) cudaFree(c->d_coef[d]);
+    cudaFree(c->d_rho);
+    cudaFree(c->d_mass);
+    cudaFree(c->ps.z0);
+    cudaFree(c->ps.z1);
+    for (int d = 0; d < 3; ++d) cudaFree(c->ps.tw[d]);
+}
+
+extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
+{
+    if (!out || !g || !f_dev) return fail(nullptr, VLASOV_EINVAL, "vlasov_init: null argument");
+    *out = nullptr;
+    const int dims[6] = {g->nx, g->ny, g->nz, g->nux, g->nuy, g->nuz};
+    for (int k = 0; k < 3; ++k)
+        if (dims[k] < 4 || dims[k] > 256) return fail(nullptr, VLASOV_EINVAL, "spatial size %d outside [4, 256]", dims[k]);
+    for (int k = 3; k < 6; ++k)
+        if (dims[k] < 4 || dims[k] > kMaxVel || dims[k] % 4)
+            return fail(nullptr, VLASOV_EINVAL, "velocity size %d must be a multiple of 4 in [4, %d]", dims[k], kMaxVel);
+    if (!(g->L > 0) || !(g->V > 0)) return fail(nullptr, VLASOV_EINVAL, "L and V must be positive");
+    if (g->dtype != VLASOV_F32 && g->dtype != VLASOV_F64)
+        return fail(nullptr, VLASOV_EINVAL, "dtype %d is not supported by this build", g->dtype);
+    if (scale_dev) return fail(nullptr, VLASOV_EINVAL, "scale_dev must be NULL for FP32/FP64 storage");
+    if (reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(nullptr, VLASOV_EINVAL, "f_dev must be 16-byte aligned");
+    const long long ncell = (long long)g->nx * g->ny * g->nz;
+    const long long cube = (long long)g->nux * g->nuy * g->nuz;
+    if (ncell * g->nux * g->nuy >= (1ll << 31)) return fail(nullptr, VLASOV_EINVAL, "too many u_z lines for 32-bit TMA coordinates");
+    if (ncell * cube / g->nx >= (1ll << 32)) return fail(nullptr, VLASOV_EINVAL, "grid too large for 32-bit TMA extents");
+
+    vlasov_ctx *c = new (std::nothrow) vlasov_ctx();
+    if (!c) return fail(nullptr, VLASOV_ENOMEM, "out of host memory");
+    c->g = *g;
+    c->f = f_dev;
+    c->stream = (cudaStream_t)stream;
+    c->es = g->dtype == VLASOV_F64 ? 8 : 4;
+    c->ncell = ncell;
+    c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
+    c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
+    c->gd.L = g->L;
+    c->gd.V = g->V;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        fail(nullptr, VLASOV_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+        delete c;
+        return VLASOV_ECUDA;
+    }
+    const size_t coef_bytes = (size_t)ncell * (g->dtype == VLASOV_F64 ? sizeof(LineCoefT<double>) : sizeof(LineCoefT<float>));
+    bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess;
+    for (int d = 0; d < 3 && ok; ++d) ok = cudaMalloc(&c->d_coef[d], coef_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_rho, sizeof(double) * ncell) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_mass, sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->ps.z0, sizeof(double2) * ncell) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->ps.z1, sizeof(double2) * ncell) == cudaSuccess;
+    for (int d = 0; d < 3 && ok; ++d) {
+        const int n = dims[d];
+        ok = cudaMalloc(&c->ps.tw[d], sizeof(double2) * n) == cudaSuccess;
+        if (!ok) break;
+        double2 *h = new double2[n];
+        for (int q = 0; q < n; ++q) h[q] = make_double2(cos(2.0 * M_PI * q / n), sin(2.0 * M_PI * q / n));
+        ok = cudaMemcpy(c->ps.tw[d], h, sizeof(double2) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+        delete[] h;
+    }
+    ok = ok && cudaMemset(c->d_err, 0, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_scratch(c);
+        delete c;
+        return fail(nullptr, VLASOV_ENOMEM, "device scratch allocation failed");
+    }
+    const int rc = plan_axes(c);
+    if (rc != VLASOV_OK) {
+        snprintf(g_init_error, sizeof g_init_error, "%s", c->msg);
+        free_scratch(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return VLASOV_OK;
+}
+
+extern "C" void vlasov_destroy(vlasov_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_scratch(c);
+    for (auto &p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" int vlasov_upload(vlasov_ctx *c, const void *f_host)
+{
+    if (!c || !f_host) return c ? fail(c, VLASOV_EINVAL, "vlasov_upload: null host buffer") : VLASOV_EINVAL;
+    const size_t bytes = (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es;
+    VK_CUDA(c, cudaMemcpyAsync(c->f, f_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_download(vlasov_ctx *c, void *f_host)
+{
+    if (!c || !f_host) return c ? fail(c, VLASOV_EINVAL, "vlasov_download: null host buffer") : VLASOV_EINVAL;
+    const size_t bytes = (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es;
+    VK_CUDA(c, cudaMemcpyAsync(f_host, c->f, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_enable_timers(vlasov_ctx *c, int on)
+{
+    if (!c) return VLASOV_EINVAL;
+    c->timers_on = on != 0;
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_read_timers(vlasov_ctx *c, double *ms, long long *launches, int nkinds)
+{
+    if (!c || nkinds < 0) return VLASOV_EINVAL;
+    VK_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto &p : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) c->acc_ms[p.kind] += t;
+        c->pool.push_back(p.a);
+        c->pool.push_back(p.b);
+    }
+    c->pending.clear();
+    for (int k = 0; k < nkinds && k < VLASOV_T_KINDS; ++k) {
+        if (ms) ms[k] = c->acc_ms[k];
+        if (launches) launches[k] = c->launches[k];
+    }
+    for (int k = 0; k < VLASOV_T_KINDS; ++k) { c->acc_ms[k] = 0.0; c->launches[k] = 0; }
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_set_stream(vlasov_ctx *c, void *stream)
+{
+    if (!c) return VLASOV_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return VLASOV_OK;
+}
+
+// position sweep: per-velocity-column constants from nu_j = u_j dt / (a^2 dx)
+static int run_position(vlasov_ctx *c, int ax, double dt, double a)
+{
+    if (!(a > 0) || !isfinite(dt) || !isfinite(a)) return fail(c, VLASOV_EINVAL, "sweep %d: need finite dt and a > 0", ax);
+    const AxisPlan &p = c->plan[ax];
+    const int nvel = (&c->g.nux)[ax];
+    const double du = 2.0 * c->g.V / nvel;
+    const double dx = c->g.L / (&c->g.nx)[ax];
+    long long vstride = 1;
+    for (int k = ax + 1; k < 3; ++k) vstride *= (&c->g.nux)[k];
+    cudaError_t e;
+    if (c->g.dtype == VLASOV_F64) {
+        StridedArgs<double> A{};
+        A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 1;
+        A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+        A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
+        A.err = c->d_err;
+        for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+        PartTimer t(c, ax, 1);
+        e = launch_strided_f64(p.map, A, p.grid, p.smem, c->stream);
+    } else {
+        StridedArgs<float> A{};
+        A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 1;
+        A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+        A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
+        A.err = c->d_err;
+        for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+        PartTimer t(c, ax, 1);
+        e = launch_strided_f32(p.map, A, p.grid, p.smem, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
+    return VLASOV_OK;
+}
+
+// velocity sweep with the per-cell constants already in d_coef[ax - 3]
+static int run_velocity(vlasov_ctx *c, int ax)
+{
+    const AxisPlan &p = c->plan[ax];
+    const void *coef = c->d_coef[ax - 3];
+    cudaError_t e;
+    PartTimer t(c, ax, 1);
+    if (ax < 5) {
+        const long long opc = p.n_outer / c->ncell;
+        if (c->g.dtype == VLASOV_F64) {
+            StridedArgs<double> A{};
+            A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 0;
+            A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+            A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
+            A.cell_coef = (const LineCoefT<double> *)coef; A.err = c->d_err;
+            e = launch_strided_f64(p.map, A, p.grid, p.smem, c->stream);
+        } else {
+            StridedArgs<float> A{};
+            A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 0;
+            A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+            A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
+            A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
+            e = launch_strided_f32(p.map, A, p.grid, p.smem, c->stream);
+        }
+    } else {
+        const long long rpc = (long long)c->g.nux * c->g.nuy;
+        if (c->g.dtype == VLASOV_F64) {
+            ContigArgs<double> A{};
+            A.L = p.L; A.R = kConsumers; A.stages = p.stages; A.rows = p.n_outer; A.num_tiles = p.num_tiles;
+            A.rows_per_cell = rpc; A.cell_coef = (const LineCoefT<double> *)coef; A.err = c->d_err;
+            e = launch_contig_f64(p.map, A, p.grid, p.smem, c->stream);
+        } else {
+            ContigArgs<float> A{};
+            A.L = p.L; A.R = kConsumers; A.stages = p.stages; A.rows = p.n_outer; A.num_tiles = p.num_tiles;
+            A.rows_per_cell = rpc; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
+            e = launch_contig_f32(p.map, A, p.grid, p.smem, c->stream);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "velocity sweep launch");
+    return VLASOV_OK;
+}
+
+static int prep_velocity(vlasov_ctx *c, const float *phi, double dt, int mask)
+{
+    if (!phi) return fail(c, VLASOV_EINVAL, "velocity sweeps need phi_dev");
+    if (!isfinite(dt)) return fail(c, VLASOV_EINVAL, "dt must be finite");
+    PartTimer t(c, VLASOV_T_COEF, 1);
+    const cudaError_t e = launch_velocity_coef(c->gd, phi, dt, mask, c->d_coef[0], c->d_coef[1], c->d_coef[2],
+                                               c->g.dtype == VLASOV_F64 ? 0 : 1, c->d_err, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "velocity coefficient launch");
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_sweep(vlasov_ctx *c, int axis, double dt, double a, const float *phi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (axis < 0 || axis > 5) return fail(c, VLASOV_EINVAL, "axis %d outside 0..5", axis);
+    if (axis < 3) return run_position(c, axis, dt, a);
+    int rc = prep_velocity(c, phi_dev, dt, 1 << (axis - 3));
+    if (rc) return rc;
+    return run_velocity(c, axis);
+}
+
+extern "C" int vlasov_moment(vlasov_ctx *c, double *rho_dev, double *mass_host)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!rho_dev) return fail(c, VLASOV_EINVAL, "rho_dev is NULL");
+    cudaError_t e;
+    {
+        PartTimer t(c, VLASOV_T_MOMENT, 1);
+        e = launch_moment(c->gd, c->f, c->g.dtype == VLASOV_F64 ? 0 : 1, rho_dev, c->stream, c->sm_count);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
+    if (mass_host) {
+        {
+            PartTimer t(c, VLASOV_T_MASS, 1);
+            e = launch_mass(c->gd, rho_dev, c->d_mass, c->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "mass launch");
+        VK_CUDA(c, cudaMemcpyAsync(mass_host, c->d_mass, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        VK_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_poisson(vlasov_ctx *c, const double *rho_dev, const double *rho_bg_dev, double a,
+                              double four_pi_G, float *phi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!rho_dev || !phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_poisson: null rho or phi");
+    if (!isfinite(a) || !isfinite(four_pi_G)) return fail(c, VLASOV_EINVAL, "vlasov_poisson: a and four_pi_G must be finite");
+    PartTimer t(c, VLASOV_T_POISSON, 9);
+    const cudaError_t e = launch_poisson(c->gd, c->ps, rho_dev, rho_bg_dev, a, four_pi_G, phi_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "poisson launch");
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_full, const float *phi_n_dev,
+                           const double *rho_bg_dev, double four_pi_G, float *phi_next_dev, double *rho_nu_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!phi_n_dev) return fail(c, VLASOV_EINVAL, "vlasov_step: phi_n_dev is NULL");
+    int rc;
+    // kick D_uz D_uy D_ux (dt/2), D_ux first
+    if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
+    for (int ax = 3; ax <= 5; ++ax)
+        if ((rc = run_velocity(c, ax))) return rc;
+    // drift D_x D_y D_z (dt), D_z first, at the mid-step scale factor
+    for (int ax = 2; ax >= 0; --ax)
+        if ((rc = run_position(c, ax, dt, a_half))) return rc;
+    double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
+    if (rho_nu_dev || phi_next_dev)
+        if ((rc = vlasov_moment(c, rho, nullptr))) return rc;
+    if (phi_next_dev) {
+        if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
+        if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
+    }
+    // second kick (the constants are unchanged when phi is)
+    for (int ax = 3; ax <= 5; ++ax)
+        if ((rc = run_velocity(c, ax))) return rc;
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_status(vlasov_ctx *c)
+{
+    if (!c) return VLASOV_EINVAL;
+    unsigned bits = 0;
+    VK_CUDA(c, cudaStreamSynchronize(c->stream));
+    VK_CUDA(c, cudaMemcpy(&bits, c->d_err, sizeof bits, cudaMemcpyDeviceToHost));
+    VK_CUDA(c, cudaMemset(c->d_err, 0, sizeof bits));
+    if (bits & ERR_TIMEOUT) return fail(c, VLASOV_ETIMEOUT, "a bounded device wait ran out (error bits 0x%x)", bits);
+    if (bits & ERR_NAN) return fail(c, VLASOV_ENAN, "a sweep produced NaN/Inf or a negative line sum (error bits 0x%x)", bits);
+    if (bits & ERR_CFL) return fail(c, VLASOV_ECFL, "a velocity-sweep Courant number reached 1 (error bits 0x%x)", bits);
+    return VLASOV_OK;
+}
+
+extern "C" const char *vlasov_last_error(const vlasov_ctx *c) { return c ? c->msg : g_init_error; }
