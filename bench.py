@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput of the split 6D Vlasov step (Eq. 5, SL-MPP5 sweeps + rho_nu moment).
+
+Workload (default): 64^3 spatial x 32^3 velocity cells, FP32 f (8.59e9 cells,
+34.4 GB), |u| <= 5 u_T, f0 = (1 + delta) F_FD with delta rms 0.05 (P ~ k^-2), a fixed
+CDM background of contrast rms 1.0 and neutrino fraction 0.03, 4 pi G = 1,
+self-consistent steps (moment -> Poisson -> second kick), a from 0.5 to 0.6 over
+10 steps, each step's dt set by a seeded Courant number in [0.5, 0.9].
+
+One "step" = one vlasov_step: 9 directional sweeps of all cells, the moment, the
+Poisson solve and the velocity-sweep constants.  metric = cell updates per second
+per sweep = 9 x cells x steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload on its own GPU (the
+path has no exchange on one GPU: "replicas only"); value sums the ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "6D cell-updates/s per sweep"
+UNIT = "cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOAD = dict(name="fp32_64x32", n=64, nu=32, V=5.0, L=1.0, delta_rms=0.05, cdm_rms=1.0,
+                f_nu=0.03, four_pi_G=1.0, a0=0.5, a1=0.6, sched=10, cfl=(0.5, 0.9), seed=2)
+# CPU baseline / reference arm: the oracle on a bounded sample of the same workload:
+# the same 32^3 velocity cube on an 8^3 spatial grid (1.68e7 cells per step).
+SAMPLE = dict(n=8, nu=32)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--profile-case", action="store_true",
+                   help="run the small profiling case instead of the benchmark: sweeps on a "
+                        "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
+    p.add_argument("--axes", default="0,1,2,3,4,5", help="sweep axes of --profile-case")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def schedule(k, w=WORKLOAD):
+    """a at the start / middle / end of step k and the step's Courant number."""
+    rng = np.random.default_rng(1000 + k)
+    cfl = rng.uniform(*w["cfl"])
+    kk = k % w["sched"]
+    da = (w["a1"] - w["a0"]) / w["sched"]
+    a_start = w["a0"] + da * kk
+    a_end = a_start + da
+    return a_start, 0.5 * (a_start + a_end), a_end, cfl
+
+
+def drift_dt(cfl, a_half, n, nu, V, L):
+    """dt whose largest position-sweep Courant number u_max dt / (a^2 dx) is cfl."""
+    du = 2.0 * V / nu
+    umax = V - 0.5 * du
+    return cfl * a_half * a_half * (L / n) / umax
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2110_15867_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kind)
+    if not ent:
+        return None
+    return ent.get("bytes_per_full_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        # samples under load: the upper half of the clock readings
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_setup():
+    import oracle as O
+    from paper_2110_15867_gb300 import inputs as I
+    w = WORKLOAD
+    n, nu = SAMPLE["n"], SAMPLE["nu"]
+    g = O.grid(n, nu, L=w["L"], V=w["V"])
+    Fu = I.fermi_dirac(nu, w["V"])
+    f = I.initial_f(I.gaussian_field(n, w["delta_rms"], seed=w["seed"]), Fu, np.float32)
+    f = f.astype(np.float64)
+    rho0, _ = O.moment(g, f)
+    rbar = rho0.mean()
+    bg = rbar * (1.0 / w["f_nu"] - 1.0) * (1.0 + I.gaussian_field(n, w["cdm_rms"], seed=w["seed"] + 1))
+    phi = O.poisson(g, rho0 + bg, w["a0"], w["four_pi_G"])
+    return O, g, f, bg, phi
+
+
+def oracle_steps(O, g, f, bg, phi, k0, nsteps):
+    w = WORKLOAD
+    n, nu = SAMPLE["n"], SAMPLE["nu"]
+    for k in range(k0, k0 + nsteps):
+        a_s, a_h, a_e, cfl = schedule(k)
+        dt = drift_dt(cfl, a_h, n, nu, w["V"], w["L"])
+        phi, _ = O.step(g, f, dt, a_h, a_e, phi, rho_bg=bg, four_pi_G=w["four_pi_G"],
+                        self_consistent=True)
+    return phi
+
+
+def cpu_baseline(min_seconds=10.0):
+    O, g, f, bg, phi = oracle_sample_setup()
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        phi = oracle_steps(O, g, f, bg, phi, k, 1)
+        k += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    t = time.perf_counter() - t0
+    return {"value": 9.0 * f.size * k / t, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d steps of the FP64 oracle's Eq. (5) step on an %d^3 x %d^3 sample of the "
+                      "workload (same velocity cube, dt scaled to the sample's dx), %.1f s"
+                      % (k, SAMPLE["n"], SAMPLE["nu"], t)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    O, g, f, bg, phi = oracle_sample_setup()
+    phi = oracle_steps(O, g, f, bg, phi, 0, args.warmup)
+    t0 = time.perf_counter()
+    phi = oracle_steps(O, g, f, bg, phi, args.warmup, args.steps)
+    t = time.perf_counter() - t0
+    value = 9.0 * f.size * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s sampled: %d^3 x %d^3 cells per step" % (WORKLOAD["name"], SAMPLE["n"], SAMPLE["nu"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "FP64 oracle Eq. (5) steps on an %d^3 x %d^3 sample" % (SAMPLE["n"], SAMPLE["nu"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def build_inputs(torch, dev):
+    """f0 on the device (formed in FP64 per x-slab, rounded once), rho_bg, phi0."""
+    from paper_2110_15867_gb300 import inputs as I
+    w = WORKLOAD
+    n, nu, V = w["n"], w["nu"], w["V"]
+    delta = torch.from_numpy(I.gaussian_field(n, w["delta_rms"], seed=w["seed"])).to(dev)
+    Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
+    f = torch.empty((n, n, n, nu, nu, nu), dtype=torch.float32, device=dev)
+    for ix in range(n):
+        f[ix] = ((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None]).to(torch.float32)
+    du3 = (2.0 * V / nu) ** 3
+    rho_bar = float(Fu.sum().item()) * du3  # mean of (1 + delta) is 1
+    dc = torch.from_numpy(I.gaussian_field(n, w["cdm_rms"], seed=w["seed"] + 1)).to(dev)
+    rho_bg = (rho_bar * (1.0 / w["f_nu"] - 1.0) * (1.0 + dc)).contiguous()
+    return f, rho_bg
+
+
+def run_ours(args):
+    import torch
+    from paper_2110_15867_gb300 import binding as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.load()
+    w = WORKLOAD
+    n, nu, V, L = w["n"], w["nu"], w["V"], w["L"]
+    f, rho_bg = build_inputs(torch, dev)
+    cells = f.numel()
+    v = B.Vlasov(f, L=L, V=V)
+    rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    phi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    phi2 = torch.empty_like(phi)
+    v.moment(rho)
+    v.poisson(rho, w["a0"], w["four_pi_G"], rho_bg=rho_bg, phi=phi)
+
+    def one_step(k):
+        nonlocal phi, phi2
+        a_s, a_h, a_e, cfl = schedule(k)
+        dt = drift_dt(cfl, a_h, n, nu, V, L)
+        v.step(dt, a_h, a_e, phi, rho_bg=rho_bg, four_pi_G=w["four_pi_G"], phi_next=phi2, rho_nu=rho)
+        phi, phi2 = phi2, phi
+
+    for k in range(args.warmup):
+        one_step(k)
+    v.status()
+    v.read_timers()  # reset the launch counters
+    v.enable_timers(True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup, args.warmup + args.steps):
+        one_step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    kind_ms, kind_n = v.read_timers()
+    v.enable_timers(False)
+    v.status()
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * 9.0 * cells * args.steps / (ms_total * 1e-3)
+
+    # dominant kernel and its roofline
+    sweep_kinds = [k for k in kind_ms if k.startswith("sweep_")]
+    dom = max(sweep_kinds, key=lambda k: kind_ms[k])
+    dom_ms = kind_ms[dom] / max(1, kind_n[dom])
+    alg_bytes = 8.0 * cells  # one FP32 read + one FP32 write per cell
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = committed_traffic(dom)
+    per_kind = {k: {"ms_per_launch": (kind_ms[k] / kind_n[k]) if kind_n[k] else 0.0,
+                    "launches": kind_n[k]} for k in kind_ms if kind_n[k]}
+    for k in sweep_kinds:
+        if kind_n[k]:
+            per_kind[k]["GBs"] = alg_bytes / (per_kind[k]["ms_per_launch"] * 1e-3) / 1e9
+    gpu_launches = int(sum(kind_n.values()))
+
+    # end to end through the C ABI with host buffers: f host -> device, step, f and rho back
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.empty(f.shape, dtype=f.dtype, pin_memory=True)
+        fh.copy_(f)
+        rho_h = torch.empty(rho.shape, dtype=rho.dtype, pin_memory=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        base = args.warmup + args.steps
+        for k in range(base, base + args.e2e_steps):
+            v.upload(fh)
+            one_step(k)
+            v.download(fh)
+            rho_h.copy_(rho, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = t0.elapsed_time(t1)
+        if dist:
+            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        v.status()
+        e2e = {"value": world * 9.0 * cells * args.e2e_steps / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(f.numel() * f.element_size()),
+               "d2h_bytes_per_step": int(f.numel() * f.element_size() + rho.numel() * rho.element_size()),
+               "steps": args.e2e_steps}
+        del fh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+    v.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%s: %d^3 x %d^3 cells FP32, self-consistent Eq. (5) steps "
+                                   "(9 SL-MPP5 sweeps + moment + Poisson)" % (w["name"], n, nu),
+                       "cells": cells, "bytes_f": int(f.numel() * 4),
+                       "l2": "inputs larger than L2 (34.4 GB f vs 129 MB L2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
+            "kernels": per_kind,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """Each requested sweep twice plus the moment on a (64, 8, 8) x 32^3 FP32 grid."""
+    import torch
+    import oracle as O
+    from paper_2110_15867_gb300 import binding as B
+    from paper_2110_15867_gb300 import inputs as I
+    n, nu, V = (64, 8, 8), 32, 5.0
+    axes = [int(a) for a in args.axes.split(",")]
+    dev = torch.device("cuda", 0)
+    delta = torch.from_numpy(I.gaussian_field(n, 0.05, seed=2)).to(dev)
+    Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
+    f = ((1 + delta)[:, :, :, None, None, None] * Fu[None, None, None]).float().contiguous()
+    phi_np = I.fourier_potential(n, seed=3)
+    phi = torch.from_numpy(phi_np.astype(np.float32)).to(dev)
+    g = O.grid(n, nu, V=V)
+    v = B.Vlasov(f, V=V)
+    rho = torch.empty(n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        for ax in axes:
+            v.sweep(ax, 0.7 / O.max_abs_nu(g, ax, 1.0, 1.0, phi_np), 1.0, phi)
+        v.moment(rho)
+    v.status()
+    v.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -40,7 +40,12 @@ _VP = ctypes.c_void_p
 _lib = None
 
 SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep", "vlasov_moment",
-           "vlasov_poisson", "vlasov_step", "vlasov_status", "vlasov_last_error")
+           "vlasov_poisson", "vlasov_step", "vlasov_upload", "vlasov_download",
+           "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error")
+
+# timer kinds of vlasov_read_timers
+T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
+           "poisson", "coef", "mass")
 
 
 def library_path() -> str:
@@ -73,6 +78,15 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP,
                               ctypes.c_double, _VP, _VP]
     L.vlasov_step.restype = ctypes.c_int
+    L.vlasov_upload.argtypes = [_VP, _VP]
+    L.vlasov_upload.restype = ctypes.c_int
+    L.vlasov_download.argtypes = [_VP, _VP]
+    L.vlasov_download.restype = ctypes.c_int
+    L.vlasov_enable_timers.argtypes = [_VP, ctypes.c_int]
+    L.vlasov_enable_timers.restype = ctypes.c_int
+    L.vlasov_read_timers.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    L.vlasov_read_timers.restype = ctypes.c_int
     L.vlasov_status.argtypes = [_VP]
     L.vlasov_status.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
@@ -128,6 +142,27 @@ def vlasov_step(ctx, dt, a_half, a_full, phi_n_ptr, rho_bg_ptr, four_pi_G, phi_n
                 rho_nu_ptr):
     return _check(ctx, load().vlasov_step(ctx, dt, a_half, a_full, phi_n_ptr, rho_bg_ptr,
                                           four_pi_G, phi_next_ptr, rho_nu_ptr))
+
+
+def vlasov_upload(ctx, f_host_ptr: int):
+    return _check(ctx, load().vlasov_upload(ctx, f_host_ptr))
+
+
+def vlasov_download(ctx, f_host_ptr: int):
+    return _check(ctx, load().vlasov_download(ctx, f_host_ptr))
+
+
+def vlasov_enable_timers(ctx, on: bool):
+    return _check(ctx, load().vlasov_enable_timers(ctx, int(bool(on))))
+
+
+def vlasov_read_timers(ctx):
+    """Return ({kind: ms}, {kind: launches}) accumulated since the last read."""
+    n = len(T_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(ctx, load().vlasov_read_timers(ctx, ms, cnt, n))
+    return dict(zip(T_KINDS, list(ms))), dict(zip(T_KINDS, list(cnt)))
 
 
 def vlasov_status(ctx):
@@ -213,6 +248,27 @@ class Vlasov:
                     _ptr(self._field(rho_bg, self.torch.float64)), four_pi_G,
                     _ptr(self._field(phi_next, self.torch.float32)),
                     _ptr(self._field(rho_nu, self.torch.float64)))
+
+    def upload(self, f_host):
+        """Copy a host tensor (same shape and dtype as f, ideally pinned) into f."""
+        if f_host.is_cuda or tuple(f_host.shape) != self.shape or f_host.dtype != self.f.dtype \
+                or not f_host.is_contiguous():
+            raise ValueError("f_host must be a contiguous host tensor like f")
+        self._sync_stream()
+        vlasov_upload(self.ctx, f_host.data_ptr())
+
+    def download(self, f_host):
+        if f_host.is_cuda or tuple(f_host.shape) != self.shape or f_host.dtype != self.f.dtype \
+                or not f_host.is_contiguous():
+            raise ValueError("f_host must be a contiguous host tensor like f")
+        self._sync_stream()
+        vlasov_download(self.ctx, f_host.data_ptr())
+
+    def enable_timers(self, on: bool = True):
+        vlasov_enable_timers(self.ctx, on)
+
+    def read_timers(self):
+        return vlasov_read_timers(self.ctx)
 
     def status(self):
         return vlasov_status(self.ctx)
