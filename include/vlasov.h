@@ -148,6 +148,39 @@ int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
 
 /*
+ * Velocity sweep for callers that must not allocate device memory: code that
+ * runs under a fixed memory budget reserved up front, an allocator that is
+ * closed after start-up, or a host framework that owns every allocation and
+ * forbids the library from calling cudaMalloc.  The paper has no counterpart;
+ * this is a deployment variant of vlasov_sweep for axis 3..5 (u_x, u_y, u_z)
+ * on FP32 storage, with the same arithmetic and the same kernels.
+ *
+ * It creates no context and calls no cudaMalloc / cudaFree or any allocating
+ * routine.  Its scratch (the per-cell sweep constants and an error word) is a
+ * static device array built into the library, VLASOV_STATIC_MAX_CELLS spatial
+ * cells in size (about 1.2 MB, held on every GPU that loads the library until
+ * the process exits).  Grids with more spatial cells are rejected with
+ * VLASOV_EINVAL.  The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: calls that may overlap on the GPU (different streams,
+ * different host threads) race and must be serialised by the caller.
+ *
+ *   g        grid (dtype must be VLASOV_F32); f_dev as for vlasov_init
+ *   axis     3, 4 or 5; dt, phi_dev as for vlasov_sweep
+ *   status_dev  device word (may be NULL) into which the sweep ORs its
+ *            device-side error bits: 1 = a cell's |nu| >= 1 (that cell is
+ *            left unchanged), 2 = NaN/Inf or negative line sum, 4 = a bounded
+ *            wait ran out.  With NULL those bits are dropped.
+ *   stream   cudaStream_t the work is queued on (asynchronous).
+ * Host-side failures return a negative code; the message is
+ * vlasov_last_error(NULL).
+ */
+#define VLASOV_STATIC_MAX_CELLS 32768
+int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, int axis, double dt,
+                                 const float *phi_dev, unsigned int *status_dev, void *stream);
+
+/*
  * Synchronise the stream, read and clear the device error word.  Returns 0 or
  * the first of VLASOV_ETIMEOUT, VLASOV_ENAN, VLASOV_ECFL that was raised.
  */

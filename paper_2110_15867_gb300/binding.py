@@ -41,7 +41,11 @@ _lib = None
 
 SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep", "vlasov_moment",
            "vlasov_poisson", "vlasov_step", "vlasov_upload", "vlasov_download",
-           "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error")
+           "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
+           "vlasov_sweep_velocity_static")
+
+# spatial cells the allocation-free velocity sweep can hold (its static scratch)
+STATIC_MAX_CELLS = 32768
 
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
@@ -89,6 +93,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_read_timers.restype = ctypes.c_int
     L.vlasov_status.argtypes = [_VP]
     L.vlasov_status.restype = ctypes.c_int
+    L.vlasov_sweep_velocity_static.argtypes = [ctypes.POINTER(Grid), _VP, ctypes.c_int,
+                                               ctypes.c_double, _VP, _VP, _VP]
+    L.vlasov_sweep_velocity_static.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -167,6 +174,17 @@ def vlasov_read_timers(ctx):
 
 def vlasov_status(ctx):
     return _check(ctx, load().vlasov_status(ctx))
+
+
+def vlasov_sweep_velocity_static(grid: Grid, f_ptr: int, axis: int, dt: float, phi_ptr: int,
+                                 status_ptr, stream: int):
+    """Velocity sweep that allocates nothing (no context; static device scratch).
+
+    For callers that cannot allocate device memory after start-up.  Calls that may
+    overlap on the GPU share the scratch and must be serialised by the caller."""
+    rc = load().vlasov_sweep_velocity_static(ctypes.byref(grid), f_ptr, axis, dt, phi_ptr,
+                                             status_ptr, stream)
+    return _check(None, rc)
 
 
 # ---------------------------------------------------------------------------

@@ -519,3 +519,93 @@ extern "C" int vlasov_status(vlasov_ctx *c)
 }
 
 extern "C" const char *vlasov_last_error(const vlasov_ctx *c) { return c ? c->msg : g_init_error; }
+
+// ----------------------------------------------------------------------------
+// velocity sweep without allocation (vlasov_sweep_velocity_static)
+// ----------------------------------------------------------------------------
+// Scratch of the allocation-free entry point: 256 B of header (the error word
+// used when the caller passes no status word) followed by the per-cell sweep
+// constants of up to VLASOV_STATIC_MAX_CELLS spatial cells.  Device code could
+// name the array directly; host code must use the address that
+// cudaGetSymbolAddress returns for the current device.
+constexpr size_t kStaticHeader = 256;
+constexpr size_t kStaticBytes = kStaticHeader + (size_t)VLASOV_STATIC_MAX_CELLS * sizeof(LineCoefT<float>);
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+// Device address of g_static_scratch on device `dev` (looked up once per device).
+static cudaError_t static_scratch_address(int dev, unsigned char **out)
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex m;
+    static unsigned char *addr[kMaxDevices] = {};
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+extern "C" int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, int axis, double dt,
+                                            const float *phi_dev, unsigned int *status_dev, void *stream)
+{
+    if (!g || !f_dev || !phi_dev) return fail(nullptr, VLASOV_EINVAL, "vlasov_sweep_velocity_static: null argument");
+    if (axis < 3 || axis > 5) return fail(nullptr, VLASOV_EINVAL, "vlasov_sweep_velocity_static: axis %d is not 3..5", axis);
+    if (g->dtype != VLASOV_F32) return fail(nullptr, VLASOV_EINVAL, "vlasov_sweep_velocity_static: FP32 storage only");
+    if (!isfinite(dt)) return fail(nullptr, VLASOV_EINVAL, "vlasov_sweep_velocity_static: dt must be finite");
+    const int dims[6] = {g->nx, g->ny, g->nz, g->nux, g->nuy, g->nuz};
+    for (int k = 0; k < 3; ++k)
+        if (dims[k] < 4 || dims[k] > 256) return fail(nullptr, VLASOV_EINVAL, "spatial size %d outside [4, 256]", dims[k]);
+    for (int k = 3; k < 6; ++k)
+        if (dims[k] < 4 || dims[k] > kMaxVel || dims[k] % 4)
+            return fail(nullptr, VLASOV_EINVAL, "velocity size %d must be a multiple of 4 in [4, %d]", dims[k], kMaxVel);
+    if (!(g->L > 0) || !(g->V > 0)) return fail(nullptr, VLASOV_EINVAL, "L and V must be positive");
+    if (reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(nullptr, VLASOV_EINVAL, "f_dev must be 16-byte aligned");
+    const long long ncell = (long long)g->nx * g->ny * g->nz;
+    if (ncell > VLASOV_STATIC_MAX_CELLS)
+        return fail(nullptr, VLASOV_EINVAL,
+                    "vlasov_sweep_velocity_static: %lld spatial cells exceed the static scratch (%d cells)", ncell,
+                    VLASOV_STATIC_MAX_CELLS);
+    if (ncell * g->nux * g->nuy >= (1ll << 31)) return fail(nullptr, VLASOV_EINVAL, "too many u_z lines for 32-bit TMA coordinates");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    unsigned char *scratch = nullptr;
+    if (e == cudaSuccess) e = static_scratch_address(dev, &scratch);
+    if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "static scratch lookup: %s", cudaGetErrorString(e));
+
+    // A context on the stack: the plan and the launch helpers need no allocation.
+    vlasov_ctx c{};
+    c.g = *g;
+    c.f = f_dev;
+    c.stream = (cudaStream_t)stream;
+    c.es = 4;
+    c.ncell = ncell;
+    c.gd.n[0] = g->nx; c.gd.n[1] = g->ny; c.gd.n[2] = g->nz;
+    c.gd.nu[0] = g->nux; c.gd.nu[1] = g->nuy; c.gd.nu[2] = g->nuz;
+    c.gd.L = g->L;
+    c.gd.V = g->V;
+    e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "device query: %s", cudaGetErrorString(e));
+    int rc = plan_axes(&c);
+    if (rc != VLASOV_OK) return fail(nullptr, rc, "%s", c.msg);
+
+    unsigned *err = status_dev;
+    if (!err) {
+        // the shared error word starts every call at zero
+        err = reinterpret_cast<unsigned *>(scratch);
+        e = cudaMemsetAsync(err, 0, sizeof(unsigned), c.stream);
+        if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "clearing the static error word: %s", cudaGetErrorString(e));
+    }
+    void *coef = scratch + kStaticHeader;
+    c.d_err = err;
+    c.d_coef[axis - 3] = coef;
+    rc = prep_velocity(&c, phi_dev, dt, 1 << (axis - 3));
+    if (rc == VLASOV_OK) rc = run_velocity(&c, axis);
+    if (rc != VLASOV_OK) return fail(nullptr, rc, "%s", c.msg);
+    return VLASOV_OK;
+}
