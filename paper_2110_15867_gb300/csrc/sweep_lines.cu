@@ -1,0 +1,214 @@
+// sweep_lines.cu -- SL-MPP5 sweep along the contiguous axis u_z with whole
+// lines in registers (FP32, n_uz = 16 or 32).
+//
+// Eq. (4) for i = 3 (Yoshikawa, Tanaka & Yoshida, SC'21).  A u_z line is one
+// row of n_uz contiguous cells, 64 or 128 bytes.  TMA loads a box of 256 rows
+// with the 64-/128-byte hardware swizzle: 16-byte chunk j of row r lands at
+// chunk j ^ ((r * rowbytes >> 7) & (rowbytes / 16 - 1)), so eight threads that
+// each read a 16-byte chunk of eight consecutive rows hit eight different bank
+// groups.  Each consumer thread owns rows t and t + 128 of the tile as one
+// packed FP32 pair, pulls both lines into registers, marches them fully
+// unrolled (the orientation is a warp-uniform branch: all 256 rows of a tile
+// share a spatial cell), and writes them back for the TMA store.  This replaces
+// the shared-memory transpose of sweep_contig.cu, the GPU analogue of the
+// paper's load-and-transpose (LAT, Sec. 4.3), for these line lengths.
+#include "vk_common.cuh"
+
+namespace vk {
+
+constexpr int kLineThreads = 128;           // consumer threads; 2 rows each
+constexpr int kLineRows = 2 * kLineThreads; // rows per tile
+constexpr int kLineRing = 2;                // tile slots
+
+template <int NU> struct LineGeom {
+    static constexpr int rowbytes = NU * 4;
+    static constexpr int chunks = rowbytes / 16;
+    // swizzled byte offset of 16-byte chunk j of row r
+    __device__ static int off(int r, int j) { return r * rowbytes + 16 * (j ^ ((r * rowbytes >> 7) & (chunks - 1))); }
+};
+
+// Advance both lines of the pair (forward local frame; zero-flux faces).
+template <int NU>
+__device__ __forceinline__ float2 march_regs(float2 (&v)[NU], const Lim<float2> &lim)
+{
+    const float2 zero = splat<float2>(0.0);
+    float2 d[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        d[i] = curv(i > 0 ? v[i - 1] : zero, v[i], i + 1 < NU ? v[i + 1] : zero);
+    const float2 dm = v[0]; // curvature of the ghost cell -1: 0 - 0 + c_0
+    // F[k] = flux through face k - 1/2, k = 1 .. NU-1 (outer faces carry nothing)
+    float2 Fprev = zero, sum = zero;
+    float2 dm4m = dm4(dm, d[0]);
+    float2 out[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        float2 F = zero;
+        float2 dm4p = zero;
+        if (i + 1 < NU) {
+            const float2 cm2 = i >= 2 ? v[i - 2] : zero;
+            const float2 cm1 = i >= 1 ? v[i - 1] : zero;
+            const float2 cp2 = i + 2 < NU ? v[i + 2] : zero;
+            dm4p = dm4(d[i], d[i + 1]);
+            F = sl_mpp5_flux(lim, cm2, cm1, v[i], v[i + 1], cp2, dm4m, dm4p);
+        }
+        out[i] = vadd(v[i], vsub(Fprev, F));
+        sum = vadd(sum, out[i]);
+        Fprev = F;
+        dm4m = dm4p;
+    }
+#pragma unroll
+    for (int i = 0; i < NU; ++i) v[i] = out[i];
+    return sum;
+}
+
+// Rows r0 and r1 of a swizzled tile: gather (back to front when NEG, the
+// mirror image of a negative Courant number), march, scatter.  Returns true
+// when a line sum is negative, NaN or infinite.
+template <int NU, bool NEG>
+__device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, const Lim<float2> &lim)
+{
+    using G_ = LineGeom<NU>;
+    float2 v[NU];
+#pragma unroll
+    for (int j = 0; j < G_::chunks; ++j) {
+        const float4 a = *reinterpret_cast<const float4 *>(base + G_::off(r0, j));
+        const float4 c = *reinterpret_cast<const float4 *>(base + G_::off(r1, j));
+        const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[NEG ? NU - 1 - (4 * j + q) : 4 * j + q] = make_float2(av[q], cv[q]);
+    }
+    const float2 sum = march_regs<NU>(v, lim);
+#pragma unroll
+    for (int j = 0; j < G_::chunks; ++j) {
+        float a4[4], c4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 x = v[NEG ? NU - 1 - (4 * j + q) : 4 * j + q];
+            a4[q] = x.x;
+            c4[q] = x.y;
+        }
+        *reinterpret_cast<float4 *>(base + G_::off(r0, j)) = make_float4(a4[0], a4[1], a4[2], a4[3]);
+        *reinterpret_cast<float4 *>(base + G_::off(r1, j)) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+    }
+    return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
+}
+
+template <int NU>
+__global__ void __launch_bounds__(kLineThreads + kProducer, 3)
+    line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ ContigArgs<float> args)
+{
+    using G_ = LineGeom<NU>;
+    constexpr int S = kLineRing;
+    constexpr unsigned slot_bytes = kLineRows * NU * 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *done = full + S;
+    // swizzled boxes need a 1024-byte aligned destination
+    unsigned char *ring = smem + 128 + ((1024u - ((smem_u32(smem) + 128u) & 1023u)) & 1023u);
+    auto slot = [&](unsigned e) { return ring + slot_bytes * (e % S); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], kLineThreads);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const long long Gd = gridDim.x, b = blockIdx.x;
+    const unsigned n_my = unsigned((args.num_tiles > b) ? (args.num_tiles - b + Gd - 1) / Gd : 0);
+
+    if (threadIdx.x < kProducer) {
+        if (threadIdx.x != 0) return;
+        unsigned loaded = 0, retired = 0;
+        bool ok = true;
+        while (retired < n_my) {
+            bool progress = false;
+            while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
+                tma_store_2d(&map, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
+                bulk_commit();
+                ++retired;
+                progress = true;
+            }
+            if (loaded < n_my && loaded < retired + S) {
+                if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
+                const unsigned st = loaded % S;
+                mbar_arrive_expect_tx(&full[st], slot_bytes);
+                tma_load_2d(slot(loaded), &map, &full[st], 0, int((b + (long long)loaded * Gd) * kLineRows));
+                ++loaded;
+                progress = true;
+            }
+            if (!progress && !mbar_wait_bounded(&done[retired % S], (retired / S) & 1u)) {
+                ok = false;
+                break;
+            }
+        }
+        bulk_wait_all();
+        if (!ok) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            for (unsigned t = retired; t < loaded; ++t) mbar_wait_bounded(&full[t % S], (t / S) & 1u);
+        }
+        return;
+    }
+
+    const int tid = threadIdx.x - kProducer;
+    const int r0 = tid, r1 = tid + kLineThreads;
+    for (unsigned k = 0; k < n_my; ++k) {
+        const unsigned st = k % S;
+        if (!mbar_wait_bounded(&full[st], (k / S) & 1u)) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            break;
+        }
+        const long long row0 = (b + (long long)k * Gd) * kLineRows;
+        unsigned char *base = slot(k);
+        if (row0 + r0 < args.rows) {
+            const LineCoefT<float> kc = args.cell_coef[(row0 + r0) / args.rows_per_cell];
+            if (kc.nd >= 0) {
+                // one orientation per spatial cell, so the branch is warp-uniform
+                const bool bad = (kc.nd & 1) ? line_pair<NU, true>(base, r0, r1, to_lim2(kc, kc))
+                                             : line_pair<NU, false>(base, r0, r1, to_lim2(kc, kc));
+                if (bad) atomicOr(args.err, ERR_NAN);
+            }
+        }
+        fence_proxy_async();
+        mbar_arrive(&done[st]);
+    }
+}
+
+template <int NU> static const void *line_kernel_ptr() { return (const void *)line_sweep_kernel<NU>; }
+
+size_t line_sweep_smem(int nu) { return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * 4; }
+
+bool line_sweep_supported(int nu, long long rows_per_cell)
+{
+    return (nu == 16 || nu == 32) && rows_per_cell % kLineRows == 0;
+}
+
+cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int grid, cudaStream_t st)
+{
+    const void *k = nu == 32 ? line_kernel_ptr<32>() : line_kernel_ptr<16>();
+    const size_t smem = line_sweep_smem(nu);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    if (nu == 32)
+        line_sweep_kernel<32><<<grid, kLineThreads + kProducer, smem, st>>>(map, a);
+    else
+        line_sweep_kernel<16><<<grid, kLineThreads + kProducer, smem, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+int occupancy_line_sweep(int nu)
+{
+    const void *k = nu == 32 ? line_kernel_ptr<32>() : line_kernel_ptr<16>();
+    const size_t smem = line_sweep_smem(nu);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kLineThreads + kProducer, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+int line_sweep_rows_per_tile() { return kLineRows; }
+
+} // namespace vk

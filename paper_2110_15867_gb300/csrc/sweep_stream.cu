@@ -1,0 +1,403 @@
+// sweep_stream.cu -- SL-MPP5 sweeps along a strided axis (x, y, z, u_x, u_y),
+// lines streamed through shared memory in chunks of rows.
+//
+// Eq. (3) (position advection, periodic) and Eq. (4) (velocity advection,
+// zero-flux faces) of Yoshikawa, Tanaka & Yoshida, SC'21, for Courant numbers
+// with no whole-cell part (|nu| < 1 on every line; sweep_strided.cu handles
+// whole-cell shifts).
+//
+// f is the 3D tensor [O][L][I] (slower axes, swept axis, faster axes).  A CTA
+// owns a block of columns -- {W inner} x {P outer} -- and walks it down the
+// swept axis in chunks of R rows: TMA box {W, R, P}.  Each consumer thread owns
+// two adjacent columns (one packed FP32 pair, or one column in FP64) and keeps
+// its sliding window in registers, so a column needs only R rows of shared
+// memory in flight instead of its whole line: more CTAs fit per SM.
+//
+// Ring of S chunk slots.  For a periodic line the first entry of a block is a
+// "prologue" box starting at row L-3 (its first three rows are the upwind
+// neighbours of row 0; the rest lies outside the tensor and reads as zero).
+// Producer (warp 0, lane 0): loads entries in order into the ring and, before
+// reusing a slot, waits until the consumers release it and TMA-stores it back
+// in place when it holds a chunk.  Consumers: the output of row i is final
+// after row i + 2 has been read, so a chunk is released (done barrier) when its
+// last row has been written.  Every wait is bounded.
+#include "vk_common.cuh"
+
+namespace vk {
+
+template <typename T> struct Lane;
+template <> struct Lane<float> {
+    using X = float2; // two columns per thread
+    static constexpr int V = 2;
+    __device__ static X load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static void store(float *p, X v) { *reinterpret_cast<float2 *>(p) = v; }
+    __device__ static bool bad(X s) { return !(s.x >= 0.f) || !(s.y >= 0.f) || isinf(s.x) || isinf(s.y); }
+};
+template <> struct Lane<double> {
+    using X = double;
+    static constexpr int V = 1;
+    __device__ static X load(const double *p) { return *p; }
+    __device__ static void store(double *p, X v) { *p = v; }
+    __device__ static bool bad(X s) { return !(s >= 0.0) || isinf(s); }
+};
+
+template <typename C> __device__ __forceinline__ Lim<typename Lane<C>::X> pair_lim(const LineCoefT<C> &a, const LineCoefT<C> &b);
+template <> __device__ __forceinline__ Lim<float2> pair_lim<float>(const LineCoefT<float> &a, const LineCoefT<float> &b)
+{
+    return to_lim2(a, b);
+}
+template <> __device__ __forceinline__ Lim<double> pair_lim<double>(const LineCoefT<double> &a, const LineCoefT<double> &)
+{
+    return to_lim(a);
+}
+
+// March one block's column(s) down the line in physical row order, reading the
+// rows from the ring (chunk c of the line is ring entry ec + c; a periodic
+// line's prologue entry e holds rows L-3..L-1 first).  NEG selects the
+// orientation: the flux through face i+1/2 has donor i (nu > 0) or donor i+1
+// with the mirrored stencil (nu < 0); either way rows are consumed in order and
+// a chunk is released once its last row has been written.  Returns the sum of
+// the new values.
+template <typename T, bool PERIODIC, bool NEG, typename X, typename SlotPtr, typename Acq, typename Rel>
+__device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigned ec, int coff, int L, int W,
+                                          SlotPtr slot_ptr, Acq acquire, Rel release, bool &alive)
+{
+    using LN = Lane<T>;
+    constexpr int R = kStreamRows;
+    const X zero = splat<X>(0.0);
+    auto row_ptr = [&](int r) { return slot_ptr(ec + unsigned(r / R)) + coff + (r % R) * W; };
+    X p3 = zero, p2 = zero, p1 = zero; // c_{-3}, c_{-2}, c_{-1}
+    if (PERIODIC) {
+        if (!acquire(e)) return zero;
+        const T *q = slot_ptr(e) + coff;
+        p3 = LN::load(q);
+        p2 = LN::load(q + W);
+        p1 = LN::load(q + 2 * W);
+        release(e);
+    }
+    if (!acquire(ec)) return zero; // rows 0..3 lie in chunk 0 (R >= 4)
+    const X s0 = LN::load(row_ptr(0));
+    const X s1 = LN::load(row_ptr(1));
+    X sum = zero;
+    // Rows i whose look-ahead rows i + LA all lie inside the line and whose chunk
+    // is complete are marched chunk by chunk with compile-time offsets (chunk c is
+    // "simple" when c R + R - 1 + LA < L); the rest row by row.
+    if (!NEG) {
+        constexpr int LA = 2;
+        // window c_{i-2} .. c_{i+2}, donor c_i
+        X cm2, cm1, c0 = s0, cp1 = s1, dcur, dm4m, Fm;
+        const X dm = curv(p2, p1, s0);
+        const X d0 = curv(p1, s0, s1);
+        dm4m = dm4(dm, d0);
+        if (PERIODIC) Fm = sl_mpp5_flux(lim, p3, p2, p1, s0, s1, dm4(curv(p3, p2, p1), dm), dm4m);
+        else Fm = zero;
+        cm2 = p2;
+        cm1 = p1;
+        dcur = d0;
+        auto face = [&](X cp2, T *dst) {
+            const X dn = curv(c0, cp1, cp2);
+            const X dm4p = dm4(dcur, dn);
+            const X F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
+            const X out = vadd(c0, vsub(Fm, F));
+            LN::store(dst, out);
+            sum = vadd(sum, out);
+            cm2 = cm1;
+            cm1 = c0;
+            c0 = cp1;
+            cp1 = cp2;
+            dcur = dn;
+            dm4m = dm4p;
+            Fm = F;
+        };
+        const int nsimple = (L - LA + 1) / R - 1 > 0 ? (L - LA + 1) / R - 1 : 0;
+        for (int c = 0; c < nsimple; ++c) {
+            T *cur = slot_ptr(ec + unsigned(c)) + coff;
+            T *nxt = slot_ptr(ec + unsigned(c + 1)) + coff;
+            if (!acquire(ec + unsigned(c + 1))) return zero;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const X cp2 = (q + LA < R) ? LN::load(cur + (q + LA) * W) : LN::load(nxt + (q + LA - R) * W);
+                face(cp2, cur + q * W);
+            }
+            release(ec + unsigned(c));
+        }
+        for (int i = nsimple * R; i < L; ++i) {
+            const int r = i + LA;
+            X cp2;
+            if (r < L) {
+                if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
+                cp2 = LN::load(row_ptr(r));
+            } else {
+                cp2 = PERIODIC ? (r == L ? s0 : s1) : zero;
+            }
+            if (!PERIODIC && i == L - 1) {
+                // outer velocity face: nothing crosses it
+                const X out = vadd(c0, Fm);
+                LN::store(row_ptr(i), out);
+                sum = vadd(sum, out);
+            } else {
+                face(cp2, row_ptr(i));
+            }
+            if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
+        }
+    } else {
+        constexpr int LA = 3;
+        // window c_{i-1} .. c_{i+3}, donor c_{i+1}, flux toward -index
+        const X s2 = LN::load(row_ptr(2));
+        const X dmn = curv(p2, p1, s0); // d_{-1}
+        const X d0 = curv(p1, s0, s1);
+        const X d1 = curv(s0, s1, s2);
+        X dm4a = dm4(d0, d1);           // limited curvature at face i+1/2
+        X Fm;                            // mass moving left through face i-1/2
+        if (PERIODIC) Fm = sl_mpp5_flux(lim, s2, s1, s0, p1, p2, dm4a, dm4(dmn, d0));
+        else Fm = zero;
+        X cm1 = p1, c0 = s0, cp1 = s1, cp2 = s2, d_1 = d1;
+        auto face = [&](X cp3, T *dst) {
+            const X d_2 = curv(cp1, cp2, cp3);
+            const X dm4b = dm4(d_1, d_2); // face i+3/2
+            const X F = sl_mpp5_flux(lim, cp3, cp2, cp1, c0, cm1, dm4b, dm4a);
+            const X out = vadd(c0, vsub(F, Fm));
+            LN::store(dst, out);
+            sum = vadd(sum, out);
+            cm1 = c0;
+            c0 = cp1;
+            cp1 = cp2;
+            cp2 = cp3;
+            d_1 = d_2;
+            dm4a = dm4b;
+            Fm = F;
+        };
+        const int nsimple = (L - LA + 1) / R - 1 > 0 ? (L - LA + 1) / R - 1 : 0;
+        for (int c = 0; c < nsimple; ++c) {
+            T *cur = slot_ptr(ec + unsigned(c)) + coff;
+            T *nxt = slot_ptr(ec + unsigned(c + 1)) + coff;
+            if (!acquire(ec + unsigned(c + 1))) return zero;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const X cp3 = (q + LA < R) ? LN::load(cur + (q + LA) * W) : LN::load(nxt + (q + LA - R) * W);
+                face(cp3, cur + q * W);
+            }
+            release(ec + unsigned(c));
+        }
+        for (int i = nsimple * R; i < L; ++i) {
+            const int r = i + LA;
+            X cp3;
+            if (r < L) {
+                if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
+                cp3 = LN::load(row_ptr(r));
+            } else {
+                cp3 = PERIODIC ? (r == L ? s0 : (r == L + 1 ? s1 : s2)) : zero;
+            }
+            if (!PERIODIC && i == L - 1) {
+                const X out = vsub(c0, Fm); // nothing enters through the outer face
+                LN::store(row_ptr(i), out);
+                sum = vadd(sum, out);
+            } else {
+                face(cp3, row_ptr(i));
+            }
+            if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
+        }
+    }
+    return sum;
+}
+
+template <typename T, bool PERIODIC>
+__global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
+    stream_sweep_kernel(const __grid_constant__ CUtensorMap map,
+                        const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
+{
+    using C = typename Compute<T>::type;
+    using LN = Lane<T>;
+    using X = typename LN::X;
+    constexpr int V = LN::V;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStreamRing;
+    constexpr int R = kStreamRows;
+    const int L = args.L, W = args.W, P = args.P;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *done = full + S;
+    int4 *meta = reinterpret_cast<int4 *>(done + S); // per slot: store coordinates, is-chunk flag
+    LineCoefT<C> *tab = reinterpret_cast<LineCoefT<C> *>(smem + 512);
+    const size_t tab_bytes = (args.coef_mode == 0) ? ((sizeof(LineCoefT<C>) * args.nvel + 127) & ~size_t(127)) : 0;
+    unsigned char *ring = smem + 512 + tab_bytes;
+    const int slot_elems = W * R * P;
+    const unsigned slot_bytes = unsigned(slot_elems * sizeof(T));
+    const unsigned slot_pitch = (slot_bytes + 127u) & ~127u;
+    auto slot_ptr = [&](unsigned e) { return reinterpret_cast<T *>(ring + slot_pitch * (e & (S - 1))); };
+    const int nC = (L + R - 1) / R;                // chunks per line
+    const int E = nC + (PERIODIC ? 1 : 0);         // ring entries per block
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], kStreamConsumers);
+        }
+        fence_barrier_init();
+    }
+    if (args.coef_mode == 0)
+        for (int j = threadIdx.x; j < args.nvel; j += blockDim.x) tab[j] = args.table[j];
+    __syncthreads();
+
+    const long long G = gridDim.x, b = blockIdx.x;
+    const long long n_my = (args.num_blocks > b) ? (args.num_blocks - b + G - 1) / G : 0;
+
+    if (threadIdx.x < kProducer) {
+        if (threadIdx.x != 0) return;
+        // Entries are loaded in order into slot e % S and retired in order: once the
+        // consumers release an entry its chunk is stored back (one bulk group per
+        // entry, empty for a prologue), without waiting.  A slot is reloaded only
+        // after the store of its previous entry has read the slot out.
+        const unsigned total = unsigned(n_my) * unsigned(E);
+        unsigned loaded = 0, retired = 0;
+        long long k = 0;
+        int j = 0, c0 = 0, c2 = 0;
+        bool ok = true;
+        while (retired < total) {
+            bool progress = false;
+            while (retired < loaded && mbar_test_wait(&done[retired & (S - 1)], (retired / S) & 1u)) {
+                const int4 m = meta[retired & (S - 1)];
+                if (m.w) tma_store_3d(&map, slot_ptr(retired), m.x, m.y, m.z);
+                bulk_commit();
+                ++retired;
+                progress = true;
+            }
+            if (loaded < total && loaded < retired + S) {
+                // the store of entry loaded - S is group loaded - S of `retired` groups
+                if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
+                if (j == 0) {
+                    const long long t = b + k * G;
+                    c0 = int((t % args.tiles_inner) * W);
+                    c2 = int((t / args.tiles_inner) * P);
+                }
+                const int ch = PERIODIC ? j - 1 : j;
+                const int c1 = ch >= 0 ? ch * R : L - 3;
+                const unsigned st = loaded & (S - 1);
+                meta[st] = make_int4(c0, c1, c2, ch >= 0);
+                mbar_arrive_expect_tx(&full[st], slot_bytes);
+                tma_load_3d(slot_ptr(loaded), &map, &full[st], c0, c1, c2);
+                ++loaded;
+                if (++j == E) { j = 0; ++k; }
+                progress = true;
+            }
+            if (!progress && !mbar_wait_bounded(&done[retired & (S - 1)], (retired / S) & 1u)) {
+                ok = false;
+                break;
+            }
+        }
+        bulk_wait_all();
+        if (!ok) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            for (unsigned t = retired; t < loaded; ++t) mbar_wait_bounded(&full[t & (S - 1)], (t / S) & 1u);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int tid = threadIdx.x - kProducer;
+    int col;  // first of this thread's V columns inside the block
+    if (args.perm_line > 0) {
+        // z sweep: the Courant number changes sign in the middle of each velocity
+        // line; threads [0, H) take the columns with u_z < 0 and [H, 2H) those
+        // with u_z > 0, so that whole warps march with one orientation.
+        const int Lz = args.perm_line, q = Lz / (2 * V);   // pairs per half line
+        const int lines = W / Lz, H = lines * q;
+        const int tt = tid < H ? tid : tid - H;
+        col = (tt / q) * Lz + (tid < H ? 0 : Lz / 2) + V * (tt % q);
+        if (tid >= 2 * H) col = W * P;                      // idle thread
+    } else {
+        col = tid * V;
+    }
+    const int w = col % W, p = col / W;
+    const bool has_col = col < W * P;
+    const int coff = p * R * W + w;          // column offset inside a slot; rows are W apart
+    bool alive = true;
+    unsigned e = 0;                          // next ring entry
+    auto acquire = [&](unsigned ee) {
+        if (!mbar_wait_bounded(&full[ee & (S - 1)], (ee / S) & 1u)) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            alive = false;
+        }
+        return alive;
+    };
+    auto release = [&](unsigned ee) {
+        fence_proxy_async();
+        mbar_arrive(&done[ee & (S - 1)]);
+    };
+
+    for (long long k = 0; k < n_my && alive; ++k) {
+        const long long t = b + k * G;
+        const long long inner = (t % args.tiles_inner) * W + w;
+        const long long outer = (t / args.tiles_inner) * P + p;
+        bool work = has_col && inner < args.n_inner && outer < args.n_outer;
+        Lim<X> lim{};
+        bool neg = false;
+        if (work) {
+            LineCoefT<C> ka, kb;
+            if (args.coef_mode == 0) {
+                ka = tab[(inner / args.vstride) % args.nvel];
+                kb = tab[((inner + V - 1) / args.vstride) % args.nvel];
+            } else {
+                ka = args.cell_coef[outer / args.outer_per_cell];
+                kb = ka;
+            }
+            if (ka.nd < 0 || kb.nd < 0) work = false; // Courant number out of range: leave as is
+            neg = ka.nd & 1;
+            lim = pair_lim<C>(ka, kb);
+        }
+        const unsigned ec = e + (PERIODIC ? 1u : 0u); // entry of chunk 0
+        if (!work) {
+            // keep the barrier phases in step with the other consumers
+            for (int j = 0; j < E && alive; ++j)
+                if (acquire(e + unsigned(j))) release(e + unsigned(j));
+            e += E;
+            continue;
+        }
+        X sum;
+        if (neg)
+            sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, L, W, slot_ptr, acquire, release, alive);
+        else
+            sum = march_stream<T, PERIODIC, false>(lim, e, ec, coff, L, W, slot_ptr, acquire, release, alive);
+        if (!alive) break;
+        if (LN::bad(sum)) atomicOr(args.err, ERR_NAN);
+        e += unsigned(E);
+    }
+}
+
+template <typename T>
+static cudaError_t launch_stream_t(const CUtensorMap &map, const StreamArgs<typename Compute<T>::type> &a, int grid,
+                                   size_t smem, cudaStream_t st)
+{
+    auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                              cudaStream_t st)
+{
+    return launch_stream_t<float>(map, a, grid, smem, st);
+}
+
+cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
+                              cudaStream_t st)
+{
+    return launch_stream_t<double>(map, a, grid, smem, st);
+}
+
+int occupancy_stream(int dtype, int periodic, size_t smem)
+{
+    const void *k;
+    if (dtype == 0)
+        k = periodic ? (const void *)stream_sweep_kernel<double, true> : (const void *)stream_sweep_kernel<double, false>;
+    else
+        k = periodic ? (const void *)stream_sweep_kernel<float, true> : (const void *)stream_sweep_kernel<float, false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStreamConsumers + kProducer, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+} // namespace vk

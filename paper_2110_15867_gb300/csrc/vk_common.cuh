@@ -79,6 +79,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 
+// Non-blocking probe: has the phase with this parity completed?
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of `bar` with the given parity; false if the wait ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
 {
@@ -138,6 +152,21 @@ __device__ __forceinline__ void bulk_wait_read_all()
 
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// wait until at most n (0..7) of the most recent bulk groups are still reading shared memory
+__device__ __forceinline__ void bulk_wait_read_at_most(unsigned n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.bulk.wait_group.read 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.bulk.wait_group.read 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.bulk.wait_group.read 6;" ::: "memory"); break;
+    default: asm volatile("cp.async.bulk.wait_group.read 7;" ::: "memory"); break;
+    }
+}
+
 // barrier among the consumer warps only (named barrier 1)
 __device__ __forceinline__ void consumer_sync(int nthreads)
 {
@@ -188,25 +217,90 @@ __device__ __forceinline__ float mx2(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double mn2(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double mx2(double a, double b) { return fmax(a, b); }
 
-// minmod: 0 unless all arguments share a sign, else the one of least magnitude
-template <typename C> __device__ __forceinline__ C minmod2(C a, C b)
+// ----------------------------------------------------------------------------
+// arithmetic on float, double and float2 (two independent lines in packed FP32:
+// add / sub / mul / fma use the f32x2 instructions of sm_100+, min / max / select
+// act per component)
+// ----------------------------------------------------------------------------
+
+#ifndef VK_PACKED
+#define VK_PACKED 1 // 1: float2 add/sub/mul/fma as one f32x2 instruction; 0: two FP32 instructions
+#endif
+#if VK_PACKED
+#define VK_F2_BINOP(name, op)                                                                        \
+    __device__ __forceinline__ float2 name(float2 a, float2 b)                                        \
+    {                                                                                                 \
+        float2 d;                                                                                     \
+        asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op     \
+            " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"                                                    \
+            : "=f"(d.x), "=f"(d.y)                                                                    \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                \
+        return d;                                                                                     \
+    }
+VK_F2_BINOP(vadd, "add.rn.f32x2")
+VK_F2_BINOP(vsub, "sub.rn.f32x2")
+VK_F2_BINOP(vmul, "mul.rn.f32x2")
+#undef VK_F2_BINOP
+
+// a * b + c
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
 {
-    return mx2(mn2(a, b), C(0)) + mn2(mx2(a, b), C(0));
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+#else
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
+{
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#endif
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+
+__device__ __forceinline__ float2 mn2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 mx2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ float2 mn3(float2 a, float2 b, float2 c)
+{
+    return make_float2(mn3(a.x, b.x, c.x), mn3(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 mx3(float2 a, float2 b, float2 c)
+{
+    return make_float2(mx3(a.x, b.x, c.x), mx3(a.y, b.y, c.y));
 }
 
-template <typename C> __device__ __forceinline__ C minmod4(C a, C b, C c, C d)
+template <typename X> __device__ __forceinline__ X splat(double v);
+template <> __device__ __forceinline__ float splat<float>(double v) { return float(v); }
+template <> __device__ __forceinline__ double splat<double>(double v) { return v; }
+template <> __device__ __forceinline__ float2 splat<float2>(double v) { return make_float2(float(v), float(v)); }
+
+// minmod: 0 unless all arguments share a sign, else the one of least magnitude;
+// = median(lo, 0, hi) with lo / hi the smallest / largest argument
+template <typename X> __device__ __forceinline__ X minmod4(X a, X b, X c, X d)
 {
-    const C lo = mn2(mn3(a, b, c), d);
-    const C hi = mx2(mx3(a, b, c), d);
-    return mx2(lo, C(0)) + mn2(hi, C(0));
+    const X lo = mn2(mn3(a, b, c), d);
+    const X hi = mx2(mx3(a, b, c), d);
+    return mn2(mx2(lo, splat<X>(0.0)), hi);
 }
 
 // ----------------------------------------------------------------------------
 // SL-MPP5 line coefficients
 // ----------------------------------------------------------------------------
 
-template <typename C> struct Lim {
-    C w0, w1, w2, w3, w4, s, alpha;
+template <typename X> struct Lim {
+    X w0, w1, w2, w3, w4, s, alpha;
 };
 
 template <typename C> __device__ __forceinline__ Lim<C> to_lim(const LineCoefT<C> &k)
@@ -214,35 +308,51 @@ template <typename C> __device__ __forceinline__ Lim<C> to_lim(const LineCoefT<C
     return Lim<C>{k.w[0], k.w[1], k.w[2], k.w[3], k.w[4], k.s, k.alpha};
 }
 
-// Fractional flux through the downwind face of the donor c0 (local frame, flow
-// toward +index): SL reconstruction mean fbar, Suresh-Huynh constraint on
-// fbar with the given alpha (skipped when fbar lies between c0 and the MP
-// bound), then s * fbar clamped to [0, c0] (positivity).
-// dm4m / dm4p are the limited curvatures at the upwind / downwind faces.
-template <typename C>
-__device__ __forceinline__ C sl_mpp5_flux(const Lim<C> &k, C cm2, C cm1, C c0, C cp1, C cp2, C dm4m,
-                                          C dm4p)
+// two lines in one packed pair
+__device__ __forceinline__ Lim<float2> to_lim2(const LineCoefT<float> &a, const LineCoefT<float> &b)
 {
-    const C fbar = k.w0 * cm2 + k.w1 * cm1 + k.w2 * c0 + k.w3 * cp1 + k.w4 * cp2;
-    const C dlm = c0 - cm1;
-    const C dlp = cp1 - c0;
-    const C up = k.alpha * dlm;
-    const C fmp = c0 + minmod2(dlp, up);
-    const C ful = c0 + up;
-    const C fmd = C(0.5) * (c0 + cp1 - dm4p);
-    const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * dm4m;
-    const C fmin = mx2(mn3(c0, cp1, fmd), mn3(c0, ful, flc));
-    const C fmax = mn2(mx3(c0, cp1, fmd), mx3(c0, ful, flc));
-    // fmin <= c0 <= fmax, so the median of (fbar, fmin, fmax) is a clamp
-    const C clamp = mn2(mx2(fbar, fmin), fmax);
-    const C v = ((fbar - c0) * (fbar - fmp) <= C(0)) ? fbar : clamp;
-    return mn2(mx2(k.s * v, C(0)), c0);
+    return Lim<float2>{make_float2(a.w[0], b.w[0]), make_float2(a.w[1], b.w[1]), make_float2(a.w[2], b.w[2]),
+                       make_float2(a.w[3], b.w[3]), make_float2(a.w[4], b.w[4]), make_float2(a.s, b.s),
+                       make_float2(a.alpha, b.alpha)};
+}
+
+// Fractional flux through the downwind face of the donor c0 (local frame, flow
+// toward +index): SL reconstruction mean fbar, Suresh-Huynh monotonicity
+// constraint on fbar with the given alpha, then s * fbar clamped to [0, c0]
+// (positivity).  dm4m / dm4p are the limited curvatures at the upwind /
+// downwind faces of the donor.
+//
+// Suresh & Huynh keep fbar when it lies between c0 and the MP bound
+// f_MP = c0 + minmod(cp1 - c0, alpha (c0 - cm1)) and otherwise take
+// median(fbar, fmin, fmax).  f_MP is the median of (c0, cp1, f_UL), and every
+// one of the sets bounding fmin and fmax contains c0 together with cp1 or f_UL,
+// so [c0, f_MP] lies inside [fmin, fmax] (both are pure selections, exactly so
+// in floating point): the constraint is the clamp of fbar to [fmin, fmax].
+template <typename X>
+__device__ __forceinline__ X sl_mpp5_flux(const Lim<X> &k, X cm2, X cm1, X c0, X cp1, X cp2, X dm4m, X dm4p)
+{
+    const X fbar = vfma(k.w4, cp2, vfma(k.w3, cp1, vfma(k.w2, c0, vfma(k.w1, cm1, vmul(k.w0, cm2)))));
+    const X dlm = vsub(c0, cm1);
+    const X ful = vfma(k.alpha, dlm, c0);
+    const X fmd = vmul(splat<X>(0.5), vsub(vadd(c0, cp1), dm4p));
+    const X flc = vfma(splat<X>(4.0 / 3.0), dm4m, vfma(splat<X>(0.5), dlm, c0));
+    const X fmin = mx2(mn3(c0, cp1, fmd), mn3(c0, ful, flc));
+    const X fmax = mn2(mx3(c0, cp1, fmd), mx3(c0, ful, flc));
+    const X v = mn2(mx2(fbar, fmin), fmax);
+    return mn2(mx2(vmul(k.s, v), splat<X>(0.0)), c0);
 }
 
 // limited curvature at the face between two cells with curvatures d0, d1
-template <typename C> __device__ __forceinline__ C dm4(C d0, C d1)
+template <typename X> __device__ __forceinline__ X dm4(X d0, X d1)
 {
-    return minmod4(C(4) * d0 - d1, C(4) * d1 - d0, d0, d1);
+    const X four = splat<X>(4.0);
+    return minmod4(vsub(vmul(four, d0), d1), vsub(vmul(four, d1), d0), d0, d1);
+}
+
+// curvature c_{i-1} - 2 c_i + c_{i+1}
+template <typename X> __device__ __forceinline__ X curv(X a, X b, X c)
+{
+    return vadd(vfma(splat<X>(-2.0), b, a), c);
 }
 
 // ----------------------------------------------------------------------------
@@ -265,9 +375,9 @@ __device__ __forceinline__ C march_line(T *p, long step, int L, const Lim<C> &k)
         const C a = to_c(p[(long)(L - 3) * step]);
         const C b = to_c(p[(long)(L - 2) * step]);
         const C c = to_c(p[(long)(L - 1) * step]);
-        const C dmm = a - C(2) * b + c;
-        const C dm = b - C(2) * c + s0;
-        const C d0 = c - C(2) * s0 + s1;
+        const C dmm = curv(a, b, c);
+        const C dm = curv(b, c, s0);
+        const C d0 = curv(c, s0, s1);
         const C dm4_mm = dm4(dmm, dm);
         const C dm4_m = dm4(dm, d0);
         Fm = sl_mpp5_flux(k, a, b, c, s0, s1, dm4_mm, dm4_m); // face -1/2, donor c_{-1}
@@ -276,8 +386,8 @@ __device__ __forceinline__ C march_line(T *p, long step, int L, const Lim<C> &k)
         dcur = d0;
         dm4m = dm4_m;
     } else {
-        const C dm = s0;               // c_{-2} - 2 c_{-1} + c_0 with zero ghosts
-        const C d0 = s1 - C(2) * s0;   // c_{-1} - 2 c_0 + c_1
+        const C dm = s0;                       // c_{-2} - 2 c_{-1} + c_0 with zero ghosts
+        const C d0 = curv(C(0), s0, s1);       // c_{-1} - 2 c_0 + c_1
         cm2 = C(0);
         cm1 = C(0);
         dcur = d0;
@@ -290,7 +400,7 @@ __device__ __forceinline__ C march_line(T *p, long step, int L, const Lim<C> &k)
 #pragma unroll 4
     for (int i = 0; i < L - 2; ++i) {
         const C cp2 = to_c(p[(long)(i + 2) * step]);
-        const C dn = c0 - C(2) * cp1 + cp2;
+        const C dn = curv(c0, cp1, cp2);
         const C dm4p = dm4(dcur, dn);
         const C F = sl_mpp5_flux(k, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
         const C out = c0 + (Fm - F);
@@ -307,7 +417,7 @@ __device__ __forceinline__ C march_line(T *p, long step, int L, const Lim<C> &k)
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const C cp2 = PERIODIC ? (t == 0 ? s0 : s1) : C(0);
-        const C dn = c0 - C(2) * cp1 + cp2;
+        const C dn = curv(c0, cp1, cp2);
         const C dm4p = dm4(dcur, dn);
         C F = sl_mpp5_flux(k, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
         if (!PERIODIC && t == 1) F = C(0); // outer velocity face

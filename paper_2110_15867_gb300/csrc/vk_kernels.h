@@ -87,6 +87,37 @@ template <typename C> struct StridedArgs {
 };
 
 // ----------------------------------------------------------------------------
+// streamed strided sweep (axes x, y, z, u_x, u_y with |nu| < 1): a block of
+// columns {W inner} x {P outer} walks down the swept axis in chunks of R rows
+// (TMA box {W, R, P}); each consumer thread owns Lane<T>::V columns.
+// ----------------------------------------------------------------------------
+constexpr int kStreamConsumers = 128;
+constexpr int kStreamRows = 4;  // rows per chunk (power of two, >= 3 for the periodic prologue)
+constexpr int kStreamRing = 8;  // chunk slots in the ring (power of two)
+
+template <typename C> struct StreamArgs {
+    int L, W, P, R, stages;
+    int tiles_inner;
+    int periodic;
+    int perm_line; // > 0: group the threads by the sign of u along lines of this length
+    long long n_inner, n_outer;
+    long long num_blocks;
+    long long vstride;
+    int nvel;
+    int coef_mode;
+    long long outer_per_cell;
+    const LineCoefT<C> *cell_coef;
+    unsigned *err;
+    LineCoefT<C> table[kMaxVel];
+};
+
+cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
+                              cudaStream_t st);
+int occupancy_stream(int dtype, int periodic, size_t smem);
+
+// ----------------------------------------------------------------------------
 // contiguous sweep (axis u_z): rows of nuz cells
 // ----------------------------------------------------------------------------
 template <typename C> struct ContigArgs {
@@ -100,6 +131,13 @@ template <typename C> struct ContigArgs {
     unsigned *err;
 };
 
+// u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box
+// {n_uz, 256 rows} with the 64/128-byte swizzle
+bool line_sweep_supported(int nu, long long rows_per_cell);
+size_t line_sweep_smem(int nu);
+int line_sweep_rows_per_tile();
+int occupancy_line_sweep(int nu);
+
 // host launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_strided_f32(const CUtensorMap &map, const StridedArgs<float> &a, int grid,
                                size_t smem, cudaStream_t st);
@@ -112,6 +150,7 @@ cudaError_t launch_contig_f64(const CUtensorMap &map, const ContigArgs<double> &
 // largest resident CTAs per SM for a launcher's kernel with this dynamic smem
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
+cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int grid, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // fields: velocity-sweep coefficients, moment, Poisson

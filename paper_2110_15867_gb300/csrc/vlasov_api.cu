@@ -55,6 +55,14 @@ struct vlasov_ctx {
     int sm_count;
     long long ncell; // spatial cells
     AxisPlan plan[6];
+    AxisPlan splan[5];   // streamed sweeps (|nu| < 1), axes 0..4
+    int perm_line[5];
+    int splan_R[5];
+    // u_z with whole lines in registers
+    bool use_lines;
+    CUtensorMap lmap;
+    long long lrows, ltiles;
+    int lgrid;
     // scratch
     unsigned *d_err;
     void *d_coef[3];
@@ -202,6 +210,70 @@ static int plan_axes(vlasov_ctx *c)
         }
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: cuTensorMapEncodeTiled failed (%d)", ax, int(r));
     }
+    // streamed sweeps: blocks of V * kStreamConsumers columns, chunks of R rows, a ring of S slots
+    const int V = c->g.dtype == VLASOV_F64 ? 1 : 2;
+    const int cols = V * kStreamConsumers;
+    for (int ax = 0; ax < 5; ++ax) {
+        AxisPlan &p = c->splan[ax];
+        p.L = int(d6[ax]);
+        long long I = 1, O = 1;
+        for (int k = ax + 1; k < 6; ++k) I *= d6[k];
+        for (int k = 0; k < ax; ++k) O *= d6[k];
+        p.n_inner = I;
+        p.n_outer = O;
+        int W, P;
+        c->perm_line[ax] = 0;
+        if (ax == 2 && c->g.nuz <= cols) {
+            // the z sweep's Courant number changes sign inside each u_z line: whole lines per block
+            W = (cols / c->g.nuz) * c->g.nuz;
+            P = 1;
+            c->perm_line[ax] = c->g.nuz;
+        } else if (I >= cols) { W = cols; P = 1; }
+        else { W = int(I); P = cols / W; if (P > O) P = int(O); }
+        const int R = kStreamRows;
+        const int S = kStreamRing;
+        p.W = W;
+        p.P = P;
+        p.stages = S;
+        p.tiles_inner = int((I + W - 1) / W);
+        p.num_tiles = (long long)p.tiles_inner * ((O + P - 1) / P);
+        const size_t slot = ((size_t)W * R * P * es + 127) & ~size_t(127);
+        const size_t csz = c->g.dtype == VLASOV_F64 ? sizeof(LineCoefT<double>) : sizeof(LineCoefT<float>);
+        const size_t tab = ax < 3 ? ((csz * (size_t)d6[3 + ax] + 127) & ~size_t(127)) : 0;
+        p.smem = 512 + tab + (size_t)S * slot;
+        p.grid = R; // rows per chunk (kept here; the launch grid is computed below)
+        const cuuint64_t gdim[3] = {(cuuint64_t)I, (cuuint64_t)p.L, (cuuint64_t)O};
+        const cuuint64_t gstr[2] = {(cuuint64_t)(I * es), (cuuint64_t)(I * p.L * es)};
+        const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)R, (cuuint32_t)P};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult r = enc(&p.map, tmap_type(c->g.dtype), 3, c->f, gdim, gstr, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: stream tensor map failed (%d)", ax, int(r));
+        const int occ = occupancy_stream(c->g.dtype == VLASOV_F64 ? 0 : 1, ax < 3, p.smem);
+        if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a streamed CTA does not fit (%zu B)", ax, p.smem);
+        p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
+        c->splan_R[ax] = R;
+    }
+    // u_z: register lines when the line is 64 or 128 bytes of FP32
+    c->use_lines = c->g.dtype == VLASOV_F32 && line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
+    if (c->use_lines) {
+        const int nu = c->g.nuz, rpt = line_sweep_rows_per_tile();
+        c->lrows = c->ncell * c->g.nux * c->g.nuy;
+        c->ltiles = (c->lrows + rpt - 1) / rpt;
+        const cuuint64_t gdim[2] = {(cuuint64_t)nu, (cuuint64_t)c->lrows};
+        const cuuint64_t gstr[1] = {(cuuint64_t)(nu * es)};
+        const cuuint32_t box[2] = {(cuuint32_t)nu, (cuuint32_t)rpt};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&c->lmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->f, gdim, gstr, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               nu * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "u_z line tensor map failed (%d)", int(r));
+        const int occ = occupancy_line_sweep(nu);
+        if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
+        c->lgrid = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
+    }
     return VLASOV_OK;
 }
 
@@ -348,6 +420,15 @@ extern "C" int vlasov_set_stream(vlasov_ctx *c, void *stream)
     return VLASOV_OK;
 }
 
+template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlasov_ctx *c, int ax)
+{
+    const AxisPlan &p = c->splan[ax];
+    A.L = p.L; A.W = p.W; A.P = p.P; A.R = c->splan_R[ax]; A.stages = p.stages;
+    A.tiles_inner = p.tiles_inner; A.periodic = ax < 3; A.perm_line = c->perm_line[ax];
+    A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_blocks = p.num_tiles;
+    A.err = c->d_err;
+}
+
 // position sweep: per-velocity-column constants from nu_j = u_j dt / (a^2 dx)
 static int run_position(vlasov_ctx *c, int ax, double dt, double a)
 {
@@ -358,6 +439,30 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
     const double dx = c->g.L / (&c->g.nx)[ax];
     long long vstride = 1;
     for (int k = ax + 1; k < 3; ++k) vstride *= (&c->g.nux)[k];
+    double numax = 0.0;
+    for (int j = 0; j < nvel; ++j) numax = fmax(numax, fabs((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx)));
+    if (numax < 1.0) {
+        // no whole-cell shift on any line: streamed sweep
+        const AxisPlan &sp = c->splan[ax];
+        cudaError_t e;
+        if (c->g.dtype == VLASOV_F64) {
+            StreamArgs<double> A{};
+            fill_stream_args(A, c, ax);
+            A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
+            for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+            PartTimer t(c, ax, 1);
+            e = launch_stream_f64(sp.map, A, sp.grid, sp.smem, c->stream);
+        } else {
+            StreamArgs<float> A{};
+            fill_stream_args(A, c, ax);
+            A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
+            for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+            PartTimer t(c, ax, 1);
+            e = launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
+        return VLASOV_OK;
+    }
     cudaError_t e;
     if (c->g.dtype == VLASOV_F64) {
         StridedArgs<double> A{};
@@ -390,22 +495,26 @@ static int run_velocity(vlasov_ctx *c, int ax)
     cudaError_t e;
     PartTimer t(c, ax, 1);
     if (ax < 5) {
-        const long long opc = p.n_outer / c->ncell;
+        const AxisPlan &sp = c->splan[ax];
+        const long long opc = sp.n_outer / c->ncell;
         if (c->g.dtype == VLASOV_F64) {
-            StridedArgs<double> A{};
-            A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 0;
-            A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+            StreamArgs<double> A{};
+            fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
-            A.cell_coef = (const LineCoefT<double> *)coef; A.err = c->d_err;
-            e = launch_strided_f64(p.map, A, p.grid, p.smem, c->stream);
+            A.cell_coef = (const LineCoefT<double> *)coef;
+            e = launch_stream_f64(sp.map, A, sp.grid, sp.smem, c->stream);
         } else {
-            StridedArgs<float> A{};
-            A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 0;
-            A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_tiles = p.num_tiles;
+            StreamArgs<float> A{};
+            fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
-            A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
-            e = launch_strided_f32(p.map, A, p.grid, p.smem, c->stream);
+            A.cell_coef = (const LineCoefT<float> *)coef;
+            e = launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
         }
+    } else if (c->use_lines) {
+        ContigArgs<float> A{};
+        A.L = c->g.nuz; A.R = line_sweep_rows_per_tile(); A.stages = 0; A.rows = c->lrows; A.num_tiles = c->ltiles;
+        A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
+        e = launch_line_sweep(c->lmap, A, c->g.nuz, c->lgrid, c->stream);
     } else {
         const long long rpc = (long long)c->g.nux * c->g.nuy;
         if (c->g.dtype == VLASOV_F64) {
