@@ -38,6 +38,9 @@ FALLBACK_HBM_GBS = 6800.0
 
 WORKLOAD = dict(name="fp32_64x32", n=64, nu=32, V=5.0, L=1.0, delta_rms=0.05, cdm_rms=1.0,
                 f_nu=0.03, four_pi_G=1.0, a0=0.5, a1=0.6, sched=10, cfl=(0.5, 0.9), seed=2)
+# Reduced-precision storage: BF16 / FP16 f with one FP32 scale per u_z line on
+# 96^3 x 32^3 cells, the 16^3-parity setup (delta rms 0.01, external phi, CFL 0.7, a = 1).
+LOWPREC = dict(name="lowprec_96x32", n=96, nu=32, V=5.0, delta_rms=0.01, seed=1, cfl=0.7)
 # CPU baseline / reference arm: the oracle on a bounded sample of the same workload:
 # the same 32^3 velocity cube on an 8^3 spatial grid (1.68e7 cells per step).
 SAMPLE = dict(n=8, nu=32)
@@ -52,6 +55,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-lowprec", action="store_true")
     p.add_argument("--profile-case", action="store_true",
                    help="run the small profiling case instead of the benchmark: sweeps on a "
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
@@ -263,6 +267,57 @@ def build_inputs(torch, dev):
     return f, rho_bg
 
 
+def run_lowprec(torch, B, dev, steps, warmup):
+    """Per-sweep rate of Eq. (5) steps with BF16 and FP16 storage (FP32 arithmetic)."""
+    import oracle as O  # only to pick dt: the largest Courant number of the 6 axes is 0.7
+    from paper_2110_15867_gb300 import inputs as I
+    w = LOWPREC
+    n, nu, V = w["n"], w["nu"], w["V"]
+    phi_np = I.fourier_potential(n, seed=w["seed"] + 10).astype(np.float32)
+    g = O.grid(n, nu, V=V)
+    dt = min(w["cfl"] / O.max_abs_nu(g, ax, 1.0, 1.0, phi_np.astype(np.float64)) * (2 if ax >= 3 else 1)
+             for ax in range(6))
+    delta = torch.from_numpy(I.gaussian_field(n, w["delta_rms"], seed=w["seed"])).to(dev)
+    Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
+    phi = torch.from_numpy(phi_np).to(dev)
+    out = {"workload": "%s: %d^3 x %d^3 cells, external phi, 9 sweeps + moment per step" % (w["name"], n, nu),
+           "cells": n ** 3 * nu ** 3}
+    for name, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        codes = torch.empty((n, n, n, nu, nu, nu), dtype=tdt, device=dev)
+        scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device=dev)
+        for ix in range(n):
+            c, s = B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], tdt)
+            codes[ix].copy_(c)
+            scale[ix].copy_(s)
+        v = B.Vlasov(codes, V=V, scale=scale)
+        rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            v.step(dt, 1.0, 1.0, phi, rho_nu=rho)
+        v.status()
+        v.read_timers()
+        v.enable_timers(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            v.step(dt, 1.0, 1.0, phi, rho_nu=rho)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kind_ms, kind_n = v.read_timers()
+        v.status()
+        v.close()
+        cells = codes.numel()
+        alg = 2.0 * cells * 2 + 4.0 * 2 * scale.numel()  # 16-bit read + write, scales read + write
+        out[name] = {"value": 9.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "kernels": {k: {"ms_per_launch": kind_ms[k] / kind_n[k], "launches": kind_n[k],
+                                     "GBs": alg / (kind_ms[k] / kind_n[k] * 1e-3) / 1e9}
+                                 for k in kind_ms if kind_n[k] and k.startswith("sweep_")}}
+        del codes, scale
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2110_15867_gb300 import binding as B
@@ -374,6 +429,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
     v.close()
+    lowprec = None
+    if not args.no_lowprec:
+        lowprec = run_lowprec(torch, B, dev, max(2, min(args.steps, 3)), 2)
+        for k in ("bf16", "f16"):
+            lowprec[k]["vs_fp32"] = lowprec[k]["value"] / (9.0 * cells * args.steps / (ms_total * 1e-3))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -389,6 +449,7 @@ def run_ours(args):
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
             "kernels": per_kind,
             "cpu_baseline": cpu,
+            "lowprec": lowprec,
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": ck,

@@ -195,6 +195,23 @@ def _ptr(t):
     return None if t is None else t.data_ptr()
 
 
+def encode_lines(f, dtype):
+    """Storage of f for the 16-bit codec: one FP32 scale per u_z line (the line's
+    largest value) and the codes f / scale rounded to `dtype` (torch.bfloat16 or
+    torch.float16).  f: 6D torch tensor (any device); returns (codes, scale)."""
+    import torch
+    scale = f.amax(dim=-1).to(torch.float32)
+    inv = torch.where(scale > 0, 1.0 / scale.to(f.dtype), torch.zeros_like(scale, dtype=f.dtype))
+    codes = (f * inv[..., None]).to(dtype)
+    return codes.contiguous(), scale.contiguous()
+
+
+def decode_lines(codes, scale):
+    """Values held by a 16-bit codec array (FP64, same device)."""
+    import torch
+    return codes.to(torch.float64) * scale.to(torch.float64)[..., None]
+
+
 class Vlasov:
     """A libvlasov context over the 6D CUDA tensor ``f`` [nx,ny,nz,nux,nuy,nuz].
 
@@ -202,14 +219,22 @@ class Vlasov:
     Work is queued on the torch stream current at each call.
     """
 
-    def __init__(self, f, L: float = 1.0, V: float = 5.0):
+    def __init__(self, f, L: float = 1.0, V: float = 5.0, scale=None):
         import torch
         if not f.is_cuda or f.dim() != 6 or not f.is_contiguous():
             raise ValueError("f must be a contiguous 6D CUDA tensor")
-        dt = {torch.float64: F64, torch.float32: F32}.get(f.dtype)
+        dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16,
+              torch.float16: F16}.get(f.dtype)
         if dt is None:
-            raise ValueError("f must be float32 or float64")
+            raise ValueError("f must be float64, float32, bfloat16 or float16")
+        if dt in (BF16, F16):
+            if scale is None or scale.dtype != torch.float32 or not scale.is_cuda or \
+                    not scale.is_contiguous() or tuple(scale.shape) != tuple(f.shape[:5]):
+                raise ValueError("16-bit f needs a contiguous float32 CUDA scale of shape f.shape[:5]")
+        elif scale is not None:
+            raise ValueError("scale is only used with 16-bit f")
         self.f = f
+        self.scale = scale
         self.torch = torch
         g = Grid()
         g.nx, g.ny, g.nz, g.nux, g.nuy, g.nuz = f.shape
@@ -218,7 +243,8 @@ class Vlasov:
         self.shape = tuple(f.shape)
         with torch.cuda.device(f.device):
             self._stream = torch.cuda.current_stream(f.device).cuda_stream
-            self.ctx = vlasov_init(g, f.data_ptr(), None, self._stream)
+            self.ctx = vlasov_init(g, f.data_ptr(), None if scale is None else scale.data_ptr(),
+                                   self._stream)
 
     # keep the context on the caller's current stream
     def _sync_stream(self):

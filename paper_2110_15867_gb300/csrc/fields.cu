@@ -8,6 +8,8 @@
 //   * the total mass (compensated FP64);
 //   * the periodic Poisson solve of Eq. (2) by discrete Fourier transform
 //     (the convolution method of Sec. 4.1.2 on one GPU).
+#include <type_traits>
+
 #include "vk_common.cuh"
 
 namespace vk {
@@ -131,6 +133,68 @@ __global__ void __launch_bounds__(256) moment_kernel(GridDims g, const T *__rest
         }
         __syncthreads();
     }
+}
+
+// 16-bit storage: value = code * scale of its u_z line; 16-byte vectors of 8
+// codes never straddle a line (n_uz is a multiple of 8).
+template <typename T>
+__global__ void __launch_bounds__(256) moment_coded_kernel(GridDims g, const T *__restrict__ f,
+                                                           const float *__restrict__ scale, double *rho)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int nuz = g.nu[2];
+    const long long lines = (long long)g.nu[0] * g.nu[1];
+    const long long cube = lines * nuz;
+    const double du3 = (2.0 * g.V / g.nu[0]) * (2.0 * g.V / g.nu[1]) * (2.0 * g.V / g.nu[2]);
+    __shared__ double part[8];
+    const int vshift = nuz == 32 ? 2 : 1; // log2 of the 16-byte vectors per line (n_uz 16 or 32)
+    for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(f + c * cube);
+        const float *sc = scale + c * lines;
+        float s = 0.f, e = 0.f;
+        for (int k = threadIdx.x; k < int(cube / 8); k += blockDim.x) {
+            const uint4 v = q[k];
+            const unsigned u[4] = {v.x, v.y, v.z, v.w};
+            // eight codes of 8 (BF16) or 11 (FP16) significant bits: their FP32 sum is
+            // exact or off by the last bit
+            float t = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 x;
+                if (std::is_same<T, __nv_bfloat16>::value)
+                    x = make_float2(__uint_as_float(u[j] << 16), __uint_as_float(u[j] & 0xffff0000u));
+                else
+                    x = __half22float2(*reinterpret_cast<const __half2 *>(&u[j]));
+                t += x.x + x.y;
+            }
+            // the product and its rounding error (exact, by FMA) both enter the sum
+            const float w = sc[k >> vshift];
+            const float pr = t * w;
+            neumaier(s, e, pr);
+            e += fmaf(t, w, -pr);
+        }
+        double tot = warp_sum_d((double)s + (double)e);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = tot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double r = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += part[w];
+            rho[c] = du3 * r;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_moment_coded(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
+                                cudaStream_t st, int sm_count)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long blocks = ncell < (long long)sm_count * 8 ? ncell : (long long)sm_count * 8;
+    if (dtype == 2)
+        moment_coded_kernel<__nv_bfloat16><<<int(blocks), 256, 0, st>>>(g, (const __nv_bfloat16 *)f, scale, rho);
+    else
+        moment_coded_kernel<__half><<<int(blocks), 256, 0, st>>>(g, (const __half *)f, scale, rho);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *rho, cudaStream_t st,

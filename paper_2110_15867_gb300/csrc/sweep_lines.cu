@@ -20,12 +20,69 @@ constexpr int kLineThreads = 128;           // consumer threads; 2 rows each
 constexpr int kLineRows = 2 * kLineThreads; // rows per tile
 constexpr int kLineRing = 2;                // tile slots
 
-template <int NU> struct LineGeom {
-    static constexpr int rowbytes = NU * 4;
+template <int NU, typename T> struct LineGeom {
+    static constexpr int rowbytes = NU * int(sizeof(T));
     static constexpr int chunks = rowbytes / 16;
+    static constexpr int per = 16 / int(sizeof(T)); // elements per 16-byte chunk
     // swizzled byte offset of 16-byte chunk j of row r
     __device__ static int off(int r, int j) { return r * rowbytes + 16 * (j ^ ((r * rowbytes >> 7) & (chunks - 1))); }
 };
+
+// 16-byte chunk <-> values (times / divided by the line scale for 16-bit codes)
+template <typename T> struct Chunk;
+template <> struct Chunk<float> {
+    __device__ static void get(const unsigned char *p, float s, float (&o)[4])
+    {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    }
+    __device__ static void put(unsigned char *p, float, const float (&o)[4], unsigned &)
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct Chunk<__nv_bfloat16> {
+    __device__ static void get(const unsigned char *p, float s, float (&o)[8])
+    {
+        const uint4 a = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            o[2 * q] = __uint_as_float(w[q] << 16) * s;
+            o[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u) * s;
+        }
+    }
+    // rng: stochastic-rounding stream of the line
+    __device__ static void put(unsigned char *p, float inv, const float (&o)[8], unsigned &rng)
+    {
+        unsigned w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = pack_bf16x2(o[2 * q] * inv, o[2 * q + 1] * inv, sr_pair(rng));
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct Chunk<__half> {
+    __device__ static void get(const unsigned char *p, float s, float (&o)[8])
+    {
+        const uint4 a = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
+            o[2 * q] = f.x * s;
+            o[2 * q + 1] = f.y * s;
+        }
+    }
+    __device__ static void put(unsigned char *p, float inv, const float (&o)[8], unsigned &rng)
+    {
+        unsigned w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = pack_f16x2(o[2 * q] * inv, o[2 * q + 1] * inv, sr_pair(rng));
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+
+#define CODED_RNG_INIT(e, seed) (sizeof(T) == 2 ? sr_bits((e), (seed)) : 0u)
 
 // Advance both lines of the pair (forward local frame; zero-flux faces).
 template <int NU>
@@ -63,44 +120,62 @@ __device__ __forceinline__ float2 march_regs(float2 (&v)[NU], const Lim<float2> 
 }
 
 // Rows r0 and r1 of a swizzled tile: gather (back to front when NEG, the
-// mirror image of a negative Courant number), march, scatter.  Returns true
-// when a line sum is negative, NaN or infinite.
-template <int NU, bool NEG>
-__device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, const Lim<float2> &lim)
+// mirror image of a negative Courant number), march, scatter.  16-bit codes are
+// decoded with the rows' scales s0 / s1 and re-encoded with new scales, the
+// largest updated value of each line (written back through s0 / s1).  Returns
+// true when a line sum is negative, NaN or infinite.
+template <int NU, bool NEG, typename T>
+__device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, const Lim<float2> &lim, float &s0,
+                                          float &s1, unsigned long long e0, unsigned long long e1, unsigned seed)
 {
-    using G_ = LineGeom<NU>;
+    unsigned g0 = CODED_RNG_INIT(e0, seed), g1 = CODED_RNG_INIT(e1, seed);
+    using G_ = LineGeom<NU, T>;
+    constexpr int PER = G_::per;
+    constexpr bool CODED = sizeof(T) == 2;
     float2 v[NU];
 #pragma unroll
     for (int j = 0; j < G_::chunks; ++j) {
-        const float4 a = *reinterpret_cast<const float4 *>(base + G_::off(r0, j));
-        const float4 c = *reinterpret_cast<const float4 *>(base + G_::off(r1, j));
-        const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+        float a[PER], c[PER];
+        Chunk<T>::get(base + G_::off(r0, j), s0, a);
+        Chunk<T>::get(base + G_::off(r1, j), s1, c);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[NEG ? NU - 1 - (4 * j + q) : 4 * j + q] = make_float2(av[q], cv[q]);
+        for (int q = 0; q < PER; ++q) v[NEG ? NU - 1 - (PER * j + q) : PER * j + q] = make_float2(a[q], c[q]);
     }
     const float2 sum = march_regs<NU>(v, lim);
+    float i0 = 1.f, i1 = 1.f;
+    if (CODED) {
+        float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+        for (int l = 0; l < NU; ++l) {
+            m0 = fmaxf(m0, v[l].x);
+            m1 = fmaxf(m1, v[l].y);
+        }
+        s0 = m0;
+        s1 = m1;
+        i0 = m0 > 0.f ? __fdividef(1.f, m0) : 0.f;
+        i1 = m1 > 0.f ? __fdividef(1.f, m1) : 0.f;
+    }
 #pragma unroll
     for (int j = 0; j < G_::chunks; ++j) {
-        float a4[4], c4[4];
+        float a[PER], c[PER];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 x = v[NEG ? NU - 1 - (4 * j + q) : 4 * j + q];
-            a4[q] = x.x;
-            c4[q] = x.y;
+        for (int q = 0; q < PER; ++q) {
+            const float2 x = v[NEG ? NU - 1 - (PER * j + q) : PER * j + q];
+            a[q] = x.x;
+            c[q] = x.y;
         }
-        *reinterpret_cast<float4 *>(base + G_::off(r0, j)) = make_float4(a4[0], a4[1], a4[2], a4[3]);
-        *reinterpret_cast<float4 *>(base + G_::off(r1, j)) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        Chunk<T>::put(base + G_::off(r0, j), i0, a, g0);
+        Chunk<T>::put(base + G_::off(r1, j), i1, c, g1);
     }
     return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
 }
 
-template <int NU>
+template <int NU, typename T>
 __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
     line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ ContigArgs<float> args)
 {
-    using G_ = LineGeom<NU>;
     constexpr int S = kLineRing;
-    constexpr unsigned slot_bytes = kLineRows * NU * 4;
+    constexpr unsigned slot_bytes = kLineRows * NU * sizeof(T);
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *done = full + S;
@@ -166,9 +241,20 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
         if (row0 + r0 < args.rows) {
             const LineCoefT<float> kc = args.cell_coef[(row0 + r0) / args.rows_per_cell];
             if (kc.nd >= 0) {
+                float s0 = 1.f, s1 = 1.f;
+                if (sizeof(T) == 2) {
+                    s0 = args.scale[row0 + r0];
+                    s1 = args.scale[row0 + r1];
+                }
                 // one orientation per spatial cell, so the branch is warp-uniform
-                const bool bad = (kc.nd & 1) ? line_pair<NU, true>(base, r0, r1, to_lim2(kc, kc))
-                                             : line_pair<NU, false>(base, r0, r1, to_lim2(kc, kc));
+                const unsigned long long e0 = (unsigned long long)(row0 + r0) * NU, e1 = (unsigned long long)(row0 + r1) * NU;
+                const bool bad = (kc.nd & 1)
+                                     ? line_pair<NU, true, T>(base, r0, r1, to_lim2(kc, kc), s0, s1, e0, e1, args.seed)
+                                     : line_pair<NU, false, T>(base, r0, r1, to_lim2(kc, kc), s0, s1, e0, e1, args.seed);
+                if (sizeof(T) == 2) {
+                    args.scale[row0 + r0] = s0;
+                    args.scale[row0 + r1] = s1;
+                }
                 if (bad) atomicOr(args.err, ERR_NAN);
             }
         }
@@ -177,32 +263,38 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
     }
 }
 
-template <int NU> static const void *line_kernel_ptr() { return (const void *)line_sweep_kernel<NU>; }
+template <typename T> static const void *line_kernel_ptr(int nu)
+{
+    return nu == 32 ? (const void *)line_sweep_kernel<32, T> : (const void *)line_sweep_kernel<16, T>;
+}
 
-size_t line_sweep_smem(int nu) { return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * 4; }
+static const void *line_kernel_for(int nu, int dtype)
+{
+    return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
+}
+
+size_t line_sweep_smem(int nu, int es) { return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * es; }
 
 bool line_sweep_supported(int nu, long long rows_per_cell)
 {
     return (nu == 16 || nu == 32) && rows_per_cell % kLineRows == 0;
 }
 
-cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int grid, cudaStream_t st)
+cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int dtype, int grid,
+                              cudaStream_t st)
 {
-    const void *k = nu == 32 ? line_kernel_ptr<32>() : line_kernel_ptr<16>();
-    const size_t smem = line_sweep_smem(nu);
+    const void *k = line_kernel_for(nu, dtype);
+    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    if (nu == 32)
-        line_sweep_kernel<32><<<grid, kLineThreads + kProducer, smem, st>>>(map, a);
-    else
-        line_sweep_kernel<16><<<grid, kLineThreads + kProducer, smem, st>>>(map, a);
-    return cudaGetLastError();
+    void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<ContigArgs<float> *>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(kLineThreads + kProducer), args, smem, st);
 }
 
-int occupancy_line_sweep(int nu)
+int occupancy_line_sweep(int nu, int dtype)
 {
-    const void *k = nu == 32 ? line_kernel_ptr<32>() : line_kernel_ptr<16>();
-    const size_t smem = line_sweep_smem(nu);
+    const void *k = line_kernel_for(nu, dtype);
+    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kLineThreads + kProducer, smem) != cudaSuccess) return 0;

@@ -25,31 +25,76 @@
 
 namespace vk {
 
+// Per-thread view of the storage of its column(s): load a row as the compute
+// vector X and store X back.  FP32 / FP64 store f itself.  BF16 / FP16 store
+// f / scale with one FP32 scale per u_z line; row r of the thread's columns
+// belongs to line `base + r * stride` of the scale array.
+struct RowScale {
+    const float *scale;
+    long long base, stride; // u_z line of row r: base + r stride
+    unsigned rng;           // stochastic-rounding stream of this thread's column pair
+    __device__ float at(int r) const { return __ldg(scale + base + (long long)r * stride); }
+};
+
 template <typename T> struct Lane;
 template <> struct Lane<float> {
     using X = float2; // two columns per thread
     static constexpr int V = 2;
-    __device__ static X load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-    __device__ static void store(float *p, X v) { *reinterpret_cast<float2 *>(p) = v; }
+    __device__ static X load(const float *p, const RowScale &, int) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static void store(float *p, X v, RowScale &, int) { *reinterpret_cast<float2 *>(p) = v; }
     __device__ static bool bad(X s) { return !(s.x >= 0.f) || !(s.y >= 0.f) || isinf(s.x) || isinf(s.y); }
 };
 template <> struct Lane<double> {
     using X = double;
     static constexpr int V = 1;
-    __device__ static X load(const double *p) { return *p; }
-    __device__ static void store(double *p, X v) { *p = v; }
+    __device__ static X load(const double *p, const RowScale &, int) { return *p; }
+    __device__ static void store(double *p, X v, RowScale &, int) { *p = v; }
     __device__ static bool bad(X s) { return !(s >= 0.0) || isinf(s); }
 };
+template <> struct Lane<__nv_bfloat16> {
+    using X = float2;
+    static constexpr int V = 2;
+    __device__ static X load(const __nv_bfloat16 *p, const RowScale &sc, int r)
+    {
+        const unsigned u = *reinterpret_cast<const unsigned *>(p);
+        const float s = sc.at(r);
+        // a bf16 is the upper half of an FP32
+        return vmul(make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u)), make_float2(s, s));
+    }
+    // rows are stored in order, so the stream advances once per row
+    __device__ static void store(__nv_bfloat16 *p, X v, RowScale &sc, int r)
+    {
+        const float s = sc.at(r);
+        const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+        *reinterpret_cast<unsigned *>(p) = pack_bf16x2(v.x * inv, v.y * inv, sr_pair(sc.rng));
+    }
+    __device__ static bool bad(X s) { return Lane<float>::bad(s); }
+};
+template <> struct Lane<__half> {
+    using X = float2;
+    static constexpr int V = 2;
+    __device__ static X load(const __half *p, const RowScale &sc, int r)
+    {
+        const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        const float s = sc.at(r);
+        return vmul(h, make_float2(s, s));
+    }
+    __device__ static void store(__half *p, X v, RowScale &sc, int r)
+    {
+        const float s = sc.at(r);
+        const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+        *reinterpret_cast<unsigned *>(p) = pack_f16x2(v.x * inv, v.y * inv, sr_pair(sc.rng));
+    }
+    __device__ static bool bad(X s) { return Lane<float>::bad(s); }
+};
 
-template <typename C> __device__ __forceinline__ Lim<typename Lane<C>::X> pair_lim(const LineCoefT<C> &a, const LineCoefT<C> &b);
-template <> __device__ __forceinline__ Lim<float2> pair_lim<float>(const LineCoefT<float> &a, const LineCoefT<float> &b)
-{
-    return to_lim2(a, b);
-}
-template <> __device__ __forceinline__ Lim<double> pair_lim<double>(const LineCoefT<double> &a, const LineCoefT<double> &)
-{
-    return to_lim(a);
-}
+template <typename C, typename X> struct PairLim;
+template <> struct PairLim<float, float2> {
+    __device__ static Lim<float2> make(const LineCoefT<float> &a, const LineCoefT<float> &b) { return to_lim2(a, b); }
+};
+template <> struct PairLim<double, double> {
+    __device__ static Lim<double> make(const LineCoefT<double> &a, const LineCoefT<double> &) { return to_lim(a); }
+};
 
 // March one block's column(s) down the line in physical row order, reading the
 // rows from the ring (chunk c of the line is ring entry ec + c; a periodic
@@ -58,26 +103,28 @@ template <> __device__ __forceinline__ Lim<double> pair_lim<double>(const LineCo
 // with the mirrored stencil (nu < 0); either way rows are consumed in order and
 // a chunk is released once its last row has been written.  Returns the sum of
 // the new values.
+template <typename T> constexpr int stream_rows() { return sizeof(T) == 2 ? 2 * kStreamRows : kStreamRows; }
+
 template <typename T, bool PERIODIC, bool NEG, typename X, typename SlotPtr, typename Acq, typename Rel>
 __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigned ec, int coff, int L, int W,
-                                          SlotPtr slot_ptr, Acq acquire, Rel release, bool &alive)
+                                          RowScale &rs, SlotPtr slot_ptr, Acq acquire, Rel release, bool &alive)
 {
     using LN = Lane<T>;
-    constexpr int R = kStreamRows;
+    constexpr int R = stream_rows<T>();
     const X zero = splat<X>(0.0);
     auto row_ptr = [&](int r) { return slot_ptr(ec + unsigned(r / R)) + coff + (r % R) * W; };
     X p3 = zero, p2 = zero, p1 = zero; // c_{-3}, c_{-2}, c_{-1}
     if (PERIODIC) {
         if (!acquire(e)) return zero;
         const T *q = slot_ptr(e) + coff;
-        p3 = LN::load(q);
-        p2 = LN::load(q + W);
-        p1 = LN::load(q + 2 * W);
+        p3 = LN::load(q, rs, L - 3);
+        p2 = LN::load(q + W, rs, L - 2);
+        p1 = LN::load(q + 2 * W, rs, L - 1);
         release(e);
     }
     if (!acquire(ec)) return zero; // rows 0..3 lie in chunk 0 (R >= 4)
-    const X s0 = LN::load(row_ptr(0));
-    const X s1 = LN::load(row_ptr(1));
+    const X s0 = LN::load(row_ptr(0), rs, 0);
+    const X s1 = LN::load(row_ptr(1), rs, 1);
     X sum = zero;
     // Rows i whose look-ahead rows i + LA all lie inside the line and whose chunk
     // is complete are marched chunk by chunk with compile-time offsets (chunk c is
@@ -94,12 +141,12 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         cm2 = p2;
         cm1 = p1;
         dcur = d0;
-        auto face = [&](X cp2, T *dst) {
+        auto face = [&](X cp2, T *dst, int row) {
             const X dn = curv(c0, cp1, cp2);
             const X dm4p = dm4(dcur, dn);
             const X F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
             const X out = vadd(c0, vsub(Fm, F));
-            LN::store(dst, out);
+            LN::store(dst, out, rs, row);
             sum = vadd(sum, out);
             cm2 = cm1;
             cm1 = c0;
@@ -116,8 +163,9 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             if (!acquire(ec + unsigned(c + 1))) return zero;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const X cp2 = (q + LA < R) ? LN::load(cur + (q + LA) * W) : LN::load(nxt + (q + LA - R) * W);
-                face(cp2, cur + q * W);
+                const int r = c * R + q + LA;
+                const X cp2 = (q + LA < R) ? LN::load(cur + (q + LA) * W, rs, r) : LN::load(nxt + (q + LA - R) * W, rs, r);
+                face(cp2, cur + q * W, c * R + q);
             }
             release(ec + unsigned(c));
         }
@@ -126,24 +174,24 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             X cp2;
             if (r < L) {
                 if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
-                cp2 = LN::load(row_ptr(r));
+                cp2 = LN::load(row_ptr(r), rs, r);
             } else {
                 cp2 = PERIODIC ? (r == L ? s0 : s1) : zero;
             }
             if (!PERIODIC && i == L - 1) {
                 // outer velocity face: nothing crosses it
                 const X out = vadd(c0, Fm);
-                LN::store(row_ptr(i), out);
+                LN::store(row_ptr(i), out, rs, i);
                 sum = vadd(sum, out);
             } else {
-                face(cp2, row_ptr(i));
+                face(cp2, row_ptr(i), i);
             }
             if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
         }
     } else {
         constexpr int LA = 3;
         // window c_{i-1} .. c_{i+3}, donor c_{i+1}, flux toward -index
-        const X s2 = LN::load(row_ptr(2));
+        const X s2 = LN::load(row_ptr(2), rs, 2);
         const X dmn = curv(p2, p1, s0); // d_{-1}
         const X d0 = curv(p1, s0, s1);
         const X d1 = curv(s0, s1, s2);
@@ -152,12 +200,12 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         if (PERIODIC) Fm = sl_mpp5_flux(lim, s2, s1, s0, p1, p2, dm4a, dm4(dmn, d0));
         else Fm = zero;
         X cm1 = p1, c0 = s0, cp1 = s1, cp2 = s2, d_1 = d1;
-        auto face = [&](X cp3, T *dst) {
+        auto face = [&](X cp3, T *dst, int row) {
             const X d_2 = curv(cp1, cp2, cp3);
             const X dm4b = dm4(d_1, d_2); // face i+3/2
             const X F = sl_mpp5_flux(lim, cp3, cp2, cp1, c0, cm1, dm4b, dm4a);
             const X out = vadd(c0, vsub(F, Fm));
-            LN::store(dst, out);
+            LN::store(dst, out, rs, row);
             sum = vadd(sum, out);
             cm1 = c0;
             c0 = cp1;
@@ -174,8 +222,9 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             if (!acquire(ec + unsigned(c + 1))) return zero;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const X cp3 = (q + LA < R) ? LN::load(cur + (q + LA) * W) : LN::load(nxt + (q + LA - R) * W);
-                face(cp3, cur + q * W);
+                const int r = c * R + q + LA;
+                const X cp3 = (q + LA < R) ? LN::load(cur + (q + LA) * W, rs, r) : LN::load(nxt + (q + LA - R) * W, rs, r);
+                face(cp3, cur + q * W, c * R + q);
             }
             release(ec + unsigned(c));
         }
@@ -184,16 +233,16 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             X cp3;
             if (r < L) {
                 if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
-                cp3 = LN::load(row_ptr(r));
+                cp3 = LN::load(row_ptr(r), rs, r);
             } else {
                 cp3 = PERIODIC ? (r == L ? s0 : (r == L + 1 ? s1 : s2)) : zero;
             }
             if (!PERIODIC && i == L - 1) {
                 const X out = vsub(c0, Fm); // nothing enters through the outer face
-                LN::store(row_ptr(i), out);
+                LN::store(row_ptr(i), out, rs, i);
                 sum = vadd(sum, out);
             } else {
-                face(cp3, row_ptr(i));
+                face(cp3, row_ptr(i), i);
             }
             if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
         }
@@ -212,7 +261,7 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
     constexpr int V = LN::V;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStreamRing;
-    constexpr int R = kStreamRows;
+    constexpr int R = stream_rows<T>();
     const int L = args.L, W = args.W, P = args.P;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *done = full + S;
@@ -342,7 +391,7 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
             }
             if (ka.nd < 0 || kb.nd < 0) work = false; // Courant number out of range: leave as is
             neg = ka.nd & 1;
-            lim = pair_lim<C>(ka, kb);
+            lim = PairLim<C, X>::make(ka, kb);
         }
         const unsigned ec = e + (PERIODIC ? 1u : 0u); // entry of chunk 0
         if (!work) {
@@ -352,11 +401,18 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
             e += E;
             continue;
         }
+        // u_z line of row r: ((outer L + r) I + inner) / n_uz, n_uz divides I
+        RowScale rs{args.scale, 0, 0, 0};
+        if (args.scale) {
+            rs.stride = args.n_inner / args.nuz;
+            rs.base = (outer * L * args.n_inner + inner) / args.nuz;
+            rs.rng = sr_bits((unsigned long long)(outer * L * args.n_inner + inner), args.seed);
+        }
         X sum;
         if (neg)
-            sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, L, W, slot_ptr, acquire, release, alive);
+            sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, L, W, rs, slot_ptr, acquire, release, alive);
         else
-            sum = march_stream<T, PERIODIC, false>(lim, e, ec, coff, L, W, slot_ptr, acquire, release, alive);
+            sum = march_stream<T, PERIODIC, false>(lim, e, ec, coff, L, W, rs, slot_ptr, acquire, release, alive);
         if (!alive) break;
         if (LN::bad(sum)) atomicOr(args.err, ERR_NAN);
         e += unsigned(E);
@@ -386,13 +442,29 @@ cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &
     return launch_stream_t<double>(map, a, grid, smem, st);
 }
 
+cudaError_t launch_stream_bf16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                               cudaStream_t st)
+{
+    return launch_stream_t<__nv_bfloat16>(map, a, grid, smem, st);
+}
+
+cudaError_t launch_stream_f16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                              cudaStream_t st)
+{
+    return launch_stream_t<__half>(map, a, grid, smem, st);
+}
+
+template <typename T> static const void *stream_ptr(int periodic)
+{
+    return periodic ? (const void *)stream_sweep_kernel<T, true> : (const void *)stream_sweep_kernel<T, false>;
+}
+
 int occupancy_stream(int dtype, int periodic, size_t smem)
 {
-    const void *k;
-    if (dtype == 0)
-        k = periodic ? (const void *)stream_sweep_kernel<double, true> : (const void *)stream_sweep_kernel<double, false>;
-    else
-        k = periodic ? (const void *)stream_sweep_kernel<float, true> : (const void *)stream_sweep_kernel<float, false>;
+    const void *k = dtype == 0 ? stream_ptr<double>(periodic)
+                    : dtype == 1 ? stream_ptr<float>(periodic)
+                    : dtype == 2 ? stream_ptr<__nv_bfloat16>(periodic)
+                                 : stream_ptr<__half>(periodic);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStreamConsumers + kProducer, smem) != cudaSuccess)

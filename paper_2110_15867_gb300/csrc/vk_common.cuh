@@ -218,6 +218,75 @@ __device__ __forceinline__ double mn2(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double mx2(double a, double b) { return fmax(a, b); }
 
 // ----------------------------------------------------------------------------
+// 16-bit storage codec: stochastic rounding to BF16 / FP16
+// ----------------------------------------------------------------------------
+// Re-encoding f after every sweep with round-to-nearest drops or biases the
+// small per-sweep updates; stochastic rounding keeps each encode unbiased in
+// expectation.  Random bits: the 32-bit finalizer of MurmurHash3 (Appleby)
+// seeds one stream per line of the march from the element index and a
+// per-sweep seed; the stream then advances with the 32-bit linear congruential
+// generator of Numerical Recipes (a = 1664525, c = 1013904223), whose upper 16
+// bits feed one value each.  A run is reproducible.
+#ifndef VK_SR
+#define VK_SR 1
+#endif
+
+__device__ __forceinline__ unsigned fmix32(unsigned h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ unsigned sr_bits(unsigned long long elem, unsigned seed)
+{
+    return fmix32(unsigned(elem) ^ unsigned(elem >> 32) * 0x9e3779b9u ^ seed * 0x85ebca6bu);
+}
+
+__device__ __forceinline__ unsigned lcg_next(unsigned &x)
+{
+    x = x * 1664525u + 1013904223u;
+    return x;
+}
+
+// 16 random bits in the lower half for the first value, 16 in the upper half for the second
+__device__ __forceinline__ unsigned sr_pair(unsigned &x)
+{
+    const unsigned a = lcg_next(x) >> 16;
+    const unsigned b = lcg_next(x) & 0xffff0000u;
+    return a | b;
+}
+
+// two non-negative FP32 values -> packed bf16x2; rnd supplies 16 random bits per value
+__device__ __forceinline__ unsigned pack_bf16x2(float x, float y, unsigned rnd)
+{
+#if VK_SR
+    const unsigned a = (__float_as_uint(x) + (rnd & 0xffffu)) >> 16;
+    const unsigned b = (__float_as_uint(y) + (rnd >> 16)) >> 16;
+    return a | (b << 16);
+#else
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const unsigned *>(&h);
+#endif
+}
+
+// two non-negative FP32 values -> packed f16x2 (13 random bits below the FP16 mantissa)
+__device__ __forceinline__ unsigned pack_f16x2(float x, float y, unsigned rnd)
+{
+#if VK_SR
+    const float xr = __uint_as_float(__float_as_uint(x) + (rnd & 0x1fffu));
+    const float yr = __uint_as_float(__float_as_uint(y) + ((rnd >> 16) & 0x1fffu));
+    const __half2 h = __halves2half2(__float2half_rz(xr), __float2half_rz(yr));
+#else
+    const __half2 h = __floats2half2_rn(x, y);
+#endif
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+
+// ----------------------------------------------------------------------------
 // arithmetic on float, double and float2 (two independent lines in packed FP32:
 // add / sub / mul / fma use the f32x2 instructions of sm_100+, min / max / select
 // act per component)

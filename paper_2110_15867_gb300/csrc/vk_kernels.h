@@ -108,14 +108,21 @@ template <typename C> struct StreamArgs {
     long long outer_per_cell;
     const LineCoefT<C> *cell_coef;
     unsigned *err;
+    const float *scale; // 16-bit storage: one FP32 scale per u_z line (else null)
+    long long nuz;
+    unsigned seed;      // 16-bit storage: stochastic-rounding stream of this sweep
     LineCoefT<C> table[kMaxVel];
 };
 
+cudaError_t launch_stream_bf16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_stream_f16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
+                              cudaStream_t st);
 cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
                               cudaStream_t st);
 cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
                               cudaStream_t st);
-int occupancy_stream(int dtype, int periodic, size_t smem);
+int occupancy_stream(int dtype, int periodic, size_t smem); // dtype: 0 f64, 1 f32, 2 bf16, 3 f16
 
 // ----------------------------------------------------------------------------
 // contiguous sweep (axis u_z): rows of nuz cells
@@ -129,14 +136,16 @@ template <typename C> struct ContigArgs {
     long long rows_per_cell;
     const LineCoefT<C> *cell_coef;
     unsigned *err;
+    float *scale; // 16-bit storage: one FP32 scale per row (u_z line), updated in place
+    unsigned seed;
 };
 
 // u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box
 // {n_uz, 256 rows} with the 64/128-byte swizzle
 bool line_sweep_supported(int nu, long long rows_per_cell);
-size_t line_sweep_smem(int nu);
+size_t line_sweep_smem(int nu, int es);
 int line_sweep_rows_per_tile();
-int occupancy_line_sweep(int nu);
+int occupancy_line_sweep(int nu, int dtype); // dtype: 1 f32, 2 bf16, 3 f16
 
 // host launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_strided_f32(const CUtensorMap &map, const StridedArgs<float> &a, int grid,
@@ -150,7 +159,8 @@ cudaError_t launch_contig_f64(const CUtensorMap &map, const ContigArgs<double> &
 // largest resident CTAs per SM for a launcher's kernel with this dynamic smem
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
-cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int grid, cudaStream_t st);
+cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int dtype, int grid,
+                              cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // fields: velocity-sweep coefficients, moment, Poisson
@@ -169,6 +179,9 @@ cudaError_t launch_velocity_coef(const GridDims &g, const float *phi, double dt,
 
 cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *rho, cudaStream_t st,
                           int sm_count);
+// 16-bit storage (dtype 2 bf16, 3 f16) with one scale per u_z line
+cudaError_t launch_moment_coded(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
+                                cudaStream_t st, int sm_count);
 // mass = dx dy dz * sum rho (FP64, compensated) written to out (device)
 cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st);
 

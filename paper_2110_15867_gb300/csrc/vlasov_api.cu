@@ -50,6 +50,7 @@ struct vlasov_ctx {
     vlasov_grid g;
     GridDims gd;
     void *f;
+    float *scale; // 16-bit storage: FP32 scale per u_z line (caller-owned)
     cudaStream_t stream;
     size_t es;
     int sm_count;
@@ -70,6 +71,7 @@ struct vlasov_ctx {
     double *d_mass;
     PoissonScratch ps;
     char msg[256];
+    unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
     // per-part timers
     bool timers_on;
     struct Pending { int kind; cudaEvent_t a, b; };
@@ -146,7 +148,9 @@ static int plan_axes(vlasov_ctx *c)
     const long long d6[6] = {c->g.nx, c->g.ny, c->g.nz, c->g.nux, c->g.nuy, c->g.nuz};
     const size_t es = c->es;
     const size_t kSmemBudget = 200 * 1024;
-    for (int ax = 0; ax < 6; ++ax) {
+    const bool coded = c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16;
+    // whole-line kernels (whole-cell shifts, u_z lines of other lengths): FP32 / FP64 only
+    for (int ax = 0; ax < 6 && !coded; ++ax) {
         AxisPlan &p = c->plan[ax];
         p.L = int(d6[ax]);
         long long I = 1, O = 1;
@@ -211,7 +215,7 @@ static int plan_axes(vlasov_ctx *c)
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: cuTensorMapEncodeTiled failed (%d)", ax, int(r));
     }
     // streamed sweeps: blocks of V * kStreamConsumers columns, chunks of R rows, a ring of S slots
-    const int V = c->g.dtype == VLASOV_F64 ? 1 : 2;
+    const int V = c->g.dtype == VLASOV_F64 ? 1 : 2; // columns per consumer thread
     const int cols = V * kStreamConsumers;
     for (int ax = 0; ax < 5; ++ax) {
         AxisPlan &p = c->splan[ax];
@@ -230,7 +234,7 @@ static int plan_axes(vlasov_ctx *c)
             c->perm_line[ax] = c->g.nuz;
         } else if (I >= cols) { W = cols; P = 1; }
         else { W = int(I); P = cols / W; if (P > O) P = int(O); }
-        const int R = kStreamRows;
+        const int R = coded ? 2 * kStreamRows : kStreamRows; // the kernels' stream_rows<T>()
         const int S = kStreamRing;
         p.W = W;
         p.P = P;
@@ -250,13 +254,13 @@ static int plan_axes(vlasov_ctx *c)
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: stream tensor map failed (%d)", ax, int(r));
-        const int occ = occupancy_stream(c->g.dtype == VLASOV_F64 ? 0 : 1, ax < 3, p.smem);
+        const int occ = occupancy_stream(c->g.dtype, ax < 3, p.smem);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a streamed CTA does not fit (%zu B)", ax, p.smem);
         p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
         c->splan_R[ax] = R;
     }
-    // u_z: register lines when the line is 64 or 128 bytes of FP32
-    c->use_lines = c->g.dtype == VLASOV_F32 && line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
+    // u_z: register lines when a line is 32, 64 or 128 bytes (FP32 / 16-bit, n_uz 16 or 32)
+    c->use_lines = c->g.dtype != VLASOV_F64 && line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
     if (c->use_lines) {
         const int nu = c->g.nuz, rpt = line_sweep_rows_per_tile();
         c->lrows = c->ncell * c->g.nux * c->g.nuy;
@@ -265,12 +269,15 @@ static int plan_axes(vlasov_ctx *c)
         const cuuint64_t gstr[1] = {(cuuint64_t)(nu * es)};
         const cuuint32_t box[2] = {(cuuint32_t)nu, (cuuint32_t)rpt};
         const cuuint32_t estr[2] = {1, 1};
-        const CUresult r = enc(&c->lmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->f, gdim, gstr, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               nu * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const size_t rowbytes = nu * es;
+        const CUtensorMapSwizzle sw = rowbytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                      : rowbytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                       : CU_TENSOR_MAP_SWIZZLE_32B;
+        const CUresult r = enc(&c->lmap, tmap_type(c->g.dtype), 2, c->f, gdim, gstr, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "u_z line tensor map failed (%d)", int(r));
-        const int occ = occupancy_line_sweep(nu);
+        const int occ = occupancy_line_sweep(nu, c->g.dtype);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
         c->lgrid = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
     }
@@ -299,9 +306,15 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
         if (dims[k] < 4 || dims[k] > kMaxVel || dims[k] % 4)
             return fail(nullptr, VLASOV_EINVAL, "velocity size %d must be a multiple of 4 in [4, %d]", dims[k], kMaxVel);
     if (!(g->L > 0) || !(g->V > 0)) return fail(nullptr, VLASOV_EINVAL, "L and V must be positive");
-    if (g->dtype != VLASOV_F32 && g->dtype != VLASOV_F64)
-        return fail(nullptr, VLASOV_EINVAL, "dtype %d is not supported by this build", g->dtype);
-    if (scale_dev) return fail(nullptr, VLASOV_EINVAL, "scale_dev must be NULL for FP32/FP64 storage");
+    if (g->dtype < VLASOV_F64 || g->dtype > VLASOV_F16) return fail(nullptr, VLASOV_EINVAL, "unknown dtype %d", g->dtype);
+    const bool coded = g->dtype == VLASOV_BF16 || g->dtype == VLASOV_F16;
+    if (!coded && scale_dev) return fail(nullptr, VLASOV_EINVAL, "scale_dev must be NULL for FP32/FP64 storage");
+    if (coded) {
+        if (!scale_dev || reinterpret_cast<uintptr_t>(scale_dev) % 16)
+            return fail(nullptr, VLASOV_EINVAL, "16-bit storage needs a 16-byte aligned scale_dev");
+        if (!line_sweep_supported(g->nuz, (long long)g->nux * g->nuy))
+            return fail(nullptr, VLASOV_EINVAL, "16-bit storage needs nuz = 16 or 32 and nux * nuy a multiple of 256");
+    }
     if (reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(nullptr, VLASOV_EINVAL, "f_dev must be 16-byte aligned");
     const long long ncell = (long long)g->nx * g->ny * g->nz;
     const long long cube = (long long)g->nux * g->nuy * g->nuz;
@@ -312,8 +325,9 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     if (!c) return fail(nullptr, VLASOV_ENOMEM, "out of host memory");
     c->g = *g;
     c->f = f_dev;
+    c->scale = coded ? scale_dev : nullptr;
     c->stream = (cudaStream_t)stream;
-    c->es = g->dtype == VLASOV_F64 ? 8 : 4;
+    c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
     c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
@@ -427,11 +441,25 @@ template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlaso
     A.tiles_inner = p.tiles_inner; A.periodic = ax < 3; A.perm_line = c->perm_line[ax];
     A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_blocks = p.num_tiles;
     A.err = c->d_err;
+    A.scale = c->scale;
+    A.nuz = c->g.nuz;
+    A.seed = c->sweeps;
+}
+
+// streamed launch for the storage type of c (the arguments use FP32 constants unless FP64)
+static cudaError_t launch_stream_any(const vlasov_ctx *c, const AxisPlan &sp, const StreamArgs<float> &A)
+{
+    switch (c->g.dtype) {
+    case VLASOV_BF16: return launch_stream_bf16(sp.map, A, sp.grid, sp.smem, c->stream);
+    case VLASOV_F16: return launch_stream_f16(sp.map, A, sp.grid, sp.smem, c->stream);
+    default: return launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
+    }
 }
 
 // position sweep: per-velocity-column constants from nu_j = u_j dt / (a^2 dx)
 static int run_position(vlasov_ctx *c, int ax, double dt, double a)
 {
+    ++c->sweeps;
     if (!(a > 0) || !isfinite(dt) || !isfinite(a)) return fail(c, VLASOV_EINVAL, "sweep %d: need finite dt and a > 0", ax);
     const AxisPlan &p = c->plan[ax];
     const int nvel = (&c->g.nux)[ax];
@@ -458,11 +486,13 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
             PartTimer t(c, ax, 1);
-            e = launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
+            e = launch_stream_any(c, sp, A);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
         return VLASOV_OK;
     }
+    if (c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16)
+        return fail(c, VLASOV_EINVAL, "sweep %d: |nu| = %.3g >= 1 needs FP32 or FP64 storage", ax, numax);
     cudaError_t e;
     if (c->g.dtype == VLASOV_F64) {
         StridedArgs<double> A{};
@@ -490,6 +520,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
 // velocity sweep with the per-cell constants already in d_coef[ax - 3]
 static int run_velocity(vlasov_ctx *c, int ax)
 {
+    ++c->sweeps;
     const AxisPlan &p = c->plan[ax];
     const void *coef = c->d_coef[ax - 3];
     cudaError_t e;
@@ -508,13 +539,15 @@ static int run_velocity(vlasov_ctx *c, int ax)
             fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
             A.cell_coef = (const LineCoefT<float> *)coef;
-            e = launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
+            e = launch_stream_any(c, sp, A);
         }
     } else if (c->use_lines) {
         ContigArgs<float> A{};
         A.L = c->g.nuz; A.R = line_sweep_rows_per_tile(); A.stages = 0; A.rows = c->lrows; A.num_tiles = c->ltiles;
         A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
-        e = launch_line_sweep(c->lmap, A, c->g.nuz, c->lgrid, c->stream);
+        A.scale = c->scale;
+        A.seed = c->sweeps;
+        e = launch_line_sweep(c->lmap, A, c->g.nuz, c->g.dtype, c->lgrid, c->stream);
     } else {
         const long long rpc = (long long)c->g.nux * c->g.nuy;
         if (c->g.dtype == VLASOV_F64) {
@@ -561,7 +594,10 @@ extern "C" int vlasov_moment(vlasov_ctx *c, double *rho_dev, double *mass_host)
     cudaError_t e;
     {
         PartTimer t(c, VLASOV_T_MOMENT, 1);
-        e = launch_moment(c->gd, c->f, c->g.dtype == VLASOV_F64 ? 0 : 1, rho_dev, c->stream, c->sm_count);
+        if (c->scale)
+            e = launch_moment_coded(c->gd, c->f, c->scale, c->g.dtype, rho_dev, c->stream, c->sm_count);
+        else
+            e = launch_moment(c->gd, c->f, c->g.dtype == VLASOV_F64 ? 0 : 1, rho_dev, c->stream, c->sm_count);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
     if (mass_host) {
