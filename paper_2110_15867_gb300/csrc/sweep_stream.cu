@@ -27,63 +27,56 @@ namespace vk {
 
 // Per-thread view of the storage of its column(s): load a row as the compute
 // vector X and store X back.  FP32 / FP64 store f itself.  BF16 / FP16 store
-// f / scale with one FP32 scale per u_z line; row r of the thread's columns
-// belongs to line `base + r * stride` of the scale array.
-struct RowScale {
-    const float *scale;
-    long long base, stride; // u_z line of row r: base + r stride
-    unsigned rng;           // stochastic-rounding stream of this thread's column pair
-    __device__ float at(int r) const { return __ldg(scale + base + (long long)r * stride); }
-};
-
+// f / scale with one FP32 scale per u_z line; the scale of the row comes from
+// shared memory (staged by TMA with the chunk), `sp` points at it.
 template <typename T> struct Lane;
 template <> struct Lane<float> {
     using X = float2; // two columns per thread
     static constexpr int V = 2;
-    __device__ static X load(const float *p, const RowScale &, int) { return *reinterpret_cast<const float2 *>(p); }
-    __device__ static void store(float *p, X v, RowScale &, int) { *reinterpret_cast<float2 *>(p) = v; }
+    __device__ static X load(const float *p, const float *) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static void store(float *p, X v, const float *, unsigned &) { *reinterpret_cast<float2 *>(p) = v; }
     __device__ static bool bad(X s) { return !(s.x >= 0.f) || !(s.y >= 0.f) || isinf(s.x) || isinf(s.y); }
 };
 template <> struct Lane<double> {
     using X = double;
     static constexpr int V = 1;
-    __device__ static X load(const double *p, const RowScale &, int) { return *p; }
-    __device__ static void store(double *p, X v, RowScale &, int) { *p = v; }
+    __device__ static X load(const double *p, const float *) { return *p; }
+    __device__ static void store(double *p, X v, const float *, unsigned &) { *p = v; }
     __device__ static bool bad(X s) { return !(s >= 0.0) || isinf(s); }
 };
 template <> struct Lane<__nv_bfloat16> {
     using X = float2;
     static constexpr int V = 2;
-    __device__ static X load(const __nv_bfloat16 *p, const RowScale &sc, int r)
+    __device__ static X load(const __nv_bfloat16 *p, const float *sp)
     {
         const unsigned u = *reinterpret_cast<const unsigned *>(p);
-        const float s = sc.at(r);
+        const float s = *sp;
         // a bf16 is the upper half of an FP32
         return vmul(make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u)), make_float2(s, s));
     }
-    // rows are stored in order, so the stream advances once per row
-    __device__ static void store(__nv_bfloat16 *p, X v, RowScale &sc, int r)
+    // rows are stored in order, so the rounding stream advances once per row
+    __device__ static void store(__nv_bfloat16 *p, X v, const float *sp, unsigned &rng)
     {
-        const float s = sc.at(r);
+        const float s = *sp;
         const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
-        *reinterpret_cast<unsigned *>(p) = pack_bf16x2(v.x * inv, v.y * inv, sr_pair(sc.rng));
+        *reinterpret_cast<unsigned *>(p) = pack_bf16x2(v.x * inv, v.y * inv, sr_pair(rng));
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };
 template <> struct Lane<__half> {
     using X = float2;
     static constexpr int V = 2;
-    __device__ static X load(const __half *p, const RowScale &sc, int r)
+    __device__ static X load(const __half *p, const float *sp)
     {
         const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(p));
-        const float s = sc.at(r);
+        const float s = *sp;
         return vmul(h, make_float2(s, s));
     }
-    __device__ static void store(__half *p, X v, RowScale &sc, int r)
+    __device__ static void store(__half *p, X v, const float *sp, unsigned &rng)
     {
-        const float s = sc.at(r);
+        const float s = *sp;
         const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
-        *reinterpret_cast<unsigned *>(p) = pack_f16x2(v.x * inv, v.y * inv, sr_pair(sc.rng));
+        *reinterpret_cast<unsigned *>(p) = pack_f16x2(v.x * inv, v.y * inv, sr_pair(rng));
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };
@@ -103,28 +96,32 @@ template <> struct PairLim<double, double> {
 // with the mirrored stencil (nu < 0); either way rows are consumed in order and
 // a chunk is released once its last row has been written.  Returns the sum of
 // the new values.
-template <typename T> constexpr int stream_rows() { return sizeof(T) == 2 ? 2 * kStreamRows : kStreamRows; }
+template <typename T> __host__ __device__ constexpr int stream_rows() { return sizeof(T) == 2 ? 2 * kStreamRows : kStreamRows; }
 
-template <typename T, bool PERIODIC, bool NEG, typename X, typename SlotPtr, typename Acq, typename Rel>
-__device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigned ec, int coff, int L, int W,
-                                          RowScale &rs, SlotPtr slot_ptr, Acq acquire, Rel release, bool &alive)
+template <typename T, bool PERIODIC, bool NEG, typename X, typename SlotPtr, typename ScalePtr, typename Acq,
+          typename Rel>
+__device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigned ec, int coff, int soff, int L, int W,
+                                          int Wl, unsigned &rng, SlotPtr slot_ptr, ScalePtr scale_ptr, Acq acquire,
+                                          Rel release, bool &alive)
 {
     using LN = Lane<T>;
     constexpr int R = stream_rows<T>();
     const X zero = splat<X>(0.0);
     auto row_ptr = [&](int r) { return slot_ptr(ec + unsigned(r / R)) + coff + (r % R) * W; };
+    auto srow_ptr = [&](int r) { return scale_ptr(ec + unsigned(r / R)) + soff + (r % R) * Wl; };
     X p3 = zero, p2 = zero, p1 = zero; // c_{-3}, c_{-2}, c_{-1}
     if (PERIODIC) {
         if (!acquire(e)) return zero;
         const T *q = slot_ptr(e) + coff;
-        p3 = LN::load(q, rs, L - 3);
-        p2 = LN::load(q + W, rs, L - 2);
-        p1 = LN::load(q + 2 * W, rs, L - 1);
+        const float *qs = scale_ptr(e) + soff;
+        p3 = LN::load(q, qs);
+        p2 = LN::load(q + W, qs + Wl);
+        p1 = LN::load(q + 2 * W, qs + 2 * Wl);
         release(e);
     }
     if (!acquire(ec)) return zero; // rows 0..3 lie in chunk 0 (R >= 4)
-    const X s0 = LN::load(row_ptr(0), rs, 0);
-    const X s1 = LN::load(row_ptr(1), rs, 1);
+    const X s0 = LN::load(row_ptr(0), srow_ptr(0));
+    const X s1 = LN::load(row_ptr(1), srow_ptr(1));
     X sum = zero;
     // Rows i whose look-ahead rows i + LA all lie inside the line and whose chunk
     // is complete are marched chunk by chunk with compile-time offsets (chunk c is
@@ -141,12 +138,12 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         cm2 = p2;
         cm1 = p1;
         dcur = d0;
-        auto face = [&](X cp2, T *dst, int row) {
+        auto face = [&](X cp2, T *dst, const float *dsc) {
             const X dn = curv(c0, cp1, cp2);
             const X dm4p = dm4(dcur, dn);
             const X F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
             const X out = vadd(c0, vsub(Fm, F));
-            LN::store(dst, out, rs, row);
+            LN::store(dst, out, dsc, rng);
             sum = vadd(sum, out);
             cm2 = cm1;
             cm1 = c0;
@@ -160,12 +157,14 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         for (int c = 0; c < nsimple; ++c) {
             T *cur = slot_ptr(ec + unsigned(c)) + coff;
             T *nxt = slot_ptr(ec + unsigned(c + 1)) + coff;
+            const float *scur = scale_ptr(ec + unsigned(c)) + soff;
+            const float *snxt = scale_ptr(ec + unsigned(c + 1)) + soff;
             if (!acquire(ec + unsigned(c + 1))) return zero;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const int r = c * R + q + LA;
-                const X cp2 = (q + LA < R) ? LN::load(cur + (q + LA) * W, rs, r) : LN::load(nxt + (q + LA - R) * W, rs, r);
-                face(cp2, cur + q * W, c * R + q);
+                const X cp2 = (q + LA < R) ? LN::load(cur + (q + LA) * W, scur + (q + LA) * Wl)
+                                          : LN::load(nxt + (q + LA - R) * W, snxt + (q + LA - R) * Wl);
+                face(cp2, cur + q * W, scur + q * Wl);
             }
             release(ec + unsigned(c));
         }
@@ -174,24 +173,24 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             X cp2;
             if (r < L) {
                 if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
-                cp2 = LN::load(row_ptr(r), rs, r);
+                cp2 = LN::load(row_ptr(r), srow_ptr(r));
             } else {
                 cp2 = PERIODIC ? (r == L ? s0 : s1) : zero;
             }
             if (!PERIODIC && i == L - 1) {
                 // outer velocity face: nothing crosses it
                 const X out = vadd(c0, Fm);
-                LN::store(row_ptr(i), out, rs, i);
+                LN::store(row_ptr(i), out, srow_ptr(i), rng);
                 sum = vadd(sum, out);
             } else {
-                face(cp2, row_ptr(i), i);
+                face(cp2, row_ptr(i), srow_ptr(i));
             }
             if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
         }
     } else {
         constexpr int LA = 3;
         // window c_{i-1} .. c_{i+3}, donor c_{i+1}, flux toward -index
-        const X s2 = LN::load(row_ptr(2), rs, 2);
+        const X s2 = LN::load(row_ptr(2), srow_ptr(2));
         const X dmn = curv(p2, p1, s0); // d_{-1}
         const X d0 = curv(p1, s0, s1);
         const X d1 = curv(s0, s1, s2);
@@ -200,12 +199,12 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         if (PERIODIC) Fm = sl_mpp5_flux(lim, s2, s1, s0, p1, p2, dm4a, dm4(dmn, d0));
         else Fm = zero;
         X cm1 = p1, c0 = s0, cp1 = s1, cp2 = s2, d_1 = d1;
-        auto face = [&](X cp3, T *dst, int row) {
+        auto face = [&](X cp3, T *dst, const float *dsc) {
             const X d_2 = curv(cp1, cp2, cp3);
             const X dm4b = dm4(d_1, d_2); // face i+3/2
             const X F = sl_mpp5_flux(lim, cp3, cp2, cp1, c0, cm1, dm4b, dm4a);
             const X out = vadd(c0, vsub(F, Fm));
-            LN::store(dst, out, rs, row);
+            LN::store(dst, out, dsc, rng);
             sum = vadd(sum, out);
             cm1 = c0;
             c0 = cp1;
@@ -219,12 +218,14 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
         for (int c = 0; c < nsimple; ++c) {
             T *cur = slot_ptr(ec + unsigned(c)) + coff;
             T *nxt = slot_ptr(ec + unsigned(c + 1)) + coff;
+            const float *scur = scale_ptr(ec + unsigned(c)) + soff;
+            const float *snxt = scale_ptr(ec + unsigned(c + 1)) + soff;
             if (!acquire(ec + unsigned(c + 1))) return zero;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const int r = c * R + q + LA;
-                const X cp3 = (q + LA < R) ? LN::load(cur + (q + LA) * W, rs, r) : LN::load(nxt + (q + LA - R) * W, rs, r);
-                face(cp3, cur + q * W, c * R + q);
+                const X cp3 = (q + LA < R) ? LN::load(cur + (q + LA) * W, scur + (q + LA) * Wl)
+                                          : LN::load(nxt + (q + LA - R) * W, snxt + (q + LA - R) * Wl);
+                face(cp3, cur + q * W, scur + q * Wl);
             }
             release(ec + unsigned(c));
         }
@@ -233,16 +234,16 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
             X cp3;
             if (r < L) {
                 if (r % R == 0 && !acquire(ec + unsigned(r / R))) return zero;
-                cp3 = LN::load(row_ptr(r), rs, r);
+                cp3 = LN::load(row_ptr(r), srow_ptr(r));
             } else {
                 cp3 = PERIODIC ? (r == L ? s0 : (r == L + 1 ? s1 : s2)) : zero;
             }
             if (!PERIODIC && i == L - 1) {
                 const X out = vsub(c0, Fm); // nothing enters through the outer face
-                LN::store(row_ptr(i), out, rs, i);
+                LN::store(row_ptr(i), out, srow_ptr(i), rng);
                 sum = vadd(sum, out);
             } else {
-                face(cp3, row_ptr(i), i);
+                face(cp3, row_ptr(i), srow_ptr(i));
             }
             if (i % R == R - 1 || i == L - 1) release(ec + unsigned(i / R));
         }
@@ -252,9 +253,10 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
 
 template <typename T, bool PERIODIC>
 __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
-    stream_sweep_kernel(const __grid_constant__ CUtensorMap map,
+    stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
 {
+    constexpr bool CODED = sizeof(T) == 2;
     using C = typename Compute<T>::type;
     using LN = Lane<T>;
     using X = typename LN::X;
@@ -270,9 +272,16 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
     const size_t tab_bytes = (args.coef_mode == 0) ? ((sizeof(LineCoefT<C>) * args.nvel + 127) & ~size_t(127)) : 0;
     unsigned char *ring = smem + 512 + tab_bytes;
     const int slot_elems = W * R * P;
-    const unsigned slot_bytes = unsigned(slot_elems * sizeof(T));
-    const unsigned slot_pitch = (slot_bytes + 127u) & ~127u;
+    const unsigned code_bytes = unsigned(slot_elems * sizeof(T));
+    const unsigned slot_pitch = (code_bytes + 127u) & ~127u;
     auto slot_ptr = [&](unsigned e) { return reinterpret_cast<T *>(ring + slot_pitch * (e & (S - 1))); };
+    // 16-bit storage: the scales of the chunk's u_z lines, box {Wl, R, P} (Wl = W / n_uz)
+    const int Wl = CODED ? W / int(args.nuz) : 0;
+    const unsigned scale_bytes = CODED ? unsigned(Wl * R * P * 4) : 0u;
+    const unsigned scale_pitch = (scale_bytes + 127u) & ~127u;
+    unsigned char *sring = ring + size_t(slot_pitch) * S;
+    auto scale_ptr = [&](unsigned e) { return reinterpret_cast<float *>(sring + scale_pitch * (e & (S - 1))); };
+    const unsigned slot_bytes = code_bytes + scale_bytes; // transaction bytes of one entry
     const int nC = (L + R - 1) / R;                // chunks per line
     const int E = nC + (PERIODIC ? 1 : 0);         // ring entries per block
 
@@ -324,6 +333,12 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
                 meta[st] = make_int4(c0, c1, c2, ch >= 0);
                 mbar_arrive_expect_tx(&full[st], slot_bytes);
                 tma_load_3d(slot_ptr(loaded), &map, &full[st], c0, c1, c2);
+                if (CODED) {
+                    if (args.scale_rank == 3)
+                        tma_load_3d(scale_ptr(loaded), &smap, &full[st], c0 / int(args.nuz), c1, c2);
+                    else
+                        tma_load_2d(scale_ptr(loaded), &smap, &full[st], c1, c2);
+                }
                 ++loaded;
                 if (++j == E) { j = 0; ++k; }
                 progress = true;
@@ -401,18 +416,16 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
             e += E;
             continue;
         }
-        // u_z line of row r: ((outer L + r) I + inner) / n_uz, n_uz divides I
-        RowScale rs{args.scale, 0, 0, 0};
-        if (args.scale) {
-            rs.stride = args.n_inner / args.nuz;
-            rs.base = (outer * L * args.n_inner + inner) / args.nuz;
-            rs.rng = sr_bits((unsigned long long)(outer * L * args.n_inner + inner), args.seed);
-        }
+        // 16-bit storage: a rounding stream per column pair and block, from the element index
+        unsigned rng = CODED ? sr_bits((unsigned long long)(outer * L * args.n_inner + inner), args.seed) : 0u;
+        const int soff = CODED ? (p * R * Wl + w / int(args.nuz)) : 0; // this column's line in a scale slot
         X sum;
         if (neg)
-            sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, L, W, rs, slot_ptr, acquire, release, alive);
+            sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, soff, L, W, Wl, rng, slot_ptr, scale_ptr, acquire,
+                                                  release, alive);
         else
-            sum = march_stream<T, PERIODIC, false>(lim, e, ec, coff, L, W, rs, slot_ptr, acquire, release, alive);
+            sum = march_stream<T, PERIODIC, false>(lim, e, ec, coff, soff, L, W, Wl, rng, slot_ptr, scale_ptr, acquire,
+                                                   release, alive);
         if (!alive) break;
         if (LN::bad(sum)) atomicOr(args.err, ERR_NAN);
         e += unsigned(E);
@@ -420,38 +433,38 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
 }
 
 template <typename T>
-static cudaError_t launch_stream_t(const CUtensorMap &map, const StreamArgs<typename Compute<T>::type> &a, int grid,
-                                   size_t smem, cudaStream_t st)
+static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &smap,
+                                   const StreamArgs<typename Compute<T>::type> &a, int grid, size_t smem, cudaStream_t st)
 {
     auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, a);
+    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, smap, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
                               cudaStream_t st)
 {
-    return launch_stream_t<float>(map, a, grid, smem, st);
+    return launch_stream_t<float>(map, map, a, grid, smem, st);
 }
 
 cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
                               cudaStream_t st)
 {
-    return launch_stream_t<double>(map, a, grid, smem, st);
+    return launch_stream_t<double>(map, map, a, grid, smem, st);
 }
 
-cudaError_t launch_stream_bf16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                               cudaStream_t st)
+cudaError_t launch_stream_bf16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
+                               size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<__nv_bfloat16>(map, a, grid, smem, st);
+    return launch_stream_t<__nv_bfloat16>(map, smap, a, grid, smem, st);
 }
 
-cudaError_t launch_stream_f16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                              cudaStream_t st)
+cudaError_t launch_stream_f16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
+                              size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<__half>(map, a, grid, smem, st);
+    return launch_stream_t<__half>(map, smap, a, grid, smem, st);
 }
 
 template <typename T> static const void *stream_ptr(int periodic)

@@ -111,13 +111,15 @@ template <typename C> struct StreamArgs {
     const float *scale; // 16-bit storage: one FP32 scale per u_z line (else null)
     long long nuz;
     unsigned seed;      // 16-bit storage: stochastic-rounding stream of this sweep
+    int scale_rank;     // 16-bit storage: rank of the scale tensor map (3, or 2 for the u_y sweep)
     LineCoefT<C> table[kMaxVel];
 };
 
-cudaError_t launch_stream_bf16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                               cudaStream_t st);
-cudaError_t launch_stream_f16(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                              cudaStream_t st);
+// 16-bit storage: smap views the scale array like map views f, with the u_z line collapsed
+cudaError_t launch_stream_bf16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
+                               size_t smem, cudaStream_t st);
+cudaError_t launch_stream_f16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
+                              size_t smem, cudaStream_t st);
 cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
                               cudaStream_t st);
 cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,

@@ -59,6 +59,8 @@ struct vlasov_ctx {
     AxisPlan splan[5];   // streamed sweeps (|nu| < 1), axes 0..4
     int perm_line[5];
     int splan_R[5];
+    CUtensorMap smap[5]; // 16-bit storage: scale array seen like f, the u_z line collapsed
+    int scale_rank[5];
     // u_z with whole lines in registers
     bool use_lines;
     CUtensorMap lmap;
@@ -244,7 +246,37 @@ static int plan_axes(vlasov_ctx *c)
         const size_t slot = ((size_t)W * R * P * es + 127) & ~size_t(127);
         const size_t csz = c->g.dtype == VLASOV_F64 ? sizeof(LineCoefT<double>) : sizeof(LineCoefT<float>);
         const size_t tab = ax < 3 ? ((csz * (size_t)d6[3 + ax] + 127) & ~size_t(127)) : 0;
-        p.smem = 512 + tab + (size_t)S * slot;
+        size_t sslot = 0;
+        if (coded) {
+            // scales of the lines of one chunk: box {W / nuz, R, P} over [O][L][I / nuz]
+            // (the u_y sweep has I = nuz: box {R, P} over [O][L])
+            const long long nuz = c->g.nuz;
+            const int Wl = W / int(nuz);
+            if (W % nuz || (ax < 4 && I % nuz)) return fail(c, VLASOV_EINVAL, "axis %d: block width %d is not whole u_z lines", ax, W);
+            sslot = ((size_t)Wl * R * P * 4 + 127) & ~size_t(127);
+            CUresult rs;
+            if (ax < 4) {
+                const cuuint64_t sdim[3] = {(cuuint64_t)(I / nuz), (cuuint64_t)p.L, (cuuint64_t)O};
+                const cuuint64_t sstr[2] = {(cuuint64_t)(I / nuz * 4), (cuuint64_t)(I / nuz * p.L * 4)};
+                const cuuint32_t sbox[3] = {(cuuint32_t)Wl, (cuuint32_t)R, (cuuint32_t)P};
+                const cuuint32_t sest[3] = {1, 1, 1};
+                rs = enc(&c->smap[ax], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->scale, sdim, sstr, sbox, sest,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                c->scale_rank[ax] = 3;
+            } else {
+                const cuuint64_t sdim[2] = {(cuuint64_t)p.L, (cuuint64_t)O};
+                const cuuint64_t sstr[1] = {(cuuint64_t)(p.L * 4)};
+                const cuuint32_t sbox[2] = {(cuuint32_t)R, (cuuint32_t)P};
+                const cuuint32_t sest[2] = {1, 1};
+                rs = enc(&c->smap[ax], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->scale, sdim, sstr, sbox, sest,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                c->scale_rank[ax] = 2;
+            }
+            if (rs != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: scale tensor map failed (%d)", ax, int(rs));
+        }
+        p.smem = 512 + tab + (size_t)S * (slot + sslot);
         p.grid = R; // rows per chunk (kept here; the launch grid is computed below)
         const cuuint64_t gdim[3] = {(cuuint64_t)I, (cuuint64_t)p.L, (cuuint64_t)O};
         const cuuint64_t gstr[2] = {(cuuint64_t)(I * es), (cuuint64_t)(I * p.L * es)};
@@ -444,14 +476,16 @@ template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlaso
     A.scale = c->scale;
     A.nuz = c->g.nuz;
     A.seed = c->sweeps;
+    A.scale_rank = c->scale_rank[ax];
 }
 
 // streamed launch for the storage type of c (the arguments use FP32 constants unless FP64)
-static cudaError_t launch_stream_any(const vlasov_ctx *c, const AxisPlan &sp, const StreamArgs<float> &A)
+static cudaError_t launch_stream_any(const vlasov_ctx *c, int ax, const StreamArgs<float> &A)
 {
+    const AxisPlan &sp = c->splan[ax];
     switch (c->g.dtype) {
-    case VLASOV_BF16: return launch_stream_bf16(sp.map, A, sp.grid, sp.smem, c->stream);
-    case VLASOV_F16: return launch_stream_f16(sp.map, A, sp.grid, sp.smem, c->stream);
+    case VLASOV_BF16: return launch_stream_bf16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
+    case VLASOV_F16: return launch_stream_f16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
     default: return launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
     }
 }
@@ -486,7 +520,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
             PartTimer t(c, ax, 1);
-            e = launch_stream_any(c, sp, A);
+            e = launch_stream_any(c, ax, A);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
         return VLASOV_OK;
@@ -539,7 +573,7 @@ static int run_velocity(vlasov_ctx *c, int ax)
             fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
             A.cell_coef = (const LineCoefT<float> *)coef;
-            e = launch_stream_any(c, sp, A);
+            e = launch_stream_any(c, ax, A);
         }
     } else if (c->use_lines) {
         ContigArgs<float> A{};
