@@ -102,6 +102,19 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_frac_flux_grad.argtypes = [_D, ctypes.c_double, ctypes.c_int, _D]
+        L.orc_frac_flux_grad.restype = ctypes.c_double
+        L.orc_sweep_line_adjoint.argtypes = [_D, _D, ctypes.c_long, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, _D]
+        L.orc_sweep_line_adjoint.restype = ctypes.c_double
+        L.orc_sweep_adjoint.argtypes = [_G, _D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        _D, _D, ctypes.c_int]
+        L.orc_sweep_adjoint.restype = ctypes.c_int
+        L.orc_gradient_adjoint.argtypes = [_G, _D, ctypes.c_int, _D]
+        L.orc_gradient_adjoint.restype = None
+        L.orc_step_adjoint.argtypes = [_G, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D,
+                                       ctypes.c_int]
+        L.orc_step_adjoint.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -194,3 +207,49 @@ def step(g: Grid, f: np.ndarray, dt: float, a_half: float, a_full: float, phi_n,
     lib().orc_step(ctypes.byref(g), _p(f), dt, a_half, a_full, _p(phi_a), _p(bg), four_pi_G,
                    _p(phi_next), _p(rho), flags)
     return phi_next, rho
+
+
+# ---------------------------------------------------------------------------
+# adjoint (reverse mode, limiter branches frozen at the forward choice)
+# ---------------------------------------------------------------------------
+
+def frac_flux_grad(stencil, s: float, flags: int = MPP):
+    """Return (F, grad) with grad[0..4] = dF/dc_{j-2..j+2} and grad[5] = dF/ds."""
+    st = _f64(stencil)
+    gr = np.zeros(6)
+    F = lib().orc_frac_flux_grad(_p(st), s, flags, _p(gr))
+    return F, gr
+
+
+def sweep_line_adjoint(c, lam, nu: float, periodic: bool = True, flags: int = MPP):
+    """Return (dL/dc, dL/dnu) for the line sweep given dL/dc_new = lam."""
+    cc = _f64(c).copy()
+    ll = _f64(lam).copy()
+    work = np.empty(2 * cc.size)
+    dnu = lib().orc_sweep_line_adjoint(_p(cc), _p(ll), cc.size, nu, int(periodic), flags, _p(work))
+    return ll, dnu
+
+
+def sweep_adjoint(g: Grid, f_in: np.ndarray, lam: np.ndarray, axis: int, dt: float, a: float = 1.0,
+                  phi=None, flags: int = MPP):
+    """In place lam <- J^T lam for the sweep D_axis(dt) at input f_in.  For velocity
+    sweeps returns dL/dg_axis (spatial); else None."""
+    phi_a = None if phi is None else _f64(phi)
+    dLdg = np.zeros(tuple(g.n)) if axis >= 3 else None
+    lib().orc_sweep_adjoint(ctypes.byref(g), _p(_f64(f_in)), _p(lam), axis, dt, a, _p(phi_a),
+                            _p(dLdg), flags)
+    return dLdg
+
+
+def gradient_adjoint(g: Grid, dLdg, d: int, dLdphi: np.ndarray) -> None:
+    lib().orc_gradient_adjoint(ctypes.byref(g), _p(_f64(dLdg)), d, _p(dLdphi))
+
+
+def step_adjoint(g: Grid, f_n: np.ndarray, lam: np.ndarray, dt: float, a_half: float, phi,
+                 flags: int = MPP) -> np.ndarray:
+    """In place lam <- dL/df^n from dL/df^{n+1} for one external-potential step;
+    returns dL/dphi."""
+    dphi = np.zeros(tuple(g.n))
+    lib().orc_step_adjoint(ctypes.byref(g), _p(_f64(f_n)), _p(lam), dt, a_half,
+                           _p(_f64(phi)), _p(dphi), flags)
+    return dphi

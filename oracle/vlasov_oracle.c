@@ -506,3 +506,287 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ================================================================== */
+/* Adjoint (reverse mode) of the split step                           */
+/* ================================================================== */
+/*
+ * The sweep is piecewise linear in the cell values (every limiter operation is
+ * a selection or a linear combination) and piecewise polynomial in the
+ * departure fraction s.  Its Jacobian, with every min / max / median / clamp
+ * frozen at the branch the forward evaluation takes, is obtained here in
+ * forward mode: the fractional flux is evaluated on dual numbers carrying the
+ * derivatives with respect to the five stencil cells and s.  The line adjoint
+ * then scatters (lambda_k - lambda_{k-1}) dF_k/dc, face by face.
+ */
+
+typedef struct { double v; double d[6]; } dual; /* d[0..4] = d/dc_{j-2..j+2}, d[5] = d/ds */
+
+static dual dconst(double v) { dual r; r.v = v; for (int k = 0; k < 6; ++k) r.d[k] = 0.0; return r; }
+static dual dadd(dual a, dual b) { dual r; r.v = a.v + b.v; for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+static dual dsub(dual a, dual b) { dual r; r.v = a.v - b.v; for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+static dual dmul(dual a, dual b)
+{
+    dual r; r.v = a.v * b.v;
+    for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+static dual ddiv(dual a, dual b)
+{
+    dual r; r.v = a.v / b.v;
+    for (int k = 0; k < 6; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dual dscale(double c, dual a) { dual r; r.v = c * a.v; for (int k = 0; k < 6; ++k) r.d[k] = c * a.d[k]; return r; }
+static dual dmin(dual a, dual b) { return (b.v < a.v) ? b : a; }
+static dual dmax(dual a, dual b) { return (b.v > a.v) ? b : a; }
+static dual dmin3(dual a, dual b, dual c) { return dmin(a, dmin(b, c)); }
+static dual dmax3(dual a, dual b, dual c) { return dmax(a, dmax(b, c)); }
+static dual dminmod2(dual a, dual b)
+{
+    if (a.v > 0 && b.v > 0) return dmin(a, b);
+    if (a.v < 0 && b.v < 0) return dmax(a, b);
+    return dconst(0.0);
+}
+static dual dminmod4(dual a, dual b, dual c, dual d)
+{
+    if (a.v > 0 && b.v > 0 && c.v > 0 && d.v > 0) return dmin(dmin(a, b), dmin(c, d));
+    if (a.v < 0 && b.v < 0 && c.v < 0 && d.v < 0) return dmax(dmax(a, b), dmax(c, d));
+    return dconst(0.0);
+}
+static dual dmedian3(dual a, dual b, dual c) { return dadd(a, dminmod2(dsub(b, a), dsub(c, a))); }
+
+/* R1 on duals: Lagrange interpolation of the primitive, evaluated at -s */
+static dual dsl5_raw_flux(const dual st[5], dual s)
+{
+    dual P[6];
+    P[0] = dconst(0.0);
+    for (int k = 0; k < 5; ++k) P[k + 1] = dadd(P[k], st[k]);
+    dual x = dscale(-1.0, s);
+    dual p = dconst(0.0);
+    for (int k = 0; k < 6; ++k) {
+        dual l = dconst(1.0);
+        const double xk = (double)(k - 3);
+        for (int m = 0; m < 6; ++m) {
+            if (m == k) continue;
+            const double xm = (double)(m - 3);
+            l = dmul(l, dscale(1.0 / (xk - xm), dsub(x, dconst(xm))));
+        }
+        p = dadd(p, dmul(P[k], l));
+    }
+    return dsub(P[3], p);
+}
+
+/* R2 on duals (the same steps as orc_mp_limit) */
+static dual dmp_limit(dual fbar, const dual st[5], dual s)
+{
+    const dual cm2 = st[0], cm1 = st[1], c0 = st[2], cp1 = st[3], cp2 = st[4];
+    dual alpha = ddiv(dsub(dconst(1.0), s), s);
+    if (alpha.v > 1e6) alpha = dconst(1e6);
+    const dual dm1 = dadd(dsub(cm2, dscale(2.0, cm1)), c0);
+    const dual d0 = dadd(dsub(cm1, dscale(2.0, c0)), cp1);
+    const dual dp1 = dadd(dsub(c0, dscale(2.0, cp1)), cp2);
+    const dual f_mp = dadd(c0, dminmod2(dsub(cp1, c0), dmul(alpha, dsub(c0, cm1))));
+    if ((fbar.v - c0.v) * (fbar.v - f_mp.v) <= 0.0) return fbar;
+    const dual dm4_p = dminmod4(dsub(dscale(4.0, d0), dp1), dsub(dscale(4.0, dp1), d0), d0, dp1);
+    const dual dm4_m = dminmod4(dsub(dscale(4.0, dm1), d0), dsub(dscale(4.0, d0), dm1), dm1, d0);
+    const dual f_ul = dadd(c0, dmul(alpha, dsub(c0, cm1)));
+    const dual f_md = dsub(dscale(0.5, dadd(c0, cp1)), dscale(0.5, dm4_p));
+    const dual f_lc = dadd(dadd(c0, dscale(0.5, dsub(c0, cm1))), dscale(4.0 / 3.0, dm4_m));
+    const dual f_min = dmax(dmin3(c0, cp1, f_md), dmin3(c0, f_ul, f_lc));
+    const dual f_max = dmin(dmax3(c0, cp1, f_md), dmax3(c0, f_ul, f_lc));
+    return dmedian3(fbar, f_min, f_max);
+}
+
+/*
+ * Fractional flux and its gradient: grad[0..4] = dF/dc_{j-2..j+2},
+ * grad[5] = dF/ds, branches frozen at the forward choice.  Returns F.
+ */
+double orc_frac_flux_grad(const double stv[5], double sv, int flags, double grad[6])
+{
+    dual st[5], s = dconst(sv);
+    s.d[5] = 1.0;
+    for (int k = 0; k < 5; ++k) { st[k] = dconst(stv[k]); st[k].d[k] = 1.0; }
+    dual F;
+    if (sv == 0.0) {
+        /* F = s * fbar(s) near s = 0: dF/ds = fbar(0) = the 5th-order face value */
+        const double w[5] = {1.0 / 30, -13.0 / 60, 47.0 / 60, 9.0 / 20, -1.0 / 20};
+        double f0 = 0.0;
+        for (int k = 0; k < 5; ++k) f0 += w[k] * stv[k];
+        for (int k = 0; k < 6; ++k) grad[k] = 0.0;
+        grad[5] = f0; /* one-sided, limiters off at s = 0 */
+        return 0.0;
+    }
+    F = dsl5_raw_flux(st, s);
+    if (flags & ORC_MP) F = dmul(s, dmp_limit(ddiv(F, s), st, s));
+    if (flags & ORC_PP) {
+        if (F.v < 0.0) F = dconst(0.0);
+        if (F.v > st[2].v) F = st[2];
+    }
+    for (int k = 0; k < 6; ++k) grad[k] = F.d[k];
+    return F.v;
+}
+
+/*
+ * Adjoint of one fractional line update with nu = s in [0, 1) (flow toward
+ * +index):  c_new_i = c_i - (F_{i+1/2} - F_{i-1/2}).  lam holds dL/dc_new on
+ * entry and dL/dc on exit; returns dL/ds.
+ */
+static double line_adjoint_pos(const double *c, double *lam, long n, double s, int periodic, int flags,
+                               double *out)
+{
+    double dLds = 0.0;
+    for (long i = 0; i < n; ++i) out[i] = lam[i];
+    /* face k - 1/2, k = 0..n, donor k - 1; downstream cell k, upstream k - 1 */
+    for (long k = periodic ? 1 : 1; k <= (periodic ? n : n - 1); ++k) {
+        double st[5], gr[6];
+        for (int q = 0; q < 5; ++q) st[q] = line_cell(c, n, k - 1 - 2 + q, periodic);
+        orc_frac_flux_grad(st, s, flags, gr);
+        const double ldown = line_cell(lam, n, k, periodic);
+        const double lup = line_cell(lam, n, k - 1, periodic);
+        const double g = ldown - lup; /* dL/dF of this face */
+        for (int q = 0; q < 5; ++q) {
+            const long m = k - 1 - 2 + q;
+            if (periodic) out[((m % n) + n) % n] += g * gr[q];
+            else if (m >= 0 && m < n) out[m] += g * gr[q];
+        }
+        dLds += g * gr[5];
+    }
+    for (long i = 0; i < n; ++i) lam[i] = out[i];
+    return dLds;
+}
+
+/*
+ * Adjoint of orc_sweep_line for |nu| < 1 (any sign) and, on periodic lines,
+ * any whole-cell shift: c is the line before the sweep, lam is dL/dc_new on
+ * entry and dL/dc on exit.  Returns dL/dnu.  work needs 2n doubles.
+ */
+double orc_sweep_line_adjoint(const double *c, double *lam, long n, double nu, int periodic, int flags, double *work)
+{
+    const int neg = nu < 0.0;
+    const double a = neg ? -nu : nu;
+    const double Nf = floor(a);
+    const long N = (long)Nf;
+    const double s = a - Nf;
+    double *cc = work, *tmp = work + n;
+    for (long i = 0; i < n; ++i) cc[i] = c[i];
+    if (neg) { reverse(cc, n); reverse(lam, n); }
+    if (periodic && N > 0) {
+        /* c_new_i = g_{i-N}: dL/dg_k = lam_{k+N} */
+        for (long k = 0; k < n; ++k) tmp[k] = lam[((k + N) % n + n) % n];
+        for (long k = 0; k < n; ++k) lam[k] = tmp[k];
+    }
+    double *out = (double *)malloc(sizeof(double) * n);
+    const double dLds = line_adjoint_pos(cc, lam, n, s, periodic, flags, out);
+    free(out);
+    if (neg) reverse(lam, n);
+    /* s = |nu| - N: ds/dnu = +1 (nu > 0) or -1 (nu < 0) */
+    return neg ? -dLds : dLds;
+}
+
+/*
+ * Adjoint of orc_sweep (Eq. 3 / Eq. 4): f_in is the array before the sweep,
+ * lam is dL/df_out on entry and dL/df_in on exit.  For a velocity sweep the
+ * derivative with respect to the gradient g_d(x) of the potential is added to
+ * dLdg (spatial, may be NULL): nu = -g dt / du.
+ */
+int orc_sweep_adjoint(const orc_grid *g, const double *f_in, double *lam, int axis, double dt, double a,
+                      const double *phi, double *dLdg, int flags)
+{
+    long d[6]; dims6(g, d);
+    long stride[6];
+    stride[5] = 1;
+    for (int k = 4; k >= 0; --k) stride[k] = stride[k + 1] * d[k + 1];
+    const long n = d[axis];
+    const long total = orc_num_cells(g);
+    const long nlines = total / n;
+    const long inner = stride[axis];
+    const int periodic = axis < 3;
+    const long ncell = (long)g->n[0] * g->n[1] * g->n[2];
+    double *grad = NULL, *dnu = NULL;
+    if (!periodic) {
+        grad = (double *)malloc(sizeof(double) * ncell);
+        orc_gradient(g, phi, axis - 3, grad);
+        dnu = (double *)calloc(ncell * 1, sizeof(double));
+    }
+#pragma omp parallel
+    {
+        double *line = (double *)malloc(sizeof(double) * 4 * n);
+        double *lline = line + n, *work = line + 2 * n;
+#pragma omp for schedule(static)
+        for (long l = 0; l < nlines; ++l) {
+            const long outer = l / inner, in = l % inner;
+            const long base = outer * n * inner + in;
+            long idx[6], rem = base;
+            for (int k = 0; k < 6; ++k) { idx[k] = rem / stride[k]; rem %= stride[k]; }
+            const double nu = line_nu(g, axis, idx, dt, a, grad);
+            for (long i = 0; i < n; ++i) { line[i] = f_in[base + i * inner]; lline[i] = lam[base + i * inner]; }
+            const double dLdnu = orc_sweep_line_adjoint(line, lline, n, nu, periodic, flags, work);
+            for (long i = 0; i < n; ++i) lam[base + i * inner] = lline[i];
+            if (!periodic) {
+                const long cell = (idx[0] * g->n[1] + idx[1]) * g->n[2] + idx[2];
+#pragma omp atomic
+                dnu[cell] += dLdnu;
+            }
+        }
+        free(line);
+    }
+    if (!periodic && dLdg) {
+        const double fac = -dt / orc_du(g, axis - 3);
+        for (long c = 0; c < ncell; ++c) dLdg[c] += dnu[c] * fac;
+    }
+    free(grad);
+    free(dnu);
+    return 0;
+}
+
+/* dL/dphi += G_d^T dLdg for the periodic 4th-order gradient along d (G^T = -G) */
+void orc_gradient_adjoint(const orc_grid *g, const double *dLdg, int d, double *dLdphi)
+{
+    const long ny = g->n[1], nz = g->n[2];
+    const double h = orc_dx(g, d);
+    for (long ix = 0; ix < g->n[0]; ++ix)
+        for (long iy = 0; iy < ny; ++iy)
+            for (long iz = 0; iz < nz; ++iz) {
+                const long p[3] = {ix, iy, iz};
+                const double y = dLdg[(ix * ny + iy) * nz + iz];
+                const double wts[5] = {1.0, -8.0, 0.0, 8.0, -1.0}; /* d g(x) / d phi(x + o), o = -2..2, times 12h */
+                for (int o = -2; o <= 2; ++o) {
+                    long q[3] = {p[0], p[1], p[2]};
+                    const long nd = g->n[d];
+                    q[d] = ((p[d] + o) % nd + nd) % nd;
+                    dLdphi[(q[0] * ny + q[1]) * nz + q[2]] += y * wts[o + 2] / (12.0 * h);
+                }
+            }
+}
+
+/*
+ * Adjoint of one orc_step with an external potential (both kicks use phi):
+ * f_n is the state at the start of the step, lam is dL/df^{n+1} on entry and
+ * dL/df^n on exit, dLdphi (spatial) accumulates dL/dphi.  The forward is
+ * recomputed from f_n, keeping the input of each of the nine sweeps.
+ */
+int orc_step_adjoint(const orc_grid *g, const double *f_n, double *lam, double dt, double a_half,
+                     const double *phi, double *dLdphi, int flags)
+{
+    const long total = orc_num_cells(g);
+    const long ncell = (long)g->n[0] * g->n[1] * g->n[2];
+    const int axes[9] = {3, 4, 5, 2, 1, 0, 3, 4, 5};
+    const double dts[9] = {0.5 * dt, 0.5 * dt, 0.5 * dt, dt, dt, dt, 0.5 * dt, 0.5 * dt, 0.5 * dt};
+    double *in = (double *)malloc(sizeof(double) * total * 9);
+    memcpy(in, f_n, sizeof(double) * total);
+    for (int k = 0; k < 8; ++k) {
+        memcpy(in + (k + 1) * total, in + k * total, sizeof(double) * total);
+        orc_sweep(g, in + (k + 1) * total, axes[k], dts[k], a_half, phi, flags);
+    }
+    double *dLdg = (double *)calloc(3 * ncell, sizeof(double));
+    for (int k = 8; k >= 0; --k) {
+        const int ax = axes[k];
+        orc_sweep_adjoint(g, in + k * total, lam, ax, dts[k], a_half, phi, ax >= 3 ? dLdg + (ax - 3) * ncell : NULL,
+                          flags);
+    }
+    for (int d = 0; d < 3; ++d) orc_gradient_adjoint(g, dLdg + d * ncell, d, dLdphi);
+    free(dLdg);
+    free(in);
+    return 0;
+}
