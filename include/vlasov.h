@@ -78,6 +78,13 @@ void vlasov_destroy(vlasov_ctx *ctx);
 int vlasov_set_stream(vlasov_ctx *ctx, void *stream);
 
 /*
+ * Point ctx at another distribution function of the same grid and storage type
+ * (and, for 16-bit storage, its scale array); later calls read and update that
+ * array.  The caller keeps ownership of both arrays.  Host work only.
+ */
+int vlasov_set_f(vlasov_ctx *ctx, void *f_dev, float *scale_dev);
+
+/*
  * One directional sweep D_axis(dt) of f in place (Eq. 3 for axis 0..2 =
  * x, y, z; Eq. 4 for axis 3..5 = u_x, u_y, u_z).
  *   Position sweep i: Courant number nu_j = u_j dt / (a^2 dx_i) for each
@@ -143,7 +150,10 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
 #define VLASOV_T_POISSON 7
 #define VLASOV_T_COEF 8 /* velocity-sweep constants (potential gradient)      */
 #define VLASOV_T_MASS 9
-#define VLASOV_T_KINDS 10
+#define VLASOV_T_ADJ_X 10     /* kinds 10..15: adjoint sweeps along x, y, z, u_x, u_y, u_z */
+#define VLASOV_T_GRAD_ADJ 16  /* transposed potential gradient of the step adjoint   */
+#define VLASOV_T_COPY 17      /* copies of the step adjoint's sweep inputs (no kernel) */
+#define VLASOV_T_KINDS 18
 int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
 
@@ -179,6 +189,40 @@ int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nki
 #define VLASOV_STATIC_MAX_CELLS 32768
 int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, int axis, double dt,
                                  const float *phi_dev, unsigned int *status_dev, void *stream);
+
+/*
+ * Adjoint (reverse mode) of one sweep, for gradients of a loss L through the
+ * solver.  The paper has no counterpart: it is the transpose of the sweep's
+ * Jacobian at the sweep input, with every limiter choice (min / max / clamp of
+ * Sec. 4.2's monotonicity and positivity constraints) frozen at the branch
+ * the forward evaluation takes there.
+ *   f_in_dev  the sweep's input (same grid and storage type as ctx; FP32 or
+ *             FP64 only), read only;
+ *   lam_dev   on entry dL/df_out, on exit dL/df_in (same layout as f; must not
+ *             be f_in_dev; 16-byte aligned), updated in place;
+ *   axis, dt, a, phi_dev  as for vlasov_sweep;
+ *   dLdg_dev  velocity sweeps only (else ignored, may be NULL): nx*ny*nz FP64
+ *             to which dL/dg_i(x) is ADDED, g_i the potential gradient that
+ *             sets the Courant number nu(x) = -g_i(x) dt / du_i.
+ * A whole-cell shift of a position sweep (|nu| >= 1) uses a scratch copy of
+ * lambda allocated on first use.
+ */
+int vlasov_sweep_adjoint(vlasov_ctx *ctx, const void *f_in_dev, void *lam_dev, int axis, double dt,
+                         double a, const float *phi_dev, double *dLdg_dev);
+
+/*
+ * Adjoint of one vlasov_step with an external potential (phi_next_dev NULL:
+ * both kicks use phi_dev, the drift uses a_half).  f_n_dev is the state at the
+ * start of the step (read only); lam_dev holds dL/df^{n+1} on entry and
+ * dL/df^n on exit.  The step is run forward again from f_n, keeping the
+ * input of each of its nine sweeps (eight scratch arrays the size of f,
+ * allocated on the first call and kept until vlasov_destroy); the nine
+ * adjoint sweeps then run last to first.  If dLdphi_dev (nx*ny*nz FP64) is
+ * non-NULL, dL/dphi is ADDED to it through the transposed 4th-order gradient.
+ * ctx's own array f is neither read nor changed.
+ */
+int vlasov_step_adjoint(vlasov_ctx *ctx, const void *f_n_dev, void *lam_dev, double dt, double a_half,
+                        const float *phi_dev, double *dLdphi_dev);
 
 /*
  * Synchronise the stream, read and clear the device error word.  Returns 0 or

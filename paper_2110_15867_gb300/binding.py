@@ -42,14 +42,16 @@ _lib = None
 SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep", "vlasov_moment",
            "vlasov_poisson", "vlasov_step", "vlasov_upload", "vlasov_download",
            "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
-           "vlasov_sweep_velocity_static")
+           "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
+           "vlasov_step_adjoint")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
 
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
-           "poisson", "coef", "mass")
+           "poisson", "coef", "mass", "adj_x", "adj_y", "adj_z", "adj_ux", "adj_uy", "adj_uz",
+           "grad_adj", "copy")
 
 
 def library_path() -> str:
@@ -96,6 +98,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_sweep_velocity_static.argtypes = [ctypes.POINTER(Grid), _VP, ctypes.c_int,
                                                ctypes.c_double, _VP, _VP, _VP]
     L.vlasov_sweep_velocity_static.restype = ctypes.c_int
+    L.vlasov_set_f.argtypes = [_VP, _VP, _VP]
+    L.vlasov_set_f.restype = ctypes.c_int
+    L.vlasov_sweep_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, _VP, _VP]
+    L.vlasov_sweep_adjoint.restype = ctypes.c_int
+    L.vlasov_step_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]
+    L.vlasov_step_adjoint.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -129,6 +138,22 @@ def vlasov_destroy(ctx) -> None:
 
 def vlasov_set_stream(ctx, stream: int):
     return _check(ctx, load().vlasov_set_stream(ctx, stream))
+
+
+def vlasov_set_f(ctx, f_ptr: int, scale_ptr=None):
+    return _check(ctx, load().vlasov_set_f(ctx, f_ptr, scale_ptr))
+
+
+def vlasov_sweep_adjoint(ctx, f_in_ptr: int, lam_ptr: int, axis: int, dt: float, a: float,
+                         phi_ptr, dLdg_ptr):
+    return _check(ctx, load().vlasov_sweep_adjoint(ctx, f_in_ptr, lam_ptr, axis, dt, a, phi_ptr,
+                                                   dLdg_ptr))
+
+
+def vlasov_step_adjoint(ctx, f_n_ptr: int, lam_ptr: int, dt: float, a_half: float, phi_ptr,
+                        dLdphi_ptr):
+    return _check(ctx, load().vlasov_step_adjoint(ctx, f_n_ptr, lam_ptr, dt, a_half, phi_ptr,
+                                                  dLdphi_ptr))
 
 
 def vlasov_sweep(ctx, axis: int, dt: float, a: float, phi_ptr):
@@ -292,6 +317,31 @@ class Vlasov:
                     _ptr(self._field(rho_bg, self.torch.float64)), four_pi_G,
                     _ptr(self._field(phi_next, self.torch.float32)),
                     _ptr(self._field(rho_nu, self.torch.float64)))
+
+    def _like_f(self, t, name):
+        if not t.is_cuda or tuple(t.shape) != self.shape or t.dtype != self.f.dtype or \
+                not t.is_contiguous() or t.device != self.f.device:
+            raise ValueError("%s must be a contiguous CUDA tensor like f" % name)
+        return t
+
+    def sweep_adjoint(self, f_in, lam, axis, dt: float, a: float = 1.0, phi=None, dLdg=None):
+        """lam <- (dD_axis/df at f_in)^T lam in place; for a velocity axis dL/dg is
+        added to dLdg (FP64 spatial field) when given."""
+        ax = AXES[axis] if isinstance(axis, str) else int(axis)
+        self._sync_stream()
+        vlasov_sweep_adjoint(self.ctx, self._like_f(f_in, "f_in").data_ptr(),
+                             self._like_f(lam, "lam").data_ptr(), ax, dt, a,
+                             _ptr(self._field(phi, self.torch.float32)),
+                             _ptr(self._field(dLdg, self.torch.float64)))
+
+    def step_adjoint(self, f_n, lam, dt: float, a_half: float, phi, dLdphi=None):
+        """lam <- (d step/df at f_n)^T lam in place (external potential phi for both
+        kicks); dL/dphi is added to dLdphi (FP64 spatial field) when given."""
+        self._sync_stream()
+        vlasov_step_adjoint(self.ctx, self._like_f(f_n, "f_n").data_ptr(),
+                            self._like_f(lam, "lam").data_ptr(), dt, a_half,
+                            _ptr(self._field(phi, self.torch.float32)),
+                            _ptr(self._field(dLdphi, self.torch.float64)))
 
     def upload(self, f_host):
         """Copy a host tensor (same shape and dtype as f, ideally pinned) into f."""

@@ -1,0 +1,523 @@
+// adjoint.cu -- reverse mode of the SL-MPP5 sweeps (the adjoint of the split
+// step, Eq. 5 of Yoshikawa, Tanaka & Yoshida, SC'21), FP32 or FP64 storage.
+//
+// A sweep maps the line c to c_new_i = c_i + F_{i-1/2} - F_{i+1/2}.  Every
+// operation of the limited flux F is a selection or a linear combination, so
+// with each min / max / clamp frozen at the branch the forward evaluation
+// takes, the sweep is linear in c and its transpose is
+//     lambda_old_m = lambda_m + sum_j (lambda_{j+1} - lambda_j) dF_{j+1/2}/dc_m.
+// face_adjoint() re-evaluates one face from the sweep's input and runs its
+// reverse pass by hand (partials with respect to the five stencil cells and to
+// the departure fraction s).  AdjMarch walks the faces of one line in order
+// with a five-cell window in registers: each face adds its partials to the
+// window, and a cell leaves the window (and is written) once no later face
+// touches it.  On a periodic line the first two and last two cells are
+// touched by faces at both ends; their partial sums wait in registers until
+// the last face.
+//
+// One thread per line.  Strided axes (x, y, z, u_x, u_y): neighbouring threads
+// own neighbouring columns, so every row access of a warp is one coalesced
+// segment.  u_z: a line is one contiguous row; for n_uz = 8, 16, 32 the thread
+// loads the row with 16-byte vector loads into registers and the march runs
+// on compile-time indices.  A negative Courant number is the mirror image of a
+// positive one: the line is walked from its far end (negated stride).
+//
+// For a velocity sweep dL/dnu of every line is summed over its spatial cell
+// and added, times dnu/dg = -dt/du, to dL/dg of that cell (FP64 atomics, one
+// per block and cell).
+#include <type_traits>
+
+#include "vk_common.cuh"
+
+namespace vk {
+
+constexpr int kAdjBlock = 256;
+
+template <typename C> struct AdjLim {
+    C w[5];  // weights of fbar
+    C ws[5]; // their derivatives with respect to s
+    C s, alpha, dalpha;
+};
+
+template <typename C> __device__ __forceinline__ AdjLim<C> make_adj_lim(const LineCoefT<C> &k)
+{
+    AdjLim<C> a;
+    const double s = (double)k.s;
+    const double K2[5] = {0.0, -1.0 / 24, 5.0 / 8, -5.0 / 8, 1.0 / 24};
+    const double K3[5] = {-1.0 / 24, 1.0 / 4, -1.0 / 3, 1.0 / 12, 1.0 / 24};
+    const double K4[5] = {0.0, 1.0 / 24, -1.0 / 8, 1.0 / 8, -1.0 / 24};
+    const double K5[5] = {1.0 / 120, -1.0 / 30, 1.0 / 20, -1.0 / 30, 1.0 / 120};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        a.w[m] = k.w[m];
+        // d/ds of K1 + K2 s + K3 s^2 + K4 s^3 + K5 s^4
+        a.ws[m] = C(K2[m] + s * (2.0 * K3[m] + s * (3.0 * K4[m] + s * 4.0 * K5[m])));
+    }
+    a.s = k.s;
+    a.alpha = k.alpha;
+    // alpha = (1 - s) / s below its cap of 1e6: d alpha / ds = -1 / s^2
+    a.dalpha = (s > 0.0 && (1.0 - s) / s < 1e6) ? C(-1.0 / (s * s)) : C(0);
+    return a;
+}
+
+// minmod of (4 d0 - d1, 4 d1 - d0, d0, d1) and which argument it is (-1: zero)
+template <typename C> __device__ __forceinline__ C dm4_sel(C d0, C d1, int &which)
+{
+    const C a = C(4) * d0 - d1, b = C(4) * d1 - d0;
+    const C lo = mn2(mn3(a, b, d0), d1), hi = mx2(mx3(a, b, d0), d1);
+    const C r = mn2(mx2(lo, C(0)), hi);
+    which = r == C(0) ? -1 : (r == a ? 0 : (r == b ? 1 : (r == d0 ? 2 : 3)));
+    return r;
+}
+
+// add x d(dm4)/d(argument) to the adjoints of d0 and d1
+template <typename C> __device__ __forceinline__ void dm4_back(int which, C x, C &g0, C &g1)
+{
+    if (which == 0) { g0 += C(4) * x; g1 -= x; }
+    else if (which == 1) { g1 += C(4) * x; g0 -= x; }
+    else if (which == 2) g0 += x;
+    else if (which == 3) g1 += x;
+}
+
+// Reverse pass of the flux through the downwind face of c0 (local frame) for
+// the adjoint gbar of that flux: g[0..4] += gbar dF/dc_{j-2..j+2}; returns
+// gbar dF/ds.  The forward is the flux of the sweep kernels: mean fbar over
+// the departure interval, clamp to [fmin, fmax] (Suresh-Huynh), then s * fbar
+// clamped to [0, c0] (positivity).
+template <typename C>
+__device__ __forceinline__ C face_adjoint(const AdjLim<C> &k, C cm2, C cm1, C c0, C cp1, C cp2, C gbar, C (&g)[5])
+{
+    const C fbar = k.w[0] * cm2 + k.w[1] * cm1 + k.w[2] * c0 + k.w[3] * cp1 + k.w[4] * cp2;
+    if (k.s == C(0)) return fbar * gbar; // F = s fbar(s): one-sided dF/ds at s = 0, limiters off
+    const C dlm = c0 - cm1;
+    const C ful = c0 + k.alpha * dlm;
+    const C d_m = cm2 - C(2) * cm1 + c0, d_0 = cm1 - C(2) * c0 + cp1, d_p = c0 - C(2) * cp1 + cp2;
+    int wm, wp;
+    const C dm4m = dm4_sel(d_m, d_0, wm);
+    const C dm4p = dm4_sel(d_0, d_p, wp);
+    const C fmd = C(0.5) * (c0 + cp1 - dm4p);
+    const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * dm4m;
+    const C A = mn3(c0, cp1, fmd), B = mn3(c0, ful, flc);
+    const C Cx = mx3(c0, cp1, fmd), D = mx3(c0, ful, flc);
+    const C fmin = mx2(A, B), fmax = mn2(Cx, D);
+    const C v = mn2(mx2(fbar, fmin), fmax);
+    const C sv = k.s * v;
+    // reverse
+    C gs = C(0), gv = C(0), gc0 = C(0), gm1 = C(0), gp1 = C(0);
+    if (sv > c0) gc0 += gbar; // F = c0
+    else if (sv >= C(0)) { gv = k.s * gbar; gs += v * gbar; }
+    const C gfbar = (fbar >= fmin && fbar <= fmax) ? gv : C(0);
+    const C gfmin = fbar < fmin ? gv : C(0);
+    const C gfmax = fbar > fmax ? gv : C(0);
+    const C gA = A >= B ? gfmin : C(0), gB = gfmin - gA;
+    const C gC = Cx <= D ? gfmax : C(0), gD = gfmax - gC;
+    C gfmd = C(0), gful = C(0), gflc = C(0);
+    // A = min(c0, cp1, fmd), C = max(c0, cp1, fmd): route to the selected argument
+    if (A == c0) gc0 += gA; else if (A == cp1) gp1 += gA; else gfmd += gA;
+    if (Cx == c0) gc0 += gC; else if (Cx == cp1) gp1 += gC; else gfmd += gC;
+    // B = min(c0, ful, flc), D = max(c0, ful, flc)
+    if (B == c0) gc0 += gB; else if (B == ful) gful += gB; else gflc += gB;
+    if (D == c0) gc0 += gD; else if (D == ful) gful += gD; else gflc += gD;
+    // ful = c0 + alpha (c0 - cm1)
+    gc0 += (C(1) + k.alpha) * gful;
+    gm1 -= k.alpha * gful;
+    gs += k.dalpha * dlm * gful;
+    // fmd = (c0 + cp1 - dm4p) / 2 ; flc = c0 + (c0 - cm1) / 2 + 4/3 dm4m
+    gc0 += C(0.5) * gfmd + C(1.5) * gflc;
+    gp1 += C(0.5) * gfmd;
+    gm1 -= C(0.5) * gflc;
+    C gdm = C(0), gd0 = C(0), gdp = C(0);
+    dm4_back(wp, -C(0.5) * gfmd, gd0, gdp);
+    dm4_back(wm, C(4.0 / 3.0) * gflc, gdm, gd0);
+    // fbar = sum w c
+    g[0] += k.w[0] * gfbar;
+    gm1 += k.w[1] * gfbar;
+    gc0 += k.w[2] * gfbar;
+    gp1 += k.w[3] * gfbar;
+    g[4] += k.w[4] * gfbar;
+    gs += (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2) * gfbar;
+    // curvatures d_k = c_{k-1} - 2 c_k + c_{k+1}
+    g[0] += gdm;
+    gm1 += gd0 - C(2) * gdm;
+    gc0 += gdm - C(2) * gd0 + gdp;
+    gp1 += gd0 - C(2) * gdp;
+    g[4] += gdp;
+    g[1] += gm1;
+    g[2] += gc0;
+    g[3] += gp1;
+    return gs;
+}
+
+// ----------------------------------------------------------------------------
+// the march over one line (local frame: flow toward +index)
+// ----------------------------------------------------------------------------
+// Acc supplies, for local indices 0 <= i < n: c(i) the sweep input, lam(i)
+// dL/dc_new (read only before cell i is written) and put(i, v) dL/dc.
+template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
+    Acc &acc;
+    const AdjLim<C> &k;
+    int n;
+    C cw[5], ow[5], lo[3]; // c and running dL/dc of cells j-2..j+2; original lambda of cells j..j+2
+    C dA, dB, d0, d1;      // periodic: partial sums of cells n-2, n-1 (faces 0, 1) and 0, 1 (faces up to 3)
+    C dLds, osum;
+
+    __device__ __forceinline__ AdjMarch(Acc &a, const AdjLim<C> &kk, int nn) : acc(a), k(kk), n(nn) {}
+
+    __device__ __forceinline__ C cget(int m) const
+    {
+        if (PERIODIC) return acc.c(m < 0 ? m + n : (m >= n ? m - n : m));
+        return (m >= 0 && m < n) ? acc.c(m) : C(0);
+    }
+    __device__ __forceinline__ C lget(int m) const
+    {
+        if (PERIODIC) return acc.lam(m < 0 ? m + n : (m >= n ? m - n : m));
+        return (m >= 0 && m < n) ? acc.lam(m) : C(0);
+    }
+    __device__ __forceinline__ void put(int m, C v)
+    {
+        acc.put(m, v);
+        osum += v;
+    }
+
+    __device__ __forceinline__ void begin()
+    {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) cw[q] = cget(q - 2);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) lo[q] = lget(q);
+        ow[0] = C(0); // cells -2, -1: partial sums (periodic) or ghosts
+        ow[1] = C(0);
+        ow[2] = lo[0];
+        ow[3] = lo[1];
+        ow[4] = lo[2];
+        dA = dB = d0 = d1 = C(0);
+        dLds = osum = C(0);
+    }
+
+    __device__ __forceinline__ void face(int j)
+    {
+        C g[5] = {C(0), C(0), C(0), C(0), C(0)};
+        dLds += face_adjoint(k, cw[0], cw[1], cw[2], cw[3], cw[4], lo[1] - lo[0], g);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) ow[q] += g[q];
+        // cell j - 2 leaves the window
+        const int mo = j - 2;
+        if (PERIODIC) {
+            if (mo == -2) dA = ow[0];
+            else if (mo == -1) dB = ow[0];
+            else if (mo == 0) d0 = ow[0];
+            else if (mo == 1) d1 = ow[0];
+            else put(mo, ow[0]);
+        } else if (mo >= 0) {
+            put(mo, ow[0]);
+        }
+        // cell j + 3 enters
+        const int mi = j + 3;
+        C lnew = C(0), cnew = C(0), init;
+        if (PERIODIC ? mi < n + 2 : mi < n) {
+            lnew = lget(mi);
+            cnew = cget(mi);
+        }
+        if (PERIODIC) {
+            if (mi == n - 2) init = lnew + dA;
+            else if (mi == n - 1) init = lnew + dB;
+            else if (mi == n) init = d0;
+            else if (mi == n + 1) init = d1;
+            else init = lnew;
+        } else {
+            init = lnew;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { ow[q] = ow[q + 1]; cw[q] = cw[q + 1]; }
+        ow[4] = init;
+        cw[4] = cnew;
+        lo[0] = lo[1];
+        lo[1] = lo[2];
+        lo[2] = lnew;
+    }
+
+    // after the last face the window holds cells nf - 2 .. nf + 2
+    __device__ __forceinline__ void end()
+    {
+        if (PERIODIC) {
+            put(n - 2, ow[0]);
+            put(n - 1, ow[1]);
+            put(0, ow[2]);
+            put(1, ow[3]);
+        } else {
+            put(n - 3, ow[0]);
+            put(n - 2, ow[1]);
+            put(n - 1, ow[2]);
+        }
+    }
+};
+
+// Walk a line of n cells (periodic: n >= 5; zero-flux: n >= 4).  LCT > 0:
+// compile-time length (the loop unrolls and every index is a constant).
+template <bool PERIODIC, int LCT, typename C, typename Acc>
+__device__ __forceinline__ void march_adjoint(Acc &acc, const AdjLim<C> &k, int n, C &dLds, C &osum)
+{
+    AdjMarch<PERIODIC, C, Acc> m(acc, k, LCT > 0 ? LCT : n);
+    m.begin();
+    if constexpr (LCT > 0) {
+#pragma unroll
+        for (int j = 0; j < (PERIODIC ? LCT : LCT - 1); ++j) m.face(j);
+    } else {
+        const int nf = PERIODIC ? n : n - 1;
+#pragma unroll 1
+        for (int j = 0; j < nf; ++j) m.face(j);
+    }
+    m.end();
+    dLds = m.dLds;
+    osum = m.osum;
+}
+
+// periodic line of 4 cells: whole line in registers
+template <typename C, typename Acc> __device__ __forceinline__ void march_adjoint4(Acc &acc, const AdjLim<C> &k, C &dLds, C &osum)
+{
+    C c[4], l[4], o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { c[i] = acc.c(i); l[i] = acc.lam(i); o[i] = l[i]; }
+    dLds = C(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        C g[5] = {C(0), C(0), C(0), C(0), C(0)};
+        dLds += face_adjoint(k, c[(j + 2) & 3], c[(j + 3) & 3], c[j], c[(j + 1) & 3], c[(j + 2) & 3],
+                             l[(j + 1) & 3] - l[j], g);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) o[(j + 2 + q) & 3] += g[q];
+    }
+    osum = C(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { acc.put(i, o[i]); osum += o[i]; }
+}
+
+// ----------------------------------------------------------------------------
+// accessors
+// ----------------------------------------------------------------------------
+// strided line in global memory; lam is read at (i + shift) mod n (a periodic
+// whole-cell shift folded into the read) and written at i into lout
+template <typename T> struct GlobalLine {
+    const T *f;
+    const T *lin;
+    T *lout;
+    long long st;
+    int shift, n;
+    __device__ __forceinline__ T c(int i) const { return f[i * st]; }
+    __device__ __forceinline__ T lam(int i) const
+    {
+        int r = i + shift;
+        if (r >= n) r -= n;
+        return lin[r * st];
+    }
+    __device__ __forceinline__ void put(int i, T v) const { lout[i * st] = v; }
+};
+
+// line in registers (compile-time indices after unrolling), mirrored when NEG
+template <typename T, int L, bool NEG> struct RegLine {
+    T cv[L], lv[L];
+    __device__ __forceinline__ T c(int i) const { return cv[NEG ? L - 1 - i : i]; }
+    __device__ __forceinline__ T lam(int i) const { return lv[NEG ? L - 1 - i : i]; }
+    __device__ __forceinline__ void put(int i, T v) { lv[NEG ? L - 1 - i : i] = v; }
+};
+
+// ----------------------------------------------------------------------------
+// per-cell reduction of dL/dnu (velocity sweeps)
+// ----------------------------------------------------------------------------
+template <typename C> __device__ __forceinline__ C warp_sum(C v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Every thread of the block calls this.  cell < 0: no contribution.  Lines
+// of one cell are consecutive, so a warp whose first and last lanes share a
+// cell sums in registers; the block then merges runs of equal cells.
+template <typename C>
+__device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, double fac)
+{
+    __shared__ long long s_cell[kAdjBlock / 32];
+    __shared__ double s_sum[kAdjBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long first = __shfl_sync(0xffffffffu, cell, 0), last = __shfl_sync(0xffffffffu, cell, 31);
+    const bool uniform = first == last && first >= 0;
+    if (uniform) {
+        const C s = warp_sum(dnu);
+        if (lane == 0) { s_cell[warp] = first; s_sum[warp] = (double)s; }
+    } else {
+        if (cell >= 0 && dnu != C(0)) atomicAdd(dLdg + cell, (double)dnu * fac);
+        if (lane == 0) { s_cell[warp] = -1; s_sum[warp] = 0.0; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long cur = -1;
+        double acc = 0.0;
+        for (int q = 0; q < kAdjBlock / 32; ++q) {
+            if (s_cell[q] != cur) {
+                if (cur >= 0 && acc != 0.0) atomicAdd(dLdg + cur, acc * fac);
+                cur = s_cell[q];
+                acc = 0.0;
+            }
+            acc += s_sum[q];
+        }
+        if (cur >= 0 && acc != 0.0) atomicAdd(dLdg + cur, acc * fac);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// kernels
+// ----------------------------------------------------------------------------
+// Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
+// inner = t % I).  SMALL4: periodic lines of 4 cells.
+template <typename T, bool PERIODIC, bool SMALL4>
+__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : 3) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
+{
+    using C = T;
+    const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    long long cell = -1;
+    C dnu = C(0);
+    if (t < a.nlines) {
+        const long long outer = t / a.n_inner, inner = t - outer * a.n_inner;
+        const LineCoefT<C> kc = a.coef_mode == 0 ? a.table[(inner / a.vstride) % a.nvel] : a.cell_coef[outer / a.outer_per_cell];
+        const long long base = outer * a.L * a.n_inner + inner;
+        const T *f = static_cast<const T *>(a.f_in) + base;
+        const T *lin = static_cast<const T *>(a.lam_in) + base;
+        T *lout = static_cast<T *>(a.lam_out) + base;
+        if (kc.nd < 0 || (!PERIODIC && (kc.nd >> 1) != 0)) {
+            // line left unchanged by the forward sweep: identity
+            if (lout != lin)
+                for (int i = 0; i < a.L; ++i) lout[i * a.n_inner] = lin[i * a.n_inner];
+        } else {
+            const bool neg = kc.nd & 1;
+            const long long st = neg ? -a.n_inner : a.n_inner;
+            const long long off = neg ? (long long)(a.L - 1) * a.n_inner : 0;
+            // the forward shifts whole cells N = nd / 2 after the fractional update: read lambda N cells on
+            GlobalLine<T> acc{f + off, lin + off, lout + off, st, PERIODIC ? (kc.nd >> 1) % a.L : 0, a.L};
+            const AdjLim<C> lim = make_adj_lim(kc);
+            C dLds, osum;
+            if constexpr (SMALL4) march_adjoint4<C>(acc, lim, dLds, osum);
+            else march_adjoint<PERIODIC, 0, C>(acc, lim, a.L, dLds, osum);
+            if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
+            dnu = neg ? -dLds : dLds;
+        }
+        cell = a.dLdg ? t / a.lines_per_cell : -1;
+    }
+    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg);
+}
+
+// u_z lines of L = 8, 16, 32 cells: one row per thread through 16-byte vector loads
+template <typename T, bool NEG, int L>
+__device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint4 *op, const AdjLim<T> &lim, T &dLds, T &osum)
+{
+    constexpr int per = 16 / int(sizeof(T)); // elements per 16-byte chunk
+    RegLine<T, L, NEG> acc;
+#pragma unroll
+    for (int q = 0; q < L / per; ++q) {
+        const uint4 u = __ldg(fp + q), w = __ldg(lp + q);
+        const T *pu = reinterpret_cast<const T *>(&u), *pw = reinterpret_cast<const T *>(&w);
+#pragma unroll
+        for (int e = 0; e < per; ++e) { acc.cv[q * per + e] = pu[e]; acc.lv[q * per + e] = pw[e]; }
+    }
+    march_adjoint<false, L, T>(acc, lim, L, dLds, osum);
+#pragma unroll
+    for (int q = 0; q < L / per; ++q) {
+        uint4 u;
+        T *pu = reinterpret_cast<T *>(&u);
+#pragma unroll
+        for (int e = 0; e < per; ++e) pu[e] = acc.lv[q * per + e];
+        op[q] = u;
+    }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
+{
+    using C = T;
+    constexpr int per = 16 / int(sizeof(T));
+    const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    long long cell = -1;
+    C dnu = C(0);
+    if (t < a.nlines) {
+        const LineCoefT<C> kc = a.cell_coef[t / a.outer_per_cell];
+        const uint4 *fp = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.f_in) + t * L);
+        const uint4 *lp = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.lam_in) + t * L);
+        uint4 *op = reinterpret_cast<uint4 *>(static_cast<T *>(a.lam_out) + t * L);
+        if (kc.nd < 0 || (kc.nd >> 1) != 0) {
+            if (op != lp)
+#pragma unroll
+                for (int q = 0; q < L / per; ++q) op[q] = lp[q];
+        } else {
+            const AdjLim<C> lim = make_adj_lim(kc);
+            C dLds, osum;
+            if (kc.nd & 1) rows_line<T, true, L>(fp, lp, op, lim, dLds, osum);
+            else rows_line<T, false, L>(fp, lp, op, lim, dLds, osum);
+            if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
+            dnu = (kc.nd & 1) ? -dLds : dLds;
+        }
+        cell = a.dLdg ? t / a.lines_per_cell : -1;
+    }
+    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg);
+}
+
+// dL/dphi += G^T dL/dg for the periodic 4th-order gradient along d: g(x)
+// depends on phi(x + o), o = -2..2, with weights (1, -8, 0, 8, -1) / 12h
+__global__ void gradient_adjoint_kernel(GridDims g, const double *__restrict__ dLdg, int d, double *dLdphi)
+{
+    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
+    const double h = g.L / g.n[d];
+    const double wts[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int idx[3] = {int(i / ((long long)g.n[1] * g.n[2])), int((i / g.n[2]) % g.n[1]), int(i % g.n[2])};
+        double acc = 0.0;
+        for (int o = -2; o <= 2; ++o) {
+            int q[3] = {idx[0], idx[1], idx[2]};
+            q[d] = (q[d] - o + 2 * g.n[d]) % g.n[d];
+            acc += wts[o + 2] * dLdg[((long long)q[0] * g.n[1] + q[1]) * g.n[2] + q[2]];
+        }
+        dLdphi[i] += acc / (12.0 * h);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool rows, cudaStream_t st)
+{
+    const long long blocks = (a.nlines + kAdjBlock - 1) / kAdjBlock;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)blocks);
+    if (rows) {
+        // FP32 only: a row of 32 doubles (twice, with lambda) would not stay in registers
+        if constexpr (!std::is_same<T, float>::value) return cudaErrorInvalidValue;
+        else switch (a.L) {
+        case 8: adjoint_rows_kernel<T, 8><<<grid, kAdjBlock, 0, st>>>(a); break;
+        case 16: adjoint_rows_kernel<T, 16><<<grid, kAdjBlock, 0, st>>>(a); break;
+        case 32: adjoint_rows_kernel<T, 32><<<grid, kAdjBlock, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else if (a.periodic) {
+        if (a.L == 4) adjoint_lines_kernel<T, true, true><<<grid, kAdjBlock, 0, st>>>(a);
+        else adjoint_lines_kernel<T, true, false><<<grid, kAdjBlock, 0, st>>>(a);
+    } else {
+        adjoint_lines_kernel<T, false, false><<<grid, kAdjBlock, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+bool adjoint_rows_supported(int L, int dtype) { return dtype == 1 && (L == 8 || L == 16 || L == 32); }
+
+cudaError_t launch_adjoint_f32(const AdjArgs<float> &a, bool rows, cudaStream_t st) { return launch_adj_t<float>(a, rows, st); }
+cudaError_t launch_adjoint_f64(const AdjArgs<double> &a, bool rows, cudaStream_t st) { return launch_adj_t<double>(a, rows, st); }
+
+cudaError_t launch_gradient_adjoint(const GridDims &g, const double *dLdg, int d, double *dLdphi, cudaStream_t st)
+{
+    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
+    gradient_adjoint_kernel<<<blocks, threads, 0, st>>>(g, dLdg, d, dLdphi);
+    return cudaGetLastError();
+}
+
+} // namespace vk

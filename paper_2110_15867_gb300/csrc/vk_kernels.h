@@ -173,6 +173,39 @@ struct GridDims {
     double L, V;
 };
 
+// ----------------------------------------------------------------------------
+// adjoint sweep (reverse mode, FP32 / FP64 storage): one thread per line
+// ----------------------------------------------------------------------------
+// f viewed as [O][L][I]; line t = (outer t / I, inner t % I).  Constants as in
+// the forward sweep: coef_mode 0 = table[(inner / vstride) % nvel] (position),
+// 1 = cell_coef[outer / outer_per_cell] (velocity).  lam_in = dL/df_out and
+// lam_out = dL/df_in (the same array unless a position line shifts whole cells).
+template <typename C> struct AdjArgs {
+    int L;
+    int periodic;
+    long long n_inner, n_outer, nlines;
+    long long vstride;
+    int nvel;
+    int coef_mode;
+    long long outer_per_cell;
+    const LineCoefT<C> *cell_coef;
+    unsigned *err;
+    const void *f_in;
+    const void *lam_in;
+    void *lam_out;
+    double *dLdg;             // velocity sweeps: dL/dg per spatial cell (may be null)
+    long long lines_per_cell; // velocity sweeps: cell = t / lines_per_cell
+    double dnu_dg;            // -dt / du
+    LineCoefT<C> table[kMaxVel];
+};
+
+// rows = true: u_z lines of 8, 16 or 32 cells, one row per thread in registers (FP32: dtype 1)
+bool adjoint_rows_supported(int L, int dtype);
+cudaError_t launch_adjoint_f32(const AdjArgs<float> &a, bool rows, cudaStream_t st);
+cudaError_t launch_adjoint_f64(const AdjArgs<double> &a, bool rows, cudaStream_t st);
+// dL/dphi += G_d^T dL/dg (FP64, nx*ny*nz)
+cudaError_t launch_gradient_adjoint(const GridDims &g, const double *dLdg, int d, double *dLdphi, cudaStream_t st);
+
 // For each axis d with bit d set in mask: coef[d][cell] for a velocity sweep
 // of length dt from the 4th-order gradient of phi (FP32, nx*ny*nz).
 cudaError_t launch_velocity_coef(const GridDims &g, const float *phi, double dt, int mask,

@@ -72,6 +72,11 @@ struct vlasov_ctx {
     double *d_rho;
     double *d_mass;
     PoissonScratch ps;
+    // adjoint scratch, allocated on first use: the inputs of sweeps 1..8 of a
+    // step, dL/dg per velocity axis, lambda of a whole-cell-shift position sweep
+    void *d_rec[8];
+    double *d_dLdg;
+    void *d_lam_tmp;
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
     // per-part timers
@@ -325,6 +330,9 @@ static void free_scratch(vlasov_ctx *c)
     cudaFree(c->ps.z0);
     cudaFree(c->ps.z1);
     for (int d = 0; d < 3; ++d) cudaFree(c->ps.tw[d]);
+    for (int k = 0; k < 8; ++k) cudaFree(c->d_rec[k]);
+    cudaFree(c->d_dLdg);
+    cudaFree(c->d_lam_tmp);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -464,6 +472,19 @@ extern "C" int vlasov_set_stream(vlasov_ctx *c, void *stream)
     if (!c) return VLASOV_EINVAL;
     c->stream = (cudaStream_t)stream;
     return VLASOV_OK;
+}
+
+extern "C" int vlasov_set_f(vlasov_ctx *c, void *f_dev, float *scale_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!f_dev || reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(c, VLASOV_EINVAL, "vlasov_set_f: f_dev must be 16-byte aligned");
+    const bool coded = c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16;
+    if (coded != (scale_dev != nullptr) || (scale_dev && reinterpret_cast<uintptr_t>(scale_dev) % 16))
+        return fail(c, VLASOV_EINVAL, "vlasov_set_f: scale_dev must be a 16-byte aligned array exactly for 16-bit storage");
+    if (f_dev == c->f && scale_dev == c->scale) return VLASOV_OK;
+    c->f = f_dev;
+    c->scale = scale_dev;
+    return plan_axes(c); // re-encode the tensor maps for the new arrays
 }
 
 template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlasov_ctx *c, int ax)
@@ -698,6 +719,172 @@ extern "C" int vlasov_status(vlasov_ctx *c)
 }
 
 extern "C" const char *vlasov_last_error(const vlasov_ctx *c) { return c ? c->msg : g_init_error; }
+
+// ----------------------------------------------------------------------------
+// adjoint (reverse mode) of the sweeps and of the step
+// ----------------------------------------------------------------------------
+static size_t f_bytes(const vlasov_ctx *c) { return (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es; }
+
+static int ensure_buffer(vlasov_ctx *c, void **p, size_t bytes)
+{
+    if (*p) return VLASOV_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, VLASOV_ENOMEM, "adjoint scratch allocation of %zu bytes failed", bytes);
+    }
+    return VLASOV_OK;
+}
+
+// lam <- (dD_axis/df)^T lam at the sweep input f_in.  Velocity sweeps read the
+// constants in d_coef[axis - 3] (prepared for the same phi and dt) and add
+// dL/dg to dLdg (ncell FP64, may be null).
+template <typename C>
+static int run_adjoint_t(vlasov_ctx *c, const void *f_in, void *lam, int ax, double dt, double a, double *dLdg)
+{
+    const long long d6[6] = {c->g.nx, c->g.ny, c->g.nz, c->g.nux, c->g.nuy, c->g.nuz};
+    long long I = 1, O = 1;
+    for (int k = ax + 1; k < 6; ++k) I *= d6[k];
+    for (int k = 0; k < ax; ++k) O *= d6[k];
+    AdjArgs<C> A{};
+    A.L = int(d6[ax]);
+    A.periodic = ax < 3;
+    A.n_inner = I;
+    A.n_outer = O;
+    A.nlines = I * O;
+    A.err = c->d_err;
+    A.f_in = f_in;
+    A.lam_in = lam;
+    A.lam_out = lam;
+    bool shifted = false;
+    if (ax < 3) {
+        if (!(a > 0) || !isfinite(dt) || !isfinite(a)) return fail(c, VLASOV_EINVAL, "adjoint sweep %d: need finite dt and a > 0", ax);
+        const int nvel = (&c->g.nux)[ax];
+        const double du = 2.0 * c->g.V / nvel;
+        const double dx = c->g.L / (&c->g.nx)[ax];
+        long long vstride = 1;
+        for (int k = ax + 1; k < 3; ++k) vstride *= (&c->g.nux)[k];
+        A.vstride = vstride;
+        A.nvel = nvel;
+        A.coef_mode = 0;
+        A.outer_per_cell = 1;
+        for (int j = 0; j < nvel; ++j) {
+            const double nu = (-c->g.V + (j + 0.5) * du) * dt / (a * a * dx);
+            A.table[j] = make_line_coef<C>(nu);
+            shifted = shifted || fabs(nu) >= 1.0;
+        }
+        if (shifted) {
+            // lambda is read N cells on: write the result to scratch, then copy back
+            int rc = ensure_buffer(c, &c->d_lam_tmp, f_bytes(c));
+            if (rc) return rc;
+            A.lam_out = c->d_lam_tmp;
+        }
+    } else {
+        const long long opc = O / c->ncell;
+        A.vstride = 1;
+        A.nvel = 0;
+        A.coef_mode = 1;
+        A.outer_per_cell = opc;
+        A.cell_coef = (const LineCoefT<C> *)c->d_coef[ax - 3];
+        A.dLdg = dLdg;
+        A.lines_per_cell = opc * I;
+        A.dnu_dg = -dt / (2.0 * c->g.V / (&c->g.nux)[ax - 3]);
+    }
+    const bool rows = ax == 5 && adjoint_rows_supported(A.L, c->g.dtype);
+    if (rows) A.outer_per_cell = A.lines_per_cell; // one row per line: cell = row / rows per cell
+    cudaError_t e;
+    {
+        PartTimer t(c, VLASOV_T_ADJ_X + ax, 1);
+        if constexpr (sizeof(C) == 8) e = launch_adjoint_f64(A, rows, c->stream);
+        else e = launch_adjoint_f32(A, rows, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint sweep launch");
+    if (shifted) VK_CUDA(c, cudaMemcpyAsync(lam, c->d_lam_tmp, f_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    return VLASOV_OK;
+}
+
+static int run_adjoint(vlasov_ctx *c, const void *f_in, void *lam, int ax, double dt, double a, double *dLdg)
+{
+    if (c->g.dtype == VLASOV_F64) return run_adjoint_t<double>(c, f_in, lam, ax, dt, a, dLdg);
+    return run_adjoint_t<float>(c, f_in, lam, ax, dt, a, dLdg);
+}
+
+static int check_adjoint_args(vlasov_ctx *c, const void *f, const void *lam, const char *who)
+{
+    if (c->g.dtype != VLASOV_F32 && c->g.dtype != VLASOV_F64)
+        return fail(c, VLASOV_EINVAL, "%s: FP32 or FP64 storage only", who);
+    if (!f || !lam || reinterpret_cast<uintptr_t>(f) % 16 || reinterpret_cast<uintptr_t>(lam) % 16)
+        return fail(c, VLASOV_EINVAL, "%s: f and lambda must be non-null and 16-byte aligned", who);
+    if (f == lam) return fail(c, VLASOV_EINVAL, "%s: f and lambda must be different arrays", who);
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_sweep_adjoint(vlasov_ctx *c, const void *f_in_dev, void *lam_dev, int axis, double dt, double a,
+                                    const float *phi_dev, double *dLdg_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (axis < 0 || axis > 5) return fail(c, VLASOV_EINVAL, "axis %d outside 0..5", axis);
+    int rc = check_adjoint_args(c, f_in_dev, lam_dev, "vlasov_sweep_adjoint");
+    if (rc) return rc;
+    if (axis >= 3 && (rc = prep_velocity(c, phi_dev, dt, 1 << (axis - 3)))) return rc;
+    return run_adjoint(c, f_in_dev, lam_dev, axis, dt, a, axis >= 3 ? dLdg_dev : nullptr);
+}
+
+// point the plans at another array of the same shape (host work only)
+static int repoint(vlasov_ctx *c, void *f)
+{
+    if (c->f == f) return VLASOV_OK;
+    c->f = f;
+    return plan_axes(c);
+}
+
+extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam_dev, double dt, double a_half,
+                                   const float *phi_dev, double *dLdphi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint");
+    if (rc) return rc;
+    if (!phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint: phi_dev is NULL");
+    const size_t bytes = f_bytes(c);
+    for (int k = 0; k < 8 && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
+    if (!rc && dLdphi_dev) rc = ensure_buffer(c, (void **)&c->d_dLdg, sizeof(double) * 3 * c->ncell);
+    if (rc) return rc;
+    // sweeps of one step, Eq. 5: kick u_x, u_y, u_z (dt/2), drift z, y, x (dt), kick (dt/2)
+    const int axes[9] = {3, 4, 5, 2, 1, 0, 3, 4, 5};
+    const double dts[9] = {0.5 * dt, 0.5 * dt, 0.5 * dt, dt, dt, dt, 0.5 * dt, 0.5 * dt, 0.5 * dt};
+    // forward again from f_n, keeping the input of every sweep: rec[k] = input of sweep k + 1
+    void *const f_own = c->f;
+    if ((rc = prep_velocity(c, phi_dev, 0.5 * dt, 7))) return rc;
+    for (int k = 0; k < 8 && !rc; ++k) {
+        {
+            PartTimer t(c, VLASOV_T_COPY, 0);
+            const cudaError_t e = cudaMemcpyAsync(c->d_rec[k], k == 0 ? f_n_dev : c->d_rec[k - 1], bytes,
+                                                  cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "record copy");
+        }
+        if (!rc) rc = repoint(c, c->d_rec[k]);
+        if (!rc) rc = axes[k] >= 3 ? run_velocity(c, axes[k]) : run_position(c, axes[k], dts[k], a_half);
+    }
+    const int rc2 = repoint(c, f_own);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    // reverse: the nine adjoint sweeps, last sweep first (the kick constants are still in d_coef)
+    if (dLdphi_dev) VK_CUDA(c, cudaMemsetAsync(c->d_dLdg, 0, sizeof(double) * 3 * c->ncell, c->stream));
+    for (int k = 8; k >= 0; --k) {
+        const int ax = axes[k];
+        const void *in = k == 0 ? f_n_dev : c->d_rec[k - 1];
+        double *dLdg = (ax >= 3 && dLdphi_dev) ? c->d_dLdg + (ax - 3) * c->ncell : nullptr;
+        if ((rc = run_adjoint(c, in, lam_dev, ax, dts[k], a_half, dLdg))) return rc;
+    }
+    if (dLdphi_dev) {
+        PartTimer t(c, VLASOV_T_GRAD_ADJ, 3);
+        for (int d = 0; d < 3; ++d) {
+            const cudaError_t e = launch_gradient_adjoint(c->gd, c->d_dLdg + d * c->ncell, d, dLdphi_dev, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "gradient adjoint launch");
+        }
+    }
+    return VLASOV_OK;
+}
 
 // ----------------------------------------------------------------------------
 // velocity sweep without allocation (vlasov_sweep_velocity_static)

@@ -1,0 +1,200 @@
+"""Parity of the CUDA adjoint (reverse mode of the sweeps and of one Eq. (5) step,
+through the C ABI) with the oracle's adjoint, itself pinned by finite differences and
+the dot-product identity (tests/test_oracle_adjoint.py).
+
+Tolerances.  FP64 storage: the GPU takes the oracle's limiter branches (ties need a
+difference below 1e-16 relative), so lambda agrees to rounding: relative L1 <= 1e-12,
+L_inf <= 1e-10 of max |lambda|, dL/dg and dL/dphi to 1e-10 of their largest entry.
+FP32 storage: arithmetic in FP32 against the FP64 oracle on the same FP32 input.
+Where the forward sits within FP32 rounding of a limiter switch the two sides may take
+different branches (and over a step the FP32 forward states drift from the FP64 ones
+by rounding, so more faces sit near a switch); each such face moves a few entries by
+O(|lambda|).  So at most 2e-4 of the entries may be off by more than 1e-3 of
+max |lambda|, and the others must agree to FP32 rounding: relative L1 <= 1e-6 over
+them.  The measured values are printed.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_15867_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    from paper_2110_15867_gb300 import binding as B
+    B.load()
+    return B
+
+
+def _setup(n, nu, V=5.0, seed=1, rms=0.01, dtype=np.float32):
+    Fu = I.fermi_dirac(nu, V)
+    delta = I.gaussian_field(n, rms, seed=seed)
+    f0 = I.initial_f(delta, Fu, dtype)
+    phi = I.fourier_potential(n, seed=seed + 10).astype(np.float32)
+    lam = np.random.default_rng(seed + 20).standard_normal(f0.shape).astype(dtype)
+    return f0, phi, lam
+
+
+def _dt_for(g, axis, phi, cfl, a=1.0):
+    return cfl / O.max_abs_nu(g, axis, 1.0, a, phi.astype(np.float64))
+
+
+def _dt_step(g, phi, cfl, a=1.0):
+    # kicks advance dt / 2, the drift dt
+    m = max([O.max_abs_nu(g, ax, 0.5, a, phi.astype(np.float64)) for ax in (3, 4, 5)] +
+            [O.max_abs_nu(g, ax, 1.0, a, phi.astype(np.float64)) for ax in (0, 1, 2)])
+    return cfl / m
+
+
+def _compare(gpu, ref, fp64, what=""):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    err = np.abs(gpu - ref)
+    scale = np.abs(ref).max()
+    rl1 = err.sum() / np.abs(ref).sum()
+    rinf = err.max() / scale
+    off = err > 1e-3 * scale
+    bad = np.count_nonzero(off) / err.size
+    rl1_on = err[~off].sum() / np.abs(ref[~off]).sum()
+    print("%s rel L1 %.2e  rel Linf %.2e  off-branch fraction %.2e  rel L1 on-branch %.2e"
+          % (what, rl1, rinf, bad, rl1_on))
+    if fp64:
+        assert rl1 <= 1e-12 and rinf <= 1e-10, (rl1, rinf)
+    else:
+        assert bad <= 2e-4 and rl1_on <= 1e-6, (rl1, rinf, bad, rl1_on)
+
+
+def _compare_field(gpu, ref, fp64, what=""):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    rel = np.abs(gpu - ref).max() / np.abs(ref).max()
+    rl2 = np.linalg.norm(gpu - ref) / np.linalg.norm(ref)
+    print("%s rel Linf %.2e  rel L2 %.2e" % (what, rel, rl2))
+    if fp64:
+        assert rel <= 1e-10, rel
+    else:
+        assert rl2 <= 1e-3, rl2
+
+
+SHAPES = [
+    ((16, 16, 16), (16, 16, 16)),   # u_z lines of 16 in registers
+    ((6, 5, 7), (8, 20, 12)),       # ragged; u_z lines of 12 through the column march
+    ((4, 5, 8), (4, 8, 32)),        # periodic lines of 4 and 5; u_x lines of 4; u_z rows of 32
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("n,nu", SHAPES)
+@pytest.mark.parametrize("axis", [0, 1, 2, 3, 4, 5])
+def test_sweep_adjoint(n, nu, axis, dtype):
+    B = _lib()
+    f0, phi, lam0 = _setup(n, nu, dtype=dtype)
+    g = O.grid(n, nu, V=5.0)
+    a = 1.0
+    dt = _dt_for(g, axis, phi, 0.8, a)
+    lam_ref = lam0.astype(np.float64)
+    dLdg_ref = O.sweep_adjoint(g, f0.astype(np.float64), lam_ref, axis, dt, a, phi.astype(np.float64))
+    dev = torch.device("cuda")
+    f_in = torch.from_numpy(f0).to(dev)
+    lam = torch.from_numpy(lam0).to(dev)
+    own = torch.zeros_like(f_in)
+    v = B.Vlasov(own, L=1.0, V=5.0)
+    dLdg = torch.zeros(n, dtype=torch.float64, device=dev) if axis >= 3 else None
+    v.sweep_adjoint(f_in, lam, axis, dt, a, torch.from_numpy(phi).to(dev), dLdg)
+    v.status()
+    fp64 = dtype == np.float64
+    _compare(lam.cpu().numpy(), lam_ref, fp64, "axis %d lambda" % axis)
+    if axis >= 3:
+        _compare_field(dLdg.cpu().numpy(), dLdg_ref, fp64, "axis %d dL/dg" % axis)
+    assert torch.equal(f_in.cpu(), torch.from_numpy(f0))  # the sweep input is read only
+    v.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep_adjoint_whole_cell_shift(axis, dtype):
+    # |nu| up to 2.6: the forward shifts whole cells after the fractional update
+    B = _lib()
+    n, nu = (8, 6, 10), (8, 8, 12)
+    f0, phi, lam0 = _setup(n, nu, dtype=dtype)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_for(g, axis, phi, 2.6)
+    lam_ref = lam0.astype(np.float64)
+    O.sweep_adjoint(g, f0.astype(np.float64), lam_ref, axis, dt, 1.0)
+    f_in = torch.from_numpy(f0).cuda()
+    lam = torch.from_numpy(lam0).cuda()
+    v = B.Vlasov(torch.zeros_like(f_in), V=5.0)
+    v.sweep_adjoint(f_in, lam, axis, dt, 1.0)
+    v.status()
+    _compare(lam.cpu().numpy(), lam_ref, dtype == np.float64, "axis %d shift lambda" % axis)
+    v.close()
+
+
+@pytest.mark.parametrize("n,nu", [((8, 8, 8), (8, 8, 8)), ((4, 6, 5), (12, 8, 16))])
+def test_step_adjoint_fp64(n, nu):
+    B = _lib()
+    f0, phi, lam0 = _setup(n, nu, dtype=np.float64)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_step(g, phi, 0.8)
+    a_half = 1.0
+    lam_ref = lam0.copy()
+    dphi_ref = O.step_adjoint(g, f0, lam_ref, dt, a_half, phi.astype(np.float64))
+    f_n = torch.from_numpy(f0).cuda()
+    lam = torch.from_numpy(lam0).cuda()
+    own = torch.from_numpy(f0 * 0.5).cuda()
+    own_before = own.clone()
+    v = B.Vlasov(own, V=5.0)
+    dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    v.step_adjoint(f_n, lam, dt, a_half, torch.from_numpy(phi).cuda(), dphi)
+    v.status()
+    _compare(lam.cpu().numpy(), lam_ref, True, "step lambda")
+    _compare_field(dphi.cpu().numpy(), dphi_ref, True, "step dL/dphi")
+    assert torch.equal(own, own_before)  # the context's own f is untouched
+    # a second call reuses the scratch and accumulates into dL/dphi
+    lam2 = torch.from_numpy(lam0).cuda()
+    v.step_adjoint(f_n, lam2, dt, a_half, torch.from_numpy(phi).cuda(), dphi)
+    v.status()
+    assert torch.equal(lam2, lam)
+    _compare_field(dphi.cpu().numpy(), 2 * dphi_ref, True, "step dL/dphi twice")
+    v.close()
+
+
+def test_step_adjoint_fp32():
+    B = _lib()
+    n, nu = (16, 16, 16), (16, 16, 16)
+    f0, phi, lam0 = _setup(n, nu)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_step(g, phi, 0.8)
+    lam_ref = lam0.astype(np.float64)
+    dphi_ref = O.step_adjoint(g, f0.astype(np.float64), lam_ref, dt, 1.0, phi.astype(np.float64))
+    f_n = torch.from_numpy(f0).cuda()
+    lam = torch.from_numpy(lam0).cuda()
+    v = B.Vlasov(torch.zeros_like(f_n), V=5.0)
+    dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    v.step_adjoint(f_n, lam, dt, 1.0, torch.from_numpy(phi).cuda(), dphi)
+    v.status()
+    _compare(lam.cpu().numpy(), lam_ref, False, "step lambda")
+    _compare_field(dphi.cpu().numpy(), dphi_ref, False, "step dL/dphi")
+    v.close()
+
+
+def test_adjoint_argument_errors():
+    B = _lib()
+    n, nu = (8, 8, 8), (8, 8, 16)
+    f0, phi, lam0 = _setup(n, nu)
+    f = torch.from_numpy(f0).cuda()
+    v = B.Vlasov(f, V=5.0)
+    with pytest.raises(B.VlasovError) as e:
+        v.sweep_adjoint(f, f, 0, 0.01)        # lambda aliases the input
+    assert e.value.code == B.EINVAL
+    with pytest.raises(B.VlasovError) as e:
+        v.sweep_adjoint(f, torch.from_numpy(lam0).cuda(), 3, 0.01)  # velocity sweep without phi
+    assert e.value.code == B.EINVAL
+    v.close()
+    codes, scale = B.encode_lines(f, torch.bfloat16)
+    vb = B.Vlasov(codes, V=5.0, scale=scale)
+    with pytest.raises(B.VlasovError) as e:
+        vb.sweep_adjoint(codes, codes.clone(), 0, 0.01)  # 16-bit storage has no adjoint
+    assert e.value.code == B.EINVAL
+    vb.close()
