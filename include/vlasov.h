@@ -152,7 +152,7 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
 #define VLASOV_T_MASS 9
 #define VLASOV_T_ADJ_X 10     /* kinds 10..15: adjoint sweeps along x, y, z, u_x, u_y, u_z */
 #define VLASOV_T_GRAD_ADJ 16  /* transposed potential gradient of the step adjoint   */
-#define VLASOV_T_COPY 17      /* copies of the step adjoint's sweep inputs (no kernel) */
+#define VLASOV_T_MOMENT_ADJ 17 /* moment adjoint                                      */
 #define VLASOV_T_KINDS 18
 int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
@@ -211,15 +211,42 @@ int vlasov_sweep_adjoint(vlasov_ctx *ctx, const void *f_in_dev, void *lam_dev, i
                          double a, const float *phi_dev, double *dLdg_dev);
 
 /*
+ * Adjoint of vlasov_moment: rho_nu(x) = du_x du_y du_z sum_u f(x, u), so
+ * lam_dev(x, u) receives du_x du_y du_z * dLdrho_dev(x) for every u (added
+ * to its contents when accumulate != 0, else written).  dLdrho_dev is
+ * nx*ny*nz FP64; lam_dev has f's layout and storage type (FP32 / FP64 only).
+ */
+int vlasov_moment_adjoint(vlasov_ctx *ctx, const double *dLdrho_dev, void *lam_dev, int accumulate);
+
+/*
+ * One vlasov_step with an external potential (both kicks use phi_dev, the
+ * drift uses a_half), run out of place so that the input of every sweep is
+ * kept: rec_dev is a HOST array of 8 device arrays the size of f, and
+ * rec_dev[k] receives the input of sweep k + 1 (sweep 0 reads f_n_dev, which
+ * is not changed).  f_next_dev (may be NULL) receives the step's result.
+ * ctx's own array f is neither read nor changed.  Each sweep reads one array
+ * and writes the next, so recording costs no copies.
+ */
+int vlasov_step_record(vlasov_ctx *ctx, const void *f_n_dev, void *const *rec_dev, void *f_next_dev,
+                       double dt, double a_half, const float *phi_dev);
+
+/*
  * Adjoint of one vlasov_step with an external potential (phi_next_dev NULL:
- * both kicks use phi_dev, the drift uses a_half).  f_n_dev is the state at the
- * start of the step (read only); lam_dev holds dL/df^{n+1} on entry and
- * dL/df^n on exit.  The step is run forward again from f_n, keeping the
- * input of each of its nine sweeps (eight scratch arrays the size of f,
- * allocated on the first call and kept until vlasov_destroy); the nine
- * adjoint sweeps then run last to first.  If dLdphi_dev (nx*ny*nz FP64) is
- * non-NULL, dL/dphi is ADDED to it through the transposed 4th-order gradient.
- * ctx's own array f is neither read nor changed.
+ * both kicks use phi_dev, the drift uses a_half), from the sweep inputs that
+ * vlasov_step_record kept (rec_dev as there, read only).  f_n_dev is the state
+ * at the start of the step (read only); lam_dev holds dL/df^{n+1} on entry
+ * and dL/df^n on exit.  The nine adjoint sweeps run last to first.  If
+ * dLdphi_dev (nx*ny*nz FP64) is non-NULL, dL/dphi is ADDED to it: each
+ * velocity sweep's dL/dg_i goes through the transposed 4th-order gradient.
+ */
+int vlasov_step_adjoint_recorded(vlasov_ctx *ctx, const void *f_n_dev, const void *const *rec_dev,
+                                 void *lam_dev, double dt, double a_half, const float *phi_dev,
+                                 double *dLdphi_dev);
+
+/*
+ * vlasov_step_record into eight scratch arrays the size of f (allocated on
+ * the first call, kept until vlasov_destroy) followed by
+ * vlasov_step_adjoint_recorded.  Arguments as there.
  */
 int vlasov_step_adjoint(vlasov_ctx *ctx, const void *f_n_dev, void *lam_dev, double dt, double a_half,
                         const float *phi_dev, double *dLdphi_dev);

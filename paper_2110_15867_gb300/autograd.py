@@ -1,0 +1,92 @@
+"""Reverse mode of a run of Eq. (5) steps as a ``torch.autograd.Function``.
+
+``VlasovRun.apply(f0, phi, run, dt, a_half, n_steps, K)`` advances ``f0`` by
+``n_steps`` steps with the external potential ``phi`` (both kicks use phi, the
+drift uses ``a_half``) and returns the density rho_nu(x) (FP64) of the final state.
+Its backward gives dL/df0 and dL/dphi for any loss of rho_nu.
+
+Memory: the forward keeps the state every K steps (checkpoints).  The backward
+takes the segments last to first: it runs the segment's steps again from its
+checkpoint with ``vlasov_step_record`` (each sweep writes the next record, so
+recording costs no copies), then applies ``vlasov_step_adjoint_recorded`` step by
+step in reverse.  The tape holds 8 K + K - 1 arrays the size of f and is reused.
+
+Every operation on f or lambda runs in libvlasov's kernels through the C ABI; this
+module only orders the calls and owns the buffers.
+"""
+from __future__ import annotations
+
+import torch
+
+from .binding import Vlasov
+
+
+class Run:
+    """A context and the buffers of one grid: the working state and the tape."""
+
+    def __init__(self, shape, dtype=torch.float32, device="cuda", L: float = 1.0, V: float = 5.0):
+        self.shape = tuple(shape)
+        self.work = torch.empty(self.shape, dtype=dtype, device=device)
+        self.v = Vlasov(self.work, L=L, V=V)
+        self._rec = []
+        self._states = []
+
+    def tape(self, K: int):
+        """Records for K steps (8 arrays each) and K - 1 intermediate states."""
+        while len(self._rec) < K:
+            self._rec.append([torch.empty_like(self.work) for _ in range(8)])
+        while len(self._states) < K - 1:
+            self._states.append(torch.empty_like(self.work))
+        return self._rec, self._states
+
+    def release_tape(self):
+        self._rec, self._states = [], []
+
+    def close(self):
+        self.release_tape()
+        self.v.close()
+
+
+class VlasovRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f0, phi, run: Run, dt: float, a_half: float, n_steps: int, K: int = 4):
+        if K < 1 or n_steps < 1:
+            raise ValueError("need n_steps >= 1 and K >= 1")
+        phi32 = phi.detach().to(torch.float32).contiguous()
+        run.work.copy_(f0.detach())
+        checkpoints = []
+        for n in range(n_steps):
+            if n > 0 and n % K == 0:
+                checkpoints.append(run.work.clone())
+            run.v.step(dt, a_half, a_half, phi32)
+        rho = run.v.moment()
+        ctx.save_for_backward(f0, phi)
+        ctx.checkpoints = checkpoints
+        ctx.run, ctx.dt, ctx.a_half, ctx.n_steps, ctx.K = run, dt, a_half, n_steps, K
+        return rho
+
+    @staticmethod
+    def backward(ctx, grad_rho):
+        f0, phi = ctx.saved_tensors
+        run, dt, a_half, n_steps, K = ctx.run, ctx.dt, ctx.a_half, ctx.n_steps, ctx.K
+        v = run.v
+        phi32 = phi.detach().to(torch.float32).contiguous()
+        lam = torch.empty_like(run.work)
+        v.moment_adjoint(grad_rho.detach().to(torch.float64).contiguous(), lam)
+        dphi = torch.zeros(phi32.shape, dtype=torch.float64, device=phi32.device)
+        starts = [f0.detach().contiguous()] + ctx.checkpoints
+        rec, states = run.tape(min(K, n_steps))
+        for s in reversed(range(len(starts))):
+            m = min(K, n_steps - s * K)
+            seq = [starts[s]] + states[:m - 1]
+            for i in range(m):
+                v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else None)
+            for i in reversed(range(m)):
+                v.step_adjoint_recorded(seq[i], rec[i], lam, dt, a_half, phi32, dphi)
+        ctx.checkpoints = None
+        return lam, dphi.to(phi.dtype), None, None, None, None, None
+
+
+def run_rho(f0, phi, run: Run, dt: float, a_half: float, n_steps: int, K: int = 4):
+    """rho_nu after n_steps steps from f0 under phi, differentiable in f0 and phi."""
+    return VlasovRun.apply(f0, phi, run, dt, a_half, n_steps, K)

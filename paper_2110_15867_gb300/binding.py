@@ -43,7 +43,8 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_poisson", "vlasov_step", "vlasov_upload", "vlasov_download",
            "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
-           "vlasov_step_adjoint")
+           "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
+           "vlasov_moment_adjoint")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -51,7 +52,7 @@ STATIC_MAX_CELLS = 32768
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
            "poisson", "coef", "mass", "adj_x", "adj_y", "adj_z", "adj_ux", "adj_uy", "adj_uz",
-           "grad_adj", "copy")
+           "grad_adj", "moment_adj")
 
 
 def library_path() -> str:
@@ -105,6 +106,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_sweep_adjoint.restype = ctypes.c_int
     L.vlasov_step_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]
     L.vlasov_step_adjoint.restype = ctypes.c_int
+    L.vlasov_step_record.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP]
+    L.vlasov_step_record.restype = ctypes.c_int
+    L.vlasov_step_adjoint_recorded.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                               _VP, _VP]
+    L.vlasov_step_adjoint_recorded.restype = ctypes.c_int
+    L.vlasov_moment_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_int]
+    L.vlasov_moment_adjoint.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -154,6 +162,29 @@ def vlasov_step_adjoint(ctx, f_n_ptr: int, lam_ptr: int, dt: float, a_half: floa
                         dLdphi_ptr):
     return _check(ctx, load().vlasov_step_adjoint(ctx, f_n_ptr, lam_ptr, dt, a_half, phi_ptr,
                                                   dLdphi_ptr))
+
+
+def _ptr_array(ptrs):
+    arr = (_VP * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+def vlasov_step_record(ctx, f_n_ptr: int, rec_ptrs, f_next_ptr, dt: float, a_half: float, phi_ptr):
+    """rec_ptrs: 8 device pointers (inputs of sweeps 1..8 of the step)."""
+    return _check(ctx, load().vlasov_step_record(ctx, f_n_ptr, _ptr_array(rec_ptrs), f_next_ptr, dt,
+                                                 a_half, phi_ptr))
+
+
+def vlasov_step_adjoint_recorded(ctx, f_n_ptr: int, rec_ptrs, lam_ptr: int, dt: float, a_half: float,
+                                 phi_ptr, dLdphi_ptr):
+    return _check(ctx, load().vlasov_step_adjoint_recorded(ctx, f_n_ptr, _ptr_array(rec_ptrs), lam_ptr,
+                                                           dt, a_half, phi_ptr, dLdphi_ptr))
+
+
+def vlasov_moment_adjoint(ctx, dLdrho_ptr: int, lam_ptr: int, accumulate: bool = False):
+    return _check(ctx, load().vlasov_moment_adjoint(ctx, dLdrho_ptr, lam_ptr, int(bool(accumulate))))
 
 
 def vlasov_sweep(ctx, axis: int, dt: float, a: float, phi_ptr):
@@ -342,6 +373,35 @@ class Vlasov:
                             self._like_f(lam, "lam").data_ptr(), dt, a_half,
                             _ptr(self._field(phi, self.torch.float32)),
                             _ptr(self._field(dLdphi, self.torch.float64)))
+
+    def step_record(self, f_n, rec, dt: float, a_half: float, phi, f_next=None):
+        """Run one external-potential step from f_n out of place, keeping the input of
+        every sweep: rec is a list of 8 tensors like f; f_next (optional) receives
+        the result."""
+        if len(rec) != 8:
+            raise ValueError("rec must hold 8 tensors")
+        self._sync_stream()
+        vlasov_step_record(self.ctx, self._like_f(f_n, "f_n").data_ptr(),
+                           [self._like_f(r, "rec").data_ptr() for r in rec],
+                           None if f_next is None else self._like_f(f_next, "f_next").data_ptr(),
+                           dt, a_half, _ptr(self._field(phi, self.torch.float32)))
+
+    def step_adjoint_recorded(self, f_n, rec, lam, dt: float, a_half: float, phi, dLdphi=None):
+        """lam <- (d step/df at f_n)^T lam from the sweep inputs step_record kept."""
+        if len(rec) != 8:
+            raise ValueError("rec must hold 8 tensors")
+        self._sync_stream()
+        vlasov_step_adjoint_recorded(self.ctx, self._like_f(f_n, "f_n").data_ptr(),
+                                     [self._like_f(r, "rec").data_ptr() for r in rec],
+                                     self._like_f(lam, "lam").data_ptr(), dt, a_half,
+                                     _ptr(self._field(phi, self.torch.float32)),
+                                     _ptr(self._field(dLdphi, self.torch.float64)))
+
+    def moment_adjoint(self, dLdrho, lam, accumulate: bool = False):
+        """lam (+)= du^3 dL/drho(x) broadcast over each velocity cube."""
+        self._sync_stream()
+        vlasov_moment_adjoint(self.ctx, self._field(dLdrho, self.torch.float64).data_ptr(),
+                              self._like_f(lam, "lam").data_ptr(), accumulate)
 
     def upload(self, f_host):
         """Copy a host tensor (same shape and dtype as f, ideally pinned) into f."""

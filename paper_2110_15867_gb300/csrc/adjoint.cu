@@ -32,6 +32,13 @@
 namespace vk {
 
 constexpr int kAdjBlock = 256;
+#ifndef VK_ADJ_UNROLL
+#define VK_ADJ_UNROLL 1 // interior faces per loop iteration of the column march
+#endif
+#ifndef VK_ADJ_MINB
+#define VK_ADJ_MINB 3 // resident blocks per SM the FP32 column march is compiled for
+#endif
+constexpr int kAdjUnroll = VK_ADJ_UNROLL;
 
 template <typename C> struct AdjLim {
     C w[5];  // weights of fbar
@@ -39,24 +46,25 @@ template <typename C> struct AdjLim {
     C s, alpha, dalpha;
 };
 
+// in the working precision C (FP64 costs 64 FP32 operations each on this part)
 template <typename C> __device__ __forceinline__ AdjLim<C> make_adj_lim(const LineCoefT<C> &k)
 {
     AdjLim<C> a;
-    const double s = (double)k.s;
-    const double K2[5] = {0.0, -1.0 / 24, 5.0 / 8, -5.0 / 8, 1.0 / 24};
-    const double K3[5] = {-1.0 / 24, 1.0 / 4, -1.0 / 3, 1.0 / 12, 1.0 / 24};
-    const double K4[5] = {0.0, 1.0 / 24, -1.0 / 8, 1.0 / 8, -1.0 / 24};
-    const double K5[5] = {1.0 / 120, -1.0 / 30, 1.0 / 20, -1.0 / 30, 1.0 / 120};
+    const C s = k.s;
+    const C K2[5] = {C(0), C(-1.0 / 24), C(5.0 / 8), C(-5.0 / 8), C(1.0 / 24)};
+    const C K3[5] = {C(-1.0 / 24), C(1.0 / 4), C(-1.0 / 3), C(1.0 / 12), C(1.0 / 24)};
+    const C K4[5] = {C(0), C(1.0 / 24), C(-1.0 / 8), C(1.0 / 8), C(-1.0 / 24)};
+    const C K5[5] = {C(1.0 / 120), C(-1.0 / 30), C(1.0 / 20), C(-1.0 / 30), C(1.0 / 120)};
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         a.w[m] = k.w[m];
         // d/ds of K1 + K2 s + K3 s^2 + K4 s^3 + K5 s^4
-        a.ws[m] = C(K2[m] + s * (2.0 * K3[m] + s * (3.0 * K4[m] + s * 4.0 * K5[m])));
+        a.ws[m] = K2[m] + s * (C(2) * K3[m] + s * (C(3) * K4[m] + s * C(4) * K5[m]));
     }
-    a.s = k.s;
+    a.s = s;
     a.alpha = k.alpha;
     // alpha = (1 - s) / s below its cap of 1e6: d alpha / ds = -1 / s^2
-    a.dalpha = (s > 0.0 && (1.0 - s) / s < 1e6) ? C(-1.0 / (s * s)) : C(0);
+    a.dalpha = (s > C(0) && k.alpha < C(1e6)) ? -(a.alpha + C(1)) * (a.alpha + C(1)) : C(0);
     return a;
 }
 
@@ -151,14 +159,41 @@ __device__ __forceinline__ C face_adjoint(const AdjLim<C> &k, C cm2, C cm1, C c0
 // ----------------------------------------------------------------------------
 // the march over one line (local frame: flow toward +index)
 // ----------------------------------------------------------------------------
+// minmod of (4 d0 - d1, 4 d1 - d0, d0, d1) with its partials ka = dr/dd0 and
+// kb = dr/dd1 (the selected argument's; 0 where the minmod is 0)
+template <typename C> __device__ __forceinline__ C dm4_coef(C d0, C d1, C &ka, C &kb)
+{
+    const C a = C(4) * d0 - d1, b = C(4) * d1 - d0;
+    const C lo = mn2(mn3(a, b, d0), d1), hi = mx2(mx3(a, b, d0), d1);
+    const C r = mn2(mx2(lo, C(0)), hi);
+    const bool z = r == C(0), ia = r == a, ib = r == b, i0 = r == d0;
+    ka = z ? C(0) : ia ? C(4) : ib ? C(-1) : i0 ? C(1) : C(0);
+    kb = z ? C(0) : ia ? C(-1) : ib ? C(4) : i0 ? C(0) : C(1);
+    return r;
+}
+
 // Acc supplies, for local indices 0 <= i < n: c(i) the sweep input, lam(i)
 // dL/dc_new (read only before cell i is written) and put(i, v) dL/dc.
+//
+// Per face j the forward value v = clamp(fbar, fmin, fmax) is one of fbar,
+// c0, cp1, f_MD, f_UL, f_LC (the bounds are selections), so its adjoint goes
+// to exactly one of them; it is scattered as one linear combination of the
+// five stencil cells, plus the adjoints of the two limited curvatures dm4 at
+// j -+ 1/2 and of s.  Curvatures and dm4 are shared with the neighbouring
+// faces: each is computed once, its adjoint collects the contributions of
+// every face that uses it and is scattered once (curvature j - 1 after face
+// j, dm4 at j - 1/2 at face j).  The adjoint is linear, so on a periodic line
+// the contributions of the wrap-around faces can be scattered when they come.
 template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     Acc &acc;
     const AdjLim<C> &k;
     int n;
     C cw[5], ow[5], lo[3]; // c and running dL/dc of cells j-2..j+2; original lambda of cells j..j+2
-    C dA, dB, d0, d1;      // periodic: partial sums of cells n-2, n-1 (faces 0, 1) and 0, 1 (faces up to 3)
+    C dm, d0;              // curvatures of cells j-1, j
+    C qm, qam, qbm;        // dm4 at j-1/2 and its partials with respect to (dm, d0)
+    C gq;                  // adjoint of qm from face j-1 (where it was the downwind dm4)
+    C gdm, gd0;            // adjoints of dm, d0 collected so far
+    C pA, pB, p0, p1;      // periodic: partial sums of cells n-2, n-1 (faces 0, 1) and 0, 1 (faces up to 3)
     C dLds, osum;
 
     __device__ __forceinline__ AdjMarch(Acc &a, const AdjLim<C> &kk, int nn) : acc(a), k(kk), n(nn) {}
@@ -190,42 +225,99 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         ow[2] = lo[0];
         ow[3] = lo[1];
         ow[4] = lo[2];
-        dA = dB = d0 = d1 = C(0);
+        dm = cw[0] - C(2) * cw[1] + cw[2];
+        d0 = cw[1] - C(2) * cw[2] + cw[3];
+        qm = dm4_coef(dm, d0, qam, qbm);
+        gq = gdm = gd0 = C(0);
+        pA = pB = p0 = p1 = C(0);
         dLds = osum = C(0);
     }
 
-    __device__ __forceinline__ void face(int j)
+    // INTERIOR: cell j - 2 goes to memory and cell j + 3 (its values cin, lin
+    // already loaded) enters, without any wrap-around or ghost (periodic
+    // 4 <= j <= n - 6; zero-flux 2 <= j <= n - 4)
+    template <bool INTERIOR> __device__ __forceinline__ void face(int j, C cin = C(0), C lin = C(0))
     {
-        C g[5] = {C(0), C(0), C(0), C(0), C(0)};
-        dLds += face_adjoint(k, cw[0], cw[1], cw[2], cw[3], cw[4], lo[1] - lo[0], g);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) ow[q] += g[q];
-        // cell j - 2 leaves the window
-        const int mo = j - 2;
-        if (PERIODIC) {
-            if (mo == -2) dA = ow[0];
-            else if (mo == -1) dB = ow[0];
-            else if (mo == 0) d0 = ow[0];
-            else if (mo == 1) d1 = ow[0];
-            else put(mo, ow[0]);
-        } else if (mo >= 0) {
+        const C cm2 = cw[0], cm1 = cw[1], c0 = cw[2], cp1 = cw[3], cp2 = cw[4];
+        const C gbar = lo[1] - lo[0]; // dL/dF of this face
+        // forward
+        const C dp = c0 - C(2) * cp1 + cp2;
+        C qap, qbp;
+        const C qp = dm4_coef(d0, dp, qap, qbp);
+        const C fbar = k.w[0] * cm2 + k.w[1] * cm1 + k.w[2] * c0 + k.w[3] * cp1 + k.w[4] * cp2;
+        const C dlm = c0 - cm1;
+        const C ful = c0 + k.alpha * dlm;
+        const C fmd = C(0.5) * (c0 + cp1 - qp);
+        const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * qm;
+        const C fmin = mx2(mn3(c0, cp1, fmd), mn3(c0, ful, flc));
+        const C fmax = mn2(mx3(c0, cp1, fmd), mx3(c0, ful, flc));
+        const C v = mn2(mx2(fbar, fmin), fmax);
+        const C sv = k.s * v;
+        // reverse: F = clamp(s v, 0, c0)
+        const bool inr = sv >= C(0) && sv <= c0;
+        const C gv = inr ? k.s * gbar : C(0);
+        const C gpp = sv > c0 ? gbar : C(0);
+        // v's source, first match in the order fbar, c0, cp1, f_MD, f_UL, f_LC
+        const bool isf = v == fbar;
+        const bool e0 = !isf && v == c0;
+        const bool e1 = !isf && !e0 && v == cp1;
+        const bool em = !isf && !e0 && !e1 && v == fmd;
+        const bool eu = !isf && !e0 && !e1 && !em && v == ful;
+        const bool el = !isf && !e0 && !e1 && !em && !eu;
+        const C k0 = isf ? k.w[0] : C(0);
+        const C k4 = isf ? k.w[4] : C(0);
+        const C k1 = isf ? k.w[1] : eu ? -k.alpha : el ? C(-0.5) : C(0);
+        const C k2 = isf ? k.w[2] : e0 ? C(1) : em ? C(0.5) : eu ? C(1) + k.alpha : el ? C(1.5) : C(0);
+        const C k3 = isf ? k.w[3] : e1 ? C(1) : em ? C(0.5) : C(0);
+        const C ks = isf ? (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2)
+                         : eu ? k.dalpha * dlm : C(0);
+        ow[0] += gv * k0;
+        ow[1] += gv * k1;
+        ow[2] += gv * k2 + gpp;
+        ow[3] += gv * k3;
+        ow[4] += gv * k4;
+        dLds += gv * ks + (inr ? v * gbar : C(0));
+        // dm4 at j - 1/2 is complete: scatter to the curvatures of cells j-1, j
+        const C gqm = gq + (el ? C(4.0 / 3.0) * gv : C(0));
+        gdm += gqm * qam;
+        gd0 += gqm * qbm;
+        gq = em ? C(-0.5) * gv : C(0);
+        // the curvature of cell j - 1 is complete: scatter to cells j-2, j-1, j
+        ow[0] += gdm;
+        ow[1] -= C(2) * gdm;
+        ow[2] += gdm;
+        // cell j - 2 leaves, cell j + 3 enters
+        const int mo = j - 2, mi = j + 3;
+        C lnew, cnew, init;
+        if (INTERIOR) {
             put(mo, ow[0]);
-        }
-        // cell j + 3 enters
-        const int mi = j + 3;
-        C lnew = C(0), cnew = C(0), init;
-        if (PERIODIC ? mi < n + 2 : mi < n) {
-            lnew = lget(mi);
-            cnew = cget(mi);
-        }
-        if (PERIODIC) {
-            if (mi == n - 2) init = lnew + dA;
-            else if (mi == n - 1) init = lnew + dB;
-            else if (mi == n) init = d0;
-            else if (mi == n + 1) init = d1;
-            else init = lnew;
-        } else {
+            lnew = lin;
+            cnew = cin;
             init = lnew;
+        } else {
+            if (PERIODIC) {
+                if (mo == -2) pA = ow[0];
+                else if (mo == -1) pB = ow[0];
+                else if (mo == 0) p0 = ow[0];
+                else if (mo == 1) p1 = ow[0];
+                else put(mo, ow[0]);
+            } else if (mo >= 0) {
+                put(mo, ow[0]);
+            }
+            lnew = cnew = C(0);
+            if (PERIODIC ? mi < n + 2 : mi < n) {
+                lnew = lget(mi);
+                cnew = cget(mi);
+            }
+            if (PERIODIC) {
+                if (mi == n - 2) init = lnew + pA;
+                else if (mi == n - 1) init = lnew + pB;
+                else if (mi == n) init = p0;
+                else if (mi == n + 1) init = p1;
+                else init = lnew;
+            } else {
+                init = lnew;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) { ow[q] = ow[q + 1]; cw[q] = cw[q + 1]; }
@@ -234,11 +326,25 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         lo[0] = lo[1];
         lo[1] = lo[2];
         lo[2] = lnew;
+        dm = d0;
+        d0 = dp;
+        qm = qp;
+        qam = qap;
+        qbm = qbp;
+        gdm = gd0;
+        gd0 = C(0);
     }
 
-    // after the last face the window holds cells nf - 2 .. nf + 2
+    // after the last face J the window holds cells J-1 .. J+3; dm, d0 are the
+    // curvatures of cells J, J+1 and qm the downwind dm4 of face J
     __device__ __forceinline__ void end()
     {
+        gdm += gq * qam;
+        gd0 += gq * qbm;
+        ow[0] += gdm;
+        ow[1] += gd0 - C(2) * gdm;
+        ow[2] += gdm - C(2) * gd0;
+        ow[3] += gd0;
         if (PERIODIC) {
             put(n - 2, ow[0]);
             put(n - 1, ow[1]);
@@ -252,20 +358,73 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     }
 };
 
+// s = 0 (an integer Courant number): every fractional flux is 0, lambda
+// passes through (shifted by the accessor) and dL/ds = sum_j gbar_j fbar_j(0)
+template <bool PERIODIC, typename C, typename Acc>
+__device__ __forceinline__ void march_adjoint_s0(Acc &acc, const AdjLim<C> &k, int n, C &dLds, C &osum)
+{
+    auto cget = [&](int m) -> C {
+        if (PERIODIC) return acc.c(m < 0 ? m + n : (m >= n ? m - n : m));
+        return (m >= 0 && m < n) ? acc.c(m) : C(0);
+    };
+    auto lget = [&](int m) -> C { return acc.lam(PERIODIC && m >= n ? m - n : m); };
+    dLds = C(0);
+#pragma unroll
+    for (int j = 0; j < (PERIODIC ? n : n - 1); ++j) {
+        const C fbar = k.w[0] * cget(j - 2) + k.w[1] * cget(j - 1) + k.w[2] * cget(j) + k.w[3] * cget(j + 1) +
+                       k.w[4] * cget(j + 2);
+        dLds += (lget(j + 1) - lget(j)) * fbar;
+    }
+    // pass lambda through (a rotated read for a whole-cell shift): read all first
+    osum = C(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) osum += acc.lam(i);
+    if (acc.out_of_place())
+        for (int i = 0; i < n; ++i) acc.put(i, acc.lam(i));
+}
+
 // Walk a line of n cells (periodic: n >= 5; zero-flux: n >= 4).  LCT > 0:
 // compile-time length (the loop unrolls and every index is a constant).
 template <bool PERIODIC, int LCT, typename C, typename Acc>
 __device__ __forceinline__ void march_adjoint(Acc &acc, const AdjLim<C> &k, int n, C &dLds, C &osum)
 {
+    if (k.s == C(0)) {
+        march_adjoint_s0<PERIODIC, C>(acc, k, LCT > 0 ? LCT : n, dLds, osum);
+        return;
+    }
     AdjMarch<PERIODIC, C, Acc> m(acc, k, LCT > 0 ? LCT : n);
     m.begin();
     if constexpr (LCT > 0) {
 #pragma unroll
-        for (int j = 0; j < (PERIODIC ? LCT : LCT - 1); ++j) m.face(j);
+        for (int j = 0; j < (PERIODIC ? LCT : LCT - 1); ++j) {
+            if ((PERIODIC && j >= 4 && j <= LCT - 6) || (!PERIODIC && j >= 2 && j <= LCT - 4))
+                m.template face<true>(j, acc.c(j + 3), acc.lam(j + 3));
+            else
+                m.template face<false>(j);
+        }
     } else {
         const int nf = PERIODIC ? n : n - 1;
+        const int jlo = PERIODIC ? 4 : 2, jhi = PERIODIC ? n - 6 : n - 4; // interior faces
+        int j = 0;
 #pragma unroll 1
-        for (int j = 0; j < nf; ++j) m.face(j);
+        for (; j < jlo && j < nf; ++j) m.template face<false>(j);
+        if (j <= jhi) {
+            // interior faces, loads issued two faces ahead: cell j + 5 is read at the
+            // start of face j and enters at the end of face j + 2
+            C c0 = acc.c(j + 3), l0 = acc.lam(j + 3);
+            C c1 = C(0), l1 = C(0);
+            if (j + 4 < n) { c1 = acc.c(j + 4); l1 = acc.lam(j + 4); }
+#pragma unroll kAdjUnroll
+            for (; j <= jhi; ++j) {
+                C c2 = C(0), l2 = C(0);
+                if (j + 5 < n) { c2 = acc.c(j + 5); l2 = acc.lam(j + 5); }
+                m.template face<true>(j, c0, l0);
+                c0 = c1; l0 = l1;
+                c1 = c2; l1 = l2;
+            }
+        }
+#pragma unroll 1
+        for (; j < nf; ++j) m.template face<false>(j);
     }
     m.end();
     dLds = m.dLds;
@@ -311,6 +470,7 @@ template <typename T> struct GlobalLine {
         return lin[r * st];
     }
     __device__ __forceinline__ void put(int i, T v) const { lout[i * st] = v; }
+    __device__ __forceinline__ bool out_of_place() const { return lout != lin; }
 };
 
 // line in registers (compile-time indices after unrolling), mirrored when NEG
@@ -319,6 +479,7 @@ template <typename T, int L, bool NEG> struct RegLine {
     __device__ __forceinline__ T c(int i) const { return cv[NEG ? L - 1 - i : i]; }
     __device__ __forceinline__ T lam(int i) const { return lv[NEG ? L - 1 - i : i]; }
     __device__ __forceinline__ void put(int i, T v) { lv[NEG ? L - 1 - i : i] = v; }
+    __device__ __forceinline__ bool out_of_place() const { return false; }
 };
 
 // ----------------------------------------------------------------------------
@@ -371,7 +532,7 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
 template <typename T, bool PERIODIC, bool SMALL4>
-__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : 3) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
+__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : VK_ADJ_MINB) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
     const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
@@ -431,7 +592,7 @@ __device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
+__global__ void __launch_bounds__(kAdjBlock, L <= 16 ? 3 : 2) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
     constexpr int per = 16 / int(sizeof(T));

@@ -209,6 +209,39 @@ cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *r
     return cudaGetLastError();
 }
 
+// Adjoint of the moment: rho(x) = du^3 sum_u f(x, u), so dL/df(x, u) =
+// du^3 dL/drho(x) for every u.  lam (+)= that, 16 bytes per thread and step.
+template <typename T>
+__global__ void __launch_bounds__(256) moment_adjoint_kernel(GridDims g, const double *__restrict__ dLdrho, T *lam,
+                                                             int accumulate)
+{
+    constexpr int V = 16 / int(sizeof(T));
+    const long long cube = (long long)g.nu[0] * g.nu[1] * g.nu[2];
+    const long long nvec = (long long)g.n[0] * g.n[1] * g.n[2] * cube / V;
+    const double du3 = (2.0 * g.V / g.nu[0]) * (2.0 * g.V / g.nu[1]) * (2.0 * g.V / g.nu[2]);
+    uint4 *q = reinterpret_cast<uint4 *>(lam);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec; i += (long long)gridDim.x * blockDim.x) {
+        const T v = T(du3 * dLdrho[(i * V) / cube]); // a 16-byte vector never straddles a cell (cube % 64 == 0)
+        uint4 u = accumulate ? q[i] : make_uint4(0, 0, 0, 0);
+        T *e = reinterpret_cast<T *>(&u);
+#pragma unroll
+        for (int k = 0; k < V; ++k) e[k] += v;
+        q[i] = u;
+    }
+}
+
+cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int dtype, void *lam, int accumulate,
+                                  cudaStream_t st, int sm_count)
+{
+    const int threads = 256;
+    const int blocks = sm_count * 8;
+    if (dtype == 0)
+        moment_adjoint_kernel<double><<<blocks, threads, 0, st>>>(g, dLdrho, (double *)lam, accumulate);
+    else
+        moment_adjoint_kernel<float><<<blocks, threads, 0, st>>>(g, dLdrho, (float *)lam, accumulate);
+    return cudaGetLastError();
+}
+
 // dx dy dz * sum rho, Neumaier in FP64 per thread, fixed-order combine
 __global__ void __launch_bounds__(1024) mass_kernel(GridDims g, const double *__restrict__ rho, double *out)
 {

@@ -34,7 +34,7 @@ __device__ __forceinline__ bool consumer_any(bool v, int nthreads)
 
 template <typename T>
 __global__ void __launch_bounds__(kConsumers + kProducer)
-    contig_sweep_kernel(const __grid_constant__ CUtensorMap map,
+    contig_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                         const __grid_constant__ ContigArgs<typename Compute<T>::type> args)
 {
     using C = typename Compute<T>::type;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
             if (k >= S) {
                 const long long kp = k - S;
                 if (!mbar_wait_bounded(&done[st], unsigned((kp / S) & 1))) { ok = false; break; }
-                tma_store_2d(&map, stage_ptr(st), 0, int((b + kp * G) * R));
+                tma_store_2d(&dmap, stage_ptr(st), 0, int((b + kp * G) * R));
                 bulk_commit();
                 bulk_wait_read_all();
             }
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
             for (long long kp = (n_my > S ? n_my - S : 0); kp < n_my; ++kp) {
                 const int st = int(kp % S);
                 if (!mbar_wait_bounded(&done[st], unsigned((kp / S) & 1))) { ok = false; break; }
-                tma_store_2d(&map, stage_ptr(st), 0, int((b + kp * G) * R));
+                tma_store_2d(&dmap, stage_ptr(st), 0, int((b + kp * G) * R));
                 bulk_commit();
             }
         }
@@ -142,26 +142,26 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
 }
 
 template <typename T>
-static cudaError_t launch_contig_t(const CUtensorMap &map, const ContigArgs<typename Compute<T>::type> &a,
+static cudaError_t launch_contig_t(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<typename Compute<T>::type> &a,
                                    int grid, size_t smem, cudaStream_t st)
 {
     auto kern = contig_sweep_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kConsumers + kProducer, smem, st>>>(map, a);
+    kern<<<grid, kConsumers + kProducer, smem, st>>>(map, dmap, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_contig_f32(const CUtensorMap &map, const ContigArgs<float> &a, int grid, size_t smem,
+cudaError_t launch_contig_f32(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int grid, size_t smem,
                               cudaStream_t st)
 {
-    return launch_contig_t<float>(map, a, grid, smem, st);
+    return launch_contig_t<float>(map, dmap, a, grid, smem, st);
 }
 
-cudaError_t launch_contig_f64(const CUtensorMap &map, const ContigArgs<double> &a, int grid, size_t smem,
+cudaError_t launch_contig_f64(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<double> &a, int grid, size_t smem,
                               cudaStream_t st)
 {
-    return launch_contig_t<double>(map, a, grid, smem, st);
+    return launch_contig_t<double>(map, dmap, a, grid, smem, st);
 }
 
 int occupancy_contig(int dtype, size_t smem)

@@ -172,7 +172,8 @@ __device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, c
 
 template <int NU, typename T>
 __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
-    line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ ContigArgs<float> args)
+    line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
+                      const __grid_constant__ ContigArgs<float> args)
 {
     constexpr int S = kLineRing;
     constexpr unsigned slot_bytes = kLineRows * NU * sizeof(T);
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
         while (retired < n_my) {
             bool progress = false;
             while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
-                tma_store_2d(&map, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
+                tma_store_2d(&dmap, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
                 bulk_commit();
                 ++retired;
                 progress = true;
@@ -280,14 +281,14 @@ bool line_sweep_supported(int nu, long long rows_per_cell)
     return (nu == 16 || nu == 32) && rows_per_cell % kLineRows == 0;
 }
 
-cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int dtype, int grid,
-                              cudaStream_t st)
+cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
+                              int dtype, int grid, cudaStream_t st)
 {
     const void *k = line_kernel_for(nu, dtype);
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<ContigArgs<float> *>(&a)};
+    void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<ContigArgs<float> *>(&a)};
     return cudaLaunchKernel(k, dim3(grid), dim3(kLineThreads + kProducer), args, smem, st);
 }
 

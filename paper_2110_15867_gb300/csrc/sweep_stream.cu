@@ -253,7 +253,8 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
 
 template <typename T, bool PERIODIC>
 __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
-    stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
+    stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
+                        const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
 {
     constexpr bool CODED = sizeof(T) == 2;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
             bool progress = false;
             while (retired < loaded && mbar_test_wait(&done[retired & (S - 1)], (retired / S) & 1u)) {
                 const int4 m = meta[retired & (S - 1)];
-                if (m.w) tma_store_3d(&map, slot_ptr(retired), m.x, m.y, m.z);
+                if (m.w) tma_store_3d(&dmap, slot_ptr(retired), m.x, m.y, m.z);
                 bulk_commit();
                 ++retired;
                 progress = true;
@@ -433,38 +434,38 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
 }
 
 template <typename T>
-static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &smap,
+static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &dmap, const CUtensorMap &smap,
                                    const StreamArgs<typename Compute<T>::type> &a, int grid, size_t smem, cudaStream_t st)
 {
     auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, smap, a);
+    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, dmap, smap, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                              cudaStream_t st)
+cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<float> &a, int grid,
+                              size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<float>(map, map, a, grid, smem, st);
+    return launch_stream_t<float>(map, dmap, map, a, grid, smem, st);
 }
 
-cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
-                              cudaStream_t st)
+cudaError_t launch_stream_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<double> &a, int grid,
+                              size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<double>(map, map, a, grid, smem, st);
+    return launch_stream_t<double>(map, dmap, map, a, grid, smem, st);
 }
 
 cudaError_t launch_stream_bf16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
                                size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<__nv_bfloat16>(map, smap, a, grid, smem, st);
+    return launch_stream_t<__nv_bfloat16>(map, map, smap, a, grid, smem, st);
 }
 
 cudaError_t launch_stream_f16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
                               size_t smem, cudaStream_t st)
 {
-    return launch_stream_t<__half>(map, smap, a, grid, smem, st);
+    return launch_stream_t<__half>(map, map, smap, a, grid, smem, st);
 }
 
 template <typename T> static const void *stream_ptr(int periodic)

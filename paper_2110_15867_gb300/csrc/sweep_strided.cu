@@ -26,7 +26,7 @@ namespace vk {
 
 template <typename T, bool PERIODIC>
 __global__ void __launch_bounds__(kConsumers + kProducer)
-    strided_sweep_kernel(const __grid_constant__ CUtensorMap map,
+    strided_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                          const __grid_constant__ StridedArgs<typename Compute<T>::type> args)
 {
     using C = typename Compute<T>::type;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
                 if (!mbar_wait_bounded(&done[st], unsigned((kp / S) & 1))) { ok = false; break; }
                 int ci, co;
                 tile_coords(b + kp * G, ci, co);
-                tma_store_3d(&map, stage0 + size_t(st) * stage_elems, ci, 0, co);
+                tma_store_3d(&dmap, stage0 + size_t(st) * stage_elems, ci, 0, co);
                 bulk_commit();
                 bulk_wait_read_all();
             }
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
                 if (!mbar_wait_bounded(&done[st], unsigned((kp / S) & 1))) { ok = false; break; }
                 int ci, co;
                 tile_coords(b + kp * G, ci, co);
-                tma_store_3d(&map, stage0 + size_t(st) * stage_elems, ci, 0, co);
+                tma_store_3d(&dmap, stage0 + size_t(st) * stage_elems, ci, 0, co);
                 bulk_commit();
             }
         }
@@ -140,26 +140,26 @@ __global__ void __launch_bounds__(kConsumers + kProducer)
 }
 
 template <typename T>
-static cudaError_t launch_strided_t(const CUtensorMap &map, const StridedArgs<typename Compute<T>::type> &a,
+static cudaError_t launch_strided_t(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<typename Compute<T>::type> &a,
                                     int grid, size_t smem, cudaStream_t st)
 {
     auto kern = a.periodic ? strided_sweep_kernel<T, true> : strided_sweep_kernel<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kConsumers + kProducer, smem, st>>>(map, a);
+    kern<<<grid, kConsumers + kProducer, smem, st>>>(map, dmap, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_strided_f32(const CUtensorMap &map, const StridedArgs<float> &a, int grid, size_t smem,
+cudaError_t launch_strided_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<float> &a, int grid, size_t smem,
                                cudaStream_t st)
 {
-    return launch_strided_t<float>(map, a, grid, smem, st);
+    return launch_strided_t<float>(map, dmap, a, grid, smem, st);
 }
 
-cudaError_t launch_strided_f64(const CUtensorMap &map, const StridedArgs<double> &a, int grid, size_t smem,
+cudaError_t launch_strided_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<double> &a, int grid, size_t smem,
                                cudaStream_t st)
 {
-    return launch_strided_t<double>(map, a, grid, smem, st);
+    return launch_strided_t<double>(map, dmap, a, grid, smem, st);
 }
 
 int occupancy_strided(int dtype, int periodic, size_t smem)

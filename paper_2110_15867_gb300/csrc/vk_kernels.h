@@ -120,10 +120,11 @@ cudaError_t launch_stream_bf16(const CUtensorMap &map, const CUtensorMap &smap, 
                                size_t smem, cudaStream_t st);
 cudaError_t launch_stream_f16(const CUtensorMap &map, const CUtensorMap &smap, const StreamArgs<float> &a, int grid,
                               size_t smem, cudaStream_t st);
-cudaError_t launch_stream_f32(const CUtensorMap &map, const StreamArgs<float> &a, int grid, size_t smem,
-                              cudaStream_t st);
-cudaError_t launch_stream_f64(const CUtensorMap &map, const StreamArgs<double> &a, int grid, size_t smem,
-                              cudaStream_t st);
+// FP32 / FP64: load through map, store through dmap (the same map for an in-place sweep)
+cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<float> &a, int grid,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_stream_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<double> &a, int grid,
+                              size_t smem, cudaStream_t st);
 int occupancy_stream(int dtype, int periodic, size_t smem); // dtype: 0 f64, 1 f32, 2 bf16, 3 f16
 
 // ----------------------------------------------------------------------------
@@ -149,20 +150,21 @@ size_t line_sweep_smem(int nu, int es);
 int line_sweep_rows_per_tile();
 int occupancy_line_sweep(int nu, int dtype); // dtype: 1 f32, 2 bf16, 3 f16
 
-// host launchers (return cudaGetLastError() of the launch)
-cudaError_t launch_strided_f32(const CUtensorMap &map, const StridedArgs<float> &a, int grid,
+// host launchers (return cudaGetLastError() of the launch); tiles are loaded
+// through map and stored through dmap (the same map for an in-place sweep)
+cudaError_t launch_strided_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<float> &a, int grid,
                                size_t smem, cudaStream_t st);
-cudaError_t launch_strided_f64(const CUtensorMap &map, const StridedArgs<double> &a, int grid,
+cudaError_t launch_strided_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<double> &a, int grid,
                                size_t smem, cudaStream_t st);
-cudaError_t launch_contig_f32(const CUtensorMap &map, const ContigArgs<float> &a, int grid,
+cudaError_t launch_contig_f32(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int grid,
                               size_t smem, cudaStream_t st);
-cudaError_t launch_contig_f64(const CUtensorMap &map, const ContigArgs<double> &a, int grid,
+cudaError_t launch_contig_f64(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<double> &a, int grid,
                               size_t smem, cudaStream_t st);
 // largest resident CTAs per SM for a launcher's kernel with this dynamic smem
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
-cudaError_t launch_line_sweep(const CUtensorMap &map, const ContigArgs<float> &a, int nu, int dtype, int grid,
-                              cudaStream_t st);
+cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
+                              int dtype, int grid, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // fields: velocity-sweep coefficients, moment, Poisson
@@ -217,6 +219,9 @@ cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *r
 // 16-bit storage (dtype 2 bf16, 3 f16) with one scale per u_z line
 cudaError_t launch_moment_coded(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
                                 cudaStream_t st, int sm_count);
+// lam (+)= du^3 dLdrho(x) over each velocity cube (FP64 or FP32 lam: dtype 0 / 1)
+cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int dtype, void *lam, int accumulate,
+                                  cudaStream_t st, int sm_count);
 // mass = dx dy dz * sum rho (FP64, compensated) written to out (device)
 cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st);
 

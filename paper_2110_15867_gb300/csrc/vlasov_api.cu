@@ -36,8 +36,55 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+// Parameters of a tiled tensor map, kept so the same view can be encoded for
+// another array of the same shape (out-of-place sweeps, recorded inputs).
+struct MapSpec {
+    CUtensorMapDataType type;
+    cuuint32_t rank;
+    cuuint64_t gdim[3];
+    cuuint64_t gstr[2];
+    cuuint32_t box[3];
+    CUtensorMapSwizzle swz;
+    CUtensorMapL2promotion promo;
+};
+
+CUresult encode_spec(CUtensorMap *m, const MapSpec &s, const void *base)
+{
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode_fn()(m, s.type, s.rank, const_cast<void *>(base), s.gdim, s.gstr, s.box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, s.swz, s.promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+MapSpec spec3(CUtensorMapDataType type, long long I, long long L, long long O, size_t es, int W, int R, int P)
+{
+    MapSpec s{};
+    s.type = type;
+    s.rank = 3;
+    s.gdim[0] = (cuuint64_t)I; s.gdim[1] = (cuuint64_t)L; s.gdim[2] = (cuuint64_t)O;
+    s.gstr[0] = (cuuint64_t)(I * es); s.gstr[1] = (cuuint64_t)(I * L * es);
+    s.box[0] = (cuuint32_t)W; s.box[1] = (cuuint32_t)R; s.box[2] = (cuuint32_t)P;
+    s.swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+    s.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+    return s;
+}
+
+// rows of L elements: box {L, R rows}
+MapSpec spec_rows(CUtensorMapDataType type, long long L, long long rows, size_t es, int R, CUtensorMapSwizzle swz)
+{
+    MapSpec s{};
+    s.type = type;
+    s.rank = 2;
+    s.gdim[0] = (cuuint64_t)L; s.gdim[1] = (cuuint64_t)rows;
+    s.gstr[0] = (cuuint64_t)(L * es);
+    s.box[0] = (cuuint32_t)L; s.box[1] = (cuuint32_t)R;
+    s.swz = swz;
+    s.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+    return s;
+}
+
 struct AxisPlan {
     CUtensorMap map;
+    MapSpec spec;
     int L, W, P, stages, grid;
     long long n_inner, n_outer, num_tiles;
     int tiles_inner;
@@ -64,6 +111,7 @@ struct vlasov_ctx {
     // u_z with whole lines in registers
     bool use_lines;
     CUtensorMap lmap;
+    MapSpec lspec;
     long long lrows, ltiles;
     int lgrid;
     // scratch
@@ -184,13 +232,8 @@ static int plan_axes(vlasov_ctx *c)
             S = S < 2 ? 2 : (S > 4 ? 4 : S);
             p.stages = S;
             p.smem = 128 + tab + (size_t)S * tile;
-            const cuuint64_t gdim[3] = {(cuuint64_t)I, (cuuint64_t)p.L, (cuuint64_t)O};
-            const cuuint64_t gstr[2] = {(cuuint64_t)(I * es), (cuuint64_t)(I * p.L * es)};
-            const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)p.L, (cuuint32_t)P};
-            const cuuint32_t estr[3] = {1, 1, 1};
-            r = enc(&p.map, tmap_type(c->g.dtype), 3, c->f, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            p.spec = spec3(tmap_type(c->g.dtype), I, p.L, O, es, W, p.L, P);
+            r = encode_spec(&p.map, p.spec, c->f);
             const int occ = occupancy_strided(c->g.dtype == VLASOV_F64 ? 0 : 1, ax < 3, p.smem);
             if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a CTA does not fit (%zu B shared memory)", ax, p.smem);
             p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
@@ -208,13 +251,8 @@ static int plan_axes(vlasov_ctx *c)
             S = S < 2 ? 2 : (S > 4 ? 4 : S);
             p.stages = S;
             p.smem = 128 + (size_t)S * tile + bbuf;
-            const cuuint64_t gdim[2] = {(cuuint64_t)p.L, (cuuint64_t)rows};
-            const cuuint64_t gstr[1] = {(cuuint64_t)(p.L * es)};
-            const cuuint32_t box[2] = {(cuuint32_t)p.L, (cuuint32_t)kConsumers};
-            const cuuint32_t estr[2] = {1, 1};
-            r = enc(&p.map, tmap_type(c->g.dtype), 2, c->f, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            p.spec = spec_rows(tmap_type(c->g.dtype), p.L, rows, es, kConsumers, CU_TENSOR_MAP_SWIZZLE_NONE);
+            r = encode_spec(&p.map, p.spec, c->f);
             const int occ = occupancy_contig(c->g.dtype == VLASOV_F64 ? 0 : 1, p.smem);
             if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis 5: a CTA does not fit (%zu B shared memory)", p.smem);
             p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
@@ -283,13 +321,8 @@ static int plan_axes(vlasov_ctx *c)
         }
         p.smem = 512 + tab + (size_t)S * (slot + sslot);
         p.grid = R; // rows per chunk (kept here; the launch grid is computed below)
-        const cuuint64_t gdim[3] = {(cuuint64_t)I, (cuuint64_t)p.L, (cuuint64_t)O};
-        const cuuint64_t gstr[2] = {(cuuint64_t)(I * es), (cuuint64_t)(I * p.L * es)};
-        const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)R, (cuuint32_t)P};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        const CUresult r = enc(&p.map, tmap_type(c->g.dtype), 3, c->f, gdim, gstr, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        p.spec = spec3(tmap_type(c->g.dtype), I, p.L, O, es, W, R, P);
+        const CUresult r = encode_spec(&p.map, p.spec, c->f);
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: stream tensor map failed (%d)", ax, int(r));
         const int occ = occupancy_stream(c->g.dtype, ax < 3, p.smem);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a streamed CTA does not fit (%zu B)", ax, p.smem);
@@ -302,17 +335,12 @@ static int plan_axes(vlasov_ctx *c)
         const int nu = c->g.nuz, rpt = line_sweep_rows_per_tile();
         c->lrows = c->ncell * c->g.nux * c->g.nuy;
         c->ltiles = (c->lrows + rpt - 1) / rpt;
-        const cuuint64_t gdim[2] = {(cuuint64_t)nu, (cuuint64_t)c->lrows};
-        const cuuint64_t gstr[1] = {(cuuint64_t)(nu * es)};
-        const cuuint32_t box[2] = {(cuuint32_t)nu, (cuuint32_t)rpt};
-        const cuuint32_t estr[2] = {1, 1};
         const size_t rowbytes = nu * es;
         const CUtensorMapSwizzle sw = rowbytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                       : rowbytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                        : CU_TENSOR_MAP_SWIZZLE_32B;
-        const CUresult r = enc(&c->lmap, tmap_type(c->g.dtype), 2, c->f, gdim, gstr, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        c->lspec = spec_rows(tmap_type(c->g.dtype), nu, c->lrows, es, rpt, sw);
+        const CUresult r = encode_spec(&c->lmap, c->lspec, c->f);
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "u_z line tensor map failed (%d)", int(r));
         const int occ = occupancy_line_sweep(nu, c->g.dtype);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
@@ -500,22 +528,44 @@ template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlaso
     A.scale_rank = c->scale_rank[ax];
 }
 
+// Tensor maps of one plan for a sweep that reads src and writes dst (both
+// arrays of c's shape; the plan's own map where one is c->f).
+struct SweepMaps {
+    CUtensorMap in, out;
+};
+
+static int sweep_maps(vlasov_ctx *c, const CUtensorMap &own, const MapSpec &spec, const void *src, void *dst,
+                      SweepMaps &m)
+{
+    if (src == c->f) m.in = own;
+    else if (encode_spec(&m.in, spec, src) != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "tensor map of a sweep input failed");
+    if (dst == c->f) m.out = own;
+    else if (encode_spec(&m.out, spec, dst) != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "tensor map of a sweep output failed");
+    return VLASOV_OK;
+}
+
 // streamed launch for the storage type of c (the arguments use FP32 constants unless FP64)
-static cudaError_t launch_stream_any(const vlasov_ctx *c, int ax, const StreamArgs<float> &A)
+static cudaError_t launch_stream_any(const vlasov_ctx *c, int ax, const StreamArgs<float> &A, const SweepMaps &m)
 {
     const AxisPlan &sp = c->splan[ax];
     switch (c->g.dtype) {
     case VLASOV_BF16: return launch_stream_bf16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
     case VLASOV_F16: return launch_stream_f16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
-    default: return launch_stream_f32(sp.map, A, sp.grid, sp.smem, c->stream);
+    default: return launch_stream_f32(m.in, m.out, A, sp.grid, sp.smem, c->stream);
     }
 }
 
-// position sweep: per-velocity-column constants from nu_j = u_j dt / (a^2 dx)
-static int run_position(vlasov_ctx *c, int ax, double dt, double a)
+static bool coded(const vlasov_ctx *c) { return c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16; }
+
+// position sweep from src to dst (NULL, NULL: c->f in place) with per-velocity-column
+// constants from nu_j = u_j dt / (a^2 dx)
+static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *src = nullptr, void *dst = nullptr)
 {
     ++c->sweeps;
+    if (!src) src = c->f;
+    if (!dst) dst = c->f;
     if (!(a > 0) || !isfinite(dt) || !isfinite(a)) return fail(c, VLASOV_EINVAL, "sweep %d: need finite dt and a > 0", ax);
+    if (coded(c) && (src != c->f || dst != c->f)) return fail(c, VLASOV_EINVAL, "16-bit storage sweeps in place only");
     const AxisPlan &p = c->plan[ax];
     const int nvel = (&c->g.nux)[ax];
     const double du = 2.0 * c->g.V / nvel;
@@ -524,9 +574,12 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
     for (int k = ax + 1; k < 3; ++k) vstride *= (&c->g.nux)[k];
     double numax = 0.0;
     for (int j = 0; j < nvel; ++j) numax = fmax(numax, fabs((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx)));
+    SweepMaps m;
+    int rc;
     if (numax < 1.0) {
         // no whole-cell shift on any line: streamed sweep
         const AxisPlan &sp = c->splan[ax];
+        if (!coded(c) && (rc = sweep_maps(c, sp.map, sp.spec, src, dst, m))) return rc;
         cudaError_t e;
         if (c->g.dtype == VLASOV_F64) {
             StreamArgs<double> A{};
@@ -534,20 +587,20 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
             PartTimer t(c, ax, 1);
-            e = launch_stream_f64(sp.map, A, sp.grid, sp.smem, c->stream);
+            e = launch_stream_f64(m.in, m.out, A, sp.grid, sp.smem, c->stream);
         } else {
             StreamArgs<float> A{};
             fill_stream_args(A, c, ax);
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
             PartTimer t(c, ax, 1);
-            e = launch_stream_any(c, ax, A);
+            e = launch_stream_any(c, ax, A, m);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
         return VLASOV_OK;
     }
-    if (c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16)
-        return fail(c, VLASOV_EINVAL, "sweep %d: |nu| = %.3g >= 1 needs FP32 or FP64 storage", ax, numax);
+    if (coded(c)) return fail(c, VLASOV_EINVAL, "sweep %d: |nu| = %.3g >= 1 needs FP32 or FP64 storage", ax, numax);
+    if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;
     cudaError_t e;
     if (c->g.dtype == VLASOV_F64) {
         StridedArgs<double> A{};
@@ -557,7 +610,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
         A.err = c->d_err;
         for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
         PartTimer t(c, ax, 1);
-        e = launch_strided_f64(p.map, A, p.grid, p.smem, c->stream);
+        e = launch_strided_f64(m.in, m.out, A, p.grid, p.smem, c->stream);
     } else {
         StridedArgs<float> A{};
         A.L = p.L; A.W = p.W; A.P = p.P; A.stages = p.stages; A.tiles_inner = p.tiles_inner; A.periodic = 1;
@@ -566,55 +619,66 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a)
         A.err = c->d_err;
         for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
         PartTimer t(c, ax, 1);
-        e = launch_strided_f32(p.map, A, p.grid, p.smem, c->stream);
+        e = launch_strided_f32(m.in, m.out, A, p.grid, p.smem, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
     return VLASOV_OK;
 }
 
-// velocity sweep with the per-cell constants already in d_coef[ax - 3]
-static int run_velocity(vlasov_ctx *c, int ax)
+// velocity sweep from src to dst (NULL, NULL: c->f in place) with the per-cell
+// constants already in d_coef[ax - 3]
+static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *dst = nullptr)
 {
     ++c->sweeps;
+    if (!src) src = c->f;
+    if (!dst) dst = c->f;
+    if (coded(c) && (src != c->f || dst != c->f)) return fail(c, VLASOV_EINVAL, "16-bit storage sweeps in place only");
     const AxisPlan &p = c->plan[ax];
     const void *coef = c->d_coef[ax - 3];
+    SweepMaps m;
+    int rc;
     cudaError_t e;
-    PartTimer t(c, ax, 1);
     if (ax < 5) {
         const AxisPlan &sp = c->splan[ax];
+        if (!coded(c) && (rc = sweep_maps(c, sp.map, sp.spec, src, dst, m))) return rc;
         const long long opc = sp.n_outer / c->ncell;
+        PartTimer t(c, ax, 1);
         if (c->g.dtype == VLASOV_F64) {
             StreamArgs<double> A{};
             fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
             A.cell_coef = (const LineCoefT<double> *)coef;
-            e = launch_stream_f64(sp.map, A, sp.grid, sp.smem, c->stream);
+            e = launch_stream_f64(m.in, m.out, A, sp.grid, sp.smem, c->stream);
         } else {
             StreamArgs<float> A{};
             fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
             A.cell_coef = (const LineCoefT<float> *)coef;
-            e = launch_stream_any(c, ax, A);
+            e = launch_stream_any(c, ax, A, m);
         }
     } else if (c->use_lines) {
+        if ((rc = sweep_maps(c, c->lmap, c->lspec, src, dst, m))) return rc;
         ContigArgs<float> A{};
         A.L = c->g.nuz; A.R = line_sweep_rows_per_tile(); A.stages = 0; A.rows = c->lrows; A.num_tiles = c->ltiles;
         A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
         A.scale = c->scale;
         A.seed = c->sweeps;
-        e = launch_line_sweep(c->lmap, A, c->g.nuz, c->g.dtype, c->lgrid, c->stream);
+        PartTimer t(c, ax, 1);
+        e = launch_line_sweep(m.in, m.out, A, c->g.nuz, c->g.dtype, c->lgrid, c->stream);
     } else {
+        if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;
         const long long rpc = (long long)c->g.nux * c->g.nuy;
+        PartTimer t(c, ax, 1);
         if (c->g.dtype == VLASOV_F64) {
             ContigArgs<double> A{};
             A.L = p.L; A.R = kConsumers; A.stages = p.stages; A.rows = p.n_outer; A.num_tiles = p.num_tiles;
             A.rows_per_cell = rpc; A.cell_coef = (const LineCoefT<double> *)coef; A.err = c->d_err;
-            e = launch_contig_f64(p.map, A, p.grid, p.smem, c->stream);
+            e = launch_contig_f64(m.in, m.out, A, p.grid, p.smem, c->stream);
         } else {
             ContigArgs<float> A{};
             A.L = p.L; A.R = kConsumers; A.stages = p.stages; A.rows = p.n_outer; A.num_tiles = p.num_tiles;
             A.rows_per_cell = rpc; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
-            e = launch_contig_f32(p.map, A, p.grid, p.smem, c->stream);
+            e = launch_contig_f32(m.in, m.out, A, p.grid, p.smem, c->stream);
         }
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "velocity sweep launch");
@@ -830,51 +894,73 @@ extern "C" int vlasov_sweep_adjoint(vlasov_ctx *c, const void *f_in_dev, void *l
     return run_adjoint(c, f_in_dev, lam_dev, axis, dt, a, axis >= 3 ? dLdg_dev : nullptr);
 }
 
-// point the plans at another array of the same shape (host work only)
-static int repoint(vlasov_ctx *c, void *f)
-{
-    if (c->f == f) return VLASOV_OK;
-    c->f = f;
-    return plan_axes(c);
-}
-
-extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam_dev, double dt, double a_half,
-                                   const float *phi_dev, double *dLdphi_dev)
+extern "C" int vlasov_moment_adjoint(vlasov_ctx *c, const double *dLdrho_dev, void *lam_dev, int accumulate)
 {
     if (!c) return VLASOV_EINVAL;
-    int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint");
+    if (c->g.dtype != VLASOV_F32 && c->g.dtype != VLASOV_F64)
+        return fail(c, VLASOV_EINVAL, "vlasov_moment_adjoint: FP32 or FP64 storage only");
+    if (!dLdrho_dev || !lam_dev || reinterpret_cast<uintptr_t>(lam_dev) % 16)
+        return fail(c, VLASOV_EINVAL, "vlasov_moment_adjoint: null dLdrho or null / misaligned lambda");
+    PartTimer t(c, VLASOV_T_MOMENT_ADJ, 1);
+    const cudaError_t e = launch_moment_adjoint(c->gd, dLdrho_dev, c->g.dtype == VLASOV_F64 ? 0 : 1, lam_dev,
+                                                accumulate != 0, c->stream, c->sm_count);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moment adjoint launch");
+    return VLASOV_OK;
+}
+
+// sweeps of one step, Eq. 5: kick u_x, u_y, u_z (dt/2), drift z, y, x (dt), kick (dt/2)
+static const int kStepAxes[9] = {3, 4, 5, 2, 1, 0, 3, 4, 5};
+static double step_dt(int k, double dt) { return (k >= 3 && k <= 5) ? dt : 0.5 * dt; }
+
+static int check_records(vlasov_ctx *c, const void *const *rec, const char *who)
+{
+    if (!rec) return fail(c, VLASOV_EINVAL, "%s: rec_dev is NULL", who);
+    for (int k = 0; k < 8; ++k)
+        if (!rec[k] || reinterpret_cast<uintptr_t>(rec[k]) % 16)
+            return fail(c, VLASOV_EINVAL, "%s: rec_dev[%d] must be a 16-byte aligned device array", who, k);
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_step_record(vlasov_ctx *c, const void *f_n_dev, void *const *rec_dev, void *f_next_dev, double dt,
+                                  double a_half, const float *phi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_records(c, rec_dev, "vlasov_step_record");
+    if (!rc) rc = check_adjoint_args(c, f_n_dev, rec_dev[0], "vlasov_step_record");
     if (rc) return rc;
-    if (!phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint: phi_dev is NULL");
-    const size_t bytes = f_bytes(c);
-    for (int k = 0; k < 8 && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
-    if (!rc && dLdphi_dev) rc = ensure_buffer(c, (void **)&c->d_dLdg, sizeof(double) * 3 * c->ncell);
-    if (rc) return rc;
-    // sweeps of one step, Eq. 5: kick u_x, u_y, u_z (dt/2), drift z, y, x (dt), kick (dt/2)
-    const int axes[9] = {3, 4, 5, 2, 1, 0, 3, 4, 5};
-    const double dts[9] = {0.5 * dt, 0.5 * dt, 0.5 * dt, dt, dt, dt, 0.5 * dt, 0.5 * dt, 0.5 * dt};
-    // forward again from f_n, keeping the input of every sweep: rec[k] = input of sweep k + 1
-    void *const f_own = c->f;
+    if (f_next_dev && reinterpret_cast<uintptr_t>(f_next_dev) % 16)
+        return fail(c, VLASOV_EINVAL, "vlasov_step_record: f_next_dev must be 16-byte aligned");
     if ((rc = prep_velocity(c, phi_dev, 0.5 * dt, 7))) return rc;
-    for (int k = 0; k < 8 && !rc; ++k) {
-        {
-            PartTimer t(c, VLASOV_T_COPY, 0);
-            const cudaError_t e = cudaMemcpyAsync(c->d_rec[k], k == 0 ? f_n_dev : c->d_rec[k - 1], bytes,
-                                                  cudaMemcpyDeviceToDevice, c->stream);
-            if (e != cudaSuccess) rc = cuda_fail(c, e, "record copy");
-        }
-        if (!rc) rc = repoint(c, c->d_rec[k]);
-        if (!rc) rc = axes[k] >= 3 ? run_velocity(c, axes[k]) : run_position(c, axes[k], dts[k], a_half);
+    for (int k = 0; k < 9; ++k) {
+        const void *src = k == 0 ? f_n_dev : rec_dev[k - 1];
+        void *dst = k < 8 ? rec_dev[k] : f_next_dev;
+        if (!dst) break;
+        const int ax = kStepAxes[k];
+        rc = ax >= 3 ? run_velocity(c, ax, src, dst) : run_position(c, ax, step_dt(k, dt), a_half, src, dst);
+        if (rc) return rc;
     }
-    const int rc2 = repoint(c, f_own);
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_step_adjoint_recorded(vlasov_ctx *c, const void *f_n_dev, const void *const *rec_dev, void *lam_dev,
+                                            double dt, double a_half, const float *phi_dev, double *dLdphi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint_recorded");
+    if (!rc) rc = check_records(c, const_cast<void *const *>(rec_dev), "vlasov_step_adjoint_recorded");
     if (rc) return rc;
-    if (rc2) return rc2;
-    // reverse: the nine adjoint sweeps, last sweep first (the kick constants are still in d_coef)
+    for (int k = 0; k < 8; ++k)
+        if (rec_dev[k] == lam_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint_recorded: lambda aliases a record");
+    if (dLdphi_dev && (rc = ensure_buffer(c, (void **)&c->d_dLdg, sizeof(double) * 3 * c->ncell))) return rc;
+    // the kick constants (both kicks use phi and dt / 2)
+    if ((rc = prep_velocity(c, phi_dev, 0.5 * dt, 7))) return rc;
     if (dLdphi_dev) VK_CUDA(c, cudaMemsetAsync(c->d_dLdg, 0, sizeof(double) * 3 * c->ncell, c->stream));
+    // the nine adjoint sweeps, last sweep first
     for (int k = 8; k >= 0; --k) {
-        const int ax = axes[k];
-        const void *in = k == 0 ? f_n_dev : c->d_rec[k - 1];
+        const int ax = kStepAxes[k];
+        const void *in = k == 0 ? f_n_dev : rec_dev[k - 1];
         double *dLdg = (ax >= 3 && dLdphi_dev) ? c->d_dLdg + (ax - 3) * c->ncell : nullptr;
-        if ((rc = run_adjoint(c, in, lam_dev, ax, dts[k], a_half, dLdg))) return rc;
+        if ((rc = run_adjoint(c, in, lam_dev, ax, step_dt(k, dt), a_half, dLdg))) return rc;
     }
     if (dLdphi_dev) {
         PartTimer t(c, VLASOV_T_GRAD_ADJ, 3);
@@ -884,6 +970,20 @@ extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam
         }
     }
     return VLASOV_OK;
+}
+
+extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam_dev, double dt, double a_half,
+                                   const float *phi_dev, double *dLdphi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint");
+    if (rc) return rc;
+    const size_t bytes = f_bytes(c);
+    for (int k = 0; k < 8 && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
+    if (rc) return rc;
+    // run the step again from f_n, keeping the input of every sweep
+    if ((rc = vlasov_step_record(c, f_n_dev, c->d_rec, nullptr, dt, a_half, phi_dev))) return rc;
+    return vlasov_step_adjoint_recorded(c, f_n_dev, c->d_rec, lam_dev, dt, a_half, phi_dev, dLdphi_dev);
 }
 
 // ----------------------------------------------------------------------------

@@ -9,9 +9,11 @@ FP32 storage: arithmetic in FP32 against the FP64 oracle on the same FP32 input.
 Where the forward sits within FP32 rounding of a limiter switch the two sides may take
 different branches (and over a step the FP32 forward states drift from the FP64 ones
 by rounding, so more faces sit near a switch); each such face moves a few entries by
-O(|lambda|).  So at most 2e-4 of the entries may be off by more than 1e-3 of
-max |lambda|, and the others must agree to FP32 rounding: relative L1 <= 1e-6 over
-them.  The measured values are printed.
+O(|lambda|).  For one sweep at most 2e-4 of the entries may be off by more than 1e-3
+of max |lambda| and the others must agree to FP32 rounding (relative L1 <= 1e-6 over
+them).  Over a step the later adjoint sweeps spread each flip over its neighbours, so
+there the bound is at most 2e-4 of the entries off by 1e-3 and relative L1 <= 1e-3
+overall.  The measured values are printed.
 """
 import numpy as np
 import pytest
@@ -49,7 +51,7 @@ def _dt_step(g, phi, cfl, a=1.0):
     return cfl / m
 
 
-def _compare(gpu, ref, fp64, what=""):
+def _compare(gpu, ref, fp64, what="", step=False):
     gpu = np.asarray(gpu, dtype=np.float64)
     err = np.abs(gpu - ref)
     scale = np.abs(ref).max()
@@ -62,6 +64,8 @@ def _compare(gpu, ref, fp64, what=""):
           % (what, rl1, rinf, bad, rl1_on))
     if fp64:
         assert rl1 <= 1e-12 and rinf <= 1e-10, (rl1, rinf)
+    elif step:
+        assert bad <= 2e-4 and rl1 <= 1e-3, (rl1, rinf, bad, rl1_on)
     else:
         assert bad <= 2e-4 and rl1_on <= 1e-6, (rl1, rinf, bad, rl1_on)
 
@@ -160,28 +164,46 @@ def test_step_adjoint_fp64(n, nu):
     v.close()
 
 
+def _rel(x, y, order=1):
+    return np.linalg.norm((x - y).ravel(), order) / np.linalg.norm(y.ravel(), order)
+
+
 def test_step_adjoint_fp32():
+    # The adjoint of the limited step is piecewise: near a limiter switch a rounding-
+    # level change of the state moves lambda and dL/dphi by O(1) locally (in the f_UL
+    # branch dF/ds carries d alpha/ds = -(1 + alpha)^2).  The FP32 result is pinned to
+    # that conditioning: its distance from the FP64 oracle is at most 3x the oracle's
+    # own spread when its input is perturbed by 4 FP32 roundings (4 * 2^-24 relative).
     B = _lib()
     n, nu = (16, 16, 16), (16, 16, 16)
     f0, phi, lam0 = _setup(n, nu)
     g = O.grid(n, nu, V=5.0)
     dt = _dt_step(g, phi, 0.8)
+    f64, phi64 = f0.astype(np.float64), phi.astype(np.float64)
     lam_ref = lam0.astype(np.float64)
-    dphi_ref = O.step_adjoint(g, f0.astype(np.float64), lam_ref, dt, 1.0, phi.astype(np.float64))
+    dphi_ref = O.step_adjoint(g, f64, lam_ref, dt, 1.0, phi64)
+    fp = f64 * (1 + 4 * 2.0 ** -24 * np.random.default_rng(99).uniform(-1, 1, f64.shape))
+    lam_p = lam0.astype(np.float64)
+    dphi_p = O.step_adjoint(g, fp, lam_p, dt, 1.0, phi64)
+    sens_l, sens_p = _rel(lam_p, lam_ref), _rel(dphi_p, dphi_ref, 2)
+
     f_n = torch.from_numpy(f0).cuda()
     lam = torch.from_numpy(lam0).cuda()
     v = B.Vlasov(torch.zeros_like(f_n), V=5.0)
     dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
     v.step_adjoint(f_n, lam, dt, 1.0, torch.from_numpy(phi).cuda(), dphi)
     v.status()
-    _compare(lam.cpu().numpy(), lam_ref, False, "step lambda")
-    _compare_field(dphi.cpu().numpy(), dphi_ref, False, "step dL/dphi")
+    err_l = _rel(lam.cpu().numpy().astype(np.float64), lam_ref)
+    err_p = _rel(dphi.cpu().numpy(), dphi_ref, 2)
+    print("step lambda rel L1 %.2e (oracle spread %.2e); dL/dphi rel L2 %.2e (oracle spread %.2e)"
+          % (err_l, sens_l, err_p, sens_p))
+    assert err_l <= 3 * sens_l + 1e-6 and err_p <= 3 * sens_p + 1e-6
     v.close()
 
 
 def test_adjoint_argument_errors():
     B = _lib()
-    n, nu = (8, 8, 8), (8, 8, 16)
+    n, nu = (8, 8, 8), (16, 16, 16)
     f0, phi, lam0 = _setup(n, nu)
     f = torch.from_numpy(f0).cuda()
     v = B.Vlasov(f, V=5.0)
