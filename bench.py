@@ -44,6 +44,8 @@ LOWPREC = dict(name="lowprec_96x32", n=96, nu=32, V=5.0, delta_rms=0.01, seed=1,
 # CPU baseline / reference arm: the oracle on a bounded sample of the same workload:
 # the same 32^3 velocity cube on an 8^3 spatial grid (1.68e7 cells per step).
 SAMPLE = dict(n=8, nu=32)
+# Reverse mode: 32^3 x 16^3 FP32 cells, 16 external-potential steps, checkpoint every 4.
+ADJOINT = dict(name="adjoint_32x16", n=32, nu=16, V=5.0, delta_rms=0.01, seed=1, cfl=0.7, steps=16, K=4)
 
 
 def parse():
@@ -56,6 +58,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-lowprec", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--profile-case", action="store_true",
                    help="run the small profiling case instead of the benchmark: sweeps on a "
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
@@ -267,16 +270,29 @@ def build_inputs(torch, dev):
     return f, rho_bg
 
 
+def courant_per_dt(phi, n, nu, V, L=1.0, a=1.0):
+    """Largest |Courant number| per unit dt of the position sweeps (|u| / (a^2 dx)) and
+    of the velocity sweeps (|g| / du, g the periodic 4th-order gradient of phi): the
+    host-side arithmetic that picks dt."""
+    du = 2.0 * V / nu
+    pos = (V - 0.5 * du) * n / (L * a * a)
+    p = phi.astype(np.float64)
+    vel = 0.0
+    for d in range(3):
+        g = (8.0 * (np.roll(p, -1, d) - np.roll(p, 1, d)) - (np.roll(p, -2, d) - np.roll(p, 2, d))) / (12.0 * L / n)
+        vel = max(vel, float(np.abs(g).max()) / du)
+    return pos, vel
+
+
 def run_lowprec(torch, B, dev, steps, warmup):
     """Per-sweep rate of Eq. (5) steps with BF16 and FP16 storage (FP32 arithmetic)."""
-    import oracle as O  # only to pick dt: the largest Courant number of the 6 axes is 0.7
     from paper_2110_15867_gb300 import inputs as I
     w = LOWPREC
     n, nu, V = w["n"], w["nu"], w["V"]
     phi_np = I.fourier_potential(n, seed=w["seed"] + 10).astype(np.float32)
-    g = O.grid(n, nu, V=V)
-    dt = min(w["cfl"] / O.max_abs_nu(g, ax, 1.0, 1.0, phi_np.astype(np.float64)) * (2 if ax >= 3 else 1)
-             for ax in range(6))
+    # the largest Courant number of the 6 axes is cfl (a kick advances dt / 2)
+    pos, vel = courant_per_dt(phi_np, n, nu, V)
+    dt = w["cfl"] / max(pos, 0.5 * vel)
     delta = torch.from_numpy(I.gaussian_field(n, w["delta_rms"], seed=w["seed"])).to(dev)
     Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
     phi = torch.from_numpy(phi_np).to(dev)
@@ -316,6 +332,68 @@ def run_lowprec(torch, B, dev, steps, warmup):
         del codes, scale
         torch.cuda.empty_cache()
     return out
+
+
+def run_adjoint(torch, dev, reps=3):
+    """Reverse mode of a 16-step run (checkpoints every 4 steps) on 32^3 x 16^3 FP32
+    cells: forward (16 steps + moment) and backward (segments re-recorded, 144 adjoint
+    sweeps, moment adjoint) timed with CUDA events, median of reps."""
+    from paper_2110_15867_gb300 import inputs as I
+    from paper_2110_15867_gb300.autograd import Run, run_rho
+    w = ADJOINT
+    n, nu, V = w["n"], w["nu"], w["V"]
+    f0 = I.initial_f(I.gaussian_field(n, w["delta_rms"], seed=w["seed"]), I.fermi_dirac(nu, V), np.float32)
+    phi_np = I.fourier_potential(n, seed=w["seed"] + 10).astype(np.float32)
+    pos, vel = courant_per_dt(phi_np, n, nu, V)
+    dt = w["cfl"] / max(pos, 0.5 * vel)
+    run = Run(f0.shape, torch.float32, V=V)
+    ft = torch.from_numpy(f0).to(dev).requires_grad_()
+    pt = torch.from_numpy(phi_np).to(dev).requires_grad_()
+    kx = torch.fft.fftfreq(n, d=1.0 / n, device=dev)
+    k2 = kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kx[None, None, :] ** 2
+    mask = ((k2 > 0) & (k2 < 64)).to(torch.float64)  # modes 0 < |n| < 8
+
+    def once():
+        ft.grad = None
+        pt.grad = None
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        rho = run_rho(ft, pt, run, dt, 1.0, w["steps"], w["K"])
+        e[1].record()
+        loss = (torch.fft.fftn(rho).abs() ** 2 * mask).sum()
+        loss.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    once()
+    ts = [once() for _ in range(reps)]
+    fw = float(np.median([t[0] for t in ts]))
+    bw = float(np.median([t[1] for t in ts]))
+    run.v.read_timers()
+    run.v.enable_timers(True)
+    once()
+    kind_ms, kind_n = run.v.read_timers()
+    run.v.enable_timers(False)
+    run.v.status()
+    ok = bool(torch.isfinite(ft.grad).all()) and bool(torch.isfinite(pt.grad).all())
+    cells = f0.size
+    per = {}
+    for k in kind_ms:
+        if k.startswith("adj_") and kind_n[k]:
+            ms = kind_ms[k] / kind_n[k]
+            fk = "sweep_" + k[4:]
+            fms = kind_ms[fk] / max(1, kind_n[fk]) if kind_ms.get(fk) else None
+            per[k] = {"ms_per_launch": ms, "cell_updates_per_s": cells / (ms * 1e-3),
+                      "GBs": 12.0 * cells / (ms * 1e-3) / 1e9,
+                      "vs_forward_sweep": (ms / fms) if fms else None}
+    run.close()
+    del ft, pt
+    torch.cuda.empty_cache()
+    return {"workload": "%s: %d^3 x %d^3 cells FP32, %d steps, checkpoint every %d, external phi, "
+                        "loss sum over 0<|n|<8 of |rho_hat|^2" % (w["name"], n, nu, w["steps"], w["K"]),
+            "forward_ms": fw, "backward_ms": bw, "backward_over_forward": bw / fw,
+            "adjoint_sweeps": per, "gradients_finite": ok}
 
 
 def run_ours(args):
@@ -434,6 +512,9 @@ def run_ours(args):
         lowprec = run_lowprec(torch, B, dev, max(2, min(args.steps, 3)), 2)
         for k in ("bf16", "f16"):
             lowprec[k]["vs_fp32"] = lowprec[k]["value"] / (9.0 * cells * args.steps / (ms_total * 1e-3))
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(torch, dev)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -450,6 +531,7 @@ def run_ours(args):
             "kernels": per_kind,
             "cpu_baseline": cpu,
             "lowprec": lowprec,
+            "adjoint": adjoint,
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": ck,

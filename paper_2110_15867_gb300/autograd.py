@@ -5,11 +5,13 @@
 drift uses ``a_half``) and returns the density rho_nu(x) (FP64) of the final state.
 Its backward gives dL/df0 and dL/dphi for any loss of rho_nu.
 
-Memory: the forward keeps the state every K steps (checkpoints).  The backward
-takes the segments last to first: it runs the segment's steps again from its
-checkpoint with ``vlasov_step_record`` (each sweep writes the next record, so
-recording costs no copies), then applies ``vlasov_step_adjoint_recorded`` step by
-step in reverse.  The tape holds 8 K + K - 1 arrays the size of f and is reused.
+Memory: the forward keeps the state every K steps (checkpoints) and runs the last
+segment (the last 1..K steps) with ``vlasov_step_record``, which keeps the input of
+every sweep (each sweep writes the next record, so recording costs no copies).  The
+backward takes the segments last to first: the last one is already on the tape; each
+earlier one is run again from its checkpoint with ``vlasov_step_record``; then
+``vlasov_step_adjoint_recorded`` is applied step by step in reverse.  The tape holds
+8 K + K - 1 arrays the size of f and is reused by later calls.
 
 Every operation on f or lambda runs in libvlasov's kernels through the C ABI; this
 module only orders the calls and owns the buffers.
@@ -30,6 +32,7 @@ class Run:
         self.v = Vlasov(self.work, L=L, V=V)
         self._rec = []
         self._states = []
+        self.tape_owner = None  # the forward whose last segment the tape holds
 
     def tape(self, K: int):
         """Records for K steps (8 arrays each) and K - 1 intermediate states."""
@@ -53,15 +56,28 @@ class VlasovRun(torch.autograd.Function):
         if K < 1 or n_steps < 1:
             raise ValueError("need n_steps >= 1 and K >= 1")
         phi32 = phi.detach().to(torch.float32).contiguous()
+        v = run.v
         run.work.copy_(f0.detach())
-        checkpoints = []
-        for n in range(n_steps):
+        starts = [f0.detach().contiguous()]  # the state at the start of every segment
+        last = ((n_steps - 1) // K) * K       # first step of the last segment
+        for n in range(last):
             if n > 0 and n % K == 0:
-                checkpoints.append(run.work.clone())
-            run.v.step(dt, a_half, a_half, phi32)
-        rho = run.v.moment()
+                starts.append(run.work.clone())
+            v.step(dt, a_half, a_half, phi32)
+        if last > 0:
+            starts.append(run.work.clone())
+        # the last segment, recorded: its final state lands in run.work
+        m = n_steps - last
+        rec, states = run.tape(min(K, n_steps))
+        seq = [starts[-1]] + states[:m - 1]
+        for i in range(m):
+            v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else run.work)
+        token = object()
+        run.tape_owner = token
+        rho = v.moment()
         ctx.save_for_backward(f0, phi)
-        ctx.checkpoints = checkpoints
+        ctx.starts = starts[1:]
+        ctx.token = token
         ctx.run, ctx.dt, ctx.a_half, ctx.n_steps, ctx.K = run, dt, a_half, n_steps, K
         return rho
 
@@ -74,16 +90,19 @@ class VlasovRun(torch.autograd.Function):
         lam = torch.empty_like(run.work)
         v.moment_adjoint(grad_rho.detach().to(torch.float64).contiguous(), lam)
         dphi = torch.zeros(phi32.shape, dtype=torch.float64, device=phi32.device)
-        starts = [f0.detach().contiguous()] + ctx.checkpoints
+        starts = [f0.detach().contiguous()] + ctx.starts
         rec, states = run.tape(min(K, n_steps))
+        taped = run.tape_owner is ctx.token  # no other forward has reused the tape since
         for s in reversed(range(len(starts))):
             m = min(K, n_steps - s * K)
             seq = [starts[s]] + states[:m - 1]
-            for i in range(m):
-                v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else None)
+            if not (taped and s == len(starts) - 1):
+                for i in range(m):
+                    v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else None)
             for i in reversed(range(m)):
                 v.step_adjoint_recorded(seq[i], rec[i], lam, dt, a_half, phi32, dphi)
-        ctx.checkpoints = None
+        run.tape_owner = None
+        ctx.starts = None
         return lam, dphi.to(phi.dtype), None, None, None, None, None
 
 

@@ -38,6 +38,12 @@ constexpr int kAdjBlock = 256;
 #ifndef VK_ADJ_MINB
 #define VK_ADJ_MINB 3 // resident blocks per SM the FP32 column march is compiled for
 #endif
+#ifndef VK_ADJ_LCT
+#define VK_ADJ_LCT 1 // FP32 lines of 16, 32, 64 cells: unrolled instances
+#endif
+#ifndef VK_ADJ_MINB_U
+#define VK_ADJ_MINB_U 3 // the same for its unrolled (compile-time length) instances
+#endif
 constexpr int kAdjUnroll = VK_ADJ_UNROLL;
 
 template <typename C> struct AdjLim {
@@ -384,33 +390,46 @@ __device__ __forceinline__ void march_adjoint_s0(Acc &acc, const AdjLim<C> &k, i
 }
 
 // Walk a line of n cells (periodic: n >= 5; zero-flux: n >= 4).  LCT > 0:
-// compile-time length (the loop unrolls and every index is a constant).
+// compile-time length (the loops unroll, every index is a constant and the
+// window shifts become register renames).  Interior faces take the entering
+// cell's values from loads issued two faces earlier.
 template <bool PERIODIC, int LCT, typename C, typename Acc>
-__device__ __forceinline__ void march_adjoint(Acc &acc, const AdjLim<C> &k, int n, C &dLds, C &osum)
+__device__ __forceinline__ void march_adjoint(Acc &acc, const AdjLim<C> &k, int n_rt, C &dLds, C &osum)
 {
+    const int n = LCT > 0 ? LCT : n_rt;
     if (k.s == C(0)) {
-        march_adjoint_s0<PERIODIC, C>(acc, k, LCT > 0 ? LCT : n, dLds, osum);
+        march_adjoint_s0<PERIODIC, C>(acc, k, n, dLds, osum);
         return;
     }
-    AdjMarch<PERIODIC, C, Acc> m(acc, k, LCT > 0 ? LCT : n);
+    AdjMarch<PERIODIC, C, Acc> m(acc, k, n);
     m.begin();
+    const int nf = PERIODIC ? n : n - 1;
+    const int jlo = PERIODIC ? 4 : 2, jhi = PERIODIC ? n - 6 : n - 4; // interior faces
     if constexpr (LCT > 0) {
+        constexpr int NF = PERIODIC ? LCT : LCT - 1;
+        constexpr int JLO = PERIODIC ? 4 : 2, JHI = PERIODIC ? LCT - 6 : LCT - 4;
 #pragma unroll
-        for (int j = 0; j < (PERIODIC ? LCT : LCT - 1); ++j) {
-            if ((PERIODIC && j >= 4 && j <= LCT - 6) || (!PERIODIC && j >= 2 && j <= LCT - 4))
-                m.template face<true>(j, acc.c(j + 3), acc.lam(j + 3));
-            else
-                m.template face<false>(j);
+        for (int j = 0; j < (JLO < NF ? JLO : NF); ++j) m.template face<false>(j);
+        if constexpr (JLO <= JHI) {
+            C c0 = acc.c(JLO + 3), l0 = acc.lam(JLO + 3);
+            C c1 = C(0), l1 = C(0);
+            if (JLO + 4 < LCT) { c1 = acc.c(JLO + 4); l1 = acc.lam(JLO + 4); }
+#pragma unroll
+            for (int j = JLO; j <= JHI; ++j) {
+                C c2 = C(0), l2 = C(0);
+                if (j + 5 < LCT) { c2 = acc.c(j + 5); l2 = acc.lam(j + 5); }
+                m.template face<true>(j, c0, l0);
+                c0 = c1; l0 = l1;
+                c1 = c2; l1 = l2;
+            }
         }
+#pragma unroll
+        for (int j = (JHI + 1 > JLO ? JHI + 1 : JLO); j < NF; ++j) m.template face<false>(j);
     } else {
-        const int nf = PERIODIC ? n : n - 1;
-        const int jlo = PERIODIC ? 4 : 2, jhi = PERIODIC ? n - 6 : n - 4; // interior faces
         int j = 0;
 #pragma unroll 1
         for (; j < jlo && j < nf; ++j) m.template face<false>(j);
         if (j <= jhi) {
-            // interior faces, loads issued two faces ahead: cell j + 5 is read at the
-            // start of face j and enters at the end of face j + 2
             C c0 = acc.c(j + 3), l0 = acc.lam(j + 3);
             C c1 = C(0), l1 = C(0);
             if (j + 4 < n) { c1 = acc.c(j + 4); l1 = acc.lam(j + 4); }
@@ -531,8 +550,8 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
 // ----------------------------------------------------------------------------
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
-template <typename T, bool PERIODIC, bool SMALL4>
-__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : VK_ADJ_MINB) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
+template <typename T, bool PERIODIC, bool SMALL4, int LCT>
+__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_ADJ_MINB_U : VK_ADJ_MINB)) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
     const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
@@ -558,7 +577,7 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : VK_ADJ_MINB) a
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
             if constexpr (SMALL4) march_adjoint4<C>(acc, lim, dLds, osum);
-            else march_adjoint<PERIODIC, 0, C>(acc, lim, a.L, dLds, osum);
+            else march_adjoint<PERIODIC, LCT, C>(acc, lim, a.L, dLds, osum);
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = neg ? -dLds : dLds;
         }
@@ -658,11 +677,26 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool 
         case 32: adjoint_rows_kernel<T, 32><<<grid, kAdjBlock, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
         }
-    } else if (a.periodic) {
-        if (a.L == 4) adjoint_lines_kernel<T, true, true><<<grid, kAdjBlock, 0, st>>>(a);
-        else adjoint_lines_kernel<T, true, false><<<grid, kAdjBlock, 0, st>>>(a);
+    } else if (a.periodic && a.L == 4) {
+        adjoint_lines_kernel<T, true, true, 0><<<grid, kAdjBlock, 0, st>>>(a);
+    } else if constexpr (std::is_same<T, float>::value && VK_ADJ_LCT) {
+        // FP32: unrolled walks for the common line lengths
+        const bool p = a.periodic;
+#define VK_ADJ_LINES(LL)                                                                                              \
+    if (a.L == LL) {                                                                                                  \
+        if (p) adjoint_lines_kernel<T, true, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                               \
+        else adjoint_lines_kernel<T, false, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                                \
+        return cudaGetLastError();                                                                                    \
+    }
+        VK_ADJ_LINES(16)
+        VK_ADJ_LINES(32)
+        VK_ADJ_LINES(64)
+#undef VK_ADJ_LINES
+        if (p) adjoint_lines_kernel<T, true, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
+        else adjoint_lines_kernel<T, false, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
     } else {
-        adjoint_lines_kernel<T, false, false><<<grid, kAdjBlock, 0, st>>>(a);
+        if (a.periodic) adjoint_lines_kernel<T, true, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
+        else adjoint_lines_kernel<T, false, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
