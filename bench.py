@@ -63,6 +63,7 @@ def parse():
                    help="run the small profiling case instead of the benchmark: sweeps on a "
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
     p.add_argument("--axes", default="0,1,2,3,4,5", help="sweep axes of --profile-case")
+    p.add_argument("--adjoint", action="store_true", help="--profile-case runs the adjoint sweeps")
     return p.parse_args()
 
 
@@ -271,17 +272,17 @@ def build_inputs(torch, dev):
 
 
 def courant_per_dt(phi, n, nu, V, L=1.0, a=1.0):
-    """Largest |Courant number| per unit dt of the position sweeps (|u| / (a^2 dx)) and
-    of the velocity sweeps (|g| / du, g the periodic 4th-order gradient of phi): the
-    host-side arithmetic that picks dt."""
+    """Largest |Courant number| per unit dt of each sweep axis x, y, z, u_x, u_y, u_z:
+    |u| / (a^2 dx) for the position sweeps and |g_i| / du for the velocity sweeps, g the
+    periodic 4th-order gradient of phi.  Host-side arithmetic that picks dt."""
+    n = (n, n, n) if np.isscalar(n) else tuple(n)
     du = 2.0 * V / nu
-    pos = (V - 0.5 * du) * n / (L * a * a)
+    out = [(V - 0.5 * du) * n[d] / (L * a * a) for d in range(3)]
     p = phi.astype(np.float64)
-    vel = 0.0
     for d in range(3):
-        g = (8.0 * (np.roll(p, -1, d) - np.roll(p, 1, d)) - (np.roll(p, -2, d) - np.roll(p, 2, d))) / (12.0 * L / n)
-        vel = max(vel, float(np.abs(g).max()) / du)
-    return pos, vel
+        g = (8.0 * (np.roll(p, -1, d) - np.roll(p, 1, d)) - (np.roll(p, -2, d) - np.roll(p, 2, d))) / (12.0 * L / n[d])
+        out.append(float(np.abs(g).max()) / du)
+    return out
 
 
 def run_lowprec(torch, B, dev, steps, warmup):
@@ -291,8 +292,8 @@ def run_lowprec(torch, B, dev, steps, warmup):
     n, nu, V = w["n"], w["nu"], w["V"]
     phi_np = I.fourier_potential(n, seed=w["seed"] + 10).astype(np.float32)
     # the largest Courant number of the 6 axes is cfl (a kick advances dt / 2)
-    pos, vel = courant_per_dt(phi_np, n, nu, V)
-    dt = w["cfl"] / max(pos, 0.5 * vel)
+    c = courant_per_dt(phi_np, n, nu, V)
+    dt = w["cfl"] / max(max(c[:3]), 0.5 * max(c[3:]))
     delta = torch.from_numpy(I.gaussian_field(n, w["delta_rms"], seed=w["seed"])).to(dev)
     Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
     phi = torch.from_numpy(phi_np).to(dev)
@@ -344,8 +345,8 @@ def run_adjoint(torch, dev, reps=3):
     n, nu, V = w["n"], w["nu"], w["V"]
     f0 = I.initial_f(I.gaussian_field(n, w["delta_rms"], seed=w["seed"]), I.fermi_dirac(nu, V), np.float32)
     phi_np = I.fourier_potential(n, seed=w["seed"] + 10).astype(np.float32)
-    pos, vel = courant_per_dt(phi_np, n, nu, V)
-    dt = w["cfl"] / max(pos, 0.5 * vel)
+    c = courant_per_dt(phi_np, n, nu, V)
+    dt = w["cfl"] / max(max(c[:3]), 0.5 * max(c[3:]))
     run = Run(f0.shape, torch.float32, V=V)
     ft = torch.from_numpy(f0).to(dev).requires_grad_()
     pt = torch.from_numpy(phi_np).to(dev).requires_grad_()
@@ -543,9 +544,9 @@ def run_ours(args):
 
 
 def run_profile_case(args):
-    """Each requested sweep twice plus the moment on a (64, 8, 8) x 32^3 FP32 grid."""
+    """Each requested sweep (or, with --adjoint, its adjoint) twice plus the moment on a
+    (64, 8, 8) x 32^3 FP32 grid (1.34e8 cells, 537 MB)."""
     import torch
-    import oracle as O
     from paper_2110_15867_gb300 import binding as B
     from paper_2110_15867_gb300 import inputs as I
     n, nu, V = (64, 8, 8), 32, 5.0
@@ -556,13 +557,21 @@ def run_profile_case(args):
     f = ((1 + delta)[:, :, :, None, None, None] * Fu[None, None, None]).float().contiguous()
     phi_np = I.fourier_potential(n, seed=3)
     phi = torch.from_numpy(phi_np.astype(np.float32)).to(dev)
-    g = O.grid(n, nu, V=V)
-    v = B.Vlasov(f, V=V)
+    cmax = courant_per_dt(phi_np, n, nu, V)
     rho = torch.empty(n, dtype=torch.float64, device=dev)
-    for _ in range(2):
-        for ax in axes:
-            v.sweep(ax, 0.7 / O.max_abs_nu(g, ax, 1.0, 1.0, phi_np), 1.0, phi)
-        v.moment(rho)
+    if args.adjoint:
+        lam = torch.from_numpy(np.random.default_rng(4).standard_normal(f.shape).astype(np.float32)).to(dev)
+        dLdg = torch.zeros(n, dtype=torch.float64, device=dev)
+        v = B.Vlasov(torch.empty_like(f), V=V)
+        for _ in range(2):
+            for ax in axes:
+                v.sweep_adjoint(f, lam, ax, 0.7 / cmax[ax], 1.0, phi, dLdg if ax >= 3 else None)
+    else:
+        v = B.Vlasov(f, V=V)
+        for _ in range(2):
+            for ax in axes:
+                v.sweep(ax, 0.7 / cmax[ax], 1.0, phi)
+            v.moment(rho)
     v.status()
     v.close()
     return 0
