@@ -98,6 +98,17 @@ int vlasov_set_f(vlasov_ctx *ctx, void *f_dev, float *scale_dev);
 int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *phi_dev);
 
 /*
+ * Kicks of vlasov_step (D_uz D_uy D_ux, Eq. 5) on FP32 storage with n_uy = n_uz
+ * = 16 or 32 run D_uy and D_uz in one pass over f: each u_z tile of 256 rows
+ * holds whole (cell, j_x) planes, whose columns are the u_y lines, so D_uy runs
+ * on the staged tile before D_uz (the arithmetic of the separate sweeps,
+ * bit for bit).  Off by default (the fused pass is compute-bound and only ~2 %
+ * faster than the separate sweeps); on = 1 enables it.  Other storage types and
+ * shapes always run the sweeps separately.
+ */
+int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
+
+/*
  * rho_nu(x) = du_x du_y du_z * sum over the velocity cube of f (Sec. 4.1.3),
  * written to rho_dev (nx*ny*nz FP64).  Each cell sum is formed from
  * compensated FP32 partial sums combined in FP64.  If mass_host is non-NULL
@@ -153,7 +164,8 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
 #define VLASOV_T_ADJ_X 10     /* kinds 10..15: adjoint sweeps along x, y, z, u_x, u_y, u_z */
 #define VLASOV_T_GRAD_ADJ 16  /* transposed potential gradient of the step adjoint   */
 #define VLASOV_T_MOMENT_ADJ 17 /* moment adjoint                                      */
-#define VLASOV_T_KINDS 18
+#define VLASOV_T_SWEEP_UYUZ 18 /* fused kick tail D_uz D_uy (see vlasov_set_fused_kick) */
+#define VLASOV_T_KINDS 19
 int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
 

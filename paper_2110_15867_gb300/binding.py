@@ -44,7 +44,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
-           "vlasov_moment_adjoint")
+           "vlasov_moment_adjoint", "vlasov_set_fused_kick")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -52,7 +52,7 @@ STATIC_MAX_CELLS = 32768
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
            "poisson", "coef", "mass", "adj_x", "adj_y", "adj_z", "adj_ux", "adj_uy", "adj_uz",
-           "grad_adj", "moment_adj")
+           "grad_adj", "moment_adj", "sweep_uyuz")
 
 
 def library_path() -> str:
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_adjoint_recorded.restype = ctypes.c_int
     L.vlasov_moment_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_int]
     L.vlasov_moment_adjoint.restype = ctypes.c_int
+    L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
+    L.vlasov_set_fused_kick.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -185,6 +187,10 @@ def vlasov_step_adjoint_recorded(ctx, f_n_ptr: int, rec_ptrs, lam_ptr: int, dt: 
 
 def vlasov_moment_adjoint(ctx, dLdrho_ptr: int, lam_ptr: int, accumulate: bool = False):
     return _check(ctx, load().vlasov_moment_adjoint(ctx, dLdrho_ptr, lam_ptr, int(bool(accumulate))))
+
+
+def vlasov_set_fused_kick(ctx, on: bool):
+    return _check(ctx, load().vlasov_set_fused_kick(ctx, int(bool(on))))
 
 
 def vlasov_sweep(ctx, axis: int, dt: float, a: float, phi_ptr):
@@ -417,6 +423,10 @@ class Vlasov:
             raise ValueError("f_host must be a contiguous host tensor like f")
         self._sync_stream()
         vlasov_download(self.ctx, f_host.data_ptr())
+
+    def set_fused_kick(self, on: bool = True):
+        """Run the kicks' D_uy and D_uz in one pass (FP32, n_uy = n_uz = 16 or 32)."""
+        vlasov_set_fused_kick(self.ctx, on)
 
     def enable_timers(self, on: bool = True):
         vlasov_enable_timers(self.ctx, on)

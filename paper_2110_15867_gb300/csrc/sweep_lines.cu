@@ -12,6 +12,13 @@
 // share a spatial cell), and writes them back for the TMA store.  This replaces
 // the shared-memory transpose of sweep_contig.cu, the GPU analogue of the
 // paper's load-and-transpose (LAT, Sec. 4.3), for these line lengths.
+//
+// Fused kick tail (FUSE_Y, FP32, n_uy = n_uz): a tile of 256 rows is 256 / n_uy
+// whole (cell, j_x) planes of n_uy rows (j_y) by n_uz columns (j_z), so the
+// u_y lines of the tile are its columns.  Before the u_z sweep each consumer
+// thread walks one packed pair of adjacent columns down a plane (D_uy, Eq. 4
+// for i = 2); the u_z sweep then reads the updated tile: D_uz D_uy in one pass
+// over f instead of two.
 #include "vk_common.cuh"
 
 namespace vk {
@@ -170,7 +177,34 @@ __device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, c
     return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
 }
 
-template <int NU, typename T>
+// D_uy on the tile's planes (FP32, n_uy = n_uz = NU).  Warp w later sweeps
+// rows 32w..32w+31 and 128+32w..128+32w+31 along u_z, which are whole planes
+// (NU = 16 or 32 divides 32): lanes 0-15 take the first block of rows, lanes
+// 16-31 the second, and each lane owns one packed pair of adjacent columns of
+// one plane, so a warp only touches its own rows.  Returns true when a line
+// sum is negative, NaN or infinite.
+template <int NU, bool NEG>
+__device__ __forceinline__ bool plane_columns(unsigned char *base, int tid, const Lim<float2> &lim)
+{
+    using G_ = LineGeom<NU, float>;
+    const int w = tid >> 5, l = tid & 31;
+    const int within = l & 15;
+    const int r_first = ((l >> 4) ? kLineThreads : 0) + 32 * w + (within / (NU / 2)) * NU; // first row of the plane
+    const int c = 2 * (within % (NU / 2));
+    float2 v[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        v[NEG ? NU - 1 - i : i] =
+            *reinterpret_cast<const float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4);
+    const float2 sum = march_regs<NU>(v, lim);
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        *reinterpret_cast<float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4) =
+            v[NEG ? NU - 1 - i : i];
+    return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
+}
+
+template <int NU, typename T, bool FUSE_Y>
 __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
     line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                       const __grid_constant__ ContigArgs<float> args)
@@ -233,12 +267,23 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
     const int r0 = tid, r1 = tid + kLineThreads;
     for (unsigned k = 0; k < n_my; ++k) {
         const unsigned st = k % S;
-        if (!mbar_wait_bounded(&full[st], (k / S) & 1u)) {
+        // all lanes of a warp leave together (the fused pass synchronises the warp)
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (k / S) & 1u))) {
             atomicOr(args.err, ERR_TIMEOUT);
             break;
         }
         const long long row0 = (b + (long long)k * Gd) * kLineRows;
         unsigned char *base = slot(k);
+        if constexpr (FUSE_Y) {
+            // every row of the tile belongs to one spatial cell
+            const LineCoefT<float> ky = args.cell_coef_y[row0 / args.rows_per_cell];
+            if (row0 < args.rows && ky.nd >= 0) {
+                const bool bad = (ky.nd & 1) ? plane_columns<NU, true>(base, tid, to_lim2(ky, ky))
+                                             : plane_columns<NU, false>(base, tid, to_lim2(ky, ky));
+                if (bad) atomicOr(args.err, ERR_NAN);
+            }
+            __syncwarp();
+        }
         if (row0 + r0 < args.rows) {
             const LineCoefT<float> kc = args.cell_coef[(row0 + r0) / args.rows_per_cell];
             if (kc.nd >= 0) {
@@ -266,11 +311,12 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
 
 template <typename T> static const void *line_kernel_ptr(int nu)
 {
-    return nu == 32 ? (const void *)line_sweep_kernel<32, T> : (const void *)line_sweep_kernel<16, T>;
+    return nu == 32 ? (const void *)line_sweep_kernel<32, T, false> : (const void *)line_sweep_kernel<16, T, false>;
 }
 
-static const void *line_kernel_for(int nu, int dtype)
+static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
 {
+    if (fuse_y) return nu == 32 ? (const void *)line_sweep_kernel<32, float, true> : (const void *)line_sweep_kernel<16, float, true>;
     return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
 }
 
@@ -282,9 +328,10 @@ bool line_sweep_supported(int nu, long long rows_per_cell)
 }
 
 cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
-                              int dtype, int grid, cudaStream_t st)
+                              int dtype, int grid, cudaStream_t st, bool fuse_y)
 {
-    const void *k = line_kernel_for(nu, dtype);
+    if (fuse_y && (dtype != 1 || !a.cell_coef_y)) return cudaErrorInvalidValue;
+    const void *k = line_kernel_for(nu, dtype, fuse_y);
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -292,9 +339,9 @@ cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
     return cudaLaunchKernel(k, dim3(grid), dim3(kLineThreads + kProducer), args, smem, st);
 }
 
-int occupancy_line_sweep(int nu, int dtype)
+int occupancy_line_sweep(int nu, int dtype, bool fuse_y)
 {
-    const void *k = line_kernel_for(nu, dtype);
+    const void *k = line_kernel_for(nu, dtype, fuse_y);
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;

@@ -25,6 +25,10 @@
 
 namespace vk {
 
+#ifndef VK_STREAM_MINB
+#define VK_STREAM_MINB 4 // resident CTAs per SM the streamed sweep is compiled for
+#endif
+
 // Per-thread view of the storage of its column(s): load a row as the compute
 // vector X and store X back.  FP32 / FP64 store f itself.  BF16 / FP16 store
 // f / scale with one FP32 scale per u_z line; the scale of the row comes from
@@ -252,7 +256,7 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
 }
 
 template <typename T, bool PERIODIC>
-__global__ void __launch_bounds__(kStreamConsumers + kProducer, 4)
+__global__ void __launch_bounds__(kStreamConsumers + kProducer, VK_STREAM_MINB)
     stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                         const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)

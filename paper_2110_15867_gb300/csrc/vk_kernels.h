@@ -141,6 +141,7 @@ template <typename C> struct ContigArgs {
     unsigned *err;
     float *scale; // 16-bit storage: one FP32 scale per row (u_z line), updated in place
     unsigned seed;
+    const LineCoefT<C> *cell_coef_y; // fused kick tail: the u_y sweep's per-cell constants
 };
 
 // u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box
@@ -148,7 +149,8 @@ template <typename C> struct ContigArgs {
 bool line_sweep_supported(int nu, long long rows_per_cell);
 size_t line_sweep_smem(int nu, int es);
 int line_sweep_rows_per_tile();
-int occupancy_line_sweep(int nu, int dtype); // dtype: 1 f32, 2 bf16, 3 f16
+// fuse_y: D_uy on the tile's (cell, j_x) planes first (FP32, n_uy = n_uz)
+int occupancy_line_sweep(int nu, int dtype, bool fuse_y = false); // dtype: 1 f32, 2 bf16, 3 f16
 
 // host launchers (return cudaGetLastError() of the launch); tiles are loaded
 // through map and stored through dmap (the same map for an in-place sweep)
@@ -164,7 +166,7 @@ cudaError_t launch_contig_f64(const CUtensorMap &map, const CUtensorMap &dmap, c
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
 cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
-                              int dtype, int grid, cudaStream_t st);
+                              int dtype, int grid, cudaStream_t st, bool fuse_y = false);
 
 // ----------------------------------------------------------------------------
 // fields: velocity-sweep coefficients, moment, Poisson

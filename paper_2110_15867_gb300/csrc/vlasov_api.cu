@@ -112,6 +112,9 @@ struct vlasov_ctx {
     bool use_lines;
     CUtensorMap lmap;
     MapSpec lspec;
+    // kick tail D_uz D_uy fused in the u_z line kernel (FP32, n_uy = n_uz)
+    bool can_fuse_kick, fuse_kick;
+    int lgrid_fused;
     long long lrows, ltiles;
     int lgrid;
     // scratch
@@ -346,6 +349,12 @@ static int plan_axes(vlasov_ctx *c)
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
         c->lgrid = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
     }
+    c->can_fuse_kick = c->use_lines && c->g.dtype == VLASOV_F32 && c->g.nuy == c->g.nuz;
+    if (c->can_fuse_kick) {
+        const int occ = occupancy_line_sweep(c->g.nuz, c->g.dtype, true);
+        if (occ <= 0) return fail(c, VLASOV_ECUDA, "fused kick CTA does not fit");
+        c->lgrid_fused = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
+    }
     return VLASOV_OK;
 }
 
@@ -397,6 +406,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->stream = (cudaStream_t)stream;
     c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
+    c->fuse_kick = false; // see vlasov_set_fused_kick
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
     c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
     c->gd.L = g->L;
@@ -743,6 +753,38 @@ extern "C" int vlasov_poisson(vlasov_ctx *c, const double *rho_dev, const double
     return VLASOV_OK;
 }
 
+// D_uz D_uy in one pass of the u_z line kernel (constants in d_coef[1], d_coef[2])
+static int run_kick_tail(vlasov_ctx *c)
+{
+    c->sweeps += 2;
+    ContigArgs<float> A{};
+    A.L = c->g.nuz; A.R = line_sweep_rows_per_tile(); A.stages = 0; A.rows = c->lrows; A.num_tiles = c->ltiles;
+    A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.err = c->d_err;
+    A.cell_coef = (const LineCoefT<float> *)c->d_coef[2];
+    A.cell_coef_y = (const LineCoefT<float> *)c->d_coef[1];
+    PartTimer t(c, VLASOV_T_SWEEP_UYUZ, 1);
+    const cudaError_t e = launch_line_sweep(c->lmap, c->lmap, A, c->g.nuz, c->g.dtype, c->lgrid_fused, c->stream, true);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fused kick launch");
+    return VLASOV_OK;
+}
+
+// one kick D_uz D_uy D_ux (constants already in d_coef), in place
+static int run_kick(vlasov_ctx *c)
+{
+    int rc;
+    if ((rc = run_velocity(c, 3))) return rc;
+    if (c->can_fuse_kick && c->fuse_kick) return run_kick_tail(c);
+    if ((rc = run_velocity(c, 4))) return rc;
+    return run_velocity(c, 5);
+}
+
+extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int on)
+{
+    if (!c) return VLASOV_EINVAL;
+    c->fuse_kick = on != 0;
+    return VLASOV_OK;
+}
+
 extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_full, const float *phi_n_dev,
                            const double *rho_bg_dev, double four_pi_G, float *phi_next_dev, double *rho_nu_dev)
 {
@@ -751,8 +793,7 @@ extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_ful
     int rc;
     // kick D_uz D_uy D_ux (dt/2), D_ux first
     if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
-    for (int ax = 3; ax <= 5; ++ax)
-        if ((rc = run_velocity(c, ax))) return rc;
+    if ((rc = run_kick(c))) return rc;
     // drift D_x D_y D_z (dt), D_z first, at the mid-step scale factor
     for (int ax = 2; ax >= 0; --ax)
         if ((rc = run_position(c, ax, dt, a_half))) return rc;
@@ -764,9 +805,7 @@ extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_ful
         if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
     }
     // second kick (the constants are unchanged when phi is)
-    for (int ax = 3; ax <= 5; ++ax)
-        if ((rc = run_velocity(c, ax))) return rc;
-    return VLASOV_OK;
+    return run_kick(c);
 }
 
 extern "C" int vlasov_status(vlasov_ctx *c)
