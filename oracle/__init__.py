@@ -95,6 +95,8 @@ def lib():
         L.orc_gradient.restype = None
         L.orc_moment.argtypes = [_G, _D, _D]
         L.orc_moment.restype = ctypes.c_double
+        L.orc_moments.argtypes = [_G, _D, _D, _D, _D]
+        L.orc_moments.restype = None
         L.orc_poisson.argtypes = [_G, _D, ctypes.c_double, ctypes.c_double, _D]
         L.orc_poisson.restype = None
         L.orc_step.argtypes = [_G, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D,
@@ -187,6 +189,16 @@ def moment(g: Grid, f: np.ndarray):
     rho = np.empty(tuple(g.n), dtype=np.float64)
     mass = lib().orc_moment(ctypes.byref(g), _p(f), _p(rho))
     return rho, mass
+
+
+def moments(g: Grid, f: np.ndarray):
+    """Return (rho, umean [3, nx, ny, nz], sigma2 [6, nx, ny, nz]) per Sec. 4.1.3: cell-centre
+    sums S0, S1_i, S2_ij; umean = S1 / S0, sigma2 = S2 / S0 - umean umean (xx, yy, zz, xy, xz, yz)."""
+    rho = np.empty(tuple(g.n), dtype=np.float64)
+    um = np.empty((3,) + tuple(g.n), dtype=np.float64)
+    s2 = np.empty((6,) + tuple(g.n), dtype=np.float64)
+    lib().orc_moments(ctypes.byref(g), _p(_f64(f)), _p(rho), _p(um), _p(s2))
+    return rho, um, s2
 
 
 def poisson(g: Grid, rho, a: float, four_pi_G: float = 1.0) -> np.ndarray:

@@ -393,6 +393,48 @@ double orc_moment(const orc_grid *g, const double *f, double *rho)
     return nsum_get(&m) * orc_dx(g, 0) * orc_dx(g, 1) * orc_dx(g, 2);
 }
 
+/*
+ * Velocity moments per spatial cell (Sec. 4.1.3: mass density, mean velocity and
+ * velocity dispersion tensor), as discrete sums over the velocity cell centres u_j:
+ *   S0 = sum f,  S1_i = sum u_i f,  S2_ij = sum u_i u_j f
+ *   rho = du^3 S0,  umean_i = S1_i / S0,  sigma2_ij = S2_ij / S0 - umean_i umean_j
+ * (0 where S0 = 0).  umean is [3][ncell]; sigma2 is [6][ncell] in the order
+ * xx, yy, zz, xy, xz, yz.  Any output may be NULL.
+ */
+void orc_moments(const orc_grid *g, const double *f, double *rho, double *umean, double *sigma2)
+{
+    const long ncell = (long)g->n[0] * g->n[1] * g->n[2];
+    const long nux = g->nu[0], nuy = g->nu[1], nuz = g->nu[2];
+    const long cube = nux * nuy * nuz;
+    const double du3 = orc_du(g, 0) * orc_du(g, 1) * orc_du(g, 2);
+    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < ncell; ++c) {
+        nsum s0 = {0.0, 0.0}, s1[3], s2[6];
+        for (int i = 0; i < 3; ++i) s1[i] = s0;
+        for (int k = 0; k < 6; ++k) s2[k] = s0;
+        const double *q = f + c * cube;
+        for (long jx = 0; jx < nux; ++jx)
+            for (long jy = 0; jy < nuy; ++jy)
+                for (long jz = 0; jz < nuz; ++jz) {
+                    const double v = q[(jx * nuy + jy) * nuz + jz];
+                    const double u[3] = {orc_u(g, 0, jx), orc_u(g, 1, jy), orc_u(g, 2, jz)};
+                    nsum_add(&s0, v);
+                    for (int i = 0; i < 3; ++i) nsum_add(&s1[i], u[i] * v);
+                    for (int k = 0; k < 6; ++k) nsum_add(&s2[k], u[pi[k]] * u[pj[k]] * v);
+                }
+        const double S0 = nsum_get(&s0);
+        double m[3];
+        for (int i = 0; i < 3; ++i) m[i] = S0 != 0.0 ? nsum_get(&s1[i]) / S0 : 0.0;
+        if (rho) rho[c] = du3 * S0;
+        if (umean)
+            for (int i = 0; i < 3; ++i) umean[i * ncell + c] = m[i];
+        if (sigma2)
+            for (int k = 0; k < 6; ++k)
+                sigma2[k * ncell + c] = S0 != 0.0 ? nsum_get(&s2[k]) / S0 - m[pi[k]] * m[pj[k]] : 0.0;
+    }
+}
+
 /* plain separable DFT of a complex 3D array along dimension d, sign = -1 forward */
 static void dft_axis(const orc_grid *g, double *re, double *im, int d, int sign)
 {
