@@ -472,6 +472,23 @@ def run_ours(args):
             per_kind[k]["GBs"] = alg_bytes / (per_kind[k]["ms_per_launch"] * 1e-3) / 1e9
     gpu_launches = int(sum(kind_n.values()))
 
+    # velocity moments of the final state (density, mean velocity, dispersion tensor), timed alone
+    um = torch.empty((3, n, n, n), dtype=torch.float64, device=dev)
+    s2 = torch.empty((6, n, n, n), dtype=torch.float64, device=dev)
+    B.vlasov_moments(v.ctx, rho.data_ptr(), um.data_ptr(), s2.data_ptr())
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(3):
+        B.vlasov_moments(v.ctx, rho.data_ptr(), um.data_ptr(), s2.data_ptr())
+    m1.record(stream)
+    torch.cuda.synchronize()
+    v.status()
+    m_ms = m0.elapsed_time(m1) / 3
+    moments = {"ms_per_launch": m_ms, "GBs": 4.0 * cells / (m_ms * 1e-3) / 1e9,
+               "what": "rho, mean velocity, dispersion tensor of the 64^3 x 32^3 state (4 B read per cell)"}
+    del um, s2
+
     # end to end through the C ABI with host buffers: f host -> device, step, f and rho back
     e2e = None
     if not args.no_e2e:
@@ -533,6 +550,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "lowprec": lowprec,
             "adjoint": adjoint,
+            "moments": moments,
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": ck,

@@ -117,6 +117,20 @@ int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
 int vlasov_moment(vlasov_ctx *ctx, double *rho_dev, double *mass_host);
 
 /*
+ * The velocity moments the paper keeps per spatial cell (Sec. 4.1.3, Listing 1:
+ * mass density, mean velocity, velocity dispersion tensor), as sums over the
+ * velocity cell centres u_j: S0 = sum f, S1_i = sum u_i f, S2_ij = sum u_i u_j f.
+ *   rho_dev    nx*ny*nz FP64: du_x du_y du_z S0
+ *   umean_dev  3*nx*ny*nz FP64, component-major [3][nx][ny][nz]: S1_i / S0
+ *   sigma2_dev 6*nx*ny*nz FP64, [6][nx][ny][nz] in the order xx, yy, zz, xy, xz,
+ *              yz: S2_ij / S0 - umean_i umean_j
+ * (umean and sigma2 are 0 where S0 = 0).  Any output may be NULL (not all).
+ * One pass over f, per-thread FP32 compensated sums (FP64 for FP64 storage)
+ * combined in FP64 in a fixed order; any storage type.
+ */
+int vlasov_moments(vlasov_ctx *ctx, double *rho_dev, double *umean_dev, double *sigma2_dev);
+
+/*
  * Eq. (2): solve nabla^2 phi = four_pi_G a^2 (rho - mean rho) on the periodic
  * spatial grid by a discrete Fourier transform (continuous |k|^2 =
  * (2 pi n / L)^2, the k = 0 mode set to zero).  rho = rho_dev + rho_bg_dev
@@ -165,7 +179,8 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
 #define VLASOV_T_GRAD_ADJ 16  /* transposed potential gradient of the step adjoint   */
 #define VLASOV_T_MOMENT_ADJ 17 /* moment adjoint                                      */
 #define VLASOV_T_SWEEP_UYUZ 18 /* fused kick tail D_uz D_uy (see vlasov_set_fused_kick) */
-#define VLASOV_T_KINDS 19
+#define VLASOV_T_MOMENTS 19    /* vlasov_moments                                      */
+#define VLASOV_T_KINDS 20
 int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
 

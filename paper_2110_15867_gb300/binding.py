@@ -44,7 +44,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
-           "vlasov_moment_adjoint", "vlasov_set_fused_kick")
+           "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -52,7 +52,7 @@ STATIC_MAX_CELLS = 32768
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
            "poisson", "coef", "mass", "adj_x", "adj_y", "adj_z", "adj_ux", "adj_uy", "adj_uz",
-           "grad_adj", "moment_adj", "sweep_uyuz")
+           "grad_adj", "moment_adj", "sweep_uyuz", "moments")
 
 
 def library_path() -> str:
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_adjoint_recorded.restype = ctypes.c_int
     L.vlasov_moment_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_int]
     L.vlasov_moment_adjoint.restype = ctypes.c_int
+    L.vlasov_moments.argtypes = [_VP, _VP, _VP, _VP]
+    L.vlasov_moments.restype = ctypes.c_int
     L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
     L.vlasov_set_fused_kick.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
@@ -201,6 +203,10 @@ def vlasov_moment(ctx, rho_ptr: int, want_mass: bool = False):
     m = ctypes.c_double(0.0)
     _check(ctx, load().vlasov_moment(ctx, rho_ptr, ctypes.byref(m) if want_mass else None))
     return m.value if want_mass else None
+
+
+def vlasov_moments(ctx, rho_ptr, umean_ptr, sigma2_ptr):
+    return _check(ctx, load().vlasov_moments(ctx, rho_ptr, umean_ptr, sigma2_ptr))
 
 
 def vlasov_poisson(ctx, rho_ptr, rho_bg_ptr, a: float, four_pi_G: float, phi_ptr):
@@ -337,6 +343,18 @@ class Vlasov:
         self._field(rho, self.torch.float64)
         m = vlasov_moment(self.ctx, rho.data_ptr(), mass)
         return (rho, m) if mass else rho
+
+    def moments(self):
+        """(rho [nx,ny,nz], umean [3,nx,ny,nz], sigma2 [6,nx,ny,nz]) in FP64: density, mean
+        velocity and velocity dispersion tensor (xx, yy, zz, xy, xz, yz)."""
+        self._sync_stream()
+        n = self.shape[:3]
+        T = self.torch
+        rho = T.empty(n, dtype=T.float64, device=self.f.device)
+        um = T.empty((3,) + n, dtype=T.float64, device=self.f.device)
+        s2 = T.empty((6,) + n, dtype=T.float64, device=self.f.device)
+        vlasov_moments(self.ctx, rho.data_ptr(), um.data_ptr(), s2.data_ptr())
+        return rho, um, s2
 
     def poisson(self, rho, a: float, four_pi_G: float = 1.0, rho_bg=None, phi=None):
         self._sync_stream()

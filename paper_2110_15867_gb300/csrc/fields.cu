@@ -242,6 +242,166 @@ cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int d
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// velocity moments: density, mean velocity, velocity dispersion tensor
+// ----------------------------------------------------------------------------
+// Sec. 4.1.3 keeps each spatial cell's velocity cube in one place so that these
+// need no communication.  Per cell: S0 = sum f, S1_i = sum u_i f, S2_ij = sum
+// u_i u_j f over the velocity cell centres; rho = du^3 S0, umean_i = S1_i / S0,
+// sigma2_ij = S2_ij / S0 - umean_i umean_j (0 where S0 = 0).
+
+// 16 bytes of storage -> N values (x the row's scale for 16-bit codes)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    static constexpr int N = 4;
+    __device__ static void get(const uint4 &u, float, float (&o)[4])
+    {
+        o[0] = __uint_as_float(u.x); o[1] = __uint_as_float(u.y);
+        o[2] = __uint_as_float(u.z); o[3] = __uint_as_float(u.w);
+    }
+};
+template <> struct Vec16<double> {
+    static constexpr int N = 2;
+    __device__ static void get(const uint4 &u, double, double (&o)[2])
+    {
+        o[0] = __hiloint2double(int(u.y), int(u.x));
+        o[1] = __hiloint2double(int(u.w), int(u.z));
+    }
+};
+template <> struct Vec16<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ static void get(const uint4 &u, float sc, float (&o)[8])
+    {
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            o[2 * q] = __uint_as_float(w[q] << 16) * sc;
+            o[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u) * sc;
+        }
+    }
+};
+template <> struct Vec16<__half> {
+    static constexpr int N = 8;
+    __device__ static void get(const uint4 &u, float sc, float (&o)[8])
+    {
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
+            o[2 * q] = h.x * sc;
+            o[2 * q + 1] = h.y * sc;
+        }
+    }
+};
+
+// compensated accumulator in the working precision
+template <typename C> struct NSum {
+    C s, c;
+    __device__ void add(C x)
+    {
+        const C t = s + x;
+        c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ double get() const { return (double)s + (double)c; }
+};
+
+// One warp per spatial cell: each lane sums every 32nd 16-byte vector of the
+// cube, then the ten sums are combined across the warp in FP64 in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) moments_kernel(GridDims g, const T *__restrict__ f,
+                                                      const float *__restrict__ scale, double *rho, double *umean,
+                                                      double *sigma2)
+{
+    using C = typename Compute<T>::type;
+    constexpr int N = Vec16<T>::N;
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int nux = g.nu[0], nuy = g.nu[1], nuz = g.nu[2];
+    const int nvec = nux * nuy * nuz / N; // 16-byte vectors per cube
+    const int vrow = nuz / N;             // per u_z line
+    const double du3 = (2.0 * g.V / nux) * (2.0 * g.V / nuy) * (2.0 * g.V / nuz);
+    // n / d as a multiply-high by floor((2^32 - 1) / d) + 1: exact while n d < 2^32
+    // (here n < 2^21, d <= 128)
+    const unsigned mv = 0xffffffffu / unsigned(vrow) + 1u, my = 0xffffffffu / unsigned(nuy) + 1u;
+    auto div_vrow = [&](int n) { return vrow == 1 ? n : int(__umulhi(unsigned(n), mv)); };
+    auto div_nuy = [&](int n) { return int(__umulhi(unsigned(n), my)); };
+    __shared__ C su[3][kMaxVel]; // velocity cell centres, formed in FP64 and rounded once
+    for (int j = threadIdx.x; j < kMaxVel; j += blockDim.x)
+        for (int d = 0; d < 3; ++d) su[d][j] = j < g.nu[d] ? C(-g.V + (j + 0.5) * (2.0 * g.V / g.nu[d])) : C(0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long cell = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(f + cell * (long long)nvec * N);
+        const float *sc = scale ? scale + cell * nux * nuy : nullptr;
+        // S0 compensated; the other nine sums in the working precision
+        NSum<C> s0{C(0), C(0)};
+        C acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = C(0);
+#pragma unroll 4
+        for (int k = lane; k < nvec; k += 32) {
+            const int row = div_vrow(k), jz0 = (k - row * vrow) * N;
+            const int jx = div_nuy(row), jy = row - jx * nuy;
+            C v[N];
+            Vec16<T>::get(q[k], sc ? sc[row] : 1.f, v);
+            const C ux = su[0][jx], uy = su[1][jy];
+            C t0 = C(0), t1 = C(0), t2 = C(0);
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                const C uz = su[2][jz0 + e];
+                const C w = uz * v[e];
+                t0 += v[e];
+                t1 += w;
+                t2 += uz * w;
+            }
+            s0.add(t0);
+            acc[0] += ux * t0;
+            acc[1] += uy * t0;
+            acc[2] += t1;
+            acc[3] += ux * ux * t0;
+            acc[4] += uy * uy * t0;
+            acc[5] += t2;
+            acc[6] += ux * uy * t0;
+            acc[7] += ux * t1;
+            acc[8] += uy * t1;
+        }
+        double S[10];
+        S[0] = warp_sum_d(s0.get());
+#pragma unroll
+        for (int k = 1; k < 10; ++k) S[k] = warp_sum_d((double)acc[k - 1]);
+        if (lane == 0) {
+            const double S0 = S[0], inv = S0 != 0.0 ? 1.0 / S0 : 0.0;
+            const double m[3] = {S[1] * inv, S[2] * inv, S[3] * inv};
+            // S index of sigma2 component k (xx, yy, zz, xy, xz, yz) and its pair
+            const int si[6] = {4, 5, 6, 7, 8, 9}, pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+            if (rho) rho[cell] = du3 * S0;
+            if (umean)
+                for (int i = 0; i < 3; ++i) umean[i * ncell + cell] = m[i];
+            if (sigma2)
+                for (int k = 0; k < 6; ++k)
+                    sigma2[k * ncell + cell] = S0 != 0.0 ? S[si[k]] * inv - m[pi[k]] * m[pj[k]] : 0.0;
+        }
+    }
+}
+
+cudaError_t launch_moments(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
+                           double *umean, double *sigma2, cudaStream_t st, int sm_count)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long need = (ncell + 7) / 8; // 8 warps (cells) per block
+    const long long blocks = need < (long long)sm_count * 8 ? need : (long long)sm_count * 8;
+    switch (dtype) {
+    case 0: moments_kernel<double><<<int(blocks), 256, 0, st>>>(g, (const double *)f, nullptr, rho, umean, sigma2); break;
+    case 1: moments_kernel<float><<<int(blocks), 256, 0, st>>>(g, (const float *)f, nullptr, rho, umean, sigma2); break;
+    case 2:
+        moments_kernel<__nv_bfloat16><<<int(blocks), 256, 0, st>>>(g, (const __nv_bfloat16 *)f, scale, rho, umean, sigma2);
+        break;
+    default: moments_kernel<__half><<<int(blocks), 256, 0, st>>>(g, (const __half *)f, scale, rho, umean, sigma2); break;
+    }
+    return cudaGetLastError();
+}
+
 // dx dy dz * sum rho, Neumaier in FP64 per thread, fixed-order combine
 __global__ void __launch_bounds__(1024) mass_kernel(GridDims g, const double *__restrict__ rho, double *out)
 {

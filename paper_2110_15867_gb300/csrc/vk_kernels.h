@@ -221,6 +221,10 @@ cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *r
 // 16-bit storage (dtype 2 bf16, 3 f16) with one scale per u_z line
 cudaError_t launch_moment_coded(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
                                 cudaStream_t st, int sm_count);
+// density, mean velocity [3][ncell] and dispersion tensor [6][ncell] (xx, yy, zz, xy,
+// xz, yz) per spatial cell; any output may be null; scale: 16-bit storage only
+cudaError_t launch_moments(const GridDims &g, const void *f, const float *scale, int dtype, double *rho,
+                           double *umean, double *sigma2, cudaStream_t st, int sm_count);
 // lam (+)= du^3 dLdrho(x) over each velocity cube (FP64 or FP32 lam: dtype 0 / 1)
 cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int dtype, void *lam, int accumulate,
                                   cudaStream_t st, int sm_count);

@@ -741,6 +741,17 @@ extern "C" int vlasov_moment(vlasov_ctx *c, double *rho_dev, double *mass_host)
     return VLASOV_OK;
 }
 
+extern "C" int vlasov_moments(vlasov_ctx *c, double *rho_dev, double *umean_dev, double *sigma2_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!rho_dev && !umean_dev && !sigma2_dev) return fail(c, VLASOV_EINVAL, "vlasov_moments: no output");
+    PartTimer t(c, VLASOV_T_MOMENTS, 1);
+    const cudaError_t e = launch_moments(c->gd, c->f, c->scale, c->g.dtype, rho_dev, umean_dev, sigma2_dev, c->stream,
+                                         c->sm_count);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments launch");
+    return VLASOV_OK;
+}
+
 extern "C" int vlasov_poisson(vlasov_ctx *c, const double *rho_dev, const double *rho_bg_dev, double a,
                               double four_pi_G, float *phi_dev)
 {
