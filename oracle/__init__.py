@@ -33,6 +33,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 MP = 1  # monotonicity-preserving constraint
 PP = 2  # positivity clamp
 MPP = MP | PP
+PHI32 = 4  # self-consistent step: phi^{n+1} stored in FP32, as on the GPU
 
 _lib = None
 
@@ -117,6 +118,9 @@ def lib():
         L.orc_step_adjoint.argtypes = [_G, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D,
                                        ctypes.c_int]
         L.orc_step_adjoint.restype = ctypes.c_int
+        L.orc_step_adjoint_sc.argtypes = [_G, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D,
+                                          ctypes.c_double, _D, _D, _D, ctypes.c_int]
+        L.orc_step_adjoint_sc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -265,3 +269,15 @@ def step_adjoint(g: Grid, f_n: np.ndarray, lam: np.ndarray, dt: float, a_half: f
     lib().orc_step_adjoint(ctypes.byref(g), _p(_f64(f_n)), _p(lam), dt, a_half,
                            _p(_f64(phi)), _p(dphi), flags)
     return dphi
+
+
+def step_adjoint_sc(g: Grid, f_n: np.ndarray, lam: np.ndarray, dt: float, a_half: float, a_full: float, phi_n,
+                    rho_bg=None, four_pi_G: float = 1.0, lam_phi_next=None, flags: int = MPP):
+    """Adjoint of one self-consistent step (state f, phi): in place lam <- dL/df^n from
+    dL/df^{n+1}; lam_phi_next = dL/dphi^{n+1} (or None).  Returns (dL/dphi_n, dL/drho_bg)."""
+    dphi = np.zeros(tuple(g.n))
+    dbg = np.zeros(tuple(g.n))
+    lib().orc_step_adjoint_sc(ctypes.byref(g), _p(_f64(f_n)), _p(lam), dt, a_half, a_full, _p(_f64(phi_n)),
+                              _p(None if rho_bg is None else _f64(rho_bg)), four_pi_G,
+                              _p(None if lam_phi_next is None else _f64(lam_phi_next)), _p(dphi), _p(dbg), flags)
+    return dphi, dbg

@@ -52,6 +52,7 @@
 
 #define ORC_MP 1 /* apply the monotonicity-preserving constraint */
 #define ORC_PP 2 /* apply the positivity clamp */
+#define ORC_PHI32 4 /* self-consistent step: store phi^{n+1} in FP32 (as the GPU does) */
 
 typedef struct {
     int n[3];   /* spatial cells along x, y, z                     */
@@ -830,5 +831,71 @@ int orc_step_adjoint(const orc_grid *g, const double *f_n, double *lam, double d
     for (int d = 0; d < 3; ++d) orc_gradient_adjoint(g, dLdg + d * ncell, d, dLdphi);
     free(dLdg);
     free(in);
+    return 0;
+}
+
+/*
+ * Adjoint of one self-consistent orc_step (phi_next computed): the state is (f, phi);
+ * f_n and phi_n enter the step, f^{n+1} and phi^{n+1} leave it.  lam holds
+ * dL/df^{n+1} on entry and dL/df^n on exit; lam_phi_next (may be NULL) is
+ * dL/dphi^{n+1} from later steps.  dL/dphi_n and dL/drho_bg (either may be NULL)
+ * are ADDED to.  With ORC_PHI32 in flags phi^{n+1} is rounded to FP32 in the
+ * recomputed forward (the rounding itself passes gradients unchanged).
+ * Backward order: second kick (with phi^{n+1}; its dL/dg gives dL/dphi^{n+1}),
+ * Poisson (a real circulant with an even multiplier: its own transpose), moment
+ * (dL/df += du^3 dL/drho), drift, first kick (dL/dphi_n).
+ */
+int orc_step_adjoint_sc(const orc_grid *g, const double *f_n, double *lam, double dt, double a_half, double a_full,
+                        const double *phi_n, const double *rho_bg, double four_pi_G, const double *lam_phi_next,
+                        double *dLdphi_n, double *dLdrho_bg, int flags)
+{
+    const long total = orc_num_cells(g);
+    const long ncell = (long)g->n[0] * g->n[1] * g->n[2];
+    const long cube = total / ncell;
+    const int axes[9] = {3, 4, 5, 2, 1, 0, 3, 4, 5};
+    const double dts[9] = {0.5 * dt, 0.5 * dt, 0.5 * dt, dt, dt, dt, 0.5 * dt, 0.5 * dt, 0.5 * dt};
+    const int sflags = flags & (ORC_MP | ORC_PP);
+    /* forward again: in[k] = input of sweep k, phi1 = phi^{n+1} */
+    double *in = (double *)malloc(sizeof(double) * total * 9);
+    double *rho = (double *)malloc(sizeof(double) * ncell);
+    double *phi1 = (double *)malloc(sizeof(double) * ncell);
+    double *w = (double *)calloc(3 * ncell + 2 * ncell, sizeof(double));
+    double *dLdg = w, *dphi1 = w + 3 * ncell, *drho = w + 4 * ncell;
+    memcpy(in, f_n, sizeof(double) * total);
+    for (int k = 0; k < 8; ++k) {
+        if (k == 6) { /* after the drift: moment, Poisson */
+            orc_moment(g, in + 6 * total, rho);
+            for (long c = 0; c < ncell; ++c) rho[c] += rho_bg ? rho_bg[c] : 0.0;
+            orc_poisson(g, rho, a_full, four_pi_G, phi1);
+            if (flags & ORC_PHI32)
+                for (long c = 0; c < ncell; ++c) phi1[c] = (double)(float)phi1[c];
+        }
+        memcpy(in + (k + 1) * total, in + k * total, sizeof(double) * total);
+        orc_sweep(g, in + (k + 1) * total, axes[k], dts[k], a_half, k >= 6 ? phi1 : phi_n, sflags);
+    }
+    /* second kick */
+    for (int k = 8; k >= 6; --k)
+        orc_sweep_adjoint(g, in + k * total, lam, axes[k], dts[k], a_half, phi1, dLdg + (axes[k] - 3) * ncell, sflags);
+    if (lam_phi_next)
+        for (long c = 0; c < ncell; ++c) dphi1[c] = lam_phi_next[c];
+    for (int d = 0; d < 3; ++d) orc_gradient_adjoint(g, dLdg + d * ncell, d, dphi1);
+    /* Poisson and moment */
+    orc_poisson(g, dphi1, a_full, four_pi_G, drho);
+    if (dLdrho_bg)
+        for (long c = 0; c < ncell; ++c) dLdrho_bg[c] += drho[c];
+    const double du3 = orc_du(g, 0) * orc_du(g, 1) * orc_du(g, 2);
+    for (long c = 0; c < ncell; ++c)
+        for (long j = 0; j < cube; ++j) lam[c * cube + j] += du3 * drho[c];
+    /* drift, first kick */
+    for (int k = 5; k >= 3; --k) orc_sweep_adjoint(g, in + k * total, lam, axes[k], dts[k], a_half, NULL, NULL, sflags);
+    for (long c = 0; c < 3 * ncell; ++c) dLdg[c] = 0.0;
+    for (int k = 2; k >= 0; --k)
+        orc_sweep_adjoint(g, in + k * total, lam, axes[k], dts[k], a_half, phi_n, dLdg + (axes[k] - 3) * ncell, sflags);
+    if (dLdphi_n)
+        for (int d = 0; d < 3; ++d) orc_gradient_adjoint(g, dLdg + d * ncell, d, dLdphi_n);
+    free(in);
+    free(rho);
+    free(phi1);
+    free(w);
     return 0;
 }

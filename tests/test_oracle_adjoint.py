@@ -168,3 +168,53 @@ def test_step_adjoint_finite_differences_8cubed():
             ok_p += 1
             assert abs(d[0] - dphi[q] * p[q]) <= 1e-5 * abs(dphi[q] * p[q]) + _fd_ok.rounding
     assert ok_f >= 8 and ok_p >= 8, (ok_f, ok_p)
+
+
+def test_poisson_is_its_own_transpose():
+    # phi = P rho is a real circulant with an even multiplier: <P x, y> = <x, P y>
+    g = O.grid((6, 8, 5), (4, 4, 4))
+    rng = np.random.default_rng(21)
+    x, y = rng.standard_normal((2, 6, 8, 5))
+    px, py = O.poisson(g, x, 0.7, 1.3), O.poisson(g, y, 0.7, 1.3)
+    a, b = float((px * y).sum()), float((x * py).sum())
+    assert abs(a - b) <= 1e-13 * max(abs(a), 1.0)
+
+
+def test_self_consistent_step_adjoint_matches_differences():
+    # L = <w_f, f^{n+1}> + <w_phi, phi^{n+1}> for one self-consistent step: the adjoint's
+    # directional derivatives along f_n, phi_n and rho_bg against one-sided differences.
+    # The step is piecewise linear in f with many switching surfaces, so f is moved by
+    # h = 1e-8 (one side must stay on one linear piece); phi_n and rho_bg enter through
+    # the Courant numbers and the Poisson solve, smoothly almost everywhere, and are moved
+    # by 1e-5 and 1e-6 where FP64 rounding of the differences is smaller.  Differences of
+    # L are formed from differences of the outputs (no cancellation in the sums).
+    n, nu = (6, 6, 6), (8, 8, 8)
+    V = 5.0
+    g = O.grid(n, nu, V=V)
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=2), I.fermi_dirac(nu, V), np.float64)
+    bg = 3.0 * (1.0 + I.gaussian_field(n, 0.5, seed=4))
+    rho0, _ = O.moment(g, f0)
+    phi0 = O.poisson(g, rho0 + bg, 0.5, 1.0)
+    dt, ah, af = 0.02, 0.52, 0.55
+    rng = np.random.default_rng(8)
+    wf = rng.standard_normal(f0.shape)
+    wp = rng.standard_normal(n)
+
+    def out(f, p, b):
+        f = f.copy()
+        p1, _ = O.step(g, f, dt, ah, af, p, rho_bg=b, self_consistent=True)
+        return f, p1
+
+    lam = wf.copy()
+    dphi, dbg = O.step_adjoint_sc(g, f0, lam, dt, ah, af, phi0, bg, 1.0, lam_phi_next=wp)
+    F0, P0 = out(f0, phi0, bg)
+    dirs = [(f0 * rng.standard_normal(n)[..., None, None, None], 0, 0, 1e-8),
+            (0, phi0.std() * rng.standard_normal(n), 0, 1e-5),
+            (0, 0, bg.std() * rng.standard_normal(n), 1e-6)]
+    for ef, ep, eb, h in dirs:
+        an = float((lam * ef).sum() + (dphi * ep).sum() + (dbg * eb).sum())
+        Fp, Pp = out(f0 + h * ef, phi0 + h * ep, bg + h * eb)
+        Fm, Pm = out(f0 - h * ef, phi0 - h * ep, bg - h * eb)
+        fw = float((wf * (Fp - F0)).sum() + (wp * (Pp - P0)).sum()) / h
+        bw = float((wf * (F0 - Fm)).sum() + (wp * (P0 - Pm)).sum()) / h
+        assert min(abs(fw - an), abs(bw - an)) <= 1e-5 * abs(an), (h, fw, bw, an)
