@@ -271,6 +271,34 @@ int vlasov_step_adjoint_recorded(vlasov_ctx *ctx, const void *f_n_dev, const voi
                                  double *dLdphi_dev);
 
 /*
+ * Self-consistent versions (Eq. 5 with phi^{n+1} from the post-drift moment,
+ * as vlasov_step with phi_next_dev): the state is (f, phi).
+ *
+ * vlasov_step_record_sc: one step from f_n_dev and phi_n_dev, out of place,
+ * keeping the input of every sweep in rec_dev (as vlasov_step_record);
+ * phi_next_dev (FP32, required) receives phi^{n+1}, rho_nu_dev (FP64, may be
+ * NULL) the post-drift moment; rho_bg_dev, four_pi_G, a_full as vlasov_step.
+ *
+ * vlasov_step_adjoint_recorded_sc: from those records and both potentials,
+ * lam_dev <- dL/df^n (in: dL/df^{n+1}).  lam_phi_next_dev (FP64, may be NULL)
+ * is dL/dphi^{n+1} from later steps; dL/dphi_n and dL/drho_bg are ADDED to
+ * dLdphi_n_dev and dLdrho_bg_dev (FP64, either may be NULL).  Order: second
+ * kick (whose dL/dg adds to dL/dphi^{n+1}), the Poisson solve (a real
+ * circulant with an even multiplier: its own transpose, applied in FP64),
+ * the moment (dL/df += du^3 dL/drho), drift, first kick.  The FP32 rounding
+ * of phi^{n+1} passes gradients unchanged.  The paper has no counterpart.
+ */
+int vlasov_step_record_sc(vlasov_ctx *ctx, const void *f_n_dev, void *const *rec_dev, void *f_next_dev,
+                          double dt, double a_half, double a_full, const float *phi_n_dev,
+                          const double *rho_bg_dev, double four_pi_G, float *phi_next_dev,
+                          double *rho_nu_dev);
+int vlasov_step_adjoint_recorded_sc(vlasov_ctx *ctx, const void *f_n_dev, const void *const *rec_dev,
+                                    void *lam_dev, double dt, double a_half, double a_full,
+                                    const float *phi_n_dev, const float *phi_next_dev, double four_pi_G,
+                                    const double *lam_phi_next_dev, double *dLdphi_n_dev,
+                                    double *dLdrho_bg_dev);
+
+/*
  * vlasov_step_record into eight scratch arrays the size of f (allocated on
  * the first call, kept until vlasov_destroy) followed by
  * vlasov_step_adjoint_recorded.  Arguments as there.

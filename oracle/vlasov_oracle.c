@@ -515,15 +515,18 @@ void orc_poisson(const orc_grid *g, const double *rho, double a, double four_pi_
  * is non-NULL the step is self-consistent: after the drift the moment of f
  * plus rho_bg (may be NULL) is turned into phi_next by the Poisson solve at
  * scale factor a_full, and the second kick uses it; otherwise the second kick
- * reuses phi_n.  rho_nu (may be NULL) receives the post-drift moment.
+ * reuses phi_n.  rho_nu (may be NULL) receives the post-drift moment.  With
+ * ORC_PHI32 in flags phi_next is rounded to FP32 (the precision the GPU stores
+ * phi in) before the second kick uses it.
  */
 int orc_step(const orc_grid *g, double *f, double dt, double a_half, double a_full,
              const double *phi_n, const double *rho_bg, double four_pi_G, double *phi_next,
              double *rho_nu, int flags)
 {
     const long ncell = (long)g->n[0] * g->n[1] * g->n[2];
-    for (int ax = 3; ax <= 5; ++ax) orc_sweep(g, f, ax, 0.5 * dt, a_half, phi_n, flags);
-    for (int ax = 2; ax >= 0; --ax) orc_sweep(g, f, ax, dt, a_half, phi_n, flags);
+    const int sflags = flags & (ORC_MP | ORC_PP);
+    for (int ax = 3; ax <= 5; ++ax) orc_sweep(g, f, ax, 0.5 * dt, a_half, phi_n, sflags);
+    for (int ax = 2; ax >= 0; --ax) orc_sweep(g, f, ax, dt, a_half, phi_n, sflags);
     const double *phi2 = phi_n;
     double *rho = rho_nu;
     double *own = NULL;
@@ -533,10 +536,12 @@ int orc_step(const orc_grid *g, double *f, double dt, double a_half, double a_fu
         double *tot = (double *)malloc(sizeof(double) * ncell);
         for (long c = 0; c < ncell; ++c) tot[c] = rho[c] + (rho_bg ? rho_bg[c] : 0.0);
         orc_poisson(g, tot, a_full, four_pi_G, phi_next);
+        if (flags & ORC_PHI32)
+            for (long c = 0; c < ncell; ++c) phi_next[c] = (double)(float)phi_next[c];
         free(tot);
         phi2 = phi_next;
     }
-    for (int ax = 3; ax <= 5; ++ax) orc_sweep(g, f, ax, 0.5 * dt, a_half, phi2, flags);
+    for (int ax = 3; ax <= 5; ++ax) orc_sweep(g, f, ax, 0.5 * dt, a_half, phi2, sflags);
     free(own);
     return 0;
 }

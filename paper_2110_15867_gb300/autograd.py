@@ -106,6 +106,94 @@ class VlasovRun(torch.autograd.Function):
         return lam, dphi.to(phi.dtype), None, None, None, None, None
 
 
+def _sched(x, n):
+    return [float(x)] * n if isinstance(x, (int, float)) else [float(v) for v in x]
+
+
+class VlasovRunSC(torch.autograd.Function):
+    """rho_nu after n self-consistent steps (Eq. 5 with phi^{n+1} from the post-drift moment
+    plus rho_bg): the state is (f, phi).  Inputs f0, phi0 (FP32) and rho_bg (FP64, may be
+    None); a_half / a_full: one value or one per step.  Checkpoints (f, phi) every K steps;
+    the backward chains dL/dphi^{n+1} from step to step through
+    ``vlasov_step_adjoint_recorded_sc`` and returns dL/df0, dL/dphi0, dL/drho_bg."""
+
+    @staticmethod
+    def forward(ctx, f0, phi0, rho_bg, run: Run, dt: float, a_half, a_full, n_steps: int, K: int = 4,
+                four_pi_G: float = 1.0):
+        if K < 1 or n_steps < 1:
+            raise ValueError("need n_steps >= 1 and K >= 1")
+        ah, af = _sched(a_half, n_steps), _sched(a_full, n_steps)
+        v = run.v
+        bg = None if rho_bg is None else rho_bg.detach().to(torch.float64).contiguous()
+        phi = phi0.detach().to(torch.float32).contiguous()
+        run.work.copy_(f0.detach())
+        starts = [(f0.detach().contiguous(), phi)]
+        last = ((n_steps - 1) // K) * K
+        for n in range(last):
+            if n > 0 and n % K == 0:
+                starts.append((run.work.clone(), phi))
+            phi_next = torch.empty_like(phi)
+            v.step(dt, ah[n], af[n], phi, rho_bg=bg, four_pi_G=four_pi_G, phi_next=phi_next)
+            phi = phi_next
+        if last > 0:
+            starts.append((run.work.clone(), phi))
+        m = n_steps - last
+        rec, states = run.tape(min(K, n_steps))
+        seq = [starts[-1][0]] + states[:m - 1]
+        phis = [starts[-1][1]] + [torch.empty_like(phi) for _ in range(m)]
+        for i in range(m):
+            v.step_record_sc(seq[i], rec[i], dt, ah[last + i], af[last + i], phis[i], phis[i + 1], rho_bg=bg,
+                             four_pi_G=four_pi_G, f_next=seq[i + 1] if i + 1 < m else run.work)
+        token = object()
+        run.tape_owner = token
+        rho = v.moment()
+        ctx.save_for_backward(f0, phi0)
+        ctx.bg, ctx.starts, ctx.last_phis, ctx.token = bg, starts, phis, token
+        ctx.has_bg = rho_bg is not None
+        ctx.run, ctx.dt, ctx.ah, ctx.af, ctx.n_steps, ctx.K, ctx.G = run, dt, ah, af, n_steps, K, four_pi_G
+        return rho
+
+    @staticmethod
+    def backward(ctx, grad_rho):
+        f0, phi0 = ctx.saved_tensors
+        run, dt, ah, af, n_steps, K, G = ctx.run, ctx.dt, ctx.ah, ctx.af, ctx.n_steps, ctx.K, ctx.G
+        v = run.v
+        shape3 = tuple(phi0.shape)
+        lam = torch.empty_like(run.work)
+        v.moment_adjoint(grad_rho.detach().to(torch.float64).contiguous(), lam)
+        lam_phi = None
+        dbg = torch.zeros(shape3, dtype=torch.float64, device=lam.device) if ctx.has_bg else None
+        starts = ctx.starts
+        rec, states = run.tape(min(K, n_steps))
+        taped = run.tape_owner is ctx.token
+        for s in reversed(range(len(starts))):
+            m = min(K, n_steps - s * K)
+            seq = [starts[s][0]] + states[:m - 1]
+            if taped and s == len(starts) - 1:
+                phis = ctx.last_phis
+            else:
+                phis = [starts[s][1]] + [torch.empty_like(starts[s][1]) for _ in range(m)]
+                for i in range(m):
+                    v.step_record_sc(seq[i], rec[i], dt, ah[s * K + i], af[s * K + i], phis[i], phis[i + 1],
+                                     rho_bg=ctx.bg, four_pi_G=G, f_next=seq[i + 1] if i + 1 < m else None)
+            for i in reversed(range(m)):
+                dphi = torch.zeros(shape3, dtype=torch.float64, device=lam.device)
+                v.step_adjoint_recorded_sc(seq[i], rec[i], lam, dt, ah[s * K + i], af[s * K + i], phis[i],
+                                           phis[i + 1], G, lam_phi_next=lam_phi, dLdphi_n=dphi, dLdrho_bg=dbg)
+                lam_phi = dphi
+        run.tape_owner = None
+        ctx.starts = ctx.last_phis = None
+        dphi0 = lam_phi.to(phi0.dtype) if lam_phi is not None else None
+        return lam, dphi0, dbg, None, None, None, None, None, None, None
+
+
+def run_rho_sc(f0, phi0, rho_bg, run: Run, dt: float, a_half, a_full, n_steps: int, K: int = 4,
+               four_pi_G: float = 1.0):
+    """rho_nu after n_steps self-consistent steps from (f0, phi0), differentiable in f0, phi0
+    and rho_bg."""
+    return VlasovRunSC.apply(f0, phi0, rho_bg, run, dt, a_half, a_full, n_steps, K, four_pi_G)
+
+
 def run_rho(f0, phi, run: Run, dt: float, a_half: float, n_steps: int, K: int = 4):
     """rho_nu after n_steps steps from f0 under phi, differentiable in f0 and phi."""
     return VlasovRun.apply(f0, phi, run, dt, a_half, n_steps, K)

@@ -44,7 +44,8 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_enable_timers", "vlasov_read_timers", "vlasov_status", "vlasov_last_error",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
-           "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments")
+           "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
+           "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -113,6 +114,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_adjoint_recorded.restype = ctypes.c_int
     L.vlasov_moment_adjoint.argtypes = [_VP, _VP, _VP, ctypes.c_int]
     L.vlasov_moment_adjoint.restype = ctypes.c_int
+    L.vlasov_step_record_sc.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        _VP, _VP, ctypes.c_double, _VP, _VP]
+    L.vlasov_step_record_sc.restype = ctypes.c_int
+    L.vlasov_step_adjoint_recorded_sc.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, _VP, _VP, ctypes.c_double, _VP, _VP, _VP]
+    L.vlasov_step_adjoint_recorded_sc.restype = ctypes.c_int
     L.vlasov_moments.argtypes = [_VP, _VP, _VP, _VP]
     L.vlasov_moments.restype = ctypes.c_int
     L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
@@ -185,6 +192,20 @@ def vlasov_step_adjoint_recorded(ctx, f_n_ptr: int, rec_ptrs, lam_ptr: int, dt: 
                                  phi_ptr, dLdphi_ptr):
     return _check(ctx, load().vlasov_step_adjoint_recorded(ctx, f_n_ptr, _ptr_array(rec_ptrs), lam_ptr,
                                                            dt, a_half, phi_ptr, dLdphi_ptr))
+
+
+def vlasov_step_record_sc(ctx, f_n_ptr, rec_ptrs, f_next_ptr, dt, a_half, a_full, phi_n_ptr, rho_bg_ptr,
+                          four_pi_G, phi_next_ptr, rho_nu_ptr):
+    return _check(ctx, load().vlasov_step_record_sc(ctx, f_n_ptr, _ptr_array(rec_ptrs), f_next_ptr, dt, a_half,
+                                                    a_full, phi_n_ptr, rho_bg_ptr, four_pi_G, phi_next_ptr,
+                                                    rho_nu_ptr))
+
+
+def vlasov_step_adjoint_recorded_sc(ctx, f_n_ptr, rec_ptrs, lam_ptr, dt, a_half, a_full, phi_n_ptr, phi_next_ptr,
+                                    four_pi_G, lam_phi_next_ptr, dLdphi_n_ptr, dLdrho_bg_ptr):
+    return _check(ctx, load().vlasov_step_adjoint_recorded_sc(ctx, f_n_ptr, _ptr_array(rec_ptrs), lam_ptr, dt,
+                                                              a_half, a_full, phi_n_ptr, phi_next_ptr, four_pi_G,
+                                                              lam_phi_next_ptr, dLdphi_n_ptr, dLdrho_bg_ptr))
 
 
 def vlasov_moment_adjoint(ctx, dLdrho_ptr: int, lam_ptr: int, accumulate: bool = False):
@@ -420,6 +441,36 @@ class Vlasov:
                                      self._like_f(lam, "lam").data_ptr(), dt, a_half,
                                      _ptr(self._field(phi, self.torch.float32)),
                                      _ptr(self._field(dLdphi, self.torch.float64)))
+
+    def step_record_sc(self, f_n, rec, dt: float, a_half: float, a_full: float, phi_n, phi_next,
+                       rho_bg=None, four_pi_G: float = 1.0, f_next=None, rho_nu=None):
+        """Self-consistent step from (f_n, phi_n) out of place, keeping every sweep's input
+        in rec (8 tensors like f); phi_next (FP32) receives phi^{n+1}."""
+        if len(rec) != 8:
+            raise ValueError("rec must hold 8 tensors")
+        self._sync_stream()
+        T = self.torch
+        vlasov_step_record_sc(self.ctx, self._like_f(f_n, "f_n").data_ptr(),
+                              [self._like_f(r, "rec").data_ptr() for r in rec],
+                              None if f_next is None else self._like_f(f_next, "f_next").data_ptr(), dt, a_half,
+                              a_full, _ptr(self._field(phi_n, T.float32)), _ptr(self._field(rho_bg, T.float64)),
+                              four_pi_G, _ptr(self._field(phi_next, T.float32)), _ptr(self._field(rho_nu, T.float64)))
+
+    def step_adjoint_recorded_sc(self, f_n, rec, lam, dt: float, a_half: float, a_full: float, phi_n, phi_next,
+                                 four_pi_G: float = 1.0, lam_phi_next=None, dLdphi_n=None, dLdrho_bg=None):
+        """Adjoint of one self-consistent step from step_record_sc's records: lam <- dL/df^n;
+        dL/dphi_n and dL/drho_bg are added to dLdphi_n / dLdrho_bg (FP64) when given."""
+        if len(rec) != 8:
+            raise ValueError("rec must hold 8 tensors")
+        self._sync_stream()
+        T = self.torch
+        vlasov_step_adjoint_recorded_sc(self.ctx, self._like_f(f_n, "f_n").data_ptr(),
+                                        [self._like_f(r, "rec").data_ptr() for r in rec],
+                                        self._like_f(lam, "lam").data_ptr(), dt, a_half, a_full,
+                                        _ptr(self._field(phi_n, T.float32)), _ptr(self._field(phi_next, T.float32)),
+                                        four_pi_G, _ptr(self._field(lam_phi_next, T.float64)),
+                                        _ptr(self._field(dLdphi_n, T.float64)),
+                                        _ptr(self._field(dLdrho_bg, T.float64)))
 
     def moment_adjoint(self, dLdrho, lam, accumulate: bool = False):
         """lam (+)= du^3 dL/drho(x) broadcast over each velocity cube."""

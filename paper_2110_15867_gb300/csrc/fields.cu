@@ -402,6 +402,21 @@ cudaError_t launch_moments(const GridDims &g, const void *f, const float *scale,
     return cudaGetLastError();
 }
 
+// y += x (FP64), or y = x when x_only
+__global__ void axpy_kernel(long long n, const double *__restrict__ x, double *y, int assign)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = assign ? x[i] : y[i] + x[i];
+}
+
+cudaError_t launch_add(long long n, const double *x, double *y, bool assign, cudaStream_t st)
+{
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
+    axpy_kernel<<<blocks, threads, 0, st>>>(n, x, y, assign ? 1 : 0);
+    return cudaGetLastError();
+}
+
 // dx dy dz * sum rho, Neumaier in FP64 per thread, fixed-order combine
 __global__ void __launch_bounds__(1024) mass_kernel(GridDims g, const double *__restrict__ rho, double *out)
 {
@@ -492,15 +507,18 @@ __global__ void poisson_scale_kernel(GridDims g, double2 *z, double fac)
     }
 }
 
-__global__ void poisson_store_kernel(long long n, const double2 *__restrict__ z, float *phi)
+// FP32 phi (the field the kicks read) or FP64 (the adjoint's dL/drho)
+__global__ void poisson_store_kernel(long long n, const double2 *__restrict__ z, float *phi, double *phi64)
 {
     const double inv = 1.0 / (double)n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        phi[i] = (float)(z[i].x * inv);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (phi) phi[i] = (float)(z[i].x * inv);
+        if (phi64) phi64[i] = z[i].x * inv;
+    }
 }
 
 cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const double *rho, const double *bg,
-                           double a, double four_pi_G, float *phi, cudaStream_t st)
+                           double a, double four_pi_G, float *phi, cudaStream_t st, double *phi64)
 {
     const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
     const int threads = 256;
@@ -516,7 +534,7 @@ cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const do
         dft_axis_kernel<<<blocks, threads, 0, st>>>(g, d, +1, a0, a1, ps.tw[d]);
         double2 *t = a0; a0 = a1; a1 = t;
     }
-    poisson_store_kernel<<<blocks, threads, 0, st>>>(n, a0, phi);
+    poisson_store_kernel<<<blocks, threads, 0, st>>>(n, a0, phi, phi64);
     return cudaGetLastError();
 }
 

@@ -228,6 +228,8 @@ cudaError_t launch_moments(const GridDims &g, const void *f, const float *scale,
 // lam (+)= du^3 dLdrho(x) over each velocity cube (FP64 or FP32 lam: dtype 0 / 1)
 cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int dtype, void *lam, int accumulate,
                                   cudaStream_t st, int sm_count);
+// y += x (or y = x when assign), FP64, n values
+cudaError_t launch_add(long long n, const double *x, double *y, bool assign, cudaStream_t st);
 // mass = dx dy dz * sum rho (FP64, compensated) written to out (device)
 cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st);
 
@@ -236,8 +238,9 @@ struct PoissonScratch {
     double2 *z0, *z1;
     double2 *tw[3]; // tw[d][q] = (cos, sin)(2 pi q / n_d)
 };
+// phi (FP32) and / or phi64 (FP64) receive the solution (either may be null)
 cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const double *rho,
                            const double *rho_bg, double a, double four_pi_G, float *phi,
-                           cudaStream_t st);
+                           cudaStream_t st, double *phi64 = nullptr);
 
 } // namespace vk

@@ -128,6 +128,7 @@ struct vlasov_ctx {
     void *d_rec[8];
     double *d_dLdg;
     void *d_lam_tmp;
+    double *d_sc; // self-consistent adjoint: dL/dphi^{n+1} and dL/drho (2 * ncell)
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
     // per-part timers
@@ -370,6 +371,7 @@ static void free_scratch(vlasov_ctx *c)
     for (int k = 0; k < 8; ++k) cudaFree(c->d_rec[k]);
     cudaFree(c->d_dLdg);
     cudaFree(c->d_lam_tmp);
+    cudaFree(c->d_sc);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -1034,6 +1036,112 @@ extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam
     // run the step again from f_n, keeping the input of every sweep
     if ((rc = vlasov_step_record(c, f_n_dev, c->d_rec, nullptr, dt, a_half, phi_dev))) return rc;
     return vlasov_step_adjoint_recorded(c, f_n_dev, c->d_rec, lam_dev, dt, a_half, phi_dev, dLdphi_dev);
+}
+
+// ----------------------------------------------------------------------------
+// self-consistent step: record and adjoint
+// ----------------------------------------------------------------------------
+extern "C" int vlasov_step_record_sc(vlasov_ctx *c, const void *f_n_dev, void *const *rec_dev, void *f_next_dev,
+                                     double dt, double a_half, double a_full, const float *phi_n_dev,
+                                     const double *rho_bg_dev, double four_pi_G, float *phi_next_dev,
+                                     double *rho_nu_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_records(c, rec_dev, "vlasov_step_record_sc");
+    if (!rc) rc = check_adjoint_args(c, f_n_dev, rec_dev[0], "vlasov_step_record_sc");
+    if (rc) return rc;
+    if (!phi_next_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_record_sc: phi_next_dev is NULL");
+    if (f_next_dev && reinterpret_cast<uintptr_t>(f_next_dev) % 16)
+        return fail(c, VLASOV_EINVAL, "vlasov_step_record_sc: f_next_dev must be 16-byte aligned");
+    if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
+    for (int k = 0; k < 9; ++k) {
+        if (k == 6) {
+            // after the drift (rec[5] = input of sweep 6): moment, Poisson, the second kick's constants
+            double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
+            cudaError_t e;
+            {
+                PartTimer t(c, VLASOV_T_MOMENT, 1);
+                e = launch_moment(c->gd, rec_dev[5], c->g.dtype == VLASOV_F64 ? 0 : 1, rho, c->stream, c->sm_count);
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
+            if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
+            if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
+        }
+        const void *src = k == 0 ? f_n_dev : rec_dev[k - 1];
+        void *dst = k < 8 ? rec_dev[k] : f_next_dev;
+        if (!dst) break;
+        const int ax = kStepAxes[k];
+        rc = ax >= 3 ? run_velocity(c, ax, src, dst) : run_position(c, ax, step_dt(k, dt), a_half, src, dst);
+        if (rc) return rc;
+    }
+    return VLASOV_OK;
+}
+
+static int gradient_adjoint_all(vlasov_ctx *c, double *dLdphi)
+{
+    PartTimer t(c, VLASOV_T_GRAD_ADJ, 3);
+    for (int d = 0; d < 3; ++d) {
+        const cudaError_t e = launch_gradient_adjoint(c->gd, c->d_dLdg + d * c->ncell, d, dLdphi, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient adjoint launch");
+    }
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_step_adjoint_recorded_sc(vlasov_ctx *c, const void *f_n_dev, const void *const *rec_dev,
+                                               void *lam_dev, double dt, double a_half, double a_full,
+                                               const float *phi_n_dev, const float *phi_next_dev, double four_pi_G,
+                                               const double *lam_phi_next_dev, double *dLdphi_n_dev,
+                                               double *dLdrho_bg_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint_recorded_sc");
+    if (!rc) rc = check_records(c, const_cast<void *const *>(rec_dev), "vlasov_step_adjoint_recorded_sc");
+    if (rc) return rc;
+    for (int k = 0; k < 8; ++k)
+        if (rec_dev[k] == lam_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint_recorded_sc: lambda aliases a record");
+    if (!phi_next_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint_recorded_sc: phi_next_dev is NULL");
+    if ((rc = ensure_buffer(c, (void **)&c->d_dLdg, sizeof(double) * 3 * c->ncell))) return rc;
+    if ((rc = ensure_buffer(c, (void **)&c->d_sc, sizeof(double) * 2 * c->ncell))) return rc;
+    const long long nc = c->ncell;
+    double *dphi1 = c->d_sc, *drho = c->d_sc + nc;
+    // second kick, with phi^{n+1}
+    if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
+    VK_CUDA(c, cudaMemsetAsync(c->d_dLdg, 0, sizeof(double) * 3 * nc, c->stream));
+    for (int k = 8; k >= 6; --k) {
+        const int ax = kStepAxes[k];
+        if ((rc = run_adjoint(c, rec_dev[k - 1], lam_dev, ax, step_dt(k, dt), a_half, c->d_dLdg + (ax - 3) * nc))) return rc;
+    }
+    // dL/dphi^{n+1}: from later steps plus the second kick's G^T dL/dg
+    if (lam_phi_next_dev) VK_CUDA(c, cudaMemcpyAsync(dphi1, lam_phi_next_dev, sizeof(double) * nc, cudaMemcpyDeviceToDevice, c->stream));
+    else VK_CUDA(c, cudaMemsetAsync(dphi1, 0, sizeof(double) * nc, c->stream));
+    if ((rc = gradient_adjoint_all(c, dphi1))) return rc;
+    // Poisson (its own transpose) and the moment
+    cudaError_t e;
+    {
+        PartTimer t(c, VLASOV_T_POISSON, 9);
+        e = launch_poisson(c->gd, c->ps, dphi1, nullptr, a_full, four_pi_G, nullptr, c->stream, drho);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "poisson adjoint launch");
+    if (dLdrho_bg_dev && (e = launch_add(nc, drho, dLdrho_bg_dev, false, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "rho_bg gradient launch");
+    {
+        PartTimer t(c, VLASOV_T_MOMENT_ADJ, 1);
+        e = launch_moment_adjoint(c->gd, drho, c->g.dtype == VLASOV_F64 ? 0 : 1, lam_dev, 1, c->stream, c->sm_count);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "moment adjoint launch");
+    // drift
+    for (int k = 5; k >= 3; --k)
+        if ((rc = run_adjoint(c, rec_dev[k - 1], lam_dev, kStepAxes[k], step_dt(k, dt), a_half, nullptr))) return rc;
+    // first kick, with phi_n
+    if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
+    VK_CUDA(c, cudaMemsetAsync(c->d_dLdg, 0, sizeof(double) * 3 * nc, c->stream));
+    for (int k = 2; k >= 0; --k) {
+        const int ax = kStepAxes[k];
+        const void *in = k == 0 ? f_n_dev : rec_dev[k - 1];
+        if ((rc = run_adjoint(c, in, lam_dev, ax, step_dt(k, dt), a_half, c->d_dLdg + (ax - 3) * nc))) return rc;
+    }
+    if (dLdphi_n_dev && (rc = gradient_adjoint_all(c, dLdphi_n_dev))) return rc;
+    return VLASOV_OK;
 }
 
 // ----------------------------------------------------------------------------
