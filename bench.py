@@ -529,16 +529,23 @@ def run_ours(args):
             dist.barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]  # phases of the last step
         t0.record(stream)
         base = args.warmup + args.steps
         for k in range(base, base + args.e2e_steps):
+            ph[0].record(stream)
             v.upload(fh)
+            ph[1].record(stream)
             one_step(k)
+            ph[2].record(stream)
             v.download(fh)
             rho_h.copy_(rho, non_blocking=True)
+            ph[3].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
         e_ms = t0.elapsed_time(t1)
+        phases = {"h2d_ms": ph[0].elapsed_time(ph[1]), "step_ms": ph[1].elapsed_time(ph[2]),
+                  "d2h_ms": ph[2].elapsed_time(ph[3])}
         if dist:
             t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -547,7 +554,7 @@ def run_ours(args):
         e2e = {"value": world * 9.0 * cells * args.e2e_steps / (e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(f.numel() * f.element_size()),
                "d2h_bytes_per_step": int(f.numel() * f.element_size() + rho.numel() * rho.element_size()),
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "last_step_phases": phases}
         del fh
 
     cpu = None

@@ -255,9 +255,8 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         const C ful = c0 + k.alpha * dlm;
         const C fmd = C(0.5) * (c0 + cp1 - qp);
         const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * qm;
-        const C fmin = mx2(mn3(c0, cp1, fmd), mn3(c0, ful, flc));
-        const C fmax = mn2(mx3(c0, cp1, fmd), mx3(c0, ful, flc));
-        const C v = mn2(mx2(fbar, fmin), fmax);
+        // clamp(fbar, max(A, B), min(C, D)) as min(max(fbar, A, B), C, D)
+        const C v = mn3(mx3(fbar, mn3(c0, cp1, fmd), mn3(c0, ful, flc)), mx3(c0, cp1, fmd), mx3(c0, ful, flc));
         const C sv = k.s * v;
         // reverse: F = clamp(s v, 0, c0)
         const bool inr = sv >= C(0) && sv <= c0;

@@ -405,9 +405,9 @@ __device__ __forceinline__ X sl_mpp5_flux(const Lim<X> &k, X cm2, X cm1, X c0, X
     const X ful = vfma(k.alpha, dlm, c0);
     const X fmd = vmul(splat<X>(0.5), vsub(vadd(c0, cp1), dm4p));
     const X flc = vfma(splat<X>(4.0 / 3.0), dm4m, vfma(splat<X>(0.5), dlm, c0));
-    const X fmin = mx2(mn3(c0, cp1, fmd), mn3(c0, ful, flc));
-    const X fmax = mn2(mx3(c0, cp1, fmd), mx3(c0, ful, flc));
-    const X v = mn2(mx2(fbar, fmin), fmax);
+    // clamp(fbar, fmin, fmax) with fmin = max(A, B), fmax = min(C, D): by associativity
+    // of max and min, min(max(fbar, A, B), C, D) -- two 3-input operations instead of four
+    const X v = mn3(mx3(fbar, mn3(c0, cp1, fmd), mn3(c0, ful, flc)), mx3(c0, cp1, fmd), mx3(c0, ful, flc));
     return mn2(mx2(vmul(k.s, v), splat<X>(0.0)), c0);
 }
 
