@@ -74,6 +74,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, dist, device):
+    """The largest of the ranks' times (every rank gets it); ms itself on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, cells, steps, ms, sweeps=9):
+    """Cell updates per second per sweep of the whole job: every rank advances its own
+    replica of `cells` cells by `steps` steps of `sweeps` sweeps in the slowest rank's time."""
+    return world * sweeps * cells * steps / (ms * 1e-3)
+
+
 def schedule(k, w=WORKLOAD):
     """a at the start / middle / end of step k and the step's Courant number."""
     rng = np.random.default_rng(1000 + k)
@@ -480,11 +496,8 @@ def run_ours(args):
     kind_ms, kind_n = v.read_timers()
     v.enable_timers(False)
     v.status()
-    if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * 9.0 * cells * args.steps / (ms_total * 1e-3)
+    ms_total = max_over_ranks(ms_total, dist, dev)
+    value = whole_job_rate(world, cells, args.steps, ms_total)
 
     # dominant kernel and its roofline
     sweep_kinds = [k for k in kind_ms if k.startswith("sweep_")]
@@ -546,12 +559,9 @@ def run_ours(args):
         e_ms = t0.elapsed_time(t1)
         phases = {"h2d_ms": ph[0].elapsed_time(ph[1]), "step_ms": ph[1].elapsed_time(ph[2]),
                   "d2h_ms": ph[2].elapsed_time(ph[3])}
-        if dist:
-            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e_ms, dist, dev)
         v.status()
-        e2e = {"value": world * 9.0 * cells * args.e2e_steps / (e_ms * 1e-3), "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, cells, args.e2e_steps, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(f.numel() * f.element_size()),
                "d2h_bytes_per_step": int(f.numel() * f.element_size() + rho.numel() * rho.element_size()),
                "steps": args.e2e_steps, "last_step_phases": phases}
