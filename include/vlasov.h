@@ -301,10 +301,18 @@ int vlasov_step_adjoint_recorded_sc(vlasov_ctx *ctx, const void *f_n_dev, const 
 /*
  * vlasov_step_record into eight scratch arrays the size of f (allocated on
  * the first call, kept until vlasov_destroy) followed by
- * vlasov_step_adjoint_recorded.  Arguments as there.
+ * vlasov_step_adjoint_recorded.  Arguments as there.  When eight arrays do not
+ * fit on the device (or vlasov_set_adjoint_arrays(ctx, 4) asked for it) it uses
+ * four: it keeps the inputs of sweeps 3 and 6 and rebuilds the other inputs of
+ * each group of three sweeps before their adjoints (12 forward sweeps instead of
+ * 8, the same results).
  */
 int vlasov_step_adjoint(vlasov_ctx *ctx, const void *f_n_dev, void *lam_dev, double dt, double a_half,
                         const float *phi_dev, double *dLdphi_dev);
+
+/* Scratch arrays the size of f that vlasov_step_adjoint may hold: 8, 4, or 0 =
+ * 8 when they fit, else 4 (the default).  Arrays already held are kept. */
+int vlasov_set_adjoint_arrays(vlasov_ctx *ctx, int arrays);
 
 /*
  * Synchronise the stream, read and clear the device error word.  Returns 0 or

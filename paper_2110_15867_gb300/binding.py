@@ -45,7 +45,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
-           "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc")
+           "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_adjoint_recorded_sc.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_double, _VP, _VP, ctypes.c_double, _VP, _VP, _VP]
     L.vlasov_step_adjoint_recorded_sc.restype = ctypes.c_int
+    L.vlasov_set_adjoint_arrays.argtypes = [_VP, ctypes.c_int]
+    L.vlasov_set_adjoint_arrays.restype = ctypes.c_int
     L.vlasov_moments.argtypes = [_VP, _VP, _VP, _VP]
     L.vlasov_moments.restype = ctypes.c_int
     L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
@@ -492,6 +494,10 @@ class Vlasov:
             raise ValueError("f_host must be a contiguous host tensor like f")
         self._sync_stream()
         vlasov_download(self.ctx, f_host.data_ptr())
+
+    def set_adjoint_arrays(self, arrays: int):
+        """f-sized scratch arrays step_adjoint may hold: 8, 4 or 0 (8 if they fit, else 4)."""
+        _check(self.ctx, load().vlasov_set_adjoint_arrays(self.ctx, int(arrays)))
 
     def set_fused_kick(self, on: bool = True):
         """Run the kicks' D_uy and D_uz in one pass (FP32, n_uy = n_uz = 16 or 32)."""

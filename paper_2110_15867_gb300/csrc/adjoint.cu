@@ -510,15 +510,30 @@ template <typename C> __device__ __forceinline__ C warp_sum(C v)
     return v;
 }
 
+__device__ __forceinline__ double warp_sum_d(double v) { return warp_sum<double>(v); }
+
 // Every thread of the block calls this.  cell < 0: no contribution.  Lines
 // of one cell are consecutive, so a warp whose first and last lanes share a
-// cell sums in registers; the block then merges runs of equal cells.
+// cell sums in registers; the block then merges runs of equal cells.  With
+// part non-null every block lies in one cell: the block's sum goes to
+// part[blockIdx.x] (summed per cell in a fixed order by a second kernel).
 template <typename C>
-__device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, double fac)
+__device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, double fac, double *part)
 {
     __shared__ long long s_cell[kAdjBlock / 32];
     __shared__ double s_sum[kAdjBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (part) {
+        const double s = warp_sum_d((double)dnu);
+        if (lane == 0) s_sum[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double acc = 0.0;
+            for (int q = 0; q < kAdjBlock / 32; ++q) acc += s_sum[q];
+            part[blockIdx.x] = acc;
+        }
+        return;
+    }
     const long long first = __shfl_sync(0xffffffffu, cell, 0), last = __shfl_sync(0xffffffffu, cell, 31);
     const bool uniform = first == last && first >= 0;
     if (uniform) {
@@ -582,7 +597,7 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_
         }
         cell = a.dLdg ? t / a.lines_per_cell : -1;
     }
-    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg);
+    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
 
 // u_z lines of L = 8, 16, 32 cells: one row per thread through 16-byte vector loads
@@ -636,7 +651,18 @@ __global__ void __launch_bounds__(kAdjBlock, L <= 16 ? 3 : 2) adjoint_rows_kerne
         }
         cell = a.dLdg ? t / a.lines_per_cell : -1;
     }
-    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg);
+    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
+}
+
+// dLdg[c] += fac * sum of part over the blocks of cell c, in block order
+__global__ void cell_sum_kernel(long long ncell, int blocks_per_cell, const double *__restrict__ part, double fac,
+                                double *dLdg)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < blocks_per_cell; ++q) acc += part[c * blocks_per_cell + q];
+        dLdg[c] += acc * fac;
+    }
 }
 
 // dL/dphi += G^T dL/dg for the periodic 4th-order gradient along d: g(x)
@@ -699,6 +725,17 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool 
     }
     return cudaGetLastError();
 }
+
+cudaError_t launch_cell_sum(long long ncell, int blocks_per_cell, const double *part, double fac, double *dLdg,
+                            cudaStream_t st)
+{
+    const int threads = 256;
+    const int blocks = int((ncell + threads - 1) / threads < 4096 ? (ncell + threads - 1) / threads : 4096);
+    cell_sum_kernel<<<blocks, threads, 0, st>>>(ncell, blocks_per_cell, part, fac, dLdg);
+    return cudaGetLastError();
+}
+
+int adjoint_block_threads() { return kAdjBlock; }
 
 bool adjoint_rows_supported(int L, int dtype) { return dtype == 1 && (L == 8 || L == 16 || L == 32); }
 

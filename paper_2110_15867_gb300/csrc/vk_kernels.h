@@ -200,6 +200,7 @@ template <typename C> struct AdjArgs {
     double *dLdg;             // velocity sweeps: dL/dg per spatial cell (may be null)
     long long lines_per_cell; // velocity sweeps: cell = t / lines_per_cell
     double dnu_dg;            // -dt / du
+    double *block_part;       // non-null: every block lies in one cell; block sums go here (no atomics)
     LineCoefT<C> table[kMaxVel];
 };
 
@@ -207,6 +208,10 @@ template <typename C> struct AdjArgs {
 bool adjoint_rows_supported(int L, int dtype);
 cudaError_t launch_adjoint_f32(const AdjArgs<float> &a, bool rows, cudaStream_t st);
 cudaError_t launch_adjoint_f64(const AdjArgs<double> &a, bool rows, cudaStream_t st);
+int adjoint_block_threads(); // lines (threads) per block of the adjoint kernels
+// dLdg[c] += fac * sum_q part[c * blocks_per_cell + q] in order
+cudaError_t launch_cell_sum(long long ncell, int blocks_per_cell, const double *part, double fac, double *dLdg,
+                            cudaStream_t st);
 // dL/dphi += G_d^T dL/dg (FP64, nx*ny*nz)
 cudaError_t launch_gradient_adjoint(const GridDims &g, const double *dLdg, int d, double *dLdphi, cudaStream_t st);
 

@@ -129,6 +129,9 @@ struct vlasov_ctx {
     double *d_dLdg;
     void *d_lam_tmp;
     double *d_sc; // self-consistent adjoint: dL/dphi^{n+1} and dL/drho (2 * ncell)
+    double *d_part; // adjoint: per-block sums of dL/dnu (deterministic per-cell reduction)
+    size_t part_len;
+    int adj_arrays; // f-sized scratch arrays vlasov_step_adjoint may use: 8, 4 or 0 (8 if they fit, else 4)
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
     // per-part timers
@@ -372,6 +375,7 @@ static void free_scratch(vlasov_ctx *c)
     cudaFree(c->d_dLdg);
     cudaFree(c->d_lam_tmp);
     cudaFree(c->d_sc);
+    cudaFree(c->d_part);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -908,11 +912,29 @@ static int run_adjoint_t(vlasov_ctx *c, const void *f_in, void *lam, int ax, dou
     }
     const bool rows = ax == 5 && adjoint_rows_supported(A.L, c->g.dtype);
     if (rows) A.outer_per_cell = A.lines_per_cell; // one row per line: cell = row / rows per cell
+    // when a cell's lines fill whole blocks, each block writes its sum and a second pass adds
+    // them per cell in a fixed order (reproducible); otherwise FP64 atomics
+    const int bt = adjoint_block_threads();
+    const bool det = A.dLdg && A.lines_per_cell % bt == 0;
+    if (det) {
+        const size_t nblk = (size_t)(A.nlines / bt);
+        if (c->part_len < nblk) {
+            cudaFree(c->d_part);
+            c->d_part = nullptr;
+            c->part_len = 0;
+            int rc = ensure_buffer(c, (void **)&c->d_part, sizeof(double) * nblk);
+            if (rc) return rc;
+            c->part_len = nblk;
+        }
+        A.block_part = c->d_part;
+    }
     cudaError_t e;
     {
-        PartTimer t(c, VLASOV_T_ADJ_X + ax, 1);
+        PartTimer t(c, VLASOV_T_ADJ_X + ax, det ? 2 : 1);
         if constexpr (sizeof(C) == 8) e = launch_adjoint_f64(A, rows, c->stream);
         else e = launch_adjoint_f32(A, rows, c->stream);
+        if (e == cudaSuccess && det)
+            e = launch_cell_sum(c->ncell, int(A.lines_per_cell / bt), c->d_part, A.dnu_dg, A.dLdg, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint sweep launch");
     if (shifted) VK_CUDA(c, cudaMemcpyAsync(lam, c->d_lam_tmp, f_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
@@ -1024,15 +1046,78 @@ extern "C" int vlasov_step_adjoint_recorded(vlasov_ctx *c, const void *f_n_dev, 
     return VLASOV_OK;
 }
 
+static int gradient_adjoint_all(vlasov_ctx *c, double *dLdphi);
+
+// one sweep k of the external-potential step from src to dst (constants for the kicks in d_coef)
+static int step_sweep(vlasov_ctx *c, int k, const void *src, void *dst, double dt, double a_half)
+{
+    const int ax = kStepAxes[k];
+    return ax >= 3 ? run_velocity(c, ax, src, dst) : run_position(c, ax, step_dt(k, dt), a_half, src, dst);
+}
+
+// Step adjoint with four scratch arrays: keep the inputs of sweeps 3 and 6 and, for
+// each group of three sweeps, rebuild the other two inputs just before their adjoints
+// (12 forward sweeps instead of 8).
+static int step_adjoint_low_memory(vlasov_ctx *c, const void *f_n, void *lam, double dt, double a_half,
+                                   const float *phi, double *dLdphi)
+{
+    void *r3 = c->d_rec[0], *r6 = c->d_rec[1], *w1 = c->d_rec[2], *w2 = c->d_rec[3];
+    int rc;
+    if ((rc = prep_velocity(c, phi, 0.5 * dt, 7))) return rc;
+    // inputs of sweeps 3 and 6, through the other two arrays
+    if ((rc = step_sweep(c, 0, f_n, w1, dt, a_half)) || (rc = step_sweep(c, 1, w1, w2, dt, a_half)) ||
+        (rc = step_sweep(c, 2, w2, r3, dt, a_half)) || (rc = step_sweep(c, 3, r3, w1, dt, a_half)) ||
+        (rc = step_sweep(c, 4, w1, w2, dt, a_half)) || (rc = step_sweep(c, 5, w2, r6, dt, a_half)))
+        return rc;
+    if (dLdphi) VK_CUDA(c, cudaMemsetAsync(c->d_dLdg, 0, sizeof(double) * 3 * c->ncell, c->stream));
+    const void *starts[3] = {f_n, r3, r6};
+    for (int grp = 2; grp >= 0; --grp) {
+        const int k0 = 3 * grp;
+        // inputs of sweeps k0 + 1 and k0 + 2
+        if ((rc = step_sweep(c, k0, starts[grp], w1, dt, a_half)) || (rc = step_sweep(c, k0 + 1, w1, w2, dt, a_half)))
+            return rc;
+        const void *in[3] = {starts[grp], w1, w2};
+        for (int j = 2; j >= 0; --j) {
+            const int ax = kStepAxes[k0 + j];
+            double *dLdg = (ax >= 3 && dLdphi) ? c->d_dLdg + (ax - 3) * c->ncell : nullptr;
+            if ((rc = run_adjoint(c, in[j], lam, ax, step_dt(k0 + j, dt), a_half, dLdg))) return rc;
+        }
+    }
+    if (dLdphi && (rc = gradient_adjoint_all(c, dLdphi))) return rc;
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_set_adjoint_arrays(vlasov_ctx *c, int arrays)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (arrays != 0 && arrays != 4 && arrays != 8) return fail(c, VLASOV_EINVAL, "adjoint arrays must be 0, 4 or 8");
+    c->adj_arrays = arrays;
+    return VLASOV_OK;
+}
+
 extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam_dev, double dt, double a_half,
                                    const float *phi_dev, double *dLdphi_dev)
 {
     if (!c) return VLASOV_EINVAL;
     int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint");
     if (rc) return rc;
+    if (!phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint: phi_dev is NULL");
     const size_t bytes = f_bytes(c);
-    for (int k = 0; k < 8 && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
+    if (dLdphi_dev && (rc = ensure_buffer(c, (void **)&c->d_dLdg, sizeof(double) * 3 * c->ncell))) return rc;
+    // as many scratch arrays as the setting allows and the device holds: 8 (record every
+    // input) or 4 (recompute within the step)
+    int want = c->adj_arrays ? c->adj_arrays : 8;
+    for (int k = 0; k < want && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
+    if (rc && c->adj_arrays == 0) {
+        for (int k = 4; k < 8; ++k) { cudaFree(c->d_rec[k]); c->d_rec[k] = nullptr; }
+        rc = VLASOV_OK;
+        want = 4;
+        for (int k = 0; k < 4 && !rc; ++k) rc = ensure_buffer(c, &c->d_rec[k], bytes);
+    }
     if (rc) return rc;
+    bool all8 = want == 8;
+    for (int k = 0; k < 8 && all8; ++k) all8 = c->d_rec[k] != nullptr;
+    if (!all8) return step_adjoint_low_memory(c, f_n_dev, lam_dev, dt, a_half, phi_dev, dLdphi_dev);
     // run the step again from f_n, keeping the input of every sweep
     if ((rc = vlasov_step_record(c, f_n_dev, c->d_rec, nullptr, dt, a_half, phi_dev))) return rc;
     return vlasov_step_adjoint_recorded(c, f_n_dev, c->d_rec, lam_dev, dt, a_half, phi_dev, dLdphi_dev);

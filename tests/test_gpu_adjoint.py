@@ -220,3 +220,56 @@ def test_adjoint_argument_errors():
         vb.sweep_adjoint(codes, codes.clone(), 0, 0.01)  # 16-bit storage has no adjoint
     assert e.value.code == B.EINVAL
     vb.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("cfl", [0.8, 1.7])
+def test_step_adjoint_low_memory_is_the_same(dtype, cfl):
+    # four scratch arrays (inputs of sweeps 3 and 6 kept, the rest rebuilt) against eight
+    # (every input recorded): the same kernels on the same inputs, so lambda is bit for bit;
+    # dL/dphi sums the lines of each cell with FP64 atomics, whose order varies from run to
+    # run, so it agrees to 1e-12 of its largest entry; cfl 1.7 includes whole-cell shifts
+    B = _lib()
+    n, nu = (8, 6, 8), (8, 12, 16)
+    f0, phi, lam0 = _setup(n, nu, dtype=dtype)
+    g = O.grid(n, nu, V=5.0)
+    m = max([O.max_abs_nu(g, ax, 1.0, 1.0, phi.astype(np.float64)) for ax in (0, 1, 2)])
+    mv = max([O.max_abs_nu(g, ax, 0.5, 1.0, phi.astype(np.float64)) for ax in (3, 4, 5)])
+    dt = min(cfl / m, 0.8 / mv)
+    out = {}
+    for arrays in (8, 4):
+        v = B.Vlasov(torch.from_numpy(f0).cuda(), V=5.0)
+        v.set_adjoint_arrays(arrays)
+        lam = torch.from_numpy(lam0).cuda()
+        dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        v.step_adjoint(torch.from_numpy(f0).cuda(), lam, dt, 1.0, torch.from_numpy(phi).cuda(), dphi)
+        v.status()
+        out[arrays] = (lam.cpu().numpy(), dphi.cpu().numpy())
+        v.close()
+    assert np.array_equal(out[4][0], out[8][0])
+    assert np.abs(out[4][1] - out[8][1]).max() <= 1e-12 * np.abs(out[8][1]).max()
+    if dtype == np.float64:
+        lam_ref = lam0.copy()
+        dphi_ref = O.step_adjoint(g, f0, lam_ref, dt, 1.0, phi.astype(np.float64))
+        _compare(out[4][0], lam_ref, True, "low-memory step lambda")
+        _compare_field(out[4][1], dphi_ref, True, "low-memory step dL/dphi")
+
+
+def test_dLdphi_is_reproducible_when_cells_fill_blocks():
+    # n_u = 16: every velocity line set of a cell (256 lines) fills whole 256-thread blocks,
+    # so dL/dg is summed per cell in a fixed order: two runs agree bit for bit
+    B = _lib()
+    n, nu = (6, 8, 4), (16, 16, 16)
+    f0, phi, lam0 = _setup(n, nu)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_step(g, phi, 0.8)
+    runs = []
+    for _ in range(2):
+        v = B.Vlasov(torch.from_numpy(f0).cuda(), V=5.0)
+        lam = torch.from_numpy(lam0).cuda()
+        dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        v.step_adjoint(torch.from_numpy(f0).cuda(), lam, dt, 1.0, torch.from_numpy(phi).cuda(), dphi)
+        v.status()
+        runs.append((lam.cpu().numpy(), dphi.cpu().numpy()))
+        v.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
