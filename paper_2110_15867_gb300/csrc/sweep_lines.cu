@@ -92,27 +92,28 @@ template <> struct Chunk<__half> {
 #define CODED_RNG_INIT(e, seed) (sizeof(T) == 2 ? sr_bits((e), (seed)) : 0u)
 
 // Advance both lines of the pair (forward local frame; zero-flux faces).
-template <int NU>
-__device__ __forceinline__ float2 march_regs(float2 (&v)[NU], const Lim<float2> &lim)
+// X = float2: two lines as one packed pair; X = float: one line.
+template <int NU, typename X>
+__device__ __forceinline__ X march_regs(X (&v)[NU], const Lim<X> &lim)
 {
-    const float2 zero = splat<float2>(0.0);
-    float2 d[NU];
+    const X zero = splat<X>(0.0);
+    X d[NU];
 #pragma unroll
     for (int i = 0; i < NU; ++i)
         d[i] = curv(i > 0 ? v[i - 1] : zero, v[i], i + 1 < NU ? v[i + 1] : zero);
-    const float2 dm = v[0]; // curvature of the ghost cell -1: 0 - 0 + c_0
+    const X dm = v[0]; // curvature of the ghost cell -1: 0 - 0 + c_0
     // F[k] = flux through face k - 1/2, k = 1 .. NU-1 (outer faces carry nothing)
-    float2 Fprev = zero, sum = zero;
-    float2 dm4m = dm4(dm, d[0]);
-    float2 out[NU];
+    X Fprev = zero, sum = zero;
+    X dm4m = dm4(dm, d[0]);
+    X out[NU];
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
-        float2 F = zero;
-        float2 dm4p = zero;
+        X F = zero;
+        X dm4p = zero;
         if (i + 1 < NU) {
-            const float2 cm2 = i >= 2 ? v[i - 2] : zero;
-            const float2 cm1 = i >= 1 ? v[i - 1] : zero;
-            const float2 cp2 = i + 2 < NU ? v[i + 2] : zero;
+            const X cm2 = i >= 2 ? v[i - 2] : zero;
+            const X cm1 = i >= 1 ? v[i - 1] : zero;
+            const X cp2 = i + 2 < NU ? v[i + 2] : zero;
             dm4p = dm4(d[i], d[i + 1]);
             F = sl_mpp5_flux(lim, cm2, cm1, v[i], v[i + 1], cp2, dm4m, dm4p);
         }
@@ -148,7 +149,7 @@ __device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, c
 #pragma unroll
         for (int q = 0; q < PER; ++q) v[NEG ? NU - 1 - (PER * j + q) : PER * j + q] = make_float2(a[q], c[q]);
     }
-    const float2 sum = march_regs<NU>(v, lim);
+    const float2 sum = march_regs<NU, float2>(v, lim);
     float i0 = 1.f, i1 = 1.f;
     if (CODED) {
         float m0 = 0.f, m1 = 0.f;
@@ -196,7 +197,7 @@ __device__ __forceinline__ bool plane_columns(unsigned char *base, int tid, cons
     for (int i = 0; i < NU; ++i)
         v[NEG ? NU - 1 - i : i] =
             *reinterpret_cast<const float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4);
-    const float2 sum = march_regs<NU>(v, lim);
+    const float2 sum = march_regs<NU, float2>(v, lim);
 #pragma unroll
     for (int i = 0; i < NU; ++i)
         *reinterpret_cast<float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4) =
@@ -309,14 +310,140 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
     }
 }
 
+// One row per consumer thread (256 consumer threads, the same tiles and tensor
+// map as the paired kernel): half the registers of a row pair, so twice the
+// warps per SM, at the price of unpacked FP32 arithmetic.  16-bit codes use
+// the same per-row rounding streams as the paired kernel (bit-identical).
+constexpr int kLine1Threads = kLineRows;
+
+template <int NU, typename T>
+__global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
+    line_sweep1_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
+                       const __grid_constant__ ContigArgs<float> args)
+{
+    constexpr int S = kLineRing;
+    constexpr unsigned slot_bytes = kLineRows * NU * sizeof(T);
+    constexpr bool CODED = sizeof(T) == 2;
+    using G_ = LineGeom<NU, T>;
+    constexpr int PER = G_::per;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *done = full + S;
+    unsigned char *ring = smem + 128 + ((1024u - ((smem_u32(smem) + 128u) & 1023u)) & 1023u);
+    auto slot = [&](unsigned e) { return ring + slot_bytes * (e % S); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], kLine1Threads);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const long long Gd = gridDim.x, b = blockIdx.x;
+    const unsigned n_my = unsigned((args.num_tiles > b) ? (args.num_tiles - b + Gd - 1) / Gd : 0);
+
+    if (threadIdx.x < kProducer) {
+        if (threadIdx.x != 0) return;
+        unsigned loaded = 0, retired = 0;
+        bool ok = true;
+        while (retired < n_my) {
+            bool progress = false;
+            while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
+                tma_store_2d(&dmap, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
+                bulk_commit();
+                ++retired;
+                progress = true;
+            }
+            if (loaded < n_my && loaded < retired + S) {
+                if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
+                const unsigned st = loaded % S;
+                mbar_arrive_expect_tx(&full[st], slot_bytes);
+                tma_load_2d(slot(loaded), &map, &full[st], 0, int((b + (long long)loaded * Gd) * kLineRows));
+                ++loaded;
+                progress = true;
+            }
+            if (!progress && !mbar_wait_bounded(&done[retired % S], (retired / S) & 1u)) {
+                ok = false;
+                break;
+            }
+        }
+        bulk_wait_all();
+        if (!ok) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            for (unsigned t = retired; t < loaded; ++t) mbar_wait_bounded(&full[t % S], (t / S) & 1u);
+        }
+        return;
+    }
+
+    const int r = threadIdx.x - kProducer;
+    for (unsigned k = 0; k < n_my; ++k) {
+        const unsigned st = k % S;
+        if (!mbar_wait_bounded(&full[st], (k / S) & 1u)) {
+            atomicOr(args.err, ERR_TIMEOUT);
+            break;
+        }
+        const long long row0 = (b + (long long)k * Gd) * kLineRows;
+        unsigned char *base = slot(k);
+        if (row0 + r < args.rows) {
+            const LineCoefT<float> kc = args.cell_coef[(row0 + r) / args.rows_per_cell];
+            if (kc.nd >= 0) {
+                const bool neg = kc.nd & 1; // one orientation per spatial cell: warp-uniform
+                const float sc = CODED ? args.scale[row0 + r] : 1.f;
+                unsigned rng = CODED_RNG_INIT((unsigned long long)(row0 + r) * NU, args.seed);
+                float v[NU];
+#pragma unroll
+                for (int j = 0; j < G_::chunks; ++j) {
+                    float a[PER];
+                    Chunk<T>::get(base + G_::off(r, j), sc, a);
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) v[neg ? NU - 1 - (PER * j + q) : PER * j + q] = a[q];
+                }
+                const float sum = march_regs<NU, float>(v, to_lim(kc));
+                float inv = 1.f;
+                if (CODED) {
+                    // new scale: the line's largest value
+                    float m = 0.f;
+#pragma unroll
+                    for (int l = 0; l < NU; ++l) m = fmaxf(m, v[l]);
+                    args.scale[row0 + r] = m;
+                    inv = m > 0.f ? __fdividef(1.f, m) : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < G_::chunks; ++j) {
+                    float a[PER];
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) a[q] = v[neg ? NU - 1 - (PER * j + q) : PER * j + q];
+                    Chunk<T>::put(base + G_::off(r, j), inv, a, rng);
+                }
+                if (!(sum >= 0.f) || isinf(sum)) atomicOr(args.err, ERR_NAN);
+            }
+        }
+        fence_proxy_async();
+        mbar_arrive(&done[st]);
+    }
+}
+
+#ifndef VK_LINE_SINGLE
+#define VK_LINE_SINGLE 1 // 1: u_z lines one row per thread (0: two rows as a packed pair)
+#endif
+
 template <typename T> static const void *line_kernel_ptr(int nu)
 {
     return nu == 32 ? (const void *)line_sweep_kernel<32, T, false> : (const void *)line_sweep_kernel<16, T, false>;
 }
 
+static bool line_single(int, bool fuse_y) { return VK_LINE_SINGLE && !fuse_y; }
+
 static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
 {
     if (fuse_y) return nu == 32 ? (const void *)line_sweep_kernel<32, float, true> : (const void *)line_sweep_kernel<16, float, true>;
+    if (line_single(dtype, fuse_y)) {
+        if (dtype == 2) return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16> : (const void *)line_sweep1_kernel<16, __nv_bfloat16>;
+        if (dtype == 3) return nu == 32 ? (const void *)line_sweep1_kernel<32, __half> : (const void *)line_sweep1_kernel<16, __half>;
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, float> : (const void *)line_sweep1_kernel<16, float>;
+    }
     return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
 }
 
@@ -336,7 +463,8 @@ cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<ContigArgs<float> *>(&a)};
-    return cudaLaunchKernel(k, dim3(grid), dim3(kLineThreads + kProducer), args, smem, st);
+    const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;
+    return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st);
 }
 
 int occupancy_line_sweep(int nu, int dtype, bool fuse_y)
@@ -345,7 +473,8 @@ int occupancy_line_sweep(int nu, int dtype, bool fuse_y)
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kLineThreads + kProducer, smem) != cudaSuccess) return 0;
+    const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
     return n;
 }
 

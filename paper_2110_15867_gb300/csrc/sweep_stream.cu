@@ -28,29 +28,33 @@ namespace vk {
 #ifndef VK_STREAM_MINB
 #define VK_STREAM_MINB 4 // resident CTAs per SM the streamed sweep is compiled for
 #endif
+#ifndef VK_STREAM_SINGLE
+#define VK_STREAM_SINGLE 0 // 1: FP32 columns one per thread (0: packed pairs)
+#endif
 
 // Per-thread view of the storage of its column(s): load a row as the compute
 // vector X and store X back.  FP32 / FP64 store f itself.  BF16 / FP16 store
 // f / scale with one FP32 scale per u_z line; the scale of the row comes from
 // shared memory (staged by TMA with the chunk), `sp` points at it.
+// NC: consumer threads per CTA; a CTA's block is V * NC columns wide.
 template <typename T> struct Lane;
 template <> struct Lane<float> {
     using X = float2; // two columns per thread
-    static constexpr int V = 2;
+    static constexpr int V = 2, NC = kStreamConsumers;
     __device__ static X load(const float *p, const float *) { return *reinterpret_cast<const float2 *>(p); }
     __device__ static void store(float *p, X v, const float *, unsigned &) { *reinterpret_cast<float2 *>(p) = v; }
     __device__ static bool bad(X s) { return !(s.x >= 0.f) || !(s.y >= 0.f) || isinf(s.x) || isinf(s.y); }
 };
 template <> struct Lane<double> {
     using X = double;
-    static constexpr int V = 1;
+    static constexpr int V = 1, NC = kStreamConsumers;
     __device__ static X load(const double *p, const float *) { return *p; }
     __device__ static void store(double *p, X v, const float *, unsigned &) { *p = v; }
     __device__ static bool bad(X s) { return !(s >= 0.0) || isinf(s); }
 };
 template <> struct Lane<__nv_bfloat16> {
     using X = float2;
-    static constexpr int V = 2;
+    static constexpr int V = 2, NC = kStreamConsumers;
     __device__ static X load(const __nv_bfloat16 *p, const float *sp)
     {
         const unsigned u = *reinterpret_cast<const unsigned *>(p);
@@ -69,7 +73,7 @@ template <> struct Lane<__nv_bfloat16> {
 };
 template <> struct Lane<__half> {
     using X = float2;
-    static constexpr int V = 2;
+    static constexpr int V = 2, NC = kStreamConsumers;
     __device__ static X load(const __half *p, const float *sp)
     {
         const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(p));
@@ -85,7 +89,24 @@ template <> struct Lane<__half> {
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };
 
+// FP32 storage walked one column per thread (twice the consumer threads of the
+// packed pairs, the same 256-column blocks)
+struct F32Single {
+    float v;
+};
+template <> struct Lane<F32Single> {
+    using X = float;
+    static constexpr int V = 1, NC = 2 * kStreamConsumers;
+    __device__ static X load(const F32Single *p, const float *) { return p->v; }
+    __device__ static void store(F32Single *p, X v, const float *, unsigned &) { p->v = v; }
+    __device__ static bool bad(X s) { return !(s >= 0.f) || isinf(s); }
+};
+template <> struct Compute<F32Single> { using type = float; };
+
 template <typename C, typename X> struct PairLim;
+template <> struct PairLim<float, float> {
+    __device__ static Lim<float> make(const LineCoefT<float> &a, const LineCoefT<float> &) { return to_lim(a); }
+};
 template <> struct PairLim<float, float2> {
     __device__ static Lim<float2> make(const LineCoefT<float> &a, const LineCoefT<float> &b) { return to_lim2(a, b); }
 };
@@ -256,7 +277,7 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
 }
 
 template <typename T, bool PERIODIC>
-__global__ void __launch_bounds__(kStreamConsumers + kProducer, VK_STREAM_MINB)
+__global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
     stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                         const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
@@ -293,7 +314,7 @@ __global__ void __launch_bounds__(kStreamConsumers + kProducer, VK_STREAM_MINB)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&done[s], kStreamConsumers);
+            mbar_init(&done[s], Lane<T>::NC);
         }
         fence_barrier_init();
     }
@@ -444,13 +465,14 @@ static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &dm
     auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kStreamConsumers + kProducer, smem, st>>>(map, dmap, smap, a);
+    kern<<<grid, Lane<T>::NC + kProducer, smem, st>>>(map, dmap, smap, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<float> &a, int grid,
                               size_t smem, cudaStream_t st)
 {
+    if (VK_STREAM_SINGLE) return launch_stream_t<F32Single>(map, dmap, map, a, grid, smem, st);
     return launch_stream_t<float>(map, dmap, map, a, grid, smem, st);
 }
 
@@ -477,15 +499,18 @@ template <typename T> static const void *stream_ptr(int periodic)
     return periodic ? (const void *)stream_sweep_kernel<T, true> : (const void *)stream_sweep_kernel<T, false>;
 }
 
+int stream_columns_per_thread(int dtype) { return dtype == 0 || (dtype == 1 && VK_STREAM_SINGLE) ? 1 : 2; }
+int stream_consumers(int dtype) { return dtype == 1 && VK_STREAM_SINGLE ? Lane<F32Single>::NC : kStreamConsumers; }
+
 int occupancy_stream(int dtype, int periodic, size_t smem)
 {
     const void *k = dtype == 0 ? stream_ptr<double>(periodic)
-                    : dtype == 1 ? stream_ptr<float>(periodic)
+                    : dtype == 1 ? (VK_STREAM_SINGLE ? stream_ptr<F32Single>(periodic) : stream_ptr<float>(periodic))
                     : dtype == 2 ? stream_ptr<__nv_bfloat16>(periodic)
                                  : stream_ptr<__half>(periodic);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStreamConsumers + kProducer, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stream_consumers(dtype) + kProducer, smem) != cudaSuccess)
         return 0;
     return n;
 }

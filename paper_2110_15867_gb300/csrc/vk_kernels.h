@@ -126,6 +126,8 @@ cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, c
 cudaError_t launch_stream_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<double> &a, int grid,
                               size_t smem, cudaStream_t st);
 int occupancy_stream(int dtype, int periodic, size_t smem); // dtype: 0 f64, 1 f32, 2 bf16, 3 f16
+int stream_columns_per_thread(int dtype); // V: the streamed block is V * stream_consumers columns
+int stream_consumers(int dtype);
 
 // ----------------------------------------------------------------------------
 // contiguous sweep (axis u_z): rows of nuz cells

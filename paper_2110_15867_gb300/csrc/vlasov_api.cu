@@ -266,9 +266,9 @@ static int plan_axes(vlasov_ctx *c)
         }
         if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "axis %d: cuTensorMapEncodeTiled failed (%d)", ax, int(r));
     }
-    // streamed sweeps: blocks of V * kStreamConsumers columns, chunks of R rows, a ring of S slots
-    const int V = c->g.dtype == VLASOV_F64 ? 1 : 2; // columns per consumer thread
-    const int cols = V * kStreamConsumers;
+    // streamed sweeps: blocks of V * consumers columns, chunks of R rows, a ring of S slots
+    const int V = stream_columns_per_thread(c->g.dtype); // columns per consumer thread
+    const int cols = V * stream_consumers(c->g.dtype);
     for (int ax = 0; ax < 5; ++ax) {
         AxisPlan &p = c->splan[ax];
         p.L = int(d6[ax]);
