@@ -102,9 +102,9 @@ int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *ph
  * = 16 or 32 run D_uy and D_uz in one pass over f: each u_z tile of 256 rows
  * holds whole (cell, j_x) planes, whose columns are the u_y lines, so D_uy runs
  * on the staged tile before D_uz (the arithmetic of the separate sweeps,
- * bit for bit).  Off by default (the fused pass is compute-bound and only ~2 %
- * faster than the separate sweeps); on = 1 enables it.  Other storage types and
- * shapes always run the sweeps separately.
+ * bit for bit).  On by default (11 % faster than the two sweeps at n_u = 32);
+ * on = 0 runs them separately.  Other storage types and shapes always run the
+ * sweeps separately.
  */
 int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
 

@@ -316,7 +316,29 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
 // the same per-row rounding streams as the paired kernel (bit-identical).
 constexpr int kLine1Threads = kLineRows;
 
-template <int NU, typename T>
+// D_uy on the tile's planes for the one-row kernel (FP32, n_uy = n_uz = NU):
+// warp w later sweeps rows 32w..32w+31 along u_z, whole planes; lane l walks
+// column l % NU of the plane that starts at row 32w + (l / NU) NU.
+template <int NU, bool NEG>
+__device__ __forceinline__ bool plane_column1(unsigned char *base, int tid, const Lim<float> &lim)
+{
+    using G_ = LineGeom<NU, float>;
+    const int w = tid >> 5, l = tid & 31;
+    const int r_first = 32 * w + (l / NU) * NU, c = l % NU;
+    float v[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        v[NEG ? NU - 1 - i : i] =
+            *reinterpret_cast<const float *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4);
+    const float sum = march_regs<NU, float>(v, lim);
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        *reinterpret_cast<float *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4) =
+            v[NEG ? NU - 1 - i : i];
+    return !(sum >= 0.f) || isinf(sum);
+}
+
+template <int NU, typename T, bool FUSE_Y>
 __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
     line_sweep1_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                        const __grid_constant__ ContigArgs<float> args)
@@ -380,12 +402,23 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
     const int r = threadIdx.x - kProducer;
     for (unsigned k = 0; k < n_my; ++k) {
         const unsigned st = k % S;
-        if (!mbar_wait_bounded(&full[st], (k / S) & 1u)) {
+        // all lanes of a warp leave together (the fused pass synchronises the warp)
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (k / S) & 1u))) {
             atomicOr(args.err, ERR_TIMEOUT);
             break;
         }
         const long long row0 = (b + (long long)k * Gd) * kLineRows;
         unsigned char *base = slot(k);
+        if constexpr (FUSE_Y) {
+            // every row of the tile belongs to one spatial cell
+            const LineCoefT<float> ky = args.cell_coef_y[row0 / args.rows_per_cell];
+            if (row0 < args.rows && ky.nd >= 0) {
+                const bool bad = (ky.nd & 1) ? plane_column1<NU, true>(base, r, to_lim(ky))
+                                             : plane_column1<NU, false>(base, r, to_lim(ky));
+                if (bad) atomicOr(args.err, ERR_NAN);
+            }
+            __syncwarp();
+        }
         if (row0 + r < args.rows) {
             const LineCoefT<float> kc = args.cell_coef[(row0 + r) / args.rows_per_cell];
             if (kc.nd >= 0) {
@@ -434,16 +467,17 @@ template <typename T> static const void *line_kernel_ptr(int nu)
     return nu == 32 ? (const void *)line_sweep_kernel<32, T, false> : (const void *)line_sweep_kernel<16, T, false>;
 }
 
-static bool line_single(int, bool fuse_y) { return VK_LINE_SINGLE && !fuse_y; }
+static bool line_single(int, bool) { return VK_LINE_SINGLE; }
 
 static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
 {
-    if (fuse_y) return nu == 32 ? (const void *)line_sweep_kernel<32, float, true> : (const void *)line_sweep_kernel<16, float, true>;
     if (line_single(dtype, fuse_y)) {
-        if (dtype == 2) return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16> : (const void *)line_sweep1_kernel<16, __nv_bfloat16>;
-        if (dtype == 3) return nu == 32 ? (const void *)line_sweep1_kernel<32, __half> : (const void *)line_sweep1_kernel<16, __half>;
-        return nu == 32 ? (const void *)line_sweep1_kernel<32, float> : (const void *)line_sweep1_kernel<16, float>;
+        if (fuse_y) return nu == 32 ? (const void *)line_sweep1_kernel<32, float, true> : (const void *)line_sweep1_kernel<16, float, true>;
+        if (dtype == 2) return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, false> : (const void *)line_sweep1_kernel<16, __nv_bfloat16, false>;
+        if (dtype == 3) return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, false> : (const void *)line_sweep1_kernel<16, __half, false>;
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, float, false> : (const void *)line_sweep1_kernel<16, float, false>;
     }
+    if (fuse_y) return nu == 32 ? (const void *)line_sweep_kernel<32, float, true> : (const void *)line_sweep_kernel<16, float, true>;
     return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
 }
 

@@ -412,7 +412,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->stream = (cudaStream_t)stream;
     c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
-    c->fuse_kick = false; // see vlasov_set_fused_kick
+    c->fuse_kick = true; // see vlasov_set_fused_kick
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
     c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
     c->gd.L = g->L;
