@@ -396,6 +396,14 @@ def run_adjoint(torch, dev, reps=3):
     ts = [once() for _ in range(reps)]
     fw = float(np.median([t[0] for t in ts]))
     bw = float(np.median([t[1] for t in ts]))
+    # the same run with the last two segments recorded by the forward (one more segment of tape)
+    run.tape_segments = 2
+    once()
+    ts2 = [once() for _ in range(reps)]
+    fw2 = float(np.median([t[0] for t in ts2]))
+    bw2 = float(np.median([t[1] for t in ts2]))
+    run.tape_segments = 1
+    seg_gb = (8 * w["K"] + w["K"] - 1) * f0.size * 4 / 1e9
     run.v.read_timers()
     run.v.enable_timers(True)
     once()
@@ -445,6 +453,8 @@ def run_adjoint(torch, dev, reps=3):
     return {"workload": "%s: %d^3 x %d^3 cells FP32, %d steps, checkpoint every %d, external phi, "
                         "loss sum over 0<|n|<8 of |rho_hat|^2" % (w["name"], n, nu, w["steps"], w["K"]),
             "forward_ms": fw, "backward_ms": bw, "backward_over_forward": bw / fw,
+            "tape_2_segments": {"forward_ms": fw2, "backward_ms": bw2, "backward_over_forward": bw2 / fw2,
+                                "extra_tape_GB": seg_gb},
             "adjoint_sweeps": per, "gradients_finite": ok,
             "self_consistent": {"what": "the same run with phi^{n+1} from the post-drift moment plus a "
                                         "background (Poisson every step); gradients for f0, phi0, rho_bg",

@@ -6,12 +6,12 @@ drift uses ``a_half``) and returns the density rho_nu(x) (FP64) of the final sta
 Its backward gives dL/df0 and dL/dphi for any loss of rho_nu.
 
 Memory: the forward keeps the state every K steps (checkpoints) and runs the last
-segment (the last 1..K steps) with ``vlasov_step_record``, which keeps the input of
-every sweep (each sweep writes the next record, so recording costs no copies).  The
-backward takes the segments last to first: the last one is already on the tape; each
-earlier one is run again from its checkpoint with ``vlasov_step_record``; then
-``vlasov_step_adjoint_recorded`` is applied step by step in reverse.  The tape holds
-8 K + K - 1 arrays the size of f and is reused by later calls.
+``run.tape_segments`` segments (default 1) with ``vlasov_step_record``, which keeps the
+input of every sweep (each sweep writes the next record, so recording costs no copies).
+The backward takes the segments last to first: a taped one is already recorded; each
+other one is run again from its checkpoint with ``vlasov_step_record``; then
+``vlasov_step_adjoint_recorded`` is applied step by step in reverse.  Each taped segment
+holds 8 K + K - 1 arrays the size of f; the tape is reused by later calls.
 
 Every operation on f or lambda runs in libvlasov's kernels through the C ABI; this
 module only orders the calls and owns the buffers.
@@ -24,26 +24,39 @@ from .binding import Vlasov
 
 
 class Run:
-    """A context and the buffers of one grid: the working state and the tape."""
+    """A context and the buffers of one grid: the working state and the tape.
 
-    def __init__(self, shape, dtype=torch.float32, device="cuda", L: float = 1.0, V: float = 5.0):
+    tape_segments: how many trailing checkpoint segments the forward records directly
+    (each holds 8 K + K - 1 arrays the size of f); the backward runs the other segments
+    again.  More segments trade memory for less recomputation."""
+
+    def __init__(self, shape, dtype=torch.float32, device="cuda", L: float = 1.0, V: float = 5.0,
+                 tape_segments: int = 1):
+        if tape_segments < 1:
+            raise ValueError("tape_segments must be >= 1")
         self.shape = tuple(shape)
         self.work = torch.empty(self.shape, dtype=dtype, device=device)
         self.v = Vlasov(self.work, L=L, V=V)
-        self._rec = []
-        self._states = []
-        self.tape_owner = None  # the forward whose last segment the tape holds
+        self.tape_segments = tape_segments
+        self._slots = []
+        self.tape_owner = None  # the forward whose trailing segments the tape holds
+
+    def slot(self, i: int, K: int):
+        """Tape slot i: records for K steps (8 arrays each) and K - 1 intermediate states."""
+        while len(self._slots) <= i:
+            self._slots.append(([], []))
+        rec, states = self._slots[i]
+        while len(rec) < K:
+            rec.append([torch.empty_like(self.work) for _ in range(8)])
+        while len(states) < K - 1:
+            states.append(torch.empty_like(self.work))
+        return rec, states
 
     def tape(self, K: int):
-        """Records for K steps (8 arrays each) and K - 1 intermediate states."""
-        while len(self._rec) < K:
-            self._rec.append([torch.empty_like(self.work) for _ in range(8)])
-        while len(self._states) < K - 1:
-            self._states.append(torch.empty_like(self.work))
-        return self._rec, self._states
+        return self.slot(0, K)
 
     def release_tape(self):
-        self._rec, self._states = [], []
+        self._slots = []
 
     def close(self):
         self.release_tape()
@@ -57,26 +70,32 @@ class VlasovRun(torch.autograd.Function):
             raise ValueError("need n_steps >= 1 and K >= 1")
         phi32 = phi.detach().to(torch.float32).contiguous()
         v = run.v
+        nseg = (n_steps + K - 1) // K
+        first_taped = max(0, nseg - run.tape_segments)
         run.work.copy_(f0.detach())
         starts = [f0.detach().contiguous()]  # the state at the start of every segment
-        last = ((n_steps - 1) // K) * K       # first step of the last segment
-        for n in range(last):
+        for n in range(first_taped * K):
             if n > 0 and n % K == 0:
                 starts.append(run.work.clone())
             v.step(dt, a_half, a_half, phi32)
-        if last > 0:
+        if first_taped > 0:
             starts.append(run.work.clone())
-        # the last segment, recorded: its final state lands in run.work
-        m = n_steps - last
-        rec, states = run.tape(min(K, n_steps))
-        seq = [starts[-1]] + states[:m - 1]
-        for i in range(m):
-            v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else run.work)
+        # the trailing segments, recorded: each one's final state starts the next; the last lands in run.work
+        for sgi in range(first_taped, nseg):
+            m = min(K, n_steps - sgi * K)
+            rec, states = run.slot(sgi - first_taped, K)
+            last_seg = sgi == nseg - 1
+            end = run.work if last_seg else torch.empty_like(run.work)
+            seq = [starts[sgi]] + states[:m - 1] + [end]
+            for i in range(m):
+                v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1])
+            if not last_seg:
+                starts.append(end)
         token = object()
         run.tape_owner = token
         rho = v.moment()
         ctx.save_for_backward(f0, phi)
-        ctx.starts = starts[1:]
+        ctx.starts, ctx.first_taped = starts[1:], first_taped
         ctx.token = token
         ctx.run, ctx.dt, ctx.a_half, ctx.n_steps, ctx.K = run, dt, a_half, n_steps, K
         return rho
@@ -91,16 +110,19 @@ class VlasovRun(torch.autograd.Function):
         v.moment_adjoint(grad_rho.detach().to(torch.float64).contiguous(), lam)
         dphi = torch.zeros(phi32.shape, dtype=torch.float64, device=phi32.device)
         starts = [f0.detach().contiguous()] + ctx.starts
-        rec, states = run.tape(min(K, n_steps))
         taped = run.tape_owner is ctx.token  # no other forward has reused the tape since
         for s in reversed(range(len(starts))):
             m = min(K, n_steps - s * K)
+            on_tape = taped and s >= ctx.first_taped
+            rec, states = run.slot(s - ctx.first_taped if on_tape else 0, K)
             seq = [starts[s]] + states[:m - 1]
-            if not (taped and s == len(starts) - 1):
+            if not on_tape:
                 for i in range(m):
                     v.step_record(seq[i], rec[i], dt, a_half, phi32, f_next=seq[i + 1] if i + 1 < m else None)
             for i in reversed(range(m)):
                 v.step_adjoint_recorded(seq[i], rec[i], lam, dt, a_half, phi32, dphi)
+            if on_tape and s == ctx.first_taped:
+                taped = False  # the slots are reused from here on
         run.tape_owner = None
         ctx.starts = None
         return lam, dphi.to(phi.dtype), None, None, None, None, None

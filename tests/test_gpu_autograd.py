@@ -155,3 +155,29 @@ def test_run_fp32_gradient_close_to_fp64():
         rel = np.linalg.norm(g32[k] - y) / np.linalg.norm(y)
         print("%s FP32 vs FP64 rel L2 %.2e (FP64 spread %.2e)" % (name, rel, sens))
         assert np.isfinite(g32[k]).all() and rel <= 3 * sens + 1e-6
+
+
+@pytest.mark.parametrize("tape_segments", [2, 3])
+def test_more_taped_segments_give_the_same_gradients(tape_segments):
+    # the forward records the last tape_segments segments directly; the backward runs the
+    # others again: the same sweeps on the same inputs, so lambda is bit for bit and
+    # dL/dphi (per-cell sums by FP64 atomics at this velocity size) agrees to rounding
+    A, _ = _mods()
+    n, nu = (8, 8, 8), (8, 8, 8)
+    f0, phi = _setup(n, nu, np.float64, seed=4)
+    g = O.grid(n, nu, V=V)
+    dt, a, n_steps, K = _dt(g, phi, 0.7), 1.0, 7, 2
+    w = torch.from_numpy(np.random.default_rng(12).standard_normal(n)).cuda()
+    out = {}
+    for ts in (1, tape_segments):
+        run = A.Run(f0.shape, torch.float64, L=1.0, V=V, tape_segments=ts)
+        ft = torch.from_numpy(f0).cuda().requires_grad_()
+        pt = torch.from_numpy(phi).cuda().requires_grad_()
+        rho = A.run_rho(ft, pt, run, dt, a, n_steps, K)
+        (rho * w).sum().backward()
+        run.v.status()
+        out[ts] = (rho.detach().cpu().numpy(), ft.grad.cpu().numpy(), pt.grad.double().cpu().numpy())
+        run.close()
+    assert np.array_equal(out[1][0], out[tape_segments][0])
+    assert np.array_equal(out[1][1], out[tape_segments][1])
+    assert np.abs(out[1][2] - out[tape_segments][2]).max() <= 1e-6 * np.abs(out[1][2]).max()
