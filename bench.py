@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--fused-kick", type=int, default=None,
                    help="1 / 0: run the kicks' D_uy D_uz in one pass or separately (default: the library's)")
+    p.add_argument("--fused-moment", type=int, default=None,
+                   help="1 / 0: let the x sweep sum the moment or run the moment kernel (default: the library's)")
     p.add_argument("--profile-case", action="store_true",
                    help="run the small profiling case instead of the benchmark: sweeps on a "
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
@@ -481,6 +483,8 @@ def run_ours(args):
     v = B.Vlasov(f, L=L, V=V)
     if args.fused_kick is not None:
         v.set_fused_kick(bool(args.fused_kick))
+    if args.fused_moment is not None:
+        v.set_fused_moment(bool(args.fused_moment))
     rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
     phi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
     phi2 = torch.empty_like(phi)
@@ -662,7 +666,7 @@ def run_profile_case(args):
         v = B.Vlasov(f, V=V)
         dt = 0.7 / max(max(cmax[:3]), 0.5 * max(cmax[3:]))
         for _ in range(2):
-            v.step(dt, 1.0, 1.0, phi)
+            v.step(dt, 1.0, 1.0, phi, rho_nu=rho)  # the x sweep sums the moment
     elif args.adjoint:
         lam = torch.from_numpy(np.random.default_rng(4).standard_normal(f.shape).astype(np.float32)).to(dev)
         dLdg = torch.zeros(n, dtype=torch.float64, device=dev)

@@ -109,6 +109,21 @@ int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *ph
 int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
 
 /*
+ * The moment rho_nu that vlasov_step and vlasov_step_record_sc take after the
+ * drift (Eq. 5, Sec. 4.1.3) is summed by the x sweep itself when that sweep is
+ * streamed (|nu| < 1 in every velocity column) on FP32 or FP64 storage and the
+ * velocity cube is a multiple of 256 (FP32) or 128 (FP64) cells: a moment warp in
+ * each block adds up every output row the block writes (pairwise, FP32 for FP32
+ * storage, at most 8 roundings deep) and a second kernel adds each cell's partials
+ * in FP64 in a fixed order, so f is read once less per step.  The result equals
+ * vlasov_moment's to rounding (within 10 units in the last place of FP32;
+ * reproducible run to run).  Needs ncell x cube / 64 bytes of device memory (FP32
+ * and FP64), allocated on first use (without it the separate moment kernel runs).
+ * On by default; on = 0 always runs the separate moment kernel.
+ */
+int vlasov_set_fused_moment(vlasov_ctx *ctx, int on);
+
+/*
  * rho_nu(x) = du_x du_y du_z * sum over the velocity cube of f (Sec. 4.1.3),
  * written to rho_dev (nx*ny*nz FP64).  Each cell sum is formed from
  * compensated FP32 partial sums combined in FP64.  If mass_host is non-NULL

@@ -45,7 +45,8 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_sweep_velocity_static", "vlasov_set_f", "vlasov_sweep_adjoint",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
-           "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays")
+           "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
+           "vlasov_set_fused_moment")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -126,6 +127,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_moments.restype = ctypes.c_int
     L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
     L.vlasov_set_fused_kick.restype = ctypes.c_int
+    L.vlasov_set_fused_moment.argtypes = [_VP, ctypes.c_int]
+    L.vlasov_set_fused_moment.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -216,6 +219,10 @@ def vlasov_moment_adjoint(ctx, dLdrho_ptr: int, lam_ptr: int, accumulate: bool =
 
 def vlasov_set_fused_kick(ctx, on: bool):
     return _check(ctx, load().vlasov_set_fused_kick(ctx, int(bool(on))))
+
+
+def vlasov_set_fused_moment(ctx, on: bool):
+    return _check(ctx, load().vlasov_set_fused_moment(ctx, int(bool(on))))
 
 
 def vlasov_sweep(ctx, axis: int, dt: float, a: float, phi_ptr):
@@ -502,6 +509,10 @@ class Vlasov:
     def set_fused_kick(self, on: bool = True):
         """Run the kicks' D_uy and D_uz in one pass (FP32, n_uy = n_uz = 16 or 32)."""
         vlasov_set_fused_kick(self.ctx, on)
+
+    def set_fused_moment(self, on: bool = True):
+        """Let the step's x sweep sum the moment of its output (FP32 / FP64 storage)."""
+        vlasov_set_fused_moment(self.ctx, on)
 
     def enable_timers(self, on: bool = True):
         vlasov_enable_timers(self.ctx, on)

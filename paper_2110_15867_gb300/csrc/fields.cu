@@ -209,6 +209,44 @@ cudaError_t launch_moment(const GridDims &g, const void *f, int dtype, double *r
     return cudaGetLastError();
 }
 
+// The moment fused into the x sweep: the velocity cube of spatial cell
+// x cells_per_row + c arrives as nparts partial sums (in the storage type) laid out
+// [c][part][x]; rho = du^3 x their sum in FP64 in a fixed order.  One block per c:
+// 4 groups of 64 threads (x) take every 4th part, then one group adds the 4 sums.
+template <typename P>
+__global__ void __launch_bounds__(256) moment_finish_kernel(const P *__restrict__ mpart, int nparts, int nx,
+                                                            long long cells_per_row, double du3, double *rho)
+{
+    __shared__ double red[4][64];
+    const int tx = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    for (long long c = blockIdx.x; c < cells_per_row; c += gridDim.x) {
+        const P *q = mpart + c * nparts * (long long)nx;
+        for (int x0 = 0; x0 < nx; x0 += 64) {
+            const int x = x0 + tx;
+            double s = 0.0;
+            if (x < nx)
+                for (int k = grp; k < nparts; k += 4) s += double(q[(long long)k * nx + x]);
+            red[grp][tx] = s;
+            __syncthreads();
+            if (grp == 0 && x < nx) rho[x * cells_per_row + c] = du3 * (((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx]);
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_moment_finish(const void *mpart, int dtype, int nparts, int nx, long long cells_per_row, double du3,
+                                 double *rho, cudaStream_t st, int sm_count)
+{
+    const long long blocks = cells_per_row < (long long)sm_count * 8 ? cells_per_row : (long long)sm_count * 8;
+    if (dtype == 0)
+        moment_finish_kernel<double><<<int(blocks), 256, 0, st>>>((const double *)mpart, nparts, nx, cells_per_row,
+                                                                     du3, rho);
+    else
+        moment_finish_kernel<float><<<int(blocks), 256, 0, st>>>((const float *)mpart, nparts, nx, cells_per_row, du3,
+                                                                    rho);
+    return cudaGetLastError();
+}
+
 // Adjoint of the moment: rho(x) = du^3 sum_u f(x, u), so dL/df(x, u) =
 // du^3 dL/drho(x) for every u.  lam (+)= that, 16 bytes per thread and step.
 template <typename T>

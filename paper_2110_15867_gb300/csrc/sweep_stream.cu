@@ -276,8 +276,54 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
     return sum;
 }
 
-template <typename T, bool PERIODIC>
-__global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
+// ----------------------------------------------------------------------------
+// velocity moment fused into the x sweep
+// ----------------------------------------------------------------------------
+// A moment warp sums every released chunk's rows (4 rows x W values, all in one
+// spatial cell's velocity cube) while the producer stores the chunk: a lane adds
+// its 32 bytes of a row pairwise, then the warp adds the lanes pairwise in a fixed
+// order (FP32 storage: FP32, at most 8 roundings deep; FP64: FP64).  The first two
+// levels halve the rows each lane holds, the last three add within groups of 8
+// lanes, so lane l ends with the total of row l >> 3.  The producer reloads a slot
+// only after the moment warp has summed it.
+__device__ __forceinline__ float lane_row_sum(const float *row, int lane)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(row) + 2 * lane;
+    const float4 a = q[0], b = q[1];
+    return ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+}
+__device__ __forceinline__ float lane_row_sum(const F32Single *row, int lane)
+{
+    return lane_row_sum(reinterpret_cast<const float *>(row), lane);
+}
+__device__ __forceinline__ double lane_row_sum(const double *row, int lane)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(row) + 2 * lane;
+    const double2 a = q[0], b = q[1];
+    return (a.x + a.y) + (b.x + b.y);
+}
+template <typename T> __device__ __forceinline__ float lane_row_sum(const T *, int) { return 0.f; }
+
+template <typename A> __device__ __forceinline__ A rows4_warp_sum(A v0, A v1, A v2, A v3, int lane)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool hi = lane & 16, odd = lane & 8;
+    A k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+    k0 += __shfl_xor_sync(kAll, hi ? v0 : v2, 16);
+    k1 += __shfl_xor_sync(kAll, hi ? v1 : v3, 16);
+    A k = odd ? k1 : k0;
+    k += __shfl_xor_sync(kAll, odd ? k0 : k1, 8);
+    k += __shfl_xor_sync(kAll, k, 4);
+    k += __shfl_xor_sync(kAll, k, 2);
+    k += __shfl_xor_sync(kAll, k, 1);
+    return k;
+}
+
+// threads ahead of the consumers: the producer warp, and the moment warp if any
+template <bool MOMENT> __host__ __device__ constexpr int stream_head() { return kProducer + (MOMENT ? 32 : 0); }
+
+template <typename T, bool PERIODIC, bool MOMENT = false>
+__global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM_MINB)
     stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                         const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
@@ -294,6 +340,9 @@ __global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *done = full + S;
     int4 *meta = reinterpret_cast<int4 *>(done + S); // per slot: store coordinates, is-chunk flag
+    uint64_t *summed = reinterpret_cast<uint64_t *>(meta + S); // the moment warp has read the slot
+    constexpr int kHead = stream_head<MOMENT>();
+    static_assert(3 * S * sizeof(uint64_t) + S * sizeof(int4) <= 512, "ring barriers and meta fit ahead of the table");
     LineCoefT<C> *tab = reinterpret_cast<LineCoefT<C> *>(smem + 512);
     const size_t tab_bytes = (args.coef_mode == 0) ? ((sizeof(LineCoefT<C>) * args.nvel + 127) & ~size_t(127)) : 0;
     unsigned char *ring = smem + 512 + tab_bytes;
@@ -315,6 +364,7 @@ __global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&done[s], Lane<T>::NC);
+            if (MOMENT) mbar_init(&summed[s], 1);
         }
         fence_barrier_init();
     }
@@ -348,6 +398,11 @@ __global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
             if (loaded < total && loaded < retired + S) {
                 // the store of entry loaded - S is group loaded - S of `retired` groups
                 if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
+                if (MOMENT && loaded >= unsigned(S) &&
+                    !mbar_wait_bounded(&summed[loaded & (S - 1)], ((loaded - S) / S) & 1u)) {
+                    ok = false;
+                    break;
+                }
                 if (j == 0) {
                     const long long t = b + k * G;
                     c0 = int((t % args.tiles_inner) * W);
@@ -382,8 +437,47 @@ __global__ void __launch_bounds__(Lane<T>::NC + kProducer, VK_STREAM_MINB)
         return;
     }
 
+    if (MOMENT && threadIdx.x < kHead) {
+        // ------------------------------------------------------------ moment warp
+        // entries in order: wait for the consumers' release, sum the chunk's rows
+        // (row x of the block at inner offset c0 adds to spatial cell
+        // x (n_inner / cube) + c0 / cube as its partial (c0 % cube) / W, stored at
+        // mpart[((c0 / cube) nparts + part) L + x]), then free the slot for reloading
+        using A = decltype(lane_row_sum((const T *)nullptr, 0));
+        const int lane = threadIdx.x & 31;
+        const int cube = int(args.cube);
+        const unsigned total = unsigned(n_my) * unsigned(E);
+        A *base = nullptr;
+        int base_c0 = -1;
+        for (unsigned en = 0; en < total; ++en) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done[en & (S - 1)], (en / S) & 1u));
+            if (!ok) {
+                if (lane == 0) atomicOr(args.err, ERR_TIMEOUT);
+                return;
+            }
+            const int4 m = meta[en & (S - 1)];
+            if (m.w) {
+                if (m.x != base_c0) {
+                    base_c0 = m.x;
+                    base = static_cast<A *>(args.mpart) +
+                           ((long long)(m.x / cube) * args.nparts + (m.x % cube) / W) * (long long)L;
+                }
+                const T *q = slot_ptr(en);
+                const A z = A(0);
+                const A tot = rows4_warp_sum(lane_row_sum(q, lane), m.y + 1 < L ? lane_row_sum(q + W, lane) : z,
+                                             m.y + 2 < L ? lane_row_sum(q + 2 * W, lane) : z,
+                                             m.y + 3 < L ? lane_row_sum(q + 3 * W, lane) : z, lane);
+                const int r = lane >> 3;
+                if ((lane & 7) == 0 && m.y + r < L) base[m.y + r] = tot;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&summed[en & (S - 1)]);
+        }
+        return;
+    }
+
     // ---------------------------------------------------------------- consumers
-    const int tid = threadIdx.x - kProducer;
+    const int tid = threadIdx.x - kHead;
     int col;  // first of this thread's V columns inside the block
     if (args.perm_line > 0) {
         // z sweep: the Courant number changes sign in the middle of each velocity
@@ -463,9 +557,15 @@ static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &dm
                                    const StreamArgs<typename Compute<T>::type> &a, int grid, size_t smem, cudaStream_t st)
 {
     auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
+    int threads = Lane<T>::NC + stream_head<false>();
+    if constexpr (sizeof(T) != 2)
+        if (a.mpart) {
+            kern = stream_sweep_kernel<T, true, true>; // the x sweep with the moment
+            threads = Lane<T>::NC + stream_head<true>();
+        }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, Lane<T>::NC + kProducer, smem, st>>>(map, dmap, smap, a);
+    kern<<<grid, threads, smem, st>>>(map, dmap, smap, a);
     return cudaGetLastError();
 }
 

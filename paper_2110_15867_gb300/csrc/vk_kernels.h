@@ -112,6 +112,14 @@ template <typename C> struct StreamArgs {
     long long nuz;
     unsigned seed;      // 16-bit storage: stochastic-rounding stream of this sweep
     int scale_rank;     // 16-bit storage: rank of the scale tensor map (3, or 2 for the u_y sweep)
+    // x sweep with the velocity moment fused (FP32 / FP64 storage, P = 1, W x the element
+    // size = 1024 bytes, W divides the velocity cube): a moment warp sums every output row;
+    // row x of the block at inner offset c0 adds to spatial cell x (n_inner / cube) +
+    // c0 / cube as partial k = (c0 % cube) / W of nparts = cube / W, stored in the
+    // storage type at mpart[((c0 / cube) nparts + k) L + x] (null: no moment)
+    void *mpart;
+    long long cube;
+    int nparts;
     LineCoefT<C> table[kMaxVel];
 };
 
@@ -126,6 +134,10 @@ cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, c
 cudaError_t launch_stream_f64(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<double> &a, int grid,
                               size_t smem, cudaStream_t st);
 int occupancy_stream(int dtype, int periodic, size_t smem); // dtype: 0 f64, 1 f32, 2 bf16, 3 f16
+// rho[x cells_per_row + c] = du3 * sum over k of mpart[(c nparts + k) nx + x] (FP32 or FP64
+// partials: dtype 1 / 0), in FP64 in a fixed order
+cudaError_t launch_moment_finish(const void *mpart, int dtype, int nparts, int nx, long long cells_per_row, double du3,
+                                 double *rho, cudaStream_t st, int sm_count);
 int stream_columns_per_thread(int dtype); // V: the streamed block is V * stream_consumers columns
 int stream_consumers(int dtype);
 

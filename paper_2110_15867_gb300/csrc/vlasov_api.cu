@@ -131,6 +131,8 @@ struct vlasov_ctx {
     double *d_sc; // self-consistent adjoint: dL/dphi^{n+1} and dL/drho (2 * ncell)
     double *d_part; // adjoint: per-block sums of dL/dnu (deterministic per-cell reduction)
     size_t part_len;
+    void *d_mpart; // the moment fused into the x sweep: per-cell partial sums (storage type)
+    bool fuse_moment;
     int adj_arrays; // f-sized scratch arrays vlasov_step_adjoint may use: 8, 4 or 0 (8 if they fit, else 4)
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
@@ -376,6 +378,7 @@ static void free_scratch(vlasov_ctx *c)
     cudaFree(c->d_lam_tmp);
     cudaFree(c->d_sc);
     cudaFree(c->d_part);
+    cudaFree(c->d_mpart);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -413,6 +416,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
     c->fuse_kick = true; // see vlasov_set_fused_kick
+    c->fuse_moment = true; // see vlasov_set_fused_moment
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
     c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
     c->gd.L = g->L;
@@ -573,9 +577,39 @@ static cudaError_t launch_stream_any(const vlasov_ctx *c, int ax, const StreamAr
 
 static bool coded(const vlasov_ctx *c) { return c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16; }
 
+static long long velocity_cube(const vlasov_ctx *c) { return (long long)c->g.nux * c->g.nuy * c->g.nuz; }
+
+// Partial sums per spatial cell of the moment fused into the x sweep: one per block
+// (W columns) of the velocity cube.
+static int moment_parts(const vlasov_ctx *c) { return int(velocity_cube(c) / c->splan[0].W); }
+
+// Can the streamed x sweep sum its output rows into the velocity moment?  Its
+// moment warp sums chunks of 4 rows x W values (32 bytes a lane), which must lie
+// in one spatial cell's velocity cube (W | cube, one plane per block); the partial
+// sums need ncell x cube / W values.
+static bool fused_moment_ok(vlasov_ctx *c, int ax)
+{
+    if (ax != 0 || !c->fuse_moment || coded(c)) return false;
+    const AxisPlan &sp = c->splan[0];
+    const long long cube = velocity_cube(c);
+    if (sp.P != 1 || c->splan_R[0] != 4 || (long long)sp.W * c->es != 1024 || cube % sp.W) return false;
+    if (!c->d_mpart) {
+        if (cudaMalloc(&c->d_mpart, (size_t)c->es * c->ncell * moment_parts(c)) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_mpart = nullptr;
+            c->fuse_moment = false; // no room: the separate moment kernel from here on
+            return false;
+        }
+    }
+    return true;
+}
+
 // position sweep from src to dst (NULL, NULL: c->f in place) with per-velocity-column
-// constants from nu_j = u_j dt / (a^2 dx)
-static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *src = nullptr, void *dst = nullptr)
+// constants from nu_j = u_j dt / (a^2 dx).  With rho_fused (x sweep only) the sweep
+// also writes the velocity moment of its output to rho_fused when it can, and then
+// sets *fused.
+static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *src = nullptr, void *dst = nullptr,
+                        double *rho_fused = nullptr, bool *fused = nullptr)
 {
     ++c->sweeps;
     if (!src) src = c->f;
@@ -596,12 +630,15 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
         // no whole-cell shift on any line: streamed sweep
         const AxisPlan &sp = c->splan[ax];
         if (!coded(c) && (rc = sweep_maps(c, sp.map, sp.spec, src, dst, m))) return rc;
+        const bool fm = rho_fused && fused_moment_ok(c, ax);
+        const long long cube = velocity_cube(c);
         cudaError_t e;
         if (c->g.dtype == VLASOV_F64) {
             StreamArgs<double> A{};
             fill_stream_args(A, c, ax);
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+            if (fm) { A.mpart = c->d_mpart; A.cube = cube; A.nparts = moment_parts(c); }
             PartTimer t(c, ax, 1);
             e = launch_stream_f64(m.in, m.out, A, sp.grid, sp.smem, c->stream);
         } else {
@@ -609,10 +646,19 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
             fill_stream_args(A, c, ax);
             A.vstride = vstride; A.nvel = nvel; A.coef_mode = 0; A.outer_per_cell = 1; A.cell_coef = nullptr;
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+            if (fm) { A.mpart = c->d_mpart; A.cube = cube; A.nparts = moment_parts(c); }
             PartTimer t(c, ax, 1);
             e = launch_stream_any(c, ax, A, m);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
+        if (fm) {
+            const double du3 = (2.0 * c->g.V / c->g.nux) * (2.0 * c->g.V / c->g.nuy) * (2.0 * c->g.V / c->g.nuz);
+            PartTimer t(c, VLASOV_T_MOMENT, 1);
+            e = launch_moment_finish(c->d_mpart, c->g.dtype == VLASOV_F64 ? 0 : 1, moment_parts(c), c->g.nx,
+                                     c->ncell / c->g.nx, du3, rho_fused, c->stream, c->sm_count);
+            if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
+            if (fused) *fused = true;
+        }
         return VLASOV_OK;
     }
     if (coded(c)) return fail(c, VLASOV_EINVAL, "sweep %d: |nu| = %.3g >= 1 needs FP32 or FP64 storage", ax, numax);
@@ -802,6 +848,13 @@ extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int on)
     return VLASOV_OK;
 }
 
+extern "C" int vlasov_set_fused_moment(vlasov_ctx *c, int on)
+{
+    if (!c) return VLASOV_EINVAL;
+    c->fuse_moment = on != 0;
+    return VLASOV_OK;
+}
+
 extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_full, const float *phi_n_dev,
                            const double *rho_bg_dev, double four_pi_G, float *phi_next_dev, double *rho_nu_dev)
 {
@@ -811,11 +864,15 @@ extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_ful
     // kick D_uz D_uy D_ux (dt/2), D_ux first
     if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
     if ((rc = run_kick(c))) return rc;
-    // drift D_x D_y D_z (dt), D_z first, at the mid-step scale factor
-    for (int ax = 2; ax >= 0; --ax)
-        if ((rc = run_position(c, ax, dt, a_half))) return rc;
+    // drift D_x D_y D_z (dt), D_z first, at the mid-step scale factor; the x sweep
+    // writes the moment when it can
     double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
-    if (rho_nu_dev || phi_next_dev)
+    const bool need_rho = rho_nu_dev || phi_next_dev;
+    bool have_rho = false;
+    for (int ax = 2; ax >= 0; --ax)
+        if ((rc = run_position(c, ax, dt, a_half, nullptr, nullptr, ax == 0 && need_rho ? rho : nullptr, &have_rho)))
+            return rc;
+    if (need_rho && !have_rho)
         if ((rc = vlasov_moment(c, rho, nullptr))) return rc;
     if (phi_next_dev) {
         if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
@@ -1139,16 +1196,19 @@ extern "C" int vlasov_step_record_sc(vlasov_ctx *c, const void *f_n_dev, void *c
     if (f_next_dev && reinterpret_cast<uintptr_t>(f_next_dev) % 16)
         return fail(c, VLASOV_EINVAL, "vlasov_step_record_sc: f_next_dev must be 16-byte aligned");
     if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
+    double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
+    bool have_rho = false; // the x sweep (k = 5) writes the moment when it can, as in vlasov_step
     for (int k = 0; k < 9; ++k) {
         if (k == 6) {
             // after the drift (rec[5] = input of sweep 6): moment, Poisson, the second kick's constants
-            double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
-            cudaError_t e;
-            {
-                PartTimer t(c, VLASOV_T_MOMENT, 1);
-                e = launch_moment(c->gd, rec_dev[5], c->g.dtype == VLASOV_F64 ? 0 : 1, rho, c->stream, c->sm_count);
+            if (!have_rho) {
+                cudaError_t e;
+                {
+                    PartTimer t(c, VLASOV_T_MOMENT, 1);
+                    e = launch_moment(c->gd, rec_dev[5], c->g.dtype == VLASOV_F64 ? 0 : 1, rho, c->stream, c->sm_count);
+                }
+                if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
             }
-            if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
             if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
             if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
         }
@@ -1156,7 +1216,8 @@ extern "C" int vlasov_step_record_sc(vlasov_ctx *c, const void *f_n_dev, void *c
         void *dst = k < 8 ? rec_dev[k] : f_next_dev;
         if (!dst) break;
         const int ax = kStepAxes[k];
-        rc = ax >= 3 ? run_velocity(c, ax, src, dst) : run_position(c, ax, step_dt(k, dt), a_half, src, dst);
+        rc = ax >= 3 ? run_velocity(c, ax, src, dst)
+                     : run_position(c, ax, step_dt(k, dt), a_half, src, dst, k == 5 ? rho : nullptr, &have_rho);
         if (rc) return rc;
     }
     return VLASOV_OK;
