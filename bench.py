@@ -129,10 +129,23 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+# the sources each timed kernel kind is built from (its DRAM traffic record is void once
+# one of them changes)
+_COMMON_SOURCES = ("vk_common.cuh", "vk_kernels.h")
+KERNEL_SOURCES = {
+    "sweep_x": ("sweep_stream.cu",), "sweep_y": ("sweep_stream.cu",), "sweep_z": ("sweep_stream.cu",),
+    "sweep_ux": ("sweep_stream.cu",), "sweep_uy": ("sweep_stream.cu",),
+    "sweep_uz": ("sweep_lines.cu",), "sweep_uyuz": ("sweep_lines.cu",),
+}
+
+
+def kernel_source_hash(kind):
+    """Hash of the sources `kind`'s kernel is built from (None for an unknown kind)."""
+    if kind not in KERNEL_SOURCES:
+        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_15867_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in sorted(KERNEL_SOURCES[kind] + _COMMON_SOURCES):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
@@ -147,10 +160,8 @@ def committed_traffic(kind):
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("source_hash") != kernel_source_hash():
-        return None
     ent = d.get("kernels", {}).get(kind)
-    if not ent:
+    if not ent or ent.get("source_hash") is None or ent.get("source_hash") != kernel_source_hash(kind):
         return None
     return ent.get("bytes_per_full_launch")
 
