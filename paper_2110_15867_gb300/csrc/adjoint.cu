@@ -274,14 +274,17 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         const C k1 = isf ? k.w[1] : eu ? -k.alpha : el ? C(-0.5) : C(0);
         const C k2 = isf ? k.w[2] : e0 ? C(1) : em ? C(0.5) : eu ? C(1) + k.alpha : el ? C(1.5) : C(0);
         const C k3 = isf ? k.w[3] : e1 ? C(1) : em ? C(0.5) : C(0);
-        const C ks = isf ? (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2)
-                         : eu ? k.dalpha * dlm : C(0);
+        // dL/ds: velocity sweeps only (a position sweep's s does not depend on phi)
+        const C ks = PERIODIC ? C(0)
+                     : isf    ? (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2)
+                     : eu     ? k.dalpha * dlm
+                              : C(0);
         ow[0] += gv * k0;
         ow[1] += gv * k1;
         ow[2] += gv * k2 + gpp;
         ow[3] += gv * k3;
         ow[4] += gv * k4;
-        dLds += gv * ks + (inr ? v * gbar : C(0));
+        if (!PERIODIC) dLds += gv * ks + (inr ? v * gbar : C(0));
         // dm4 at j - 1/2 is complete: scatter to the curvatures of cells j-1, j
         const C gqm = gq + (el ? C(4.0 / 3.0) * gv : C(0));
         gdm += gqm * qam;
@@ -568,7 +571,12 @@ template <typename T, bool PERIODIC, bool SMALL4, int LCT>
 __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_ADJ_MINB_U : VK_ADJ_MINB)) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
-    const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    if (a.perm_line > 0) {
+        // lines of the block's u_z rows, negative halves first (the host checks Lz | kAdjBlock)
+        const int h = a.perm_line / 2, tt = threadIdx.x % (kAdjBlock / 2);
+        t = blockIdx.x * (long long)kAdjBlock + (tt / h) * a.perm_line + (threadIdx.x >= kAdjBlock / 2 ? h : 0) + tt % h;
+    }
     long long cell = -1;
     C dnu = C(0);
     if (t < a.nlines) {

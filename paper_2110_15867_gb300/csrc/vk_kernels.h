@@ -215,6 +215,9 @@ template <typename C> struct AdjArgs {
     long long lines_per_cell; // velocity sweeps: cell = t / lines_per_cell
     double dnu_dg;            // -dt / du
     double *block_part;       // non-null: every block lies in one cell; block sums go here (no atomics)
+    int perm_line;            // > 0 (z sweep): the Courant number changes sign in the middle of each u_z
+                              // line of this length; a block's first half of threads takes the u_z < 0
+                              // halves of its lines and the second half the rest (whole warps of one sign)
     LineCoefT<C> table[kMaxVel];
 };
 

@@ -950,6 +950,9 @@ static int run_adjoint_t(vlasov_ctx *c, const void *f_in, void *lam, int ax, dou
             A.table[j] = make_line_coef<C>(nu);
             shifted = shifted || fabs(nu) >= 1.0;
         }
+        // z: group each block's threads by the sign of u_z (whole u_z lines per block)
+        const int bt = adjoint_block_threads(), nuz = int(c->g.nuz);
+        if (ax == 2 && nuz % 2 == 0 && bt % nuz == 0 && I % bt == 0) A.perm_line = nuz;
         if (shifted) {
             // lambda is read N cells on: write the result to scratch, then copy back
             int rc = ensure_buffer(c, &c->d_lam_tmp, f_bytes(c));
