@@ -594,12 +594,26 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_
             const bool neg = kc.nd & 1;
             const long long st = neg ? -a.n_inner : a.n_inner;
             const long long off = neg ? (long long)(a.L - 1) * a.n_inner : 0;
-            // the forward shifts whole cells N = nd / 2 after the fractional update: read lambda N cells on
-            GlobalLine<T> acc{f + off, lin + off, lout + off, st, PERIODIC ? (kc.nd >> 1) % a.L : 0, a.L};
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
-            if constexpr (SMALL4) march_adjoint4<C>(acc, lim, dLds, osum);
-            else march_adjoint<PERIODIC, LCT, C>(acc, lim, a.L, dLds, osum);
+            if constexpr (!PERIODIC && !SMALL4 && LCT > 0 && LCT <= 16) {
+                // short zero-flux line: every load first (in walk order), the march on
+                // registers, then every store
+                RegLine<T, LCT, false> acc;
+#pragma unroll
+                for (int i = 0; i < LCT; ++i) {
+                    acc.cv[i] = f[off + i * st];
+                    acc.lv[i] = lin[off + i * st];
+                }
+                march_adjoint<false, LCT, C>(acc, lim, LCT, dLds, osum);
+#pragma unroll
+                for (int i = 0; i < LCT; ++i) lout[off + i * st] = acc.lv[i];
+            } else {
+                // the forward shifts whole cells N = nd / 2 after the fractional update: read lambda N cells on
+                GlobalLine<T> acc{f + off, lin + off, lout + off, st, PERIODIC ? (kc.nd >> 1) % a.L : 0, a.L};
+                if constexpr (SMALL4) march_adjoint4<C>(acc, lim, dLds, osum);
+                else march_adjoint<PERIODIC, LCT, C>(acc, lim, a.L, dLds, osum);
+            }
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = neg ? -dLds : dLds;
         }
