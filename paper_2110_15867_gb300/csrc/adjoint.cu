@@ -45,6 +45,10 @@ constexpr int kAdjBlock = 256;
 #define VK_ADJ_MINB_U 3 // the same for its unrolled (compile-time length) instances
 #endif
 constexpr int kAdjUnroll = VK_ADJ_UNROLL;
+#ifndef VK_ADJ_REG_MAX
+#define VK_ADJ_REG_MAX 32 // lines up to this length (compile-time instances) are marched in registers
+#endif
+constexpr int kAdjRegMax = VK_ADJ_REG_MAX;
 
 template <typename C> struct AdjLim {
     C w[5];  // weights of fbar
@@ -568,7 +572,10 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
 template <typename T, bool PERIODIC, bool SMALL4, int LCT>
-__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_ADJ_MINB_U : VK_ADJ_MINB)) adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
+__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2
+                                             : (LCT > 16 && LCT <= VK_ADJ_REG_MAX) ? 2
+                                             : (LCT > 0 ? VK_ADJ_MINB_U : VK_ADJ_MINB))
+    adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
     long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
@@ -596,16 +603,19 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 0 ? VK_
             const long long off = neg ? (long long)(a.L - 1) * a.n_inner : 0;
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
-            if constexpr (!PERIODIC && !SMALL4 && LCT > 0 && LCT <= 16) {
-                // short zero-flux line: every load first (in walk order), the march on
-                // registers, then every store
+            if constexpr (!SMALL4 && LCT > 0 && LCT <= kAdjRegMax) {
+                // short line: every load first (in walk order; lambda rotated by a
+                // periodic whole-cell shift), the march on registers, then every store
+                const int shift = PERIODIC ? (kc.nd >> 1) % LCT : 0;
                 RegLine<T, LCT, false> acc;
 #pragma unroll
                 for (int i = 0; i < LCT; ++i) {
+                    int r = i + shift;
+                    if (r >= LCT) r -= LCT;
                     acc.cv[i] = f[off + i * st];
-                    acc.lv[i] = lin[off + i * st];
+                    acc.lv[i] = lin[off + r * st];
                 }
-                march_adjoint<false, LCT, C>(acc, lim, LCT, dLds, osum);
+                march_adjoint<PERIODIC, LCT, C>(acc, lim, LCT, dLds, osum);
 #pragma unroll
                 for (int i = 0; i < LCT; ++i) lout[off + i * st] = acc.lv[i];
             } else {
