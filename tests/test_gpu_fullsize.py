@@ -1,0 +1,225 @@
+"""Parity at the full workload sizes, through the same context and kernels bench.py times.
+
+The oracle cannot hold these grids (34-88 GB), but a sweep is line-local: a line's
+output depends only on that line's input and its Courant number.  Each test forms f0 on
+the device as bench.py does ((1 + delta) F in FP64 per x-slab, rounded once to the
+storage type), copies sampled input lines to the host before each sweep, sweeps the
+whole grid through the C ABI, and compares the same lines' output with the oracle's sweep
+of their input (per-sweep tolerances of the parity tests over the sample: relative L1
+<= 1e-6, L_inf <= 1e-4 of its largest value; 16-bit storage: the codec bounds).  The
+sample holds the first and last lines of each axis besides random ones.  The step,
+which is not line-local, is checked by what holds at any size: mass, positivity, and the
+moment the x sweep sums in the step against the moment kernel on the final state (the
+second kick moves mass only within each cell's velocity cube, so the two agree to the
+FP32 rounding of three sweeps).
+
+Workloads: 64^3 x 32^3 FP32 (the benchmark), 48^3 x 48^3 FP32 with |u| <= 8 u_T (its
+velocity cube, 432 KiB, does not fit in shared memory), 96^3 x 32^3 BF16 / FP16 with a
+scale per u_z line, 32^3 x 16^3 FP32 for the adjoint sweeps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_15867_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_L1 = 1e-6
+RTOL_LINF = 1e-4
+K_LINES = 256
+
+
+def _lib():
+    from paper_2110_15867_gb300 import binding as B
+    B.load()
+    return B
+
+
+def _free():
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _build_f(cfg, dtype):
+    """f0 of a workload recipe on the device; 16-bit: (codes, scales)."""
+    B = _lib()
+    n, nu, V = cfg["n"], cfg["nu"], cfg["V"]
+    delta = torch.from_numpy(I.gaussian_field(n, cfg["delta_rms"], seed=cfg["seed"])).cuda()
+    Fu = torch.from_numpy(I.fermi_dirac(nu, V)).cuda()
+    if dtype == torch.float32:
+        f = torch.empty((n, n, n, nu, nu, nu), dtype=torch.float32, device="cuda")
+        for ix in range(n):
+            f[ix] = ((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None]).to(torch.float32)
+        return f, None
+    codes = torch.empty((n, n, n, nu, nu, nu), dtype=dtype, device="cuda")
+    scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device="cuda")
+    for ix in range(n):
+        c, s = B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], dtype)
+        codes[ix] = c
+        scale[ix] = s
+    return codes, scale
+
+
+def _line_index(shape, axis, rng, k):
+    """Index tensors selecting k whole lines along `axis` (the first and last line of the
+    axis among them): a tuple usable as f[idx] -> [k, shape[axis]]."""
+    pick = [rng.integers(0, shape[d], size=k) for d in range(6)]
+    for d in range(6):
+        pick[d][0], pick[d][1] = 0, shape[d] - 1
+    idx = []
+    for d in range(6):
+        if d == axis:
+            idx.append(torch.arange(shape[d], device="cuda")[None, :])
+        else:
+            idx.append(torch.from_numpy(pick[d]).cuda()[:, None])
+    return tuple(idx), pick
+
+
+def _values(f, scale, idx, axis):
+    """Sampled lines as FP64 host arrays (16-bit: decoded with their u_z line scales)."""
+    v = f[idx].to(torch.float64)
+    if scale is not None:
+        sidx = tuple(i for d, i in enumerate(idx) if d < 5)
+        s = scale[sidx].to(torch.float64)
+        v = v * (s if axis != 5 else s[:, :1])
+    return v.cpu().numpy()
+
+
+def _line_nu(g, cfg, axis, pick, dt, a, grad):
+    """Courant number of each sampled line: u_j dt / (a^2 dx) (position, Eq. 3) or
+    -g(x) dt / du (velocity, Eq. 4)."""
+    n, nu, V, L = cfg["n"], cfg["nu"], cfg["V"], 1.0
+    du = 2.0 * V / nu
+    if axis < 3:
+        u = -V + (pick[3 + axis] + 0.5) * du
+        return u * dt / (a * a * (L / n))
+    return -grad[axis - 3][pick[0], pick[1], pick[2]] * dt / du
+
+
+def _sweep_sampled(B, cfg, f, scale, phi, tol_l1, tol_linf, a=1.0, cfl=0.7, seed=0):
+    n, nu, V = cfg["n"], cfg["nu"], cfg["V"]
+    g = O.grid(n, nu, V=V)
+    phi64 = phi.astype(np.float64)
+    grad = [O.gradient(g, phi64, d) for d in range(3)]
+    v = B.Vlasov(f, V=V, scale=scale)
+    phit = torch.from_numpy(phi).cuda()
+    rng = np.random.default_rng(seed)
+    for axis in (3, 4, 5, 2, 1, 0):
+        dt = cfl / O.max_abs_nu(g, axis, 1.0, a, phi64)
+        idx, pick = _line_index(tuple(f.shape), axis, rng, K_LINES)
+        c_in = _values(f, scale, idx, axis)
+        v.sweep(axis, dt, a, phit)
+        v.status()
+        out = _values(f, scale, idx, axis)
+        nus = _line_nu(g, cfg, axis, pick, dt, a, grad)
+        ref = np.stack([O.sweep_line(c_in[i], float(nus[i]), periodic=axis < 3) for i in range(len(nus))])
+        err = np.abs(out - ref)
+        rl1 = err.sum() / np.abs(ref).sum()
+        rinf = err.max() / np.abs(ref).max()
+        print("axis %d: %d lines, max |nu| %.3f, rel L1 %.2e, rel Linf %.2e" %
+              (axis, len(nus), np.abs(nus).max(), rl1, rinf))
+        assert rl1 <= tol_l1 and rinf <= tol_linf, (axis, rl1, rinf)
+    v.close()
+
+
+@pytest.mark.parametrize("name", ["fp32_64x32", "large_48x48"])
+def test_fullsize_fp32_sweeps_sampled_lines(name):
+    B = _lib()
+    cfg = I.CONFIGS[name]
+    f, _ = _build_f(cfg, torch.float32)
+    phi = I.fourier_potential(cfg["n"], seed=cfg["seed"] + 10).astype(np.float32)
+    _sweep_sampled(B, cfg, f, None, phi, RTOL_L1, RTOL_LINF, seed=1)
+    del f
+    _free()
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_fullsize_16bit_sweeps_sampled_lines(fmt):
+    # the codec bounds of the 16-bit parity tests: relative L1 <= 2^-8 (BF16) / 2^-11
+    # (FP16) + 1e-6, L_inf <= 1.5 (2 x that) of the largest value
+    B = _lib()
+    cfg = I.CONFIGS["lowprec_96x32"]
+    bound = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[fmt]
+    codes, scale = _build_f(cfg, {"bf16": torch.bfloat16, "f16": torch.float16}[fmt])
+    phi = I.fourier_potential(cfg["n"], seed=cfg["seed"] + 10).astype(np.float32)
+    _sweep_sampled(B, cfg, codes, scale, phi, bound + 1e-6, 1.5 * (2 * bound + 1e-6), seed=2)
+    del codes, scale
+    _free()
+
+
+def test_fullsize_fp32_step_properties():
+    B = _lib()
+    cfg = I.CONFIGS["fp32_64x32"]
+    n, nu, V = cfg["n"], cfg["nu"], cfg["V"]
+    f, _ = _build_f(cfg, torch.float32)
+    phi = I.fourier_potential(n, seed=cfg["seed"] + 10).astype(np.float32)
+    g = O.grid(n, nu, V=V)
+    phi64 = phi.astype(np.float64)
+    a_half, a_full = 0.55, 0.6
+    dt = min([0.7 / O.max_abs_nu(g, ax, 1.0, a_half, phi64) for ax in (0, 1, 2)] +
+             [1.4 / O.max_abs_nu(g, ax, 1.0, a_full, phi64) for ax in (3, 4, 5)])
+    v = B.Vlasov(f, V=V)
+    rho0 = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    rho_step = torch.empty_like(rho0)
+    rho1 = torch.empty_like(rho0)
+    v.moment(rho0)
+    v.step(dt, a_half, a_full, torch.from_numpy(phi).cuda(), rho_nu=rho_step)
+    v.moment(rho1)
+    v.status()
+    m0, ms, m1 = (float(r.sum().item()) for r in (rho0, rho_step, rho1))
+    fmin = float(f.amin().item())
+    per_cell = float(((rho_step - rho1).abs() / rho1.abs()).max().item())
+    print("mass drift over a step %.2e, step moment vs final moment per cell %.2e, min f %.3e" %
+          ((m1 - m0) / m0, per_cell, fmin))
+    assert fmin >= 0.0
+    assert abs(m1 - m0) <= 9e-9 * abs(m0) and abs(ms - m0) <= 9e-9 * abs(m0)
+    # the second kick rounds every value (three sweeps of 2^-24) and the two moments differ
+    # by their summation (<= 10 units in the last place)
+    assert per_cell <= 2e-6
+    v.close()
+    del f
+    _free()
+
+
+def test_fullsize_adjoint_sweeps_sampled_lines():
+    # 32^3 x 16^3 FP32: lambda after each sweep adjoint, sampled lines against the oracle's
+    # line adjoint of the same f and lambda lines.  A face whose forward sits within FP32
+    # rounding of a limiter switch may take the other branch on the GPU; that changes
+    # lambda on a few cells of its own line only.  So per line: at most 1 % of the lines
+    # may differ by more than 1e-5 relative L1 (measured: up to 2 of 2048), and over the
+    # other lines the relative L1 must be <= 1e-6 (FP32 rounding; measured about 5e-8)
+    B = _lib()
+    cfg = I.CONFIGS["adjoint_32x16"]
+    n, nu, V = cfg["n"], cfg["nu"], cfg["V"]
+    f, _ = _build_f(cfg, torch.float32)
+    lam = torch.from_numpy(np.random.default_rng(3).standard_normal(tuple(f.shape)).astype(np.float32)).cuda()
+    phi = I.fourier_potential(n, seed=cfg["seed"] + 10).astype(np.float32)
+    g = O.grid(n, nu, V=V)
+    phi64 = phi.astype(np.float64)
+    grad = [O.gradient(g, phi64, d) for d in range(3)]
+    v = B.Vlasov(torch.empty_like(f), V=V)
+    phit = torch.from_numpy(phi).cuda()
+    rng = np.random.default_rng(4)
+    for axis in range(6):
+        dt = 0.7 / O.max_abs_nu(g, axis, 1.0, 1.0, phi64)
+        idx, pick = _line_index(tuple(f.shape), axis, rng, 8 * K_LINES)
+        c_in = _values(f, None, idx, axis)
+        l_in = _values(lam, None, idx, axis)
+        v.sweep_adjoint(f, lam, axis, dt, 1.0, phit, None)
+        v.status()
+        out = _values(lam, None, idx, axis)
+        nus = _line_nu(g, cfg, axis, pick, dt, 1.0, grad)
+        ref = np.stack([O.sweep_line_adjoint(c_in[i], l_in[i], float(nus[i]), periodic=axis < 3)[0]
+                        for i in range(len(nus))])
+        err = np.abs(out - ref)
+        line_l1 = err.sum(1) / np.abs(ref).sum(1)
+        flipped = line_l1 > 1e-5
+        rl1_rest = err[~flipped].sum() / np.abs(ref[~flipped]).sum()
+        print("axis %d adjoint: %d lines, %d off a branch, rel L1 over the rest %.2e" %
+              (axis, len(line_l1), np.count_nonzero(flipped), rl1_rest))
+        assert np.count_nonzero(flipped) <= 0.01 * len(line_l1) and rl1_rest <= 1e-6, (axis, rl1_rest)
+    v.close()
+    del f, lam
+    _free()
