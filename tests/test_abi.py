@@ -43,3 +43,20 @@ def test_init_rejects_bad_grids_without_touching_the_gpu():
     assert e.value.code == B.EINVAL
     with pytest.raises(B.VlasovError):
         B.vlasov_init(g, 0, None, 0)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("nz", 3), ("nuz", 0), ("nuy", 2), ("V", 0.0), ("L", -1.0),
+                                         ("dtype", 7)])
+def test_init_rejects_empty_and_degenerate_grids(field, value):
+    # an empty grid (a zero extent), lines too short for the five-cell stencil, a
+    # non-positive box or velocity bound and an unknown storage type are refused on the
+    # host with EINVAL, before any device call
+    from paper_2110_15867_gb300 import binding as B
+    B.load(build_if_missing=True)
+    g = B.Grid()
+    g.nx, g.ny, g.nz, g.nux, g.nuy, g.nuz = 8, 8, 8, 8, 8, 8
+    g.L, g.V, g.dtype = 1.0, 5.0, B.F32
+    setattr(g, field, value)
+    with pytest.raises(B.VlasovError) as e:
+        B.vlasov_init(g, 16, None, 0)
+    assert e.value.code == B.EINVAL
