@@ -102,11 +102,22 @@ int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *ph
  * = 16 or 32 run D_uy and D_uz in one pass over f: each u_z tile of 256 rows
  * holds whole (cell, j_x) planes, whose columns are the u_y lines, so D_uy runs
  * on the staged tile before D_uz (the arithmetic of the separate sweeps,
- * bit for bit).  On by default (11 % faster than the two sweeps at n_u = 32);
- * on = 0 runs them separately.  Other storage types and shapes always run the
- * sweeps separately.
+ * bit for bit; for BF16 / FP16 storage the D_uy result stays FP32 in shared
+ * memory and only D_uz's is encoded).  On by default (FP32: 11 % faster than the
+ * two sweeps at n_u = 32); on = 0 runs them separately.  FP64 storage and other
+ * shapes always run the sweeps separately.
  */
 int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
+
+/*
+ * One kick of Eq. (5): D_uz D_uy D_ux (dt), D_ux first, with the acceleration
+ * -grad phi (phi_dev: FP32 potential on the device, nx*ny*nz, as for
+ * vlasov_sweep).  vlasov_step runs it with dt/2 before and after the drift.  The
+ * u_y and u_z sweeps run as one pass where vlasov_set_fused_kick allows (FP32:
+ * the separate sweeps bit for bit; 16-bit storage: D_uy's result stays FP32 in
+ * shared memory and only D_uz's is encoded).  Same errors as vlasov_sweep.
+ */
+int vlasov_kick(vlasov_ctx *ctx, double dt, const float *phi_dev);
 
 /*
  * The moment rho_nu that vlasov_step and vlasov_step_record_sc take after the

@@ -46,7 +46,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
-           "vlasov_set_fused_moment")
+           "vlasov_set_fused_moment", "vlasov_kick")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -129,6 +129,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_set_fused_kick.restype = ctypes.c_int
     L.vlasov_set_fused_moment.argtypes = [_VP, ctypes.c_int]
     L.vlasov_set_fused_moment.restype = ctypes.c_int
+    L.vlasov_kick.argtypes = [_VP, ctypes.c_double, _VP]
+    L.vlasov_kick.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -365,6 +367,12 @@ class Vlasov:
         self._sync_stream()
         phi = self._field(phi, self.torch.float32)
         vlasov_sweep(self.ctx, ax, dt, a, _ptr(phi))
+
+    def kick(self, dt: float, phi):
+        """D_uz D_uy D_ux (dt) with the acceleration -grad phi (one kick of Eq. 5)."""
+        self._sync_stream()
+        phi = self._field(phi, self.torch.float32)
+        _check(self.ctx, load().vlasov_kick(self.ctx, dt, _ptr(phi)))
 
     def moment(self, rho=None, mass: bool = False):
         self._sync_stream()

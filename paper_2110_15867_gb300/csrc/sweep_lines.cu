@@ -13,12 +13,15 @@
 // the shared-memory transpose of sweep_contig.cu, the GPU analogue of the
 // paper's load-and-transpose (LAT, Sec. 4.3), for these line lengths.
 //
-// Fused kick tail (FUSE_Y, FP32, n_uy = n_uz): a tile of 256 rows is 256 / n_uy
+// Fused kick tail (FUSE_Y, n_uy = n_uz): a tile of 256 rows is 256 / n_uy
 // whole (cell, j_x) planes of n_uy rows (j_y) by n_uz columns (j_z), so the
 // u_y lines of the tile are its columns.  Before the u_z sweep each consumer
-// thread walks one packed pair of adjacent columns down a plane (D_uy, Eq. 4
-// for i = 2); the u_z sweep then reads the updated tile: D_uz D_uy in one pass
-// over f instead of two.
+// thread walks one column down a plane (D_uy, Eq. 4 for i = 2); the u_z sweep
+// then reads the updated tile: D_uz D_uy in one pass over f instead of two.
+// 16-bit storage: the columns are decoded with their rows' scales and the D_uy
+// result goes to an FP32 copy of the tile (same swizzled layout), from which the
+// u_z rows are read; only the D_uz result is encoded (one rounding per kick
+// tail instead of two).
 #include "vk_common.cuh"
 
 namespace vk {
@@ -338,6 +341,32 @@ __device__ __forceinline__ bool plane_column1(unsigned char *base, int tid, cons
     return !(sum >= 0.f) || isinf(sum);
 }
 
+// The same for 16-bit codes: lane l of warp w decodes column l % NU of the plane
+// at row 32w + (l / NU) NU (row 32w + i has the scale held by lane i), marches it
+// in FP32 and writes it to the FP32 tile copy `wide`.
+template <int NU, typename T, bool NEG>
+__device__ __forceinline__ bool plane_column1_coded(const unsigned char *base, unsigned char *wide, int tid,
+                                                   const Lim<float> &lim, float s_own)
+{
+    using GT = LineGeom<NU, T>;
+    using GF = LineGeom<NU, float>;
+    const int w = tid >> 5, l = tid & 31;
+    const int j0 = (l / NU) * NU, r_first = 32 * w + j0, c = l % NU;
+    float v[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        const float s = __shfl_sync(0xffffffffu, s_own, j0 + i);
+        const T code = *reinterpret_cast<const T *>(base + GT::off(r_first + i, c / GT::per) + (c % GT::per) * 2);
+        v[NEG ? NU - 1 - i : i] = float(code) * s;
+    }
+    const float sum = march_regs<NU, float>(v, lim);
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        *reinterpret_cast<float *>(wide + GF::off(r_first + i, c / GF::per) + (c % GF::per) * 4) =
+            v[NEG ? NU - 1 - i : i];
+    return !(sum >= 0.f) || isinf(sum);
+}
+
 template <int NU, typename T, bool FUSE_Y>
 __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
     line_sweep1_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
@@ -353,6 +382,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
     uint64_t *done = full + S;
     unsigned char *ring = smem + 128 + ((1024u - ((smem_u32(smem) + 128u) & 1023u)) & 1023u);
     auto slot = [&](unsigned e) { return ring + slot_bytes * (e % S); };
+    unsigned char *wide = ring + slot_bytes * S; // FP32 copy of a 16-bit tile after D_uy (fused only)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -409,12 +439,21 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
         }
         const long long row0 = (b + (long long)k * Gd) * kLineRows;
         unsigned char *base = slot(k);
+        // rows of a tile are whole planes of one spatial cell: tile-uniform
+        const float sc = CODED && row0 + r < args.rows ? args.scale[row0 + r] : 1.f;
+        bool from_wide = false; // 16-bit fused: the u_z rows come from the FP32 copy
         if constexpr (FUSE_Y) {
-            // every row of the tile belongs to one spatial cell
             const LineCoefT<float> ky = args.cell_coef_y[row0 / args.rows_per_cell];
             if (row0 < args.rows && ky.nd >= 0) {
-                const bool bad = (ky.nd & 1) ? plane_column1<NU, true>(base, r, to_lim(ky))
-                                             : plane_column1<NU, false>(base, r, to_lim(ky));
+                bool bad;
+                if constexpr (CODED) {
+                    bad = (ky.nd & 1) ? plane_column1_coded<NU, T, true>(base, wide, r, to_lim(ky), sc)
+                                      : plane_column1_coded<NU, T, false>(base, wide, r, to_lim(ky), sc);
+                    from_wide = true;
+                } else {
+                    bad = (ky.nd & 1) ? plane_column1<NU, true>(base, r, to_lim(ky))
+                                      : plane_column1<NU, false>(base, r, to_lim(ky));
+                }
                 if (bad) atomicOr(args.err, ERR_NAN);
             }
             __syncwarp();
@@ -423,15 +462,25 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
             const LineCoefT<float> kc = args.cell_coef[(row0 + r) / args.rows_per_cell];
             if (kc.nd >= 0) {
                 const bool neg = kc.nd & 1; // one orientation per spatial cell: warp-uniform
-                const float sc = CODED ? args.scale[row0 + r] : 1.f;
                 unsigned rng = CODED_RNG_INIT((unsigned long long)(row0 + r) * NU, args.seed);
                 float v[NU];
+                if (from_wide) {
+                    using GF = LineGeom<NU, float>;
 #pragma unroll
-                for (int j = 0; j < G_::chunks; ++j) {
-                    float a[PER];
-                    Chunk<T>::get(base + G_::off(r, j), sc, a);
+                    for (int j = 0; j < GF::chunks; ++j) {
+                        float a[4];
+                        Chunk<float>::get(wide + GF::off(r, j), 1.f, a);
 #pragma unroll
-                    for (int q = 0; q < PER; ++q) v[neg ? NU - 1 - (PER * j + q) : PER * j + q] = a[q];
+                        for (int q = 0; q < 4; ++q) v[neg ? NU - 1 - (4 * j + q) : 4 * j + q] = a[q];
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < G_::chunks; ++j) {
+                        float a[PER];
+                        Chunk<T>::get(base + G_::off(r, j), sc, a);
+#pragma unroll
+                        for (int q = 0; q < PER; ++q) v[neg ? NU - 1 - (PER * j + q) : PER * j + q] = a[q];
+                    }
                 }
                 const float sum = march_regs<NU, float>(v, to_lim(kc));
                 float inv = 1.f;
@@ -472,6 +521,11 @@ static bool line_single(int, bool) { return VK_LINE_SINGLE; }
 static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
 {
     if (line_single(dtype, fuse_y)) {
+        if (fuse_y && dtype == 2)
+            return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, true>
+                            : (const void *)line_sweep1_kernel<16, __nv_bfloat16, true>;
+        if (fuse_y && dtype == 3)
+            return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, true> : (const void *)line_sweep1_kernel<16, __half, true>;
         if (fuse_y) return nu == 32 ? (const void *)line_sweep1_kernel<32, float, true> : (const void *)line_sweep1_kernel<16, float, true>;
         if (dtype == 2) return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, false> : (const void *)line_sweep1_kernel<16, __nv_bfloat16, false>;
         if (dtype == 3) return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, false> : (const void *)line_sweep1_kernel<16, __half, false>;
@@ -481,7 +535,13 @@ static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
     return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
 }
 
-size_t line_sweep_smem(int nu, int es) { return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * es; }
+// the ring of tiles, plus the FP32 tile copy of the 16-bit fused pass
+size_t line_sweep_smem(int nu, int es, bool fuse_y)
+{
+    return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * es + (fuse_y && es == 2 ? (size_t)kLineRows * nu * 4 : 0);
+}
+
+bool line_sweep_fused_supported(int dtype) { return dtype == 1 || (VK_LINE_SINGLE && (dtype == 2 || dtype == 3)); }
 
 bool line_sweep_supported(int nu, long long rows_per_cell)
 {
@@ -491,9 +551,9 @@ bool line_sweep_supported(int nu, long long rows_per_cell)
 cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
                               int dtype, int grid, cudaStream_t st, bool fuse_y)
 {
-    if (fuse_y && (dtype != 1 || !a.cell_coef_y)) return cudaErrorInvalidValue;
+    if (fuse_y && (!line_sweep_fused_supported(dtype) || !a.cell_coef_y)) return cudaErrorInvalidValue;
     const void *k = line_kernel_for(nu, dtype, fuse_y);
-    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
+    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2, fuse_y);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<ContigArgs<float> *>(&a)};
@@ -504,7 +564,7 @@ cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
 int occupancy_line_sweep(int nu, int dtype, bool fuse_y)
 {
     const void *k = line_kernel_for(nu, dtype, fuse_y);
-    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2);
+    const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2, fuse_y);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
     const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;

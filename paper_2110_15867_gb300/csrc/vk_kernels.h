@@ -161,7 +161,8 @@ template <typename C> struct ContigArgs {
 // u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box
 // {n_uz, 256 rows} with the 64/128-byte swizzle
 bool line_sweep_supported(int nu, long long rows_per_cell);
-size_t line_sweep_smem(int nu, int es);
+size_t line_sweep_smem(int nu, int es, bool fuse_y = false);
+bool line_sweep_fused_supported(int dtype); // the fused kick tail for this storage type (1 f32, 2 bf16, 3 f16)
 int line_sweep_rows_per_tile();
 // fuse_y: D_uy on the tile's (cell, j_x) planes first (FP32, n_uy = n_uz)
 int occupancy_line_sweep(int nu, int dtype, bool fuse_y = false); // dtype: 1 f32, 2 bf16, 3 f16

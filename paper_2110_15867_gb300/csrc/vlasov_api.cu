@@ -355,7 +355,7 @@ static int plan_axes(vlasov_ctx *c)
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
         c->lgrid = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
     }
-    c->can_fuse_kick = c->use_lines && c->g.dtype == VLASOV_F32 && c->g.nuy == c->g.nuz;
+    c->can_fuse_kick = c->use_lines && line_sweep_fused_supported(c->g.dtype) && c->g.nuy == c->g.nuz;
     if (c->can_fuse_kick) {
         const int occ = occupancy_line_sweep(c->g.nuz, c->g.dtype, true);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "fused kick CTA does not fit");
@@ -825,6 +825,8 @@ static int run_kick_tail(vlasov_ctx *c)
     A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.err = c->d_err;
     A.cell_coef = (const LineCoefT<float> *)c->d_coef[2];
     A.cell_coef_y = (const LineCoefT<float> *)c->d_coef[1];
+    A.scale = c->scale;
+    A.seed = c->sweeps; // the stochastic-rounding stream of the D_uz encode (16-bit storage)
     PartTimer t(c, VLASOV_T_SWEEP_UYUZ, 1);
     const cudaError_t e = launch_line_sweep(c->lmap, c->lmap, A, c->g.nuz, c->g.dtype, c->lgrid_fused, c->stream, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused kick launch");
@@ -846,6 +848,14 @@ extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int on)
     if (!c) return VLASOV_EINVAL;
     c->fuse_kick = on != 0;
     return VLASOV_OK;
+}
+
+extern "C" int vlasov_kick(vlasov_ctx *c, double dt, const float *phi_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    int rc = prep_velocity(c, phi_dev, dt, 7);
+    if (rc) return rc;
+    return run_kick(c);
 }
 
 extern "C" int vlasov_set_fused_moment(vlasov_ctx *c, int on)
