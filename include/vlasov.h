@@ -189,6 +189,23 @@ int vlasov_upload(vlasov_ctx *ctx, const void *f_host);
 int vlasov_download(vlasov_ctx *ctx, void *f_host);
 
 /*
+ * One Eq. (5) step of a distribution function held in host memory: f_host is
+ * read, stepped and written back in place (the same result as vlasov_upload,
+ * vlasov_step, vlasov_download; the other arguments as for vlasov_step).  The
+ * velocity sweeps and D_z, D_y are local to planes of constant x, so f moves in
+ * up to 8 x-slabs on a second stream: each slab's first kick and D_z, D_y start
+ * as soon as it has arrived, and each slab goes back as soon as its second kick
+ * is done; only D_x, the moment and the Poisson solve wait for the whole grid.
+ * Without pinned host memory the copies do not overlap.  Falls back to the
+ * three calls in sequence for 16-bit storage, a whole-cell shift in D_z or D_y,
+ * or a grid whose tiles do not fall on x-planes.  f_host must stay valid until
+ * the context stream reaches the end of the step (vlasov_status synchronises).
+ */
+int vlasov_step_host(vlasov_ctx *ctx, void *f_host, double dt, double a_half, double a_full,
+                     const float *phi_n_dev, const double *rho_bg_dev, double four_pi_G, float *phi_next_dev,
+                     double *rho_nu_dev);
+
+/*
  * Per-part timers (the paper times each part of a step, Sec. 5.1).  While
  * enabled, every kernel the library queues is bracketed by two CUDA events on
  * the context stream.  vlasov_read_timers synchronises the stream and, for each

@@ -46,7 +46,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
-           "vlasov_set_fused_moment", "vlasov_kick")
+           "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -131,6 +131,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_set_fused_moment.restype = ctypes.c_int
     L.vlasov_kick.argtypes = [_VP, ctypes.c_double, _VP]
     L.vlasov_kick.restype = ctypes.c_int
+    L.vlasov_step_host.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                   ctypes.c_double, _VP, _VP]
+    L.vlasov_step_host.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -509,6 +512,19 @@ class Vlasov:
             raise ValueError("f_host must be a contiguous host tensor like f")
         self._sync_stream()
         vlasov_download(self.ctx, f_host.data_ptr())
+
+    def step_host(self, f_host, dt: float, a_half: float, a_full: float, phi_n, rho_bg=None,
+                  four_pi_G: float = 1.0, phi_next=None, rho_nu=None):
+        """One Eq. (5) step of the host tensor f_host (like f, ideally pinned), in place:
+        its x-slabs are copied in and out on a second stream behind the cell-local sweeps."""
+        if f_host.is_cuda or tuple(f_host.shape) != self.shape or f_host.dtype != self.f.dtype \
+                or not f_host.is_contiguous():
+            raise ValueError("f_host must be a contiguous host tensor like f")
+        self._sync_stream()
+        _check(self.ctx, load().vlasov_step_host(
+            self.ctx, f_host.data_ptr(), dt, a_half, a_full, _ptr(self._field(phi_n, self.torch.float32)),
+            _ptr(self._field(rho_bg, self.torch.float64)), four_pi_G,
+            _ptr(self._field(phi_next, self.torch.float32)), _ptr(self._field(rho_nu, self.torch.float64))))
 
     def set_adjoint_arrays(self, arrays: int):
         """f-sized scratch arrays step_adjoint may hold: 8, 4 or 0 (8 if they fit, else 4)."""

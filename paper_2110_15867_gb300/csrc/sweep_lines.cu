@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
         while (retired < n_my) {
             bool progress = false;
             while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
-                tma_store_2d(&dmap, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
+                tma_store_2d(&dmap, slot(retired), 0, int((args.tile0 + b + (long long)retired * Gd) * kLineRows));
                 bulk_commit();
                 ++retired;
                 progress = true;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
                 if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
                 const unsigned st = loaded % S;
                 mbar_arrive_expect_tx(&full[st], slot_bytes);
-                tma_load_2d(slot(loaded), &map, &full[st], 0, int((b + (long long)loaded * Gd) * kLineRows));
+                tma_load_2d(slot(loaded), &map, &full[st], 0, int((args.tile0 + b + (long long)loaded * Gd) * kLineRows));
                 ++loaded;
                 progress = true;
             }
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
             atomicOr(args.err, ERR_TIMEOUT);
             break;
         }
-        const long long row0 = (b + (long long)k * Gd) * kLineRows;
+        const long long row0 = (args.tile0 + b + (long long)k * Gd) * kLineRows;
         unsigned char *base = slot(k);
         if constexpr (FUSE_Y) {
             // every row of the tile belongs to one spatial cell
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
         while (retired < n_my) {
             bool progress = false;
             while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
-                tma_store_2d(&dmap, slot(retired), 0, int((b + (long long)retired * Gd) * kLineRows));
+                tma_store_2d(&dmap, slot(retired), 0, int((args.tile0 + b + (long long)retired * Gd) * kLineRows));
                 bulk_commit();
                 ++retired;
                 progress = true;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
                 if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
                 const unsigned st = loaded % S;
                 mbar_arrive_expect_tx(&full[st], slot_bytes);
-                tma_load_2d(slot(loaded), &map, &full[st], 0, int((b + (long long)loaded * Gd) * kLineRows));
+                tma_load_2d(slot(loaded), &map, &full[st], 0, int((args.tile0 + b + (long long)loaded * Gd) * kLineRows));
                 ++loaded;
                 progress = true;
             }
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
             atomicOr(args.err, ERR_TIMEOUT);
             break;
         }
-        const long long row0 = (b + (long long)k * Gd) * kLineRows;
+        const long long row0 = (args.tile0 + b + (long long)k * Gd) * kLineRows;
         unsigned char *base = slot(k);
         // rows of a tile are whole planes of one spatial cell: tile-uniform
         const float sc = CODED && row0 + r < args.rows ? args.scale[row0 + r] : 1.f;

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
                     break;
                 }
                 if (j == 0) {
-                    const long long t = b + k * G;
+                    const long long t = args.tile0 + b + k * G;
                     c0 = int((t % args.tiles_inner) * W);
                     c2 = int((t / args.tiles_inner) * P);
                 }
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
     };
 
     for (long long k = 0; k < n_my && alive; ++k) {
-        const long long t = b + k * G;
+        const long long t = args.tile0 + b + k * G;
         const long long inner = (t % args.tiles_inner) * W + w;
         const long long outer = (t / args.tiles_inner) * P + p;
         bool work = has_col && inner < args.n_inner && outer < args.n_outer;

@@ -102,6 +102,7 @@ template <typename C> struct StreamArgs {
     int perm_line; // > 0: group the threads by the sign of u along lines of this length
     long long n_inner, n_outer;
     long long num_blocks;
+    long long tile0; // first tile of this launch (num_blocks tiles from there)
     long long vstride;
     int nvel;
     int coef_mode;
@@ -156,6 +157,7 @@ template <typename C> struct ContigArgs {
     float *scale; // 16-bit storage: one FP32 scale per row (u_z line), updated in place
     unsigned seed;
     const LineCoefT<C> *cell_coef_y; // fused kick tail: the u_y sweep's per-cell constants
+    long long tile0;                 // first tile of this launch (num_tiles tiles from there)
 };
 
 // u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box

@@ -93,6 +93,8 @@ struct AxisPlan {
 
 } // namespace
 
+constexpr int kMaxSlabs = 8; // x-slabs of the pipelined host-buffer step
+
 struct vlasov_ctx {
     vlasov_grid g;
     GridDims gd;
@@ -133,6 +135,13 @@ struct vlasov_ctx {
     size_t part_len;
     void *d_mpart; // the moment fused into the x sweep: per-cell partial sums (storage type)
     bool fuse_moment;
+    // vlasov_step_host: sweeps restricted to the x-planes [slab_x0, slab_x1) (all if empty)
+    int slab_x0, slab_x1;
+    long long splan_tpp[5]; // tiles per x-plane of the streamed sweeps (0: a block spans planes)
+    long long ltpp;         // the same for the u_z line kernel
+    cudaStream_t copy_stream;
+    cudaEvent_t slab_ev[2 * kMaxSlabs + 2];
+    bool slab_ev_ok;
     int adj_arrays; // f-sized scratch arrays vlasov_step_adjoint may use: 8, 4 or 0 (8 if they fit, else 4)
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
@@ -337,6 +346,8 @@ static int plan_axes(vlasov_ctx *c)
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis %d: a streamed CTA does not fit (%zu B)", ax, p.smem);
         p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
         c->splan_R[ax] = R;
+        const long long opp = p.n_outer / c->g.nx; // outer lines per x-plane
+        c->splan_tpp[ax] = (p.n_outer % c->g.nx == 0 && opp % P == 0) ? (opp / P) * p.tiles_inner : 0;
     }
     // u_z: register lines when a line is 32, 64 or 128 bytes (FP32 / 16-bit, n_uz 16 or 32)
     c->use_lines = c->g.dtype != VLASOV_F64 && line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
@@ -354,6 +365,8 @@ static int plan_axes(vlasov_ctx *c)
         const int occ = occupancy_line_sweep(nu, c->g.dtype);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "u_z line sweep CTA does not fit");
         c->lgrid = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
+        const long long rpp = c->lrows / c->g.nx; // u_z rows per x-plane
+        c->ltpp = rpp % rpt == 0 ? rpp / rpt : 0;
     }
     c->can_fuse_kick = c->use_lines && line_sweep_fused_supported(c->g.dtype) && c->g.nuy == c->g.nuz;
     if (c->can_fuse_kick) {
@@ -379,6 +392,9 @@ static void free_scratch(vlasov_ctx *c)
     cudaFree(c->d_sc);
     cudaFree(c->d_part);
     cudaFree(c->d_mpart);
+    if (c->slab_ev_ok)
+        for (auto e : c->slab_ev) cudaEventDestroy(e);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -417,6 +433,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->ncell = ncell;
     c->fuse_kick = true; // see vlasov_set_fused_kick
     c->fuse_moment = true; // see vlasov_set_fused_moment
+    c->slab_x0 = c->slab_x1 = 0;
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
     c->gd.nu[0] = g->nux; c->gd.nu[1] = g->nuy; c->gd.nu[2] = g->nuz;
     c->gd.L = g->L;
@@ -472,6 +489,8 @@ extern "C" void vlasov_destroy(vlasov_ctx *c)
     for (auto e : c->pool) cudaEventDestroy(e);
     delete c;
 }
+
+static size_t f_bytes(const vlasov_ctx *c) { return (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es; }
 
 extern "C" int vlasov_upload(vlasov_ctx *c, const void *f_host)
 {
@@ -541,6 +560,12 @@ template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlaso
     A.L = p.L; A.W = p.W; A.P = p.P; A.R = c->splan_R[ax]; A.stages = p.stages;
     A.tiles_inner = p.tiles_inner; A.periodic = ax < 3; A.perm_line = c->perm_line[ax];
     A.n_inner = p.n_inner; A.n_outer = p.n_outer; A.num_blocks = p.num_tiles;
+    A.tile0 = 0;
+    if (c->slab_x1 > c->slab_x0) {
+        // the x-planes [slab_x0, slab_x1) are whole tiles (vlasov_step_host checks)
+        A.tile0 = c->slab_x0 * c->splan_tpp[ax];
+        A.num_blocks = (c->slab_x1 - c->slab_x0) * c->splan_tpp[ax];
+    }
     A.err = c->d_err;
     A.scale = c->scale;
     A.nuz = c->g.nuz;
@@ -565,13 +590,22 @@ static int sweep_maps(vlasov_ctx *c, const CUtensorMap &own, const MapSpec &spec
 }
 
 // streamed launch for the storage type of c (the arguments use FP32 constants unless FP64)
+// persistent grid of a streamed launch: no more CTAs than tiles
+static int stream_grid(const vlasov_ctx *c, int ax, long long tiles)
+{
+    const int g = c->splan[ax].grid;
+    return int(tiles < g ? tiles : g);
+}
+
 static cudaError_t launch_stream_any(const vlasov_ctx *c, int ax, const StreamArgs<float> &A, const SweepMaps &m)
 {
     const AxisPlan &sp = c->splan[ax];
+    const int grid = stream_grid(c, ax, A.num_blocks);
+    if (grid <= 0) return cudaSuccess;
     switch (c->g.dtype) {
-    case VLASOV_BF16: return launch_stream_bf16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
-    case VLASOV_F16: return launch_stream_f16(sp.map, c->smap[ax], A, sp.grid, sp.smem, c->stream);
-    default: return launch_stream_f32(m.in, m.out, A, sp.grid, sp.smem, c->stream);
+    case VLASOV_BF16: return launch_stream_bf16(sp.map, c->smap[ax], A, grid, sp.smem, c->stream);
+    case VLASOV_F16: return launch_stream_f16(sp.map, c->smap[ax], A, grid, sp.smem, c->stream);
+    default: return launch_stream_f32(m.in, m.out, A, grid, sp.smem, c->stream);
     }
 }
 
@@ -640,7 +674,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
             for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<double>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
             if (fm) { A.mpart = c->d_mpart; A.cube = cube; A.nparts = moment_parts(c); }
             PartTimer t(c, ax, 1);
-            e = launch_stream_f64(m.in, m.out, A, sp.grid, sp.smem, c->stream);
+            e = A.num_blocks > 0 ? launch_stream_f64(m.in, m.out, A, stream_grid(c, ax, A.num_blocks), sp.smem, c->stream) : cudaSuccess;
         } else {
             StreamArgs<float> A{};
             fill_stream_args(A, c, ax);
@@ -662,6 +696,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
         return VLASOV_OK;
     }
     if (coded(c)) return fail(c, VLASOV_EINVAL, "sweep %d: |nu| = %.3g >= 1 needs FP32 or FP64 storage", ax, numax);
+    if (c->slab_x1 > c->slab_x0) return fail(c, VLASOV_EINVAL, "sweep %d: a whole-cell shift cannot run on an x-slab", ax);
     if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;
     cudaError_t e;
     if (c->g.dtype == VLASOV_F64) {
@@ -687,6 +722,18 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
     return VLASOV_OK;
 }
 
+// the u_z line kernel's tiles of the current x-slab (all tiles when none is set)
+static void line_slab(const vlasov_ctx *c, ContigArgs<float> &A)
+{
+    A.tile0 = 0;
+    if (c->slab_x1 > c->slab_x0) {
+        A.tile0 = c->slab_x0 * c->ltpp;
+        A.num_tiles = (c->slab_x1 - c->slab_x0) * c->ltpp;
+    }
+}
+
+static int line_grid(const vlasov_ctx *, int grid, long long tiles) { return int(tiles < grid ? tiles : grid); }
+
 // velocity sweep from src to dst (NULL, NULL: c->f in place) with the per-cell
 // constants already in d_coef[ax - 3]
 static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *dst = nullptr)
@@ -710,7 +757,7 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
             fill_stream_args(A, c, ax);
             A.vstride = 1; A.nvel = 0; A.coef_mode = 1; A.outer_per_cell = opc;
             A.cell_coef = (const LineCoefT<double> *)coef;
-            e = launch_stream_f64(m.in, m.out, A, sp.grid, sp.smem, c->stream);
+            e = A.num_blocks > 0 ? launch_stream_f64(m.in, m.out, A, stream_grid(c, ax, A.num_blocks), sp.smem, c->stream) : cudaSuccess;
         } else {
             StreamArgs<float> A{};
             fill_stream_args(A, c, ax);
@@ -725,9 +772,12 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
         A.rows_per_cell = (long long)c->g.nux * c->g.nuy; A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
         A.scale = c->scale;
         A.seed = c->sweeps;
+        line_slab(c, A);
         PartTimer t(c, ax, 1);
-        e = launch_line_sweep(m.in, m.out, A, c->g.nuz, c->g.dtype, c->lgrid, c->stream);
+        e = A.num_tiles > 0 ? launch_line_sweep(m.in, m.out, A, c->g.nuz, c->g.dtype, line_grid(c, c->lgrid, A.num_tiles), c->stream)
+                            : cudaSuccess;
     } else {
+        if (c->slab_x1 > c->slab_x0) return fail(c, VLASOV_EINVAL, "u_z sweep: the transposing kernel cannot run on an x-slab");
         if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;
         const long long rpc = (long long)c->g.nux * c->g.nuy;
         PartTimer t(c, ax, 1);
@@ -827,8 +877,11 @@ static int run_kick_tail(vlasov_ctx *c)
     A.cell_coef_y = (const LineCoefT<float> *)c->d_coef[1];
     A.scale = c->scale;
     A.seed = c->sweeps; // the stochastic-rounding stream of the D_uz encode (16-bit storage)
+    line_slab(c, A);
+    if (A.num_tiles <= 0) return VLASOV_OK;
     PartTimer t(c, VLASOV_T_SWEEP_UYUZ, 1);
-    const cudaError_t e = launch_line_sweep(c->lmap, c->lmap, A, c->g.nuz, c->g.dtype, c->lgrid_fused, c->stream, true);
+    const cudaError_t e = launch_line_sweep(c->lmap, c->lmap, A, c->g.nuz, c->g.dtype,
+                                            line_grid(c, c->lgrid_fused, A.num_tiles), c->stream, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused kick launch");
     return VLASOV_OK;
 }
@@ -892,6 +945,114 @@ extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_ful
     return run_kick(c);
 }
 
+// ----------------------------------------------------------------------------
+// one step from and to a host buffer, transfers overlapped with the cell-local sweeps
+// ----------------------------------------------------------------------------
+// Largest |Courant number| of a position sweep (the streamed kernel needs < 1)
+static double position_numax(const vlasov_ctx *c, int ax, double dt, double a)
+{
+    const int nvel = (&c->g.nux)[ax];
+    const double du = 2.0 * c->g.V / nvel, dx = c->g.L / (&c->g.nx)[ax];
+    double m = 0.0;
+    for (int j = 0; j < nvel; ++j) m = fmax(m, fabs((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx)));
+    return m;
+}
+
+// x-slabs for the pipeline (0: the step cannot be split): every cell-local sweep
+// (the kicks, D_z, D_y) must run on whole tiles of each slab
+static int slab_count(const vlasov_ctx *c, double dt, double a_half)
+{
+    if (coded(c)) return 0; // the 16-bit encodes draw per-sweep random streams
+    const bool fused = c->can_fuse_kick && c->fuse_kick;
+    if (!c->use_lines || c->ltpp <= 0) return 0;
+    if (c->splan_tpp[3] <= 0 || (!fused && c->splan_tpp[4] <= 0)) return 0;
+    for (int ax = 1; ax <= 2; ++ax)
+        if (c->splan_tpp[ax] <= 0 || !(position_numax(c, ax, dt, a_half) < 1.0)) return 0;
+    for (int sl = kMaxSlabs; sl >= 2; --sl)
+        if (c->g.nx % sl == 0) return sl;
+    return 0;
+}
+
+extern "C" int vlasov_step_host(vlasov_ctx *c, void *f_host, double dt, double a_half, double a_full,
+                                const float *phi_n_dev, const double *rho_bg_dev, double four_pi_G,
+                                float *phi_next_dev, double *rho_nu_dev)
+{
+    if (!c) return VLASOV_EINVAL;
+    if (!f_host) return fail(c, VLASOV_EINVAL, "vlasov_step_host: null host buffer");
+    if (!phi_n_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_host: phi_n_dev is NULL");
+    if (!(a_half > 0) || !isfinite(dt) || !isfinite(a_half)) return fail(c, VLASOV_EINVAL, "vlasov_step_host: need finite dt and a_half > 0");
+    int rc;
+    const int S = slab_count(c, dt, a_half);
+    if (S == 0) {
+        // not splittable: the three calls in sequence
+        if ((rc = vlasov_upload(c, f_host))) return rc;
+        if ((rc = vlasov_step(c, dt, a_half, a_full, phi_n_dev, rho_bg_dev, four_pi_G, phi_next_dev, rho_nu_dev))) return rc;
+        return vlasov_download(c, f_host);
+    }
+    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->copy_stream = nullptr;
+        return fail(c, VLASOV_ECUDA, "vlasov_step_host: copy stream");
+    }
+    if (!c->slab_ev_ok) {
+        for (auto &e : c->slab_ev) VK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->slab_ev_ok = true;
+    }
+    cudaEvent_t *up = c->slab_ev, *ready = c->slab_ev + kMaxSlabs;
+    cudaEvent_t start = c->slab_ev[2 * kMaxSlabs], copied = c->slab_ev[2 * kMaxSlabs + 1];
+    const int planes = c->g.nx / S;
+    const size_t plane_bytes = f_bytes(c) / c->g.nx, slab_bytes = plane_bytes * planes;
+    unsigned char *fd = static_cast<unsigned char *>(c->f), *fh = static_cast<unsigned char *>(f_host);
+    auto on_slab = [&](int sl) { c->slab_x0 = sl * planes; c->slab_x1 = (sl + 1) * planes; };
+    auto all = [&]() { c->slab_x0 = c->slab_x1 = 0; };
+    struct Reset { // whatever way this function returns, later calls see the whole grid
+        vlasov_ctx *c;
+        ~Reset() { c->slab_x0 = c->slab_x1 = 0; }
+    } reset{c};
+    // the upload starts once earlier work on f (queued on the context's stream) is done
+    VK_CUDA(c, cudaEventRecord(start, c->stream));
+    VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, start, 0));
+    for (int sl = 0; sl < S; ++sl) {
+        VK_CUDA(c, cudaMemcpyAsync(fd + sl * slab_bytes, fh + sl * slab_bytes, slab_bytes, cudaMemcpyHostToDevice,
+                                   c->copy_stream));
+        VK_CUDA(c, cudaEventRecord(up[sl], c->copy_stream));
+    }
+    // first kick, D_z, D_y: cell-local, one slab at a time as its upload lands
+    if ((rc = prep_velocity(c, phi_n_dev, 0.5 * dt, 7))) return rc;
+    for (int sl = 0; sl < S && !rc; ++sl) {
+        VK_CUDA(c, cudaStreamWaitEvent(c->stream, up[sl], 0));
+        on_slab(sl);
+        if (!(rc = run_kick(c)) && !(rc = run_position(c, 2, dt, a_half))) rc = run_position(c, 1, dt, a_half);
+    }
+    all();
+    if (rc) return rc;
+    // D_x couples the slabs; it sums the moment when it can
+    double *rho = rho_nu_dev ? rho_nu_dev : c->d_rho;
+    const bool need_rho = rho_nu_dev || phi_next_dev;
+    bool have_rho = false;
+    if ((rc = run_position(c, 0, dt, a_half, nullptr, nullptr, need_rho ? rho : nullptr, &have_rho))) return rc;
+    if (need_rho && !have_rho && (rc = vlasov_moment(c, rho, nullptr))) return rc;
+    if (phi_next_dev) {
+        if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
+        if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
+    }
+    // second kick one slab at a time, each slab's download behind it
+    for (int sl = 0; sl < S && !rc; ++sl) {
+        on_slab(sl);
+        if (!(rc = run_kick(c))) {
+            VK_CUDA(c, cudaEventRecord(ready[sl], c->stream));
+            VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, ready[sl], 0));
+            VK_CUDA(c, cudaMemcpyAsync(fh + sl * slab_bytes, fd + sl * slab_bytes, slab_bytes, cudaMemcpyDeviceToHost,
+                                       c->copy_stream));
+        }
+    }
+    all();
+    if (rc) return rc;
+    // later work on the context's stream waits for the downloads
+    VK_CUDA(c, cudaEventRecord(copied, c->copy_stream));
+    VK_CUDA(c, cudaStreamWaitEvent(c->stream, copied, 0));
+    return VLASOV_OK;
+}
+
 extern "C" int vlasov_status(vlasov_ctx *c)
 {
     if (!c) return VLASOV_EINVAL;
@@ -910,7 +1071,6 @@ extern "C" const char *vlasov_last_error(const vlasov_ctx *c) { return c ? c->ms
 // ----------------------------------------------------------------------------
 // adjoint (reverse mode) of the sweeps and of the step
 // ----------------------------------------------------------------------------
-static size_t f_bytes(const vlasov_ctx *c) { return (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es; }
 
 static int ensure_buffer(vlasov_ctx *c, void **p, size_t bytes)
 {

@@ -1,0 +1,70 @@
+"""vlasov_step_host (one Eq. (5) step of a host buffer, its x-slabs copied in and out on a
+second stream behind the cell-local sweeps) against upload + vlasov_step + download: the
+same kernels on the same tiles, so the same f, rho and phi^{n+1} bit for bit, for a
+self-consistent step (Poisson between the kicks) with the fused kick tail and fused moment
+on and off, on 8 slabs of 2 x-planes and of 1 x-plane, and for a step that falls back to
+the three calls in sequence (a whole-cell shift in D_y / D_z)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_15867_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    from paper_2110_15867_gb300 import binding as B
+    B.load()
+    return B
+
+
+def _run(B, f0, phi0, bg, dt, a_half, host, fused):
+    V = 5.0
+    n = f0.shape[:3]
+    f = torch.from_numpy(f0).cuda()
+    v = B.Vlasov(f, V=V)
+    v.set_fused_kick(fused)
+    v.set_fused_moment(fused)
+    phi = torch.from_numpy(phi0).cuda()
+    phi1 = torch.empty_like(phi)
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    fh = torch.from_numpy(f0.copy()).pin_memory()
+    bgt = torch.from_numpy(bg).cuda()
+    f.zero_()  # the step must read the host buffer, not the device array
+    v.enable_timers(True)
+    if host:
+        v.step_host(fh, dt, a_half, 0.6, phi, rho_bg=bgt, phi_next=phi1, rho_nu=rho)
+    else:
+        v.upload(fh)
+        v.step(dt, a_half, 0.6, phi, rho_bg=bgt, phi_next=phi1, rho_nu=rho)
+        v.download(fh)
+    v.status()
+    _, launches = v.read_timers()
+    out = (fh.numpy().copy(), rho.cpu().numpy(), phi1.cpu().numpy())
+    v.close()
+    return out, launches["sweep_ux"]
+
+
+@pytest.mark.parametrize("n,nu,a_half", [((16, 8, 8), (16, 16, 16), 0.55), ((8, 4, 4), (32, 32, 32), 0.55),
+                                         ((16, 8, 8), (16, 16, 16), 0.12)])
+@pytest.mark.parametrize("fused", [True, False])
+def test_step_host_is_upload_step_download(n, nu, a_half, fused):
+    B = _lib()
+    V = 5.0
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=7), I.fermi_dirac(nu, V), np.float32)
+    phi0 = I.fourier_potential(n, seed=17).astype(np.float32)
+    bg = 3.0 * (1.0 + I.gaussian_field(n, 0.5, seed=8))
+    g = O.grid(n, nu, V=V)
+    p64 = phi0.astype(np.float64)
+    # CFL 0.7 for the kicks (dt / 2 each) and the drift at a = 0.55; a_half = 0.12 then
+    # makes D_x, D_y, D_z shift whole cells
+    dt = min([1.4 / O.max_abs_nu(g, ax, 1.0, 1.0, p64) for ax in (3, 4, 5)] +
+             [0.7 / O.max_abs_nu(g, ax, 1.0, 0.55, p64) for ax in (0, 1, 2)])
+    ref, _ = _run(B, f0, phi0, bg, dt, a_half, False, fused)
+    got, ux_launches = _run(B, f0, phi0, bg, dt, a_half, True, fused)
+    for r, o in zip(ref, got):
+        assert np.array_equal(r, o)
+    # 8 slabs: each kick's u_x sweep runs once per slab; the fallback runs it once
+    assert ux_launches == (2 if a_half < 0.5 else 16)
