@@ -656,8 +656,9 @@ __device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint
     }
 }
 
+// u_z rows of 8 or 16 cells: each thread loads its own row with 16-byte loads.
 template <typename T, int L>
-__global__ void __launch_bounds__(kAdjBlock, L <= 16 ? 3 : 2) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
+__global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
     constexpr int per = 16 / int(sizeof(T));
@@ -682,6 +683,80 @@ __global__ void __launch_bounds__(kAdjBlock, L <= 16 ? 3 : 2) adjoint_rows_kerne
             dnu = (kc.nd & 1) ? -dLds : dLds;
         }
         cell = a.dLdg ? t / a.lines_per_cell : -1;
+    }
+    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
+}
+
+// u_z rows of 32 cells: a warp's 32 rows are 32 L contiguous elements; it stages
+// them (f and lambda) through shared memory with coalesced 16-byte loads, rows
+// padded by one 16-byte chunk so that each lane then reads its own row without
+// bank conflicts, marches it in registers and the warp writes the rows back the
+// same way (the per-thread 16-byte loads of 128-byte rows are not coalesced).
+template <int L> constexpr int rows_pitch() { return L + 4; } // FP32 elements per staged row
+template <int L> constexpr size_t rows_smem() { return size_t(kAdjBlock) * rows_pitch<L>() * 4 * 2; }
+
+template <typename T, int L>
+__global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_staged_kernel(const __grid_constant__ AdjArgs<T> a)
+{
+    static_assert(sizeof(T) == 4, "rows of FP32 storage");
+    using C = T;
+    constexpr int P = rows_pitch<L>(), CH = L / 4; // chunks of 4 per row
+    extern __shared__ __align__(16) unsigned char rows_smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *sf = reinterpret_cast<T *>(rows_smem_raw) + w * 32 * P;
+    T *sl = sf + kAdjBlock * P;
+    const long long r0 = blockIdx.x * (long long)kAdjBlock + 32 * w; // the warp's first row
+    const long long t = r0 + lane;
+    const int nrows = a.nlines - r0 >= 32 ? 32 : (a.nlines > r0 ? int(a.nlines - r0) : 0);
+    const uint4 *gf = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.f_in) + r0 * L);
+    const uint4 *gl = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.lam_in) + r0 * L);
+    uint4 *go = reinterpret_cast<uint4 *>(static_cast<T *>(a.lam_out) + r0 * L);
+#pragma unroll
+    for (int k = lane; k < 32 * CH; k += 32) {
+        const int row = k / CH, col = 4 * (k % CH);
+        if (row < nrows) {
+            *reinterpret_cast<uint4 *>(sf + row * P + col) = __ldg(gf + k);
+            *reinterpret_cast<uint4 *>(sl + row * P + col) = __ldg(gl + k);
+        }
+    }
+    __syncwarp();
+    long long cell = -1;
+    C dnu = C(0);
+    if (lane < nrows) {
+        const LineCoefT<C> kc = a.cell_coef[t / a.outer_per_cell];
+        if (kc.nd >= 0 && (kc.nd >> 1) == 0) {
+            const AdjLim<C> lim = make_adj_lim(kc);
+            C dLds, osum;
+            const bool neg = kc.nd & 1;
+            auto run = [&](auto negc) {
+                constexpr bool NEG = decltype(negc)::value;
+                RegLine<T, L, NEG> acc;
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const float4 u = *reinterpret_cast<const float4 *>(sf + lane * P + 4 * q);
+                    const float4 v = *reinterpret_cast<const float4 *>(sl + lane * P + 4 * q);
+                    acc.cv[4 * q] = u.x; acc.cv[4 * q + 1] = u.y; acc.cv[4 * q + 2] = u.z; acc.cv[4 * q + 3] = u.w;
+                    acc.lv[4 * q] = v.x; acc.lv[4 * q + 1] = v.y; acc.lv[4 * q + 2] = v.z; acc.lv[4 * q + 3] = v.w;
+                }
+                march_adjoint<false, L, T>(acc, lim, L, dLds, osum);
+#pragma unroll
+                for (int q = 0; q < CH; ++q)
+                    *reinterpret_cast<float4 *>(sl + lane * P + 4 * q) =
+                        make_float4(acc.lv[4 * q], acc.lv[4 * q + 1], acc.lv[4 * q + 2], acc.lv[4 * q + 3]);
+            };
+            if (neg) run(std::true_type{});
+            else run(std::false_type{});
+            if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
+            dnu = neg ? -dLds : dLds;
+        }
+        cell = a.dLdg ? t / a.lines_per_cell : -1;
+    }
+    __syncwarp();
+    // lambda rows out (rows left unchanged by the forward pass through as loaded)
+#pragma unroll
+    for (int k = lane; k < 32 * CH; k += 32) {
+        const int row = k / CH, col = 4 * (k % CH);
+        if (row < nrows) go[k] = *reinterpret_cast<const uint4 *>(sl + row * P + col);
     }
     if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
@@ -719,6 +794,19 @@ __global__ void gradient_adjoint_kernel(GridDims g, const double *__restrict__ d
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
+template <typename T, int L> static cudaError_t launch_rows(const AdjArgs<T> &a, dim3 grid, cudaStream_t st)
+{
+    if constexpr (L <= 16) {
+        adjoint_rows_kernel<T, L><<<grid, kAdjBlock, 0, st>>>(a);
+    } else {
+        const cudaError_t e = cudaFuncSetAttribute(adjoint_rows_staged_kernel<T, L>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(rows_smem<L>()));
+        if (e != cudaSuccess) return e;
+        adjoint_rows_staged_kernel<T, L><<<grid, kAdjBlock, rows_smem<L>(), st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool rows, cudaStream_t st)
 {
     const long long blocks = (a.nlines + kAdjBlock - 1) / kAdjBlock;
@@ -729,9 +817,9 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool 
         // FP32 only: a row of 32 doubles (twice, with lambda) would not stay in registers
         if constexpr (!std::is_same<T, float>::value) return cudaErrorInvalidValue;
         else switch (a.L) {
-        case 8: adjoint_rows_kernel<T, 8><<<grid, kAdjBlock, 0, st>>>(a); break;
-        case 16: adjoint_rows_kernel<T, 16><<<grid, kAdjBlock, 0, st>>>(a); break;
-        case 32: adjoint_rows_kernel<T, 32><<<grid, kAdjBlock, 0, st>>>(a); break;
+        case 8: return launch_rows<T, 8>(a, grid, st);
+        case 16: return launch_rows<T, 16>(a, grid, st);
+        case 32: return launch_rows<T, 32>(a, grid, st);
         default: return cudaErrorInvalidValue;
         }
     } else if (a.periodic && a.L == 4) {
