@@ -500,31 +500,80 @@ __global__ void poisson_load_kernel(long long n, const double *__restrict__ rho,
         z[i] = make_double2(rho[i] + (bg ? bg[i] : 0.0), 0.0);
 }
 
-// DFT along dimension d: out[.., k, ..] = sum_m in[.., m, ..] e^{sign 2 pi i k m / n_d}
-__global__ void dft_axis_kernel(GridDims g, int d, int sign, const double2 *__restrict__ in, double2 *out,
-                                const double2 *__restrict__ tw)
+// DFT along dimension d: out[.., k, ..] = sum_m in[.., m, ..] e^{sign 2 pi i k m / n_d},
+// factored once (Cooley-Tukey) as n = n1 n2 with m = n2 m1 + m2 and k = k1 + n1 k2:
+//   Y[k1][m2] = W_n^{m2 k1} sum_{m1} x[n2 m1 + m2] W_{n1}^{m1 k1},
+//   X[k1 + n1 k2] = sum_{m2} Y[k1][m2] W_{n2}^{m2 k2},
+// n (n1 + n2 + 1) complex products per line instead of n^2 (n1 = 1 for a prime n: the
+// plain sum).  W_{n1} = W_n^{n2}, W_{n2} = W_n^{n1}: one twiddle table per axis.  A
+// block holds `lines` lines of the axis in shared memory, n threads per line.
+__global__ void __launch_bounds__(256) dft_axis_kernel(GridDims g, int d, int sign, int n1, int lines,
+                                                       const double2 *__restrict__ in, double2 *out,
+                                                       const double2 *__restrict__ tw)
 {
-    const long long n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const long long total = n0 * n1 * n2;
-    const long long st[3] = {n1 * n2, n2, 1};
-    const int nd = g.n[d];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long id[3] = {i / st[0], (i / st[1]) % n1, i % n2};
-        const int k = int(id[d]);
-        const long long base = i - id[d] * st[d];
-        double sr = 0.0, si = 0.0;
-        int q = 0; // (k m) mod nd
-        for (int m = 0; m < nd; ++m) {
-            const double2 x = in[base + m * st[d]];
-            const double2 w = tw[q];
-            const double wi = sign * w.y;
-            sr += x.x * w.x - x.y * wi;
-            si += x.x * wi + x.y * w.x;
-            q += k;
-            if (q >= nd) q -= nd;
+    extern __shared__ double2 dft_smem[];
+    const long long n0 = g.n[0], nn1 = g.n[1], nn2 = g.n[2];
+    const long long st[3] = {nn1 * nn2, nn2, 1};
+    const int n = g.n[d], n2 = n / n1;
+    const long long nlines = n0 * nn1 * nn2 / n;
+    // the other two dimensions of a line, in memory order
+    const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+    const long long nb = g.n[db];
+    const int li = threadIdx.x / n, k = threadIdx.x % n; // this thread: line li of the block, index k
+    double2 *x = dft_smem + li * n, *y = dft_smem + lines * n + li * n;
+    for (long long l0 = blockIdx.x * (long long)lines; l0 < nlines; l0 += (long long)gridDim.x * lines) {
+        const long long line = l0 + li;
+        const bool act = li < lines && line < nlines;
+        long long base = 0;
+        if (act) {
+            base = (line / nb) * st[da] + (line % nb) * st[db];
+            x[k] = in[base + k * st[d]];
         }
-        out[i] = make_double2(sr, si);
+        __syncthreads();
+        if (act) {
+            // stage 1 for (k1, m2) = (k / n2, k % n2)
+            const int k1 = k / n2, m2 = k % n2;
+            double sr = 0.0, si = 0.0;
+            int q = 0; // (n2 m1 k1) mod n
+            for (int m1 = 0; m1 < n1; ++m1) {
+                const double2 v = x[n2 * m1 + m2], w = tw[q];
+                const double wi = sign * w.y;
+                sr += v.x * w.x - v.y * wi;
+                si += v.x * wi + v.y * w.x;
+                q += n2 * k1; // < n
+                if (q >= n) q -= n;
+            }
+            const double2 w = tw[(m2 * k1) % n];
+            const double wi = sign * w.y;
+            y[k] = make_double2(sr * w.x - si * wi, sr * wi + si * w.x); // Y[k1][m2] at k1 n2 + m2
+        }
+        __syncthreads();
+        if (act) {
+            // stage 2 for output k = k1 + n1 k2
+            const int k1 = k % n1, k2 = k / n1;
+            double sr = 0.0, si = 0.0;
+            int q = 0; // (n1 m2 k2) mod n
+            for (int m2 = 0; m2 < n2; ++m2) {
+                const double2 v = y[k1 * n2 + m2], w = tw[q];
+                const double wi = sign * w.y;
+                sr += v.x * w.x - v.y * wi;
+                si += v.x * wi + v.y * w.x;
+                q += n1 * k2; // < n
+                if (q >= n) q -= n;
+            }
+            out[base + k * st[d]] = make_double2(sr, si);
+        }
+        __syncthreads();
     }
+}
+
+// the factor n1 of n used by dft_axis_kernel: its largest divisor <= sqrt(n)
+static int dft_n1(int n)
+{
+    int best = 1;
+    for (int f = 2; f * f <= n; ++f)
+        if (n % f == 0) best = f;
+    return best;
 }
 
 __global__ void poisson_scale_kernel(GridDims g, double2 *z, double fac)
@@ -563,15 +612,18 @@ cudaError_t launch_poisson(const GridDims &g, const PoissonScratch &ps, const do
     const int blocks = int((n + threads - 1) / threads < 8192 ? (n + threads - 1) / threads : 8192);
     poisson_load_kernel<<<blocks, threads, 0, st>>>(n, rho, bg, ps.z0);
     double2 *a0 = ps.z0, *a1 = ps.z1;
-    for (int d = 2; d >= 0; --d) {
-        dft_axis_kernel<<<blocks, threads, 0, st>>>(g, d, -1, a0, a1, ps.tw[d]);
+    auto dft = [&](int d, int sign) {
+        const int nd = g.n[d], lines = 256 / nd; // nd <= 256
+        const long long nlines = n / nd;
+        const long long nb = (nlines + lines - 1) / lines;
+        const int grid = int(nb < 8192 ? nb : 8192);
+        dft_axis_kernel<<<grid, lines * nd, 2 * lines * nd * sizeof(double2), st>>>(g, d, sign, dft_n1(nd), lines, a0,
+                                                                                   a1, ps.tw[d]);
         double2 *t = a0; a0 = a1; a1 = t;
-    }
+    };
+    for (int d = 2; d >= 0; --d) dft(d, -1);
     poisson_scale_kernel<<<blocks, threads, 0, st>>>(g, a0, four_pi_G * a * a);
-    for (int d = 0; d < 3; ++d) {
-        dft_axis_kernel<<<blocks, threads, 0, st>>>(g, d, +1, a0, a1, ps.tw[d]);
-        double2 *t = a0; a0 = a1; a1 = t;
-    }
+    for (int d = 0; d < 3; ++d) dft(d, +1);
     poisson_store_kernel<<<blocks, threads, 0, st>>>(n, a0, phi, phi64);
     return cudaGetLastError();
 }

@@ -187,9 +187,11 @@ def test_moment_and_mass(dtype):
     v.close()
 
 
-def test_poisson_matches_oracle():
+@pytest.mark.parametrize("n", [(16, 12, 10), (7, 11, 13), (64, 48, 96)])
+def test_poisson_matches_oracle(n):
+    # composite extents run the factored DFT (16 = 4 x 4, 12 = 3 x 4, 10 = 2 x 5, 64 = 8 x 8,
+    # 48 = 6 x 8, 96 = 8 x 12), prime ones the plain sum
     B = _lib()
-    n = (16, 12, 10)
     f0, _ = _setup(n, (4, 4, 4))
     g = O.grid(n, (4, 4, 4))
     rho = 5.0 + I.gaussian_field(n, 1.0, seed=9)
