@@ -281,15 +281,16 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
 // ----------------------------------------------------------------------------
 // A moment warp sums every released chunk's rows (4 rows x W values, all in one
 // spatial cell's velocity cube) while the producer stores the chunk: a lane adds
-// its 32 bytes of a row pairwise, then the warp adds the lanes pairwise in a fixed
+// its two 16-byte chunks of a row pairwise, then the warp adds the lanes pairwise in a fixed
 // order (FP32 storage: FP32, at most 8 roundings deep; FP64: FP64).  The first two
 // levels halve the rows each lane holds, the last three add within groups of 8
 // lanes, so lane l ends with the total of row l >> 3.  The producer reloads a slot
 // only after the moment warp has summed it.
 __device__ __forceinline__ float lane_row_sum(const float *row, int lane)
 {
-    const float4 *q = reinterpret_cast<const float4 *>(row) + 2 * lane;
-    const float4 a = q[0], b = q[1];
+    // 16-byte chunks lane and lane + 32: each quarter warp reads 128 contiguous bytes
+    const float4 *q = reinterpret_cast<const float4 *>(row);
+    const float4 a = q[lane], b = q[lane + 32];
     return ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
 }
 __device__ __forceinline__ float lane_row_sum(const F32Single *row, int lane)
@@ -298,8 +299,8 @@ __device__ __forceinline__ float lane_row_sum(const F32Single *row, int lane)
 }
 __device__ __forceinline__ double lane_row_sum(const double *row, int lane)
 {
-    const double2 *q = reinterpret_cast<const double2 *>(row) + 2 * lane;
-    const double2 a = q[0], b = q[1];
+    const double2 *q = reinterpret_cast<const double2 *>(row);
+    const double2 a = q[lane], b = q[lane + 32];
     return (a.x + a.y) + (b.x + b.y);
 }
 template <typename T> __device__ __forceinline__ float lane_row_sum(const T *, int) { return 0.f; }
