@@ -507,6 +507,63 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
     }
 }
 
+// ----------------------------------------------------------------------------
+// strided zero-flux lines in registers (u_x, u_y)
+// ----------------------------------------------------------------------------
+// Thread t owns line t: outer = t / n_inner, inner = t % n_inner, cell i of the line
+// at (outer L + i) n_inner + inner.  Neighbouring threads own neighbouring columns,
+// so each of the L loads (and stores) of a warp is one coalesced 128-byte segment;
+// all loads are issued before the march.  A negative Courant number reverses the
+// register order (the march always flows toward +index).
+template <int L>
+__global__ void __launch_bounds__(256, 3) reg_lines_kernel(const float *__restrict__ src, float *dst,
+                                                          const __grid_constant__ RegLineArgs a)
+{
+    const long long t = a.line0 + blockIdx.x * 256ll + threadIdx.x;
+    if (t >= a.line0 + a.nlines) return;
+    const long long outer = t / a.n_inner, inner = t - outer * a.n_inner;
+    const long long base = outer * L * a.n_inner + inner;
+    const LineCoefT<float> kc = a.cell_coef[outer / a.outer_per_cell];
+    const float *p = src + base;
+    float *q = dst + base;
+    if (kc.nd < 0) {
+        // Courant number out of range (flagged by the constants kernel): unchanged
+        if (q != p)
+#pragma unroll
+            for (int i = 0; i < L; ++i) q[i * a.n_inner] = p[i * a.n_inner];
+        return;
+    }
+    const bool neg = kc.nd & 1; // one orientation per spatial cell
+    float v[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = __ldg(p + i * a.n_inner);
+    if (neg) {
+#pragma unroll
+        for (int i = 0; i < L / 2; ++i) { const float t0 = v[i]; v[i] = v[L - 1 - i]; v[L - 1 - i] = t0; }
+    }
+    const float sum = march_regs<L, float>(v, to_lim(kc));
+    if (neg) {
+#pragma unroll
+        for (int i = 0; i < L / 2; ++i) { const float t0 = v[i]; v[i] = v[L - 1 - i]; v[L - 1 - i] = t0; }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) q[i * a.n_inner] = v[i];
+    if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
+}
+
+bool reg_lines_supported(int L) { return L == 16 || L == 32; }
+
+cudaError_t launch_reg_lines(const float *src, float *dst, const RegLineArgs &a, cudaStream_t st)
+{
+    if (a.nlines <= 0) return cudaSuccess;
+    const long long blocks = (a.nlines + 255) / 256;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (a.L == 32) reg_lines_kernel<32><<<unsigned(blocks), 256, 0, st>>>(src, dst, a);
+    else if (a.L == 16) reg_lines_kernel<16><<<unsigned(blocks), 256, 0, st>>>(src, dst, a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 #ifndef VK_LINE_SINGLE
 #define VK_LINE_SINGLE 1 // 1: u_z lines one row per thread (0: two rows as a packed pair)
 #endif

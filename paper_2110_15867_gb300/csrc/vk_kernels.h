@@ -180,6 +180,18 @@ cudaError_t launch_contig_f32(const CUtensorMap &map, const CUtensorMap &dmap, c
 cudaError_t launch_contig_f64(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<double> &a, int grid,
                               size_t smem, cudaStream_t st);
 // largest resident CTAs per SM for a launcher's kernel with this dynamic smem
+// Zero-flux velocity lines of L = 16 or 32 FP32 cells strided by n_inner (u_x, u_y):
+// one line per thread, loaded whole into registers (coalesced along the contiguous
+// axis), marched, stored.  Lines [line0, line0 + nlines) of f viewed as
+// [n_outer][L][n_inner]; constants per spatial cell (cell = outer / outer_per_cell).
+struct RegLineArgs {
+    int L;
+    long long n_inner, n_outer, line0, nlines, outer_per_cell;
+    const LineCoefT<float> *cell_coef;
+    unsigned *err;
+};
+bool reg_lines_supported(int L);
+cudaError_t launch_reg_lines(const float *src, float *dst, const RegLineArgs &a, cudaStream_t st);
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
 cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,

@@ -94,6 +94,9 @@ struct AxisPlan {
 } // namespace
 
 constexpr int kMaxSlabs = 8; // x-slabs of the pipelined host-buffer step
+#ifndef VK_REG_LINES
+#define VK_REG_LINES 1 // FP32 u_x / u_y sweeps of 16 or 32 cells: whole lines in registers (0: streamed)
+#endif
 
 struct vlasov_ctx {
     vlasov_grid g;
@@ -734,6 +737,12 @@ static void line_slab(const vlasov_ctx *c, ContigArgs<float> &A)
 
 static int line_grid(const vlasov_ctx *, int grid, long long tiles) { return int(tiles < grid ? tiles : grid); }
 
+// u_x / u_y on FP32 storage with lines of 16 or 32 cells: the register-line kernel
+static bool use_reg_lines(const vlasov_ctx *c, int ax)
+{
+    return VK_REG_LINES && c->g.dtype == VLASOV_F32 && (ax == 3 || ax == 4) && reg_lines_supported((&c->g.nux)[ax - 3]);
+}
+
 // velocity sweep from src to dst (NULL, NULL: c->f in place) with the per-cell
 // constants already in d_coef[ax - 3]
 static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *dst = nullptr)
@@ -747,7 +756,20 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
     SweepMaps m;
     int rc;
     cudaError_t e;
-    if (ax < 5) {
+    if (ax < 5 && use_reg_lines(c, ax)) {
+        const AxisPlan &sp = c->splan[ax];
+        RegLineArgs A{};
+        A.L = sp.L; A.n_inner = sp.n_inner; A.n_outer = sp.n_outer; A.outer_per_cell = sp.n_outer / c->ncell;
+        A.cell_coef = (const LineCoefT<float> *)coef; A.err = c->d_err;
+        A.line0 = 0; A.nlines = sp.n_outer * sp.n_inner;
+        if (c->slab_x1 > c->slab_x0) {
+            const long long lpp = sp.n_outer / c->g.nx * sp.n_inner; // lines per x-plane
+            A.line0 = c->slab_x0 * lpp;
+            A.nlines = (c->slab_x1 - c->slab_x0) * lpp;
+        }
+        PartTimer t(c, ax, 1);
+        e = launch_reg_lines(static_cast<const float *>(src), static_cast<float *>(dst), A, c->stream);
+    } else if (ax < 5) {
         const AxisPlan &sp = c->splan[ax];
         if (!coded(c) && (rc = sweep_maps(c, sp.map, sp.spec, src, dst, m))) return rc;
         const long long opc = sp.n_outer / c->ncell;
@@ -965,7 +987,8 @@ static int slab_count(const vlasov_ctx *c, double dt, double a_half)
     if (coded(c)) return 0; // the 16-bit encodes draw per-sweep random streams
     const bool fused = c->can_fuse_kick && c->fuse_kick;
     if (!c->use_lines || c->ltpp <= 0) return 0;
-    if (c->splan_tpp[3] <= 0 || (!fused && c->splan_tpp[4] <= 0)) return 0;
+    if ((!use_reg_lines(c, 3) && c->splan_tpp[3] <= 0) || (!fused && !use_reg_lines(c, 4) && c->splan_tpp[4] <= 0))
+        return 0;
     for (int ax = 1; ax <= 2; ++ax)
         if (c->splan_tpp[ax] <= 0 || !(position_numax(c, ax, dt, a_half) < 1.0)) return 0;
     for (int sl = kMaxSlabs; sl >= 2; --sl)
