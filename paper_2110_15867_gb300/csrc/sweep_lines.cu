@@ -512,20 +512,44 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
 // ----------------------------------------------------------------------------
 // Thread t owns line t: outer = t / n_inner, inner = t % n_inner, cell i of the line
 // at (outer L + i) n_inner + inner.  Neighbouring threads own neighbouring columns,
-// so each of the L loads (and stores) of a warp is one coalesced 128-byte segment;
-// all loads are issued before the march.  A negative Courant number reverses the
-// register order (the march always flows toward +index).
-template <int L>
-__global__ void __launch_bounds__(256, 3) reg_lines_kernel(const float *__restrict__ src, float *dst,
+// so each of the L loads (and stores) of a warp is one coalesced segment; all loads
+// are issued before the march.  A negative Courant number reverses the register
+// order (the march always flows toward +index).  16-bit codes: cell i decodes with
+// the scale of its u_z line (line0 + i Iz, Iz = n_inner / nuz u_z lines per row of
+// the swept axis), which the sweep keeps, and encodes back with stochastic rounding.
+template <typename T> struct RegCodec;
+template <> struct RegCodec<float> {
+    __device__ static float get(float c, float) { return c; }
+    __device__ static float put(float v, float, unsigned) { return v; }
+};
+template <> struct RegCodec<__nv_bfloat16> {
+    __device__ static float get(__nv_bfloat16 c, float s) { return __bfloat162float(c) * s; }
+    __device__ static __nv_bfloat16 put(float v, float inv, unsigned r16)
+    {
+        const unsigned b = (__float_as_uint(v * inv) + r16) >> 16; // stochastic rounding (v >= 0)
+        return __ushort_as_bfloat16((unsigned short)b);
+    }
+};
+template <> struct RegCodec<__half> {
+    __device__ static float get(__half c, float s) { return __half2float(c) * s; }
+    __device__ static __half put(float v, float inv, unsigned r16)
+    {
+        return __float2half_rz(__uint_as_float(__float_as_uint(v * inv) + (r16 & 0x1fffu)));
+    }
+};
+
+template <int L, typename T>
+__global__ void __launch_bounds__(256, 3) reg_lines_kernel(const T *__restrict__ src, T *dst,
                                                           const __grid_constant__ RegLineArgs a)
 {
+    constexpr bool CODED = sizeof(T) == 2;
     const long long t = a.line0 + blockIdx.x * 256ll + threadIdx.x;
     if (t >= a.line0 + a.nlines) return;
     const long long outer = t / a.n_inner, inner = t - outer * a.n_inner;
     const long long base = outer * L * a.n_inner + inner;
     const LineCoefT<float> kc = a.cell_coef[outer / a.outer_per_cell];
-    const float *p = src + base;
-    float *q = dst + base;
+    const T *p = src + base;
+    T *q = dst + base;
     if (kc.nd < 0) {
         // Courant number out of range (flagged by the constants kernel): unchanged
         if (q != p)
@@ -533,10 +557,12 @@ __global__ void __launch_bounds__(256, 3) reg_lines_kernel(const float *__restri
             for (int i = 0; i < L; ++i) q[i * a.n_inner] = p[i * a.n_inner];
         return;
     }
+    // 16-bit: the u_z line of cell i is zl + i Iz
+    const long long Iz = CODED ? a.n_inner / a.nuz : 0, zl = CODED ? outer * L * Iz + inner / a.nuz : 0;
     const bool neg = kc.nd & 1; // one orientation per spatial cell
     float v[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) v[i] = __ldg(p + i * a.n_inner);
+    for (int i = 0; i < L; ++i) v[i] = RegCodec<T>::get(p[i * a.n_inner], CODED ? __ldg(a.scale + zl + i * Iz) : 1.f);
     if (neg) {
 #pragma unroll
         for (int i = 0; i < L / 2; ++i) { const float t0 = v[i]; v[i] = v[L - 1 - i]; v[L - 1 - i] = t0; }
@@ -546,22 +572,45 @@ __global__ void __launch_bounds__(256, 3) reg_lines_kernel(const float *__restri
 #pragma unroll
         for (int i = 0; i < L / 2; ++i) { const float t0 = v[i]; v[i] = v[L - 1 - i]; v[L - 1 - i] = t0; }
     }
+    unsigned rng = CODED ? sr_bits((unsigned long long)base, a.seed) : 0u;
 #pragma unroll
-    for (int i = 0; i < L; ++i) q[i * a.n_inner] = v[i];
+    for (int i = 0; i < L; ++i) {
+        float inv = 1.f;
+        unsigned r = 0u;
+        if (CODED) {
+            const float s = __ldg(a.scale + zl + i * Iz);
+            inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+            r = lcg_next(rng) >> 16;
+        }
+        q[i * a.n_inner] = RegCodec<T>::put(v[i], inv, r);
+    }
     if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
 }
 
 bool reg_lines_supported(int L) { return L == 16 || L == 32; }
 
-cudaError_t launch_reg_lines(const float *src, float *dst, const RegLineArgs &a, cudaStream_t st)
+template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst, const RegLineArgs &a, unsigned blocks,
+                                                      cudaStream_t st)
+{
+    const T *s = static_cast<const T *>(src);
+    T *d = static_cast<T *>(dst);
+    if (a.L == 32) reg_lines_kernel<32, T><<<blocks, 256, 0, st>>>(s, d, a);
+    else if (a.L == 16) reg_lines_kernel<16, T><<<blocks, 256, 0, st>>>(s, d, a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, int dtype, cudaStream_t st)
 {
     if (a.nlines <= 0) return cudaSuccess;
     const long long blocks = (a.nlines + 255) / 256;
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
-    if (a.L == 32) reg_lines_kernel<32><<<unsigned(blocks), 256, 0, st>>>(src, dst, a);
-    else if (a.L == 16) reg_lines_kernel<16><<<unsigned(blocks), 256, 0, st>>>(src, dst, a);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    switch (dtype) {
+    case 1: return launch_reg_t<float>(src, dst, a, unsigned(blocks), st);
+    case 2: return launch_reg_t<__nv_bfloat16>(src, dst, a, unsigned(blocks), st);
+    case 3: return launch_reg_t<__half>(src, dst, a, unsigned(blocks), st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 #ifndef VK_LINE_SINGLE

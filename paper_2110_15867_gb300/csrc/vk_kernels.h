@@ -184,14 +184,20 @@ cudaError_t launch_contig_f64(const CUtensorMap &map, const CUtensorMap &dmap, c
 // one line per thread, loaded whole into registers (coalesced along the contiguous
 // axis), marched, stored.  Lines [line0, line0 + nlines) of f viewed as
 // [n_outer][L][n_inner]; constants per spatial cell (cell = outer / outer_per_cell).
+// 16-bit storage: element e's value is code * scale[e / nuz] (its u_z line), and the
+// line's codes are re-encoded with stochastic rounding (stream seeded per line and sweep).
 struct RegLineArgs {
     int L;
     long long n_inner, n_outer, line0, nlines, outer_per_cell;
     const LineCoefT<float> *cell_coef;
     unsigned *err;
+    const float *scale; // 16-bit storage only
+    int nuz;
+    unsigned seed;
 };
 bool reg_lines_supported(int L);
-cudaError_t launch_reg_lines(const float *src, float *dst, const RegLineArgs &a, cudaStream_t st);
+// dtype: 1 f32, 2 bf16, 3 f16
+cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, int dtype, cudaStream_t st);
 int occupancy_strided(int dtype, int periodic, size_t smem);
 int occupancy_contig(int dtype, size_t smem);
 cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,

@@ -737,10 +737,10 @@ static void line_slab(const vlasov_ctx *c, ContigArgs<float> &A)
 
 static int line_grid(const vlasov_ctx *, int grid, long long tiles) { return int(tiles < grid ? tiles : grid); }
 
-// u_x / u_y on FP32 storage with lines of 16 or 32 cells: the register-line kernel
+// u_x / u_y on FP32 or 16-bit storage with lines of 16 or 32 cells: the register-line kernel
 static bool use_reg_lines(const vlasov_ctx *c, int ax)
 {
-    return VK_REG_LINES && c->g.dtype == VLASOV_F32 && (ax == 3 || ax == 4) && reg_lines_supported((&c->g.nux)[ax - 3]);
+    return VK_REG_LINES && c->g.dtype != VLASOV_F64 && (ax == 3 || ax == 4) && reg_lines_supported((&c->g.nux)[ax - 3]);
 }
 
 // velocity sweep from src to dst (NULL, NULL: c->f in place) with the per-cell
@@ -767,8 +767,9 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
             A.line0 = c->slab_x0 * lpp;
             A.nlines = (c->slab_x1 - c->slab_x0) * lpp;
         }
+        A.scale = c->scale; A.nuz = int(c->g.nuz); A.seed = c->sweeps;
         PartTimer t(c, ax, 1);
-        e = launch_reg_lines(static_cast<const float *>(src), static_cast<float *>(dst), A, c->stream);
+        e = launch_reg_lines(src, dst, A, c->g.dtype, c->stream);
     } else if (ax < 5) {
         const AxisPlan &sp = c->splan[ax];
         if (!coded(c) && (rc = sweep_maps(c, sp.map, sp.spec, src, dst, m))) return rc;
