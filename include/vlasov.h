@@ -193,7 +193,7 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
  * read, stepped and written back in place (the same result as vlasov_upload,
  * vlasov_step, vlasov_download; the other arguments as for vlasov_step).  The
  * velocity sweeps and D_z, D_y are local to planes of constant x, so f moves in
- * up to 8 x-slabs on a second stream: each slab's first kick and D_z, D_y start
+ * up to 16 x-slabs on a second stream: each slab's first kick and D_z, D_y start
  * as soon as it has arrived, and each slab goes back as soon as its second kick
  * is done; only D_x, the moment and the Poisson solve wait for the whole grid.
  * Without pinned host memory the copies do not overlap.  Falls back to the

@@ -93,7 +93,7 @@ struct AxisPlan {
 
 } // namespace
 
-constexpr int kMaxSlabs = 8; // x-slabs of the pipelined host-buffer step
+constexpr int kMaxSlabs = 16; // x-slabs of the pipelined host-buffer step
 #ifndef VK_REG_LINES
 #define VK_REG_LINES 1 // FP32 u_x / u_y sweeps of 16 or 32 cells: whole lines in registers (0: streamed)
 #endif
