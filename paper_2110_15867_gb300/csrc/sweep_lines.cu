@@ -1,17 +1,20 @@
-// sweep_lines.cu -- SL-MPP5 sweep along the contiguous axis u_z with whole
-// lines in registers (FP32, n_uz = 16 or 32).
+// sweep_lines.cu -- SL-MPP5 sweeps with whole lines in registers: u_z lines of
+// n_uz = 16 or 32 cells (FP32, BF16, FP16), the fused kick tail, and strided
+// u_x / u_y lines of 16 or 32 cells.
 //
 // Eq. (4) for i = 3 (Yoshikawa, Tanaka & Yoshida, SC'21).  A u_z line is one
 // row of n_uz contiguous cells, 64 or 128 bytes.  TMA loads a box of 256 rows
 // with the 64-/128-byte hardware swizzle: 16-byte chunk j of row r lands at
 // chunk j ^ ((r * rowbytes >> 7) & (rowbytes / 16 - 1)), so eight threads that
 // each read a 16-byte chunk of eight consecutive rows hit eight different bank
-// groups.  Each consumer thread owns rows t and t + 128 of the tile as one
-// packed FP32 pair, pulls both lines into registers, marches them fully
+// groups.  In the default kernel (line_sweep1_kernel) each of 256 consumer
+// threads owns one row of the tile, pulls it into registers, marches it fully
 // unrolled (the orientation is a warp-uniform branch: all 256 rows of a tile
-// share a spatial cell), and writes them back for the TMA store.  This replaces
-// the shared-memory transpose of sweep_contig.cu, the GPU analogue of the
-// paper's load-and-transpose (LAT, Sec. 4.3), for these line lengths.
+// share a spatial cell), and writes it back for the TMA store; the older kernel
+// (line_sweep_kernel, VK_LINE_SINGLE=0) holds rows t and t + 128 as one packed
+// FP32 pair.  This replaces the shared-memory transpose of sweep_contig.cu, the
+// GPU analogue of the paper's load-and-transpose (LAT, Sec. 4.3), for these
+// line lengths.
 //
 // Fused kick tail (FUSE_Y, n_uy = n_uz): a tile of 256 rows is 256 / n_uy
 // whole (cell, j_x) planes of n_uy rows (j_y) by n_uz columns (j_z), so the

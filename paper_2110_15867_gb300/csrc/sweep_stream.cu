@@ -1,5 +1,6 @@
-// sweep_stream.cu -- SL-MPP5 sweeps along a strided axis (x, y, z, u_x, u_y),
-// lines streamed through shared memory in chunks of rows.
+// sweep_stream.cu -- SL-MPP5 sweeps along a strided axis (x, y, z; u_x, u_y when
+// their lines are not marched in registers), lines streamed through shared
+// memory in chunks of rows; the x sweep can also sum the velocity moment.
 //
 // Eq. (3) (position advection, periodic) and Eq. (4) (velocity advection,
 // zero-flux faces) of Yoshikawa, Tanaka & Yoshida, SC'21, for Courant numbers
