@@ -139,16 +139,24 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C++ source without comments and blank lines: edits to comments keep the hash."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash(kind):
-    """Hash of the sources `kind`'s kernel is built from (None for an unknown kind)."""
+    """Hash of the code of the sources `kind`'s kernel is built from (None for an unknown kind)."""
     if kind not in KERNEL_SOURCES:
         return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_15867_gb300", "csrc")
     for fn in sorted(KERNEL_SOURCES[kind] + _COMMON_SOURCES):
-        with open(os.path.join(csrc, fn), "rb") as fh:
+        with open(os.path.join(csrc, fn), encoding="utf-8") as fh:
             h.update(fn.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
