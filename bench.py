@@ -274,6 +274,18 @@ def cpu_baseline(min_seconds=10.0):
                       % (k, SAMPLE["n"], SAMPLE["nu"], t)}
 
 
+def workload_config(world):
+    """The `config` object of both arms' JSON line: the 64^3 x 32^3 workload."""
+    w = WORKLOAD
+    n, nu = w["n"], w["nu"]
+    cells = n ** 3 * nu ** 3
+    return {"workload": "%s: %d^3 x %d^3 cells FP32, self-consistent Eq. (5) steps "
+                        "(9 SL-MPP5 sweeps + moment + Poisson)" % (w["name"], n, nu),
+            "cells": cells, "bytes_f": int(cells * 4),
+            "l2": "inputs larger than L2 (34.4 GB f vs 129 MB L2)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -288,9 +300,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "%s sampled: %d^3 x %d^3 cells per step" % (WORKLOAD["name"], SAMPLE["n"], SAMPLE["nu"])},
+            "config": workload_config(world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": "FP64 oracle Eq. (5) steps on an %d^3 x %d^3 sample" % (SAMPLE["n"], SAMPLE["nu"])},
+                             "sample": "each step: the FP64 oracle's Eq. (5) step on an %d^3 x %d^3 sample of the "
+                                       "workload (same velocity cube, dt scaled to the sample's dx)"
+                                       % (SAMPLE["n"], SAMPLE["nu"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -656,11 +670,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s: %d^3 x %d^3 cells FP32, self-consistent Eq. (5) steps "
-                                   "(9 SL-MPP5 sweeps + moment + Poisson)" % (w["name"], n, nu),
-                       "cells": cells, "bytes_f": int(f.numel() * 4),
-                       "l2": "inputs larger than L2 (34.4 GB f vs 129 MB L2)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(world),
             "roofline": roofline,
             "kernels": per_kind,
             "cpu_baseline": cpu,
