@@ -20,7 +20,7 @@ def _lib():
     return B
 
 
-def _run(B, f0, phi0, bg, dt, a_half, host, fused):
+def _run(B, f0, phi0, bg, dt, a_half, host, fused, dtype=np.float32):
     V = 5.0
     n = f0.shape[:3]
     f = torch.from_numpy(f0).cuda()
@@ -68,3 +68,23 @@ def test_step_host_is_upload_step_download(n, nu, a_half, fused):
         assert np.array_equal(r, o)
     # up to 16 slabs (one per x-plane here): each kick runs u_x once per slab; the fallback once
     assert ux_launches == (2 if a_half < 0.5 else 2 * min(16, n[0]))
+
+
+def test_step_host_fp64_falls_back_to_the_three_calls():
+    # FP64 storage has no line kernel to split per slab: the same result as upload + step
+    # + download, through the sequential path
+    B = _lib()
+    V = 5.0
+    n, nu = (8, 8, 8), (8, 8, 8)
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=9), I.fermi_dirac(nu, V), np.float64)
+    phi0 = I.fourier_potential(n, seed=19).astype(np.float32)
+    bg = 3.0 * (1.0 + I.gaussian_field(n, 0.5, seed=10))
+    g = O.grid(n, nu, V=V)
+    p64 = phi0.astype(np.float64)
+    dt = min([1.4 / O.max_abs_nu(g, ax, 1.0, 1.0, p64) for ax in (3, 4, 5)] +
+             [0.7 / O.max_abs_nu(g, ax, 1.0, 0.55, p64) for ax in (0, 1, 2)])
+    ref, _ = _run(B, f0, phi0, bg, dt, 0.55, False, True)
+    got, ux_launches = _run(B, f0, phi0, bg, dt, 0.55, True, True)
+    for r, o in zip(ref, got):
+        assert np.array_equal(r, o)
+    assert ux_launches == 2
