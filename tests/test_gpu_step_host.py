@@ -20,7 +20,7 @@ def _lib():
     return B
 
 
-def _run(B, f0, phi0, bg, dt, a_half, host, fused, dtype=np.float32):
+def _run(B, f0, phi0, bg, dt, a_half, host, fused):
     V = 5.0
     n = f0.shape[:3]
     f = torch.from_numpy(f0).cuda()
