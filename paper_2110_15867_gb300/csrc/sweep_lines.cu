@@ -70,7 +70,7 @@ template <> struct Chunk<__nv_bfloat16> {
     {
         unsigned w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = pack_bf16x2(o[2 * q] * inv, o[2 * q + 1] * inv, sr_pair(rng));
+        for (int q = 0; q < 4; ++q) w[q] = sr_pack_bf16x2(o[2 * q] * inv, o[2 * q + 1] * inv, rng);
         *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 };
@@ -90,7 +90,7 @@ template <> struct Chunk<__half> {
     {
         unsigned w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = pack_f16x2(o[2 * q] * inv, o[2 * q + 1] * inv, sr_pair(rng));
+        for (int q = 0; q < 4; ++q) w[q] = sr_pack_f16x2(o[2 * q] * inv, o[2 * q + 1] * inv, rng);
         *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 };

@@ -68,7 +68,7 @@ template <> struct Lane<__nv_bfloat16> {
     {
         const float s = *sp;
         const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
-        *reinterpret_cast<unsigned *>(p) = pack_bf16x2(v.x * inv, v.y * inv, sr_pair(rng));
+        *reinterpret_cast<unsigned *>(p) = sr_pack_bf16x2(v.x * inv, v.y * inv, rng);
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };
@@ -85,7 +85,7 @@ template <> struct Lane<__half> {
     {
         const float s = *sp;
         const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
-        *reinterpret_cast<unsigned *>(p) = pack_f16x2(v.x * inv, v.y * inv, sr_pair(rng));
+        *reinterpret_cast<unsigned *>(p) = sr_pack_f16x2(v.x * inv, v.y * inv, rng);
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };

@@ -252,13 +252,6 @@ __device__ __forceinline__ unsigned lcg_next(unsigned &x)
     return x;
 }
 
-// 16 random bits in the lower half for the first value, 16 in the upper half for the second
-__device__ __forceinline__ unsigned sr_pair(unsigned &x)
-{
-    const unsigned a = lcg_next(x) >> 16;
-    const unsigned b = lcg_next(x) & 0xffff0000u;
-    return a | b;
-}
 
 // two non-negative FP32 values -> packed bf16x2; rnd supplies 16 random bits per value
 __device__ __forceinline__ unsigned pack_bf16x2(float x, float y, unsigned rnd)
@@ -273,6 +266,18 @@ __device__ __forceinline__ unsigned pack_bf16x2(float x, float y, unsigned rnd)
 #endif
 }
 
+// The same from the stream directly: the upper 16 bits of two LCG steps, added below the
+// BF16 mantissa of x and of y; one byte permute packs the two upper halves.
+__device__ __forceinline__ unsigned sr_pack_bf16x2(float x, float y, unsigned &rng)
+{
+#if VK_SR
+    const unsigned r1 = lcg_next(rng) >> 16, r2 = lcg_next(rng) >> 16;
+    return __byte_perm(__float_as_uint(x) + r1, __float_as_uint(y) + r2, 0x7632);
+#else
+    return pack_bf16x2(x, y, 0u);
+#endif
+}
+
 // two non-negative FP32 values -> packed f16x2 (13 random bits below the FP16 mantissa)
 __device__ __forceinline__ unsigned pack_f16x2(float x, float y, unsigned rnd)
 {
@@ -284,6 +289,21 @@ __device__ __forceinline__ unsigned pack_f16x2(float x, float y, unsigned rnd)
     const __half2 h = __floats2half2_rn(x, y);
 #endif
     return *reinterpret_cast<const unsigned *>(&h);
+}
+
+// The same from the stream directly (13 of the upper 16 bits of two LCG steps); one
+// round-toward-zero conversion packs both (x in the lower half).
+__device__ __forceinline__ unsigned sr_pack_f16x2(float x, float y, unsigned &rng)
+{
+#if VK_SR
+    const unsigned r1 = (lcg_next(rng) >> 16) & 0x1fffu, r2 = (lcg_next(rng) >> 16) & 0x1fffu;
+    const float xr = __uint_as_float(__float_as_uint(x) + r1), yr = __uint_as_float(__float_as_uint(y) + r2);
+    unsigned out;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yr), "f"(xr));
+    return out;
+#else
+    return pack_f16x2(x, y, 0u);
+#endif
 }
 
 // ----------------------------------------------------------------------------
