@@ -616,6 +616,86 @@ cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, i
     }
 }
 
+// ----------------------------------------------------------------------------
+// u_z rows staged per warp (other line lengths)
+// ----------------------------------------------------------------------------
+template <int NU> constexpr int rows_pitch() { return NU + 4; } // padded row (floats): conflict-free row reads
+template <int NU> constexpr size_t rows_sweep_smem() { return size_t(256) * rows_pitch<NU>() * 4; }
+
+template <int NU>
+__global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const float *__restrict__ src, float *dst,
+                                                           const __grid_constant__ RowsArgs a)
+{
+    constexpr int P = rows_pitch<NU>(), CH = NU / 4;
+    extern __shared__ __align__(16) float rows_sw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sr = rows_sw + w * 32 * P;
+    const long long r0 = a.row0 + (blockIdx.x * 8ll + w) * 32; // the warp's first row
+    const long long left = a.row0 + a.nrows - r0;
+    const int nrows = left >= 32 ? 32 : (left > 0 ? int(left) : 0);
+    const float4 *g = reinterpret_cast<const float4 *>(src + r0 * NU);
+    float4 *o = reinterpret_cast<float4 *>(dst + r0 * NU);
+#pragma unroll
+    for (int k = lane; k < 32 * CH; k += 32) {
+        const int row = k / CH, col = 4 * (k % CH);
+        if (row < nrows) *reinterpret_cast<float4 *>(sr + row * P + col) = __ldg(g + k);
+    }
+    __syncwarp();
+    if (lane < nrows) {
+        const LineCoefT<float> kc = a.cell_coef[(r0 + lane) / a.rows_per_cell];
+        if (kc.nd >= 0) {
+            const bool neg = kc.nd & 1; // one orientation per spatial cell
+            float v[NU];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const float4 u = *reinterpret_cast<const float4 *>(sr + lane * P + 4 * q);
+                const float e[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[neg ? NU - 1 - (4 * q + j) : 4 * q + j] = e[j];
+            }
+            const float sum = march_regs<NU, float>(v, to_lim(kc));
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                float e[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) e[j] = v[neg ? NU - 1 - (4 * q + j) : 4 * q + j];
+                *reinterpret_cast<float4 *>(sr + lane * P + 4 * q) = make_float4(e[0], e[1], e[2], e[3]);
+            }
+            if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = lane; k < 32 * CH; k += 32) {
+        const int row = k / CH, col = 4 * (k % CH);
+        if (row < nrows) o[k] = *reinterpret_cast<const float4 *>(sr + row * P + col);
+    }
+}
+
+bool rows_sweep_supported(int L, int dtype) { return dtype == 1 && (L == 24 || L == 40 || L == 48); }
+
+template <int NU> static cudaError_t launch_rows_t(const float *src, float *dst, const RowsArgs &a, cudaStream_t st)
+{
+    const long long blocks = (a.nrows + 255) / 256;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaFuncSetAttribute(rows_sweep_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(rows_sweep_smem<NU>()));
+    if (e != cudaSuccess) return e;
+    rows_sweep_kernel<NU><<<unsigned(blocks), 256, rows_sweep_smem<NU>(), st>>>(src, dst, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_sweep(const float *src, float *dst, const RowsArgs &a, cudaStream_t st)
+{
+    if (a.nrows <= 0) return cudaSuccess;
+    switch (a.L) {
+    case 24: return launch_rows_t<24>(src, dst, a, st);
+    case 40: return launch_rows_t<40>(src, dst, a, st);
+    case 48: return launch_rows_t<48>(src, dst, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 #ifndef VK_LINE_SINGLE
 #define VK_LINE_SINGLE 1 // 1: u_z lines one row per thread (0: two rows as a packed pair)
 #endif

@@ -195,6 +195,18 @@ struct RegLineArgs {
     int nuz;
     unsigned seed;
 };
+// u_z lines (rows of n_uz contiguous FP32 cells) of lengths the TMA line kernel does not
+// take (n_uz = 24, 40, 48): each warp stages 32 rows through shared memory with coalesced
+// 16-byte loads (padded pitch), each lane marches its row in registers, and the warp
+// writes the rows back the same way.  Rows [row0, row0 + nrows).
+struct RowsArgs {
+    int L;
+    long long row0, nrows, rows_per_cell;
+    const LineCoefT<float> *cell_coef;
+    unsigned *err;
+};
+bool rows_sweep_supported(int L, int dtype);
+cudaError_t launch_rows_sweep(const float *src, float *dst, const RowsArgs &a, cudaStream_t st);
 bool reg_lines_supported(int L);
 // dtype: 1 f32, 2 bf16, 3 f16
 cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, int dtype, cudaStream_t st);

@@ -799,6 +799,21 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
         PartTimer t(c, ax, 1);
         e = A.num_tiles > 0 ? launch_line_sweep(m.in, m.out, A, c->g.nuz, c->g.dtype, line_grid(c, c->lgrid, A.num_tiles), c->stream)
                             : cudaSuccess;
+    } else if (rows_sweep_supported(int(c->g.nuz), c->g.dtype)) {
+        RowsArgs A{};
+        A.L = int(c->g.nuz);
+        A.rows_per_cell = (long long)c->g.nux * c->g.nuy;
+        A.row0 = 0;
+        A.nrows = c->ncell * A.rows_per_cell;
+        if (c->slab_x1 > c->slab_x0) {
+            const long long rpp = A.nrows / c->g.nx; // rows per x-plane
+            A.row0 = c->slab_x0 * rpp;
+            A.nrows = (c->slab_x1 - c->slab_x0) * rpp;
+        }
+        A.cell_coef = (const LineCoefT<float> *)coef;
+        A.err = c->d_err;
+        PartTimer t(c, ax, 1);
+        e = launch_rows_sweep(static_cast<const float *>(src), static_cast<float *>(dst), A, c->stream);
     } else {
         if (c->slab_x1 > c->slab_x0) return fail(c, VLASOV_EINVAL, "u_z sweep: the transposing kernel cannot run on an x-slab");
         if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;
@@ -987,7 +1002,8 @@ static int slab_count(const vlasov_ctx *c, double dt, double a_half)
 {
     if (coded(c)) return 0; // the 16-bit encodes draw per-sweep random streams
     const bool fused = c->can_fuse_kick && c->fuse_kick;
-    if (!c->use_lines || c->ltpp <= 0) return 0;
+    const bool rows = rows_sweep_supported(int(c->g.nuz), c->g.dtype);
+    if (!rows && (!c->use_lines || c->ltpp <= 0)) return 0;
     if ((!use_reg_lines(c, 3) && c->splan_tpp[3] <= 0) || (!fused && !use_reg_lines(c, 4) && c->splan_tpp[4] <= 0))
         return 0;
     for (int ax = 1; ax <= 2; ++ax)

@@ -52,6 +52,8 @@ def _compare(gpu, ref, l1=RTOL_L1, linf=RTOL_LINF):
 SHAPES = [
     ((16, 16, 16), (16, 16, 16)),   # the 16^3 x 16^3 parity workload
     ((6, 5, 7), (8, 20, 12)),       # ragged: no tile size divides the extents
+    ((5, 5, 7), (4, 12, 24)),       # u_z rows of 24 staged per warp; the last warp holds 16 rows
+    ((4, 4, 4), (8, 8, 48)),        # u_z rows of 48 (the 48^3 velocity grid's line length)
 ]
 
 
