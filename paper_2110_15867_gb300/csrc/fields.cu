@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(256) moment_coded_kernel(GridDims g, const T *
     const long long cube = lines * nuz;
     const double du3 = (2.0 * g.V / g.nu[0]) * (2.0 * g.V / g.nu[1]) * (2.0 * g.V / g.nu[2]);
     __shared__ double part[8];
-    const int vshift = nuz == 32 ? 2 : 1; // log2 of the 16-byte vectors per line (n_uz 16 or 32)
+    // 16-byte vectors per line: 2 or 4 (n_uz 16 or 32, a shift), else 3, 5 or 6 (n_uz 24, 40, 48)
+    const int vpl = nuz / 8, vshift = nuz == 32 ? 2 : 1;
+    const bool pow2 = nuz == 16 || nuz == 32;
     for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
         const uint4 *q = reinterpret_cast<const uint4 *>(f + c * cube);
         const float *sc = scale + c * lines;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(256) moment_coded_kernel(GridDims g, const T *
                 t += x.x + x.y;
             }
             // the product and its rounding error (exact, by FMA) both enter the sum
-            const float w = sc[k >> vshift];
+            const float w = sc[pow2 ? k >> vshift : k / vpl];
             const float pr = t * w;
             neumaier(s, e, pr);
             e += fmaf(t, w, -pr);

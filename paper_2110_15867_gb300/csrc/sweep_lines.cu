@@ -619,47 +619,70 @@ cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, i
 // ----------------------------------------------------------------------------
 // u_z rows staged per warp (other line lengths)
 // ----------------------------------------------------------------------------
-template <int NU> constexpr int rows_pitch() { return NU + 4; } // padded row (floats): conflict-free row reads
-template <int NU> constexpr size_t rows_sweep_smem() { return size_t(256) * rows_pitch<NU>() * 4; }
+// Each warp owns 32 consecutive rows: it copies them to shared memory with
+// coalesced 16-byte loads, each lane marches its own row in registers, and the
+// warp copies the rows back.  A row takes NU es / 16 chunks of 16 bytes; the
+// pitch is rounded up to an odd number of chunks, so that the 8 lanes of a phase
+// reading chunk j of their rows hit 8 different groups of 4 banks.  16-bit codes:
+// the row decodes with its scale, the sweep sets the scale to the row's largest
+// new value and encodes with stochastic rounding (one stream per row and sweep).
+template <int NU, typename T> constexpr int rows_chunks() { return NU * int(sizeof(T)) / 16; }
+template <int NU, typename T> constexpr int rows_pitch() { return rows_chunks<NU, T>() | 1; } // in chunks
+template <int NU, typename T> constexpr size_t rows_sweep_smem() { return size_t(256) * rows_pitch<NU, T>() * 16; }
 
-template <int NU>
-__global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const float *__restrict__ src, float *dst,
+template <int NU, typename T>
+__global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const T *__restrict__ src, T *dst,
                                                            const __grid_constant__ RowsArgs a)
 {
-    constexpr int P = rows_pitch<NU>(), CH = NU / 4;
-    extern __shared__ __align__(16) float rows_sw[];
+    constexpr bool CODED = sizeof(T) == 2;
+    constexpr int CH = rows_chunks<NU, T>(), PC = rows_pitch<NU, T>(), PER = 16 / int(sizeof(T));
+    static_assert(CH * 16 == NU * int(sizeof(T)), "a row is whole 16-byte chunks");
+    extern __shared__ __align__(16) uint4 rows_sw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *sr = rows_sw + w * 32 * P;
+    uint4 *sr = rows_sw + w * 32 * PC;
     const long long r0 = a.row0 + (blockIdx.x * 8ll + w) * 32; // the warp's first row
     const long long left = a.row0 + a.nrows - r0;
     const int nrows = left >= 32 ? 32 : (left > 0 ? int(left) : 0);
-    const float4 *g = reinterpret_cast<const float4 *>(src + r0 * NU);
-    float4 *o = reinterpret_cast<float4 *>(dst + r0 * NU);
+    const uint4 *g = reinterpret_cast<const uint4 *>(src + r0 * NU);
+    uint4 *o = reinterpret_cast<uint4 *>(dst + r0 * NU);
 #pragma unroll
     for (int k = lane; k < 32 * CH; k += 32) {
-        const int row = k / CH, col = 4 * (k % CH);
-        if (row < nrows) *reinterpret_cast<float4 *>(sr + row * P + col) = __ldg(g + k);
+        const int row = k / CH, col = k % CH;
+        if (row < nrows) sr[row * PC + col] = __ldg(g + k);
     }
     __syncwarp();
     if (lane < nrows) {
-        const LineCoefT<float> kc = a.cell_coef[(r0 + lane) / a.rows_per_cell];
+        const long long row = r0 + lane;
+        const LineCoefT<float> kc = a.cell_coef[row / a.rows_per_cell];
         if (kc.nd >= 0) {
             const bool neg = kc.nd & 1; // one orientation per spatial cell
+            unsigned char *mine = reinterpret_cast<unsigned char *>(sr + lane * PC);
+            const float sc = CODED ? a.scale[row] : 1.f;
             float v[NU];
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
-                const float4 u = *reinterpret_cast<const float4 *>(sr + lane * P + 4 * q);
-                const float e[4] = {u.x, u.y, u.z, u.w};
+                float e[PER];
+                Chunk<T>::get(mine + 16 * q, sc, e);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[neg ? NU - 1 - (4 * q + j) : 4 * q + j] = e[j];
+                for (int j = 0; j < PER; ++j) v[neg ? NU - 1 - (PER * q + j) : PER * q + j] = e[j];
             }
             const float sum = march_regs<NU, float>(v, to_lim(kc));
+            float inv = 1.f;
+            if (CODED) {
+                // new scale: the row's largest value
+                float m = 0.f;
+#pragma unroll
+                for (int l = 0; l < NU; ++l) m = fmaxf(m, v[l]);
+                a.scale[row] = m;
+                inv = m > 0.f ? __fdividef(1.f, m) : 0.f;
+            }
+            unsigned rng = CODED_RNG_INIT((unsigned long long)row * NU, a.seed);
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
-                float e[4];
+                float e[PER];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) e[j] = v[neg ? NU - 1 - (4 * q + j) : 4 * q + j];
-                *reinterpret_cast<float4 *>(sr + lane * P + 4 * q) = make_float4(e[0], e[1], e[2], e[3]);
+                for (int j = 0; j < PER; ++j) e[j] = v[neg ? NU - 1 - (PER * q + j) : PER * q + j];
+                Chunk<T>::put(mine + 16 * q, inv, e, rng);
             }
             if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
         }
@@ -667,31 +690,44 @@ __global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const float *__restr
     __syncwarp();
 #pragma unroll
     for (int k = lane; k < 32 * CH; k += 32) {
-        const int row = k / CH, col = 4 * (k % CH);
-        if (row < nrows) o[k] = *reinterpret_cast<const float4 *>(sr + row * P + col);
+        const int row = k / CH, col = k % CH;
+        if (row < nrows) o[k] = sr[row * PC + col];
     }
 }
 
-bool rows_sweep_supported(int L, int dtype) { return dtype == 1 && (L == 24 || L == 40 || L == 48); }
+bool rows_sweep_supported(int L, int dtype) { return dtype >= 1 && dtype <= 3 && (L == 24 || L == 40 || L == 48); }
 
-template <int NU> static cudaError_t launch_rows_t(const float *src, float *dst, const RowsArgs &a, cudaStream_t st)
+template <int NU, typename T>
+static cudaError_t launch_rows_t(const void *src, void *dst, const RowsArgs &a, cudaStream_t st)
 {
     const long long blocks = (a.nrows + 255) / 256;
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
-    const cudaError_t e = cudaFuncSetAttribute(rows_sweep_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(rows_sweep_smem<NU>()));
+    const cudaError_t e = cudaFuncSetAttribute(rows_sweep_kernel<NU, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(rows_sweep_smem<NU, T>()));
     if (e != cudaSuccess) return e;
-    rows_sweep_kernel<NU><<<unsigned(blocks), 256, rows_sweep_smem<NU>(), st>>>(src, dst, a);
+    rows_sweep_kernel<NU, T><<<unsigned(blocks), 256, rows_sweep_smem<NU, T>(), st>>>(static_cast<const T *>(src),
+                                                                                     static_cast<T *>(dst), a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_sweep(const float *src, float *dst, const RowsArgs &a, cudaStream_t st)
+template <typename T> static cudaError_t launch_rows_len(const void *src, void *dst, const RowsArgs &a, cudaStream_t st)
+{
+    switch (a.L) {
+    case 24: return launch_rows_t<24, T>(src, dst, a, st);
+    case 40: return launch_rows_t<40, T>(src, dst, a, st);
+    case 48: return launch_rows_t<48, T>(src, dst, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &a, int dtype, cudaStream_t st)
 {
     if (a.nrows <= 0) return cudaSuccess;
-    switch (a.L) {
-    case 24: return launch_rows_t<24>(src, dst, a, st);
-    case 40: return launch_rows_t<40>(src, dst, a, st);
-    case 48: return launch_rows_t<48>(src, dst, a, st);
+    if ((dtype == 2 || dtype == 3) && !a.scale) return cudaErrorInvalidValue;
+    switch (dtype) {
+    case 1: return launch_rows_len<float>(src, dst, a, st);
+    case 2: return launch_rows_len<__nv_bfloat16>(src, dst, a, st);
+    case 3: return launch_rows_len<__half>(src, dst, a, st);
     default: return cudaErrorInvalidValue;
     }
 }

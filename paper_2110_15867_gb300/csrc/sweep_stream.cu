@@ -352,8 +352,10 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
     const unsigned code_bytes = unsigned(slot_elems * sizeof(T));
     const unsigned slot_pitch = (code_bytes + 127u) & ~127u;
     auto slot_ptr = [&](unsigned e) { return reinterpret_cast<T *>(ring + slot_pitch * (e & (S - 1))); };
-    // 16-bit storage: the scales of the chunk's u_z lines, box {Wl, R, P} (Wl = W / n_uz)
-    const int Wl = CODED ? W / int(args.nuz) : 0;
+    // 16-bit storage: the scales of the chunk's u_z lines, box {Wl, R, P} starting at line
+    // (c0 / n_uz) & ~3 (16-byte aligned), wide enough for every line the block touches
+    const int nuz = CODED ? int(args.nuz) : 1;
+    const int Wl = CODED ? args.swidth : 0;
     const unsigned scale_bytes = CODED ? unsigned(Wl * R * P * 4) : 0u;
     const unsigned scale_pitch = (scale_bytes + 127u) & ~127u;
     unsigned char *sring = ring + size_t(slot_pitch) * S;
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
                 tma_load_3d(slot_ptr(loaded), &map, &full[st], c0, c1, c2);
                 if (CODED) {
                     if (args.scale_rank == 3)
-                        tma_load_3d(scale_ptr(loaded), &smap, &full[st], c0 / int(args.nuz), c1, c2);
+                        tma_load_3d(scale_ptr(loaded), &smap, &full[st], (c0 / nuz) & ~3, c1, c2);
                     else
                         tma_load_2d(scale_ptr(loaded), &smap, &full[st], c1, c2);
                 }
@@ -540,7 +542,9 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
         }
         // 16-bit storage: a rounding stream per column pair and block, from the element index
         unsigned rng = CODED ? sr_bits((unsigned long long)(outer * L * args.n_inner + inner), args.seed) : 0u;
-        const int soff = CODED ? (p * R * Wl + w / int(args.nuz)) : 0; // this column's line in a scale slot
+        // this column's line in a scale slot
+        const int c0 = int((t % args.tiles_inner) * W);
+        const int soff = CODED ? (p * R * Wl + (c0 + w) / nuz - ((c0 / nuz) & ~3)) : 0;
         X sum;
         if (neg)
             sum = march_stream<T, PERIODIC, true>(lim, e, ec, coff, soff, L, W, Wl, rng, slot_ptr, scale_ptr, acquire,

@@ -113,6 +113,8 @@ template <typename C> struct StreamArgs {
     long long nuz;
     unsigned seed;      // 16-bit storage: stochastic-rounding stream of this sweep
     int scale_rank;     // 16-bit storage: rank of the scale tensor map (3, or 2 for the u_y sweep)
+    int swidth;         // 16-bit storage: inner extent of the scale box (a multiple of 4); a block at
+                        // inner offset c0 loads the scales of u_z lines (c0 / nuz) & ~3 onward
     // x sweep with the velocity moment fused (FP32 / FP64 storage, P = 1, W x the element
     // size = 1024 bytes, W divides the velocity cube): a moment warp sums every output row;
     // row x of the block at inner offset c0 adds to spatial cell x (n_inner / cube) +
@@ -204,9 +206,12 @@ struct RowsArgs {
     long long row0, nrows, rows_per_cell;
     const LineCoefT<float> *cell_coef;
     unsigned *err;
+    float *scale;  // 16-bit storage: the FP32 scale of each row, refreshed by the sweep (else null)
+    unsigned seed; // 16-bit storage: stochastic-rounding stream of this sweep
 };
+// u_z rows of L = 24, 40 or 48 cells (dtype 1 f32, 2 bf16, 3 f16), in place or src -> dst
 bool rows_sweep_supported(int L, int dtype);
-cudaError_t launch_rows_sweep(const float *src, float *dst, const RowsArgs &a, cudaStream_t st);
+cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &a, int dtype, cudaStream_t st);
 bool reg_lines_supported(int L);
 // dtype: 1 f32, 2 bf16, 3 f16
 cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, int dtype, cudaStream_t st);

@@ -113,6 +113,7 @@ struct vlasov_ctx {
     int splan_R[5];
     CUtensorMap smap[5]; // 16-bit storage: scale array seen like f, the u_z line collapsed
     int scale_rank[5];
+    int swidth[5]; // inner extent of each axis' scale box
     // u_z with whole lines in registers
     bool use_lines;
     CUtensorMap lmap;
@@ -312,11 +313,20 @@ static int plan_axes(vlasov_ctx *c)
         const size_t tab = ax < 3 ? ((csz * (size_t)d6[3 + ax] + 127) & ~size_t(127)) : 0;
         size_t sslot = 0;
         if (coded) {
-            // scales of the lines of one chunk: box {W / nuz, R, P} over [O][L][I / nuz]
-            // (the u_y sweep has I = nuz: box {R, P} over [O][L])
-            const long long nuz = c->g.nuz;
-            const int Wl = W / int(nuz);
-            if (W % nuz || (ax < 4 && I % nuz)) return fail(c, VLASOV_EINVAL, "axis %d: block width %d is not whole u_z lines", ax, W);
+            // scales of the lines of one chunk: box {Wl, R, P} over [O][L][I / nuz] from line
+            // (c0 / nuz) & ~3 of a block at inner offset c0 (the u_y sweep has I = nuz: box
+            // {R, P} over [O][L]).  Wl = W / nuz when that is a multiple of 4 (every c0 / nuz
+            // then is one too), else it covers the up to 3 lines ahead of c0's own line and
+            // the ceil((W - 1) / nuz) + 1 lines a block of W columns can touch.
+            const int nuz = int(c->g.nuz);
+            int Wl = 1;
+            if (ax < 4) {
+                Wl = (W % nuz == 0 && (W / nuz) % 4 == 0) ? W / nuz : 3 + (W - 1 + nuz - 1) / nuz + 1;
+                Wl = (Wl + 3) & ~3;
+            } else if (I != nuz || W != nuz) {
+                return fail(c, VLASOV_EINVAL, "axis %d: u_y blocks must be whole u_z lines", ax);
+            }
+            c->swidth[ax] = Wl;
             sslot = ((size_t)Wl * R * P * 4 + 127) & ~size_t(127);
             CUresult rs;
             if (ax < 4) {
@@ -417,8 +427,9 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     if (coded) {
         if (!scale_dev || reinterpret_cast<uintptr_t>(scale_dev) % 16)
             return fail(nullptr, VLASOV_EINVAL, "16-bit storage needs a 16-byte aligned scale_dev");
-        if (!line_sweep_supported(g->nuz, (long long)g->nux * g->nuy))
-            return fail(nullptr, VLASOV_EINVAL, "16-bit storage needs nuz = 16 or 32 and nux * nuy a multiple of 256");
+        if (!line_sweep_supported(g->nuz, (long long)g->nux * g->nuy) && !rows_sweep_supported(g->nuz, g->dtype))
+            return fail(nullptr, VLASOV_EINVAL,
+                        "16-bit storage needs nuz = 16 or 32 with nux * nuy a multiple of 256, or nuz = 24, 40 or 48");
     }
     if (reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(nullptr, VLASOV_EINVAL, "f_dev must be 16-byte aligned");
     const long long ncell = (long long)g->nx * g->ny * g->nz;
@@ -574,6 +585,7 @@ template <typename C> static void fill_stream_args(StreamArgs<C> &A, const vlaso
     A.nuz = c->g.nuz;
     A.seed = c->sweeps;
     A.scale_rank = c->scale_rank[ax];
+    A.swidth = c->swidth[ax];
 }
 
 // Tensor maps of one plan for a sweep that reads src and writes dst (both
@@ -812,8 +824,10 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
         }
         A.cell_coef = (const LineCoefT<float> *)coef;
         A.err = c->d_err;
+        A.scale = c->scale;
+        A.seed = c->sweeps;
         PartTimer t(c, ax, 1);
-        e = launch_rows_sweep(static_cast<const float *>(src), static_cast<float *>(dst), A, c->stream);
+        e = launch_rows_sweep(src, dst, A, c->g.dtype, c->stream);
     } else {
         if (c->slab_x1 > c->slab_x0) return fail(c, VLASOV_EINVAL, "u_z sweep: the transposing kernel cannot run on an x-slab");
         if ((rc = sweep_maps(c, p.map, p.spec, src, dst, m))) return rc;

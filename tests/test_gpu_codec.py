@@ -29,12 +29,19 @@ def _setup(n, nu, V=5.0, seed=1, rms=0.01):
     return f0, phi
 
 
+# u_z lines of 16/32 cells (TMA tiles of 256 lines), and of 48/24/40 cells (rows staged
+# per warp; the streamed sweeps' 256-column blocks then cut u_z lines, and the u_y
+# blocks hold 5, 10 or 6 whole lines)
+CODEC_SHAPES = [((8, 6, 5), (16, 16, 32)), ((6, 5, 4), (24, 16, 48)), ((5, 4, 6), (48, 24, 24)),
+                ((4, 5, 4), (16, 8, 40))]
+
+
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
 @pytest.mark.parametrize("axis", [0, 1, 2, 3, 4, 5])
-def test_codec_single_sweep(fmt, axis):
+@pytest.mark.parametrize("n,nu", CODEC_SHAPES)
+def test_codec_single_sweep(fmt, axis, n, nu):
     from paper_2110_15867_gb300 import binding as B
     B.load()
-    n, nu = (8, 6, 5), (16, 16, 32)
     f0, phi = _setup(n, nu)
     codes, scale = B.encode_lines(torch.from_numpy(f0).cuda(), TDT[fmt])
     ref = B.decode_lines(codes, scale).cpu().numpy()
@@ -53,10 +60,11 @@ def test_codec_single_sweep(fmt, axis):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
-def test_codec_moment(fmt):
+@pytest.mark.parametrize("nu", [(16, 16, 16), (8, 12, 24), (16, 8, 40), (12, 8, 48)])
+def test_codec_moment(fmt, nu):
     from paper_2110_15867_gb300 import binding as B
     B.load()
-    n, nu = (4, 4, 4), (16, 16, 16)
+    n = (4, 4, 4)
     f0, _ = _setup(n, nu, rms=0.3)
     codes, scale = B.encode_lines(torch.from_numpy(f0).cuda(), TDT[fmt])
     dec = B.decode_lines(codes, scale).cpu().numpy()
@@ -102,5 +110,35 @@ def test_codec_density_after_20_steps(fmt):
     r = rho.cpu().numpy()
     l1 = np.abs(r - ref["rho"]).sum() / np.abs(ref["rho"]).sum()
     print("%s density rel L1 after 20 steps: %.3e" % (fmt, l1))
+    assert l1 <= 1e-3
+    v.close()
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_codec_steps_with_48_cell_rows(fmt):
+    # five Eq. (5) steps with u_z lines of 48 cells (the staged-rows u_z sweep and the
+    # streamed sweeps whose blocks cut u_z lines): density within 1e-3 relative L1 of
+    # the FP64 oracle, the bound of the 20-step run above
+    from paper_2110_15867_gb300 import binding as B
+    B.load()
+    n, nu = (8, 6, 6), (16, 24, 48)
+    f0, phi = _setup(n, nu, seed=3)
+    g = O.grid(n, nu, V=5.0)
+    dt = min(0.7 / O.max_abs_nu(g, ax, 1.0, 1.0, phi.astype(np.float64)) * (2 if ax >= 3 else 1)
+             for ax in range(6))
+    f = f0.copy()
+    for _ in range(5):
+        _, rho_ref = O.step(g, f, dt, 1.0, 1.0, phi.astype(np.float64))
+    codes, scale = B.encode_lines(torch.from_numpy(f0).cuda(), TDT[fmt])
+    v = B.Vlasov(codes, V=5.0, scale=scale)
+    phit = torch.from_numpy(phi).cuda()
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        v.step(dt, 1.0, 1.0, phit, rho_nu=rho)
+    v.status()
+    r = rho.cpu().numpy()
+    l1 = np.abs(r - rho_ref).sum() / np.abs(rho_ref).sum()
+    fl1 = np.abs(B.decode_lines(codes, scale).cpu().numpy() - f).sum() / np.abs(f).sum()
+    print("%s n_uz 48: density rel L1 after 5 steps %.3e, f rel L1 %.3e" % (fmt, l1, fl1))
     assert l1 <= 1e-3
     v.close()

@@ -13,9 +13,9 @@ moment the x sweep sums in the step against the moment kernel on the final state
 second kick moves mass only within each cell's velocity cube, so the two agree to the
 FP32 rounding of three sweeps).
 
-Workloads: 64^3 x 32^3 FP32 (the benchmark), 48^3 x 48^3 FP32 with |u| <= 8 u_T (its
-velocity cube, 432 KiB, does not fit in shared memory), 96^3 x 32^3 BF16 / FP16 with a
-scale per u_z line, 32^3 x 16^3 FP32 for the adjoint sweeps.
+Workloads: 64^3 x 32^3 FP32 (the benchmark), 48^3 x 48^3 FP32 and BF16 with |u| <= 8 u_T
+(its velocity cube, 432 KiB in FP32, does not fit in shared memory), 96^3 x 32^3 BF16 /
+FP16 with a scale per u_z line, 32^3 x 16^3 FP32 for the adjoint sweeps.
 """
 import numpy as np
 import pytest
@@ -135,12 +135,12 @@ def test_fullsize_fp32_sweeps_sampled_lines(name):
     _free()
 
 
-@pytest.mark.parametrize("fmt", ["bf16", "f16"])
-def test_fullsize_16bit_sweeps_sampled_lines(fmt):
+@pytest.mark.parametrize("name,fmt", [("lowprec_96x32", "bf16"), ("lowprec_96x32", "f16"), ("large_48x48", "bf16")])
+def test_fullsize_16bit_sweeps_sampled_lines(name, fmt):
     # the codec bounds of the 16-bit parity tests: relative L1 <= 2^-8 (BF16) / 2^-11
     # (FP16) + 1e-6, L_inf <= 1.5 (2 x that) of the largest value
     B = _lib()
-    cfg = I.CONFIGS["lowprec_96x32"]
+    cfg = I.CONFIGS[name]
     bound = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[fmt]
     codes, scale = _build_f(cfg, {"bf16": torch.bfloat16, "f16": torch.float16}[fmt])
     phi = I.fourier_potential(cfg["n"], seed=cfg["seed"] + 10).astype(np.float32)
