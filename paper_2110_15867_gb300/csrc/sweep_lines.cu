@@ -541,8 +541,12 @@ template <> struct RegCodec<__half> {
     }
 };
 
+#ifndef VK_REG_LINES48
+#define VK_REG_LINES48 1 // 1: u_x / u_y lines of 48 cells in registers too (128 registers, 2 CTAs per SM)
+#endif
+
 template <int L, typename T>
-__global__ void __launch_bounds__(256, 3) reg_lines_kernel(const T *__restrict__ src, T *dst,
+__global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T *__restrict__ src, T *dst,
                                                           const __grid_constant__ RegLineArgs a)
 {
     constexpr bool CODED = sizeof(T) == 2;
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(256, 3) reg_lines_kernel(const T *__restrict__
     if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
 }
 
-bool reg_lines_supported(int L) { return L == 16 || L == 32; }
+bool reg_lines_supported(int L) { return L == 16 || L == 32 || (VK_REG_LINES48 && L == 48); }
 
 template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst, const RegLineArgs &a, unsigned blocks,
                                                       cudaStream_t st)
@@ -599,6 +603,7 @@ template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst
     T *d = static_cast<T *>(dst);
     if (a.L == 32) reg_lines_kernel<32, T><<<blocks, 256, 0, st>>>(s, d, a);
     else if (a.L == 16) reg_lines_kernel<16, T><<<blocks, 256, 0, st>>>(s, d, a);
+    else if (VK_REG_LINES48 && a.L == 48) reg_lines_kernel<48, T><<<blocks, 256, 0, st>>>(s, d, a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -485,13 +485,15 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
     int col;  // first of this thread's V columns inside the block
     if (args.perm_line > 0) {
         // z sweep: the Courant number changes sign in the middle of each velocity
-        // line; threads [0, H) take the columns with u_z < 0 and [H, 2H) those
-        // with u_z > 0, so that whole warps march with one orientation.
+        // line; threads [0, H) take the columns with u_z < 0 and [Hp, Hp + H) those
+        // with u_z > 0, so that whole warps march with one orientation (Hp: H rounded
+        // up to whole warps when both halves still fit, e.g. 60 -> 64 for 5 lines of 48)
         const int Lz = args.perm_line, q = Lz / (2 * V);   // pairs per half line
         const int lines = W / Lz, H = lines * q;
-        const int tt = tid < H ? tid : tid - H;
-        col = (tt / q) * Lz + (tid < H ? 0 : Lz / 2) + V * (tt % q);
-        if (tid >= 2 * H) col = W * P;                      // idle thread
+        const int Hw = (H + 31) & ~31, Hp = 2 * Hw <= LN::NC ? Hw : H;
+        const int tt = tid < Hp ? tid : tid - Hp;
+        col = (tt / q) * Lz + (tid < Hp ? 0 : Lz / 2) + V * (tt % q);
+        if (tt >= H || tid >= Hp + H) col = W * P;          // idle thread
     } else {
         col = tid * V;
     }

@@ -54,6 +54,7 @@ SHAPES = [
     ((6, 5, 7), (8, 20, 12)),       # ragged: no tile size divides the extents
     ((5, 5, 7), (4, 12, 24)),       # u_z rows of 24 staged per warp; the last warp holds 16 rows
     ((4, 4, 4), (8, 8, 48)),        # u_z rows of 48 (the 48^3 velocity grid's line length)
+    ((4, 5, 4), (48, 48, 8)),       # u_x, u_y lines of 48 in registers; z blocks of 32 u_z lines
 ]
 
 
