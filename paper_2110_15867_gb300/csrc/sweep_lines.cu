@@ -95,6 +95,18 @@ template <> struct Chunk<__half> {
     }
 };
 
+template <> struct Chunk<double> {
+    __device__ static void get(const unsigned char *p, float, double (&o)[2])
+    {
+        const double2 a = *reinterpret_cast<const double2 *>(p);
+        o[0] = a.x; o[1] = a.y;
+    }
+    __device__ static void put(unsigned char *p, float, const double (&o)[2], unsigned &)
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    }
+};
+
 #define CODED_RNG_INIT(e, seed) (sizeof(T) == 2 ? sr_bits((e), (seed)) : 0u)
 
 // Advance both lines of the pair (forward local frame; zero-flux faces).
@@ -636,9 +648,10 @@ template <int NU, typename T> constexpr int rows_pitch() { return rows_chunks<NU
 template <int NU, typename T> constexpr size_t rows_sweep_smem() { return size_t(256) * rows_pitch<NU, T>() * 16; }
 
 template <int NU, typename T>
-__global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const T *__restrict__ src, T *dst,
-                                                           const __grid_constant__ RowsArgs a)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) rows_sweep_kernel(const T *__restrict__ src, T *dst,
+                                                                                const __grid_constant__ RowsArgs a)
 {
+    using C = typename Compute<T>::type;
     constexpr bool CODED = sizeof(T) == 2;
     constexpr int CH = rows_chunks<NU, T>(), PC = rows_pitch<NU, T>(), PER = 16 / int(sizeof(T));
     static_assert(CH * 16 == NU * int(sizeof(T)), "a row is whole 16-byte chunks");
@@ -658,22 +671,22 @@ __global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const T *__restrict_
     __syncwarp();
     if (lane < nrows) {
         const long long row = r0 + lane;
-        const LineCoefT<float> kc = a.cell_coef[row / a.rows_per_cell];
+        const LineCoefT<C> kc = static_cast<const LineCoefT<C> *>(a.cell_coef)[row / a.rows_per_cell];
         if (kc.nd >= 0) {
             const bool neg = kc.nd & 1; // one orientation per spatial cell
             unsigned char *mine = reinterpret_cast<unsigned char *>(sr + lane * PC);
             const float sc = CODED ? a.scale[row] : 1.f;
-            float v[NU];
+            C v[NU];
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
-                float e[PER];
+                C e[PER];
                 Chunk<T>::get(mine + 16 * q, sc, e);
 #pragma unroll
                 for (int j = 0; j < PER; ++j) v[neg ? NU - 1 - (PER * q + j) : PER * q + j] = e[j];
             }
-            const float sum = march_regs<NU, float>(v, to_lim(kc));
+            const C sum = march_regs<NU, C>(v, to_lim(kc));
             float inv = 1.f;
-            if (CODED) {
+            if constexpr (CODED) {
                 // new scale: the row's largest value
                 float m = 0.f;
 #pragma unroll
@@ -684,12 +697,12 @@ __global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const T *__restrict_
             unsigned rng = CODED_RNG_INIT((unsigned long long)row * NU, a.seed);
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
-                float e[PER];
+                C e[PER];
 #pragma unroll
                 for (int j = 0; j < PER; ++j) e[j] = v[neg ? NU - 1 - (PER * q + j) : PER * q + j];
                 Chunk<T>::put(mine + 16 * q, inv, e, rng);
             }
-            if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
+            if (!(sum >= C(0)) || isinf(sum)) atomicOr(a.err, ERR_NAN);
         }
     }
     __syncwarp();
@@ -700,7 +713,7 @@ __global__ void __launch_bounds__(256, 2) rows_sweep_kernel(const T *__restrict_
     }
 }
 
-bool rows_sweep_supported(int L, int dtype) { return dtype >= 1 && dtype <= 3 && (L == 24 || L == 40 || L == 48); }
+bool rows_sweep_supported(int L, int dtype) { return dtype >= 0 && dtype <= 3 && (L == 24 || L == 40 || L == 48); }
 
 template <int NU, typename T>
 static cudaError_t launch_rows_t(const void *src, void *dst, const RowsArgs &a, cudaStream_t st)
@@ -730,6 +743,7 @@ cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &a, int
     if (a.nrows <= 0) return cudaSuccess;
     if ((dtype == 2 || dtype == 3) && !a.scale) return cudaErrorInvalidValue;
     switch (dtype) {
+    case 0: return launch_rows_len<double>(src, dst, a, st);
     case 1: return launch_rows_len<float>(src, dst, a, st);
     case 2: return launch_rows_len<__nv_bfloat16>(src, dst, a, st);
     case 3: return launch_rows_len<__half>(src, dst, a, st);

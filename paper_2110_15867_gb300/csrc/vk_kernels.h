@@ -204,12 +204,12 @@ struct RegLineArgs {
 struct RowsArgs {
     int L;
     long long row0, nrows, rows_per_cell;
-    const LineCoefT<float> *cell_coef;
+    const void *cell_coef; // LineCoefT<double> for FP64 storage, else LineCoefT<float>
     unsigned *err;
     float *scale;  // 16-bit storage: the FP32 scale of each row, refreshed by the sweep (else null)
     unsigned seed; // 16-bit storage: stochastic-rounding stream of this sweep
 };
-// u_z rows of L = 24, 40 or 48 cells (dtype 1 f32, 2 bf16, 3 f16), in place or src -> dst
+// u_z rows of L = 24, 40 or 48 cells (dtype 0 f64, 1 f32, 2 bf16, 3 f16), in place or src -> dst
 bool rows_sweep_supported(int L, int dtype);
 cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &a, int dtype, cudaStream_t st);
 bool reg_lines_supported(int L);

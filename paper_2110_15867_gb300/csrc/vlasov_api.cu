@@ -276,6 +276,11 @@ static int plan_axes(vlasov_ctx *c)
             p.spec = spec_rows(tmap_type(c->g.dtype), p.L, rows, es, kConsumers, CU_TENSOR_MAP_SWIZZLE_NONE);
             r = encode_spec(&p.map, p.spec, c->f);
             const int occ = occupancy_contig(c->g.dtype == VLASOV_F64 ? 0 : 1, p.smem);
+            // u_z rows of 24, 40 or 48 cells never take the transposing kernel
+            if (occ <= 0 && rows_sweep_supported(int(c->g.nuz), c->g.dtype)) {
+                p.grid = 0;
+                continue;
+            }
             if (occ <= 0) return fail(c, VLASOV_ECUDA, "axis 5: a CTA does not fit (%zu B shared memory)", p.smem);
             p.grid = int(p.num_tiles < (long long)occ * c->sm_count ? p.num_tiles : (long long)occ * c->sm_count);
         }
@@ -827,7 +832,7 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
             A.row0 = c->slab_x0 * rpp;
             A.nrows = (c->slab_x1 - c->slab_x0) * rpp;
         }
-        A.cell_coef = (const LineCoefT<float> *)coef;
+        A.cell_coef = coef;
         A.err = c->d_err;
         A.scale = c->scale;
         A.seed = c->sweeps;

@@ -84,9 +84,9 @@ def test_single_sweep_fp32(n, nu, axis):
 
 
 @pytest.mark.parametrize("axis", [0, 1, 2, 3, 4, 5])
-def test_single_sweep_fp64(axis):
+@pytest.mark.parametrize("n,nu", [((8, 6, 5), (8, 12, 16)), ((4, 5, 4), (16, 8, 48)), ((5, 4, 4), (8, 12, 40))])
+def test_single_sweep_fp64(axis, n, nu):
     B = _lib()
-    n, nu = (8, 6, 5), (8, 12, 16)
     f0, phi = _setup(n, nu, dtype=np.float64)
     g = O.grid(n, nu, V=5.0)
     dt = _dt_for(g, axis, phi, 0.8)
