@@ -300,10 +300,14 @@ def _ptr(t):
 
 def encode_lines(f, dtype):
     """Storage of f for the 16-bit codec: one FP32 scale per u_z line (the line's
-    largest value) and the codes f / scale rounded to `dtype` (torch.bfloat16 or
-    torch.float16).  f: 6D torch tensor (any device); returns (codes, scale)."""
+    largest value; BF16 at least 2^-64, as the sweeps' refresh keeps it, so that an
+    empty line can take in mass) and the codes f / scale rounded to `dtype`
+    (torch.bfloat16 or torch.float16).  f: 6D torch tensor (any device); returns
+    (codes, scale)."""
     import torch
     scale = f.amax(dim=-1).to(torch.float32)
+    if dtype == torch.bfloat16:
+        scale = scale.clamp(min=2.0 ** -64)
     inv = torch.where(scale > 0, 1.0 / scale.to(f.dtype), torch.zeros_like(scale, dtype=f.dtype))
     codes = (f * inv[..., None]).to(dtype)
     return codes.contiguous(), scale.contiguous()

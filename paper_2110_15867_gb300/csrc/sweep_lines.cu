@@ -176,10 +176,10 @@ __device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, c
             m0 = fmaxf(m0, v[l].x);
             m1 = fmaxf(m1, v[l].y);
         }
-        s0 = m0;
-        s1 = m1;
-        i0 = m0 > 0.f ? __fdividef(1.f, m0) : 0.f;
-        i1 = m1 > 0.f ? __fdividef(1.f, m1) : 0.f;
+        s0 = coded_scale<T>(m0);
+        s1 = coded_scale<T>(m1);
+        i0 = inv_scale(s0);
+        i1 = inv_scale(s1);
     }
 #pragma unroll
     for (int j = 0; j < G_::chunks; ++j) {
@@ -504,8 +504,9 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
                     float m = 0.f;
 #pragma unroll
                     for (int l = 0; l < NU; ++l) m = fmaxf(m, v[l]);
+                    m = coded_scale<T>(m);
                     args.scale[row0 + r] = m;
-                    inv = m > 0.f ? __fdividef(1.f, m) : 0.f;
+                    inv = inv_scale(m);
                 }
 #pragma unroll
                 for (int j = 0; j < G_::chunks; ++j) {
@@ -597,8 +598,7 @@ __global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T 
         float inv = 1.f;
         unsigned r = 0u;
         if (CODED) {
-            const float s = __ldg(a.scale + zl + i * Iz);
-            inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+            inv = inv_scale(__ldg(a.scale + zl + i * Iz));
             r = lcg_next(rng) >> 16;
         }
         q[i * a.n_inner] = RegCodec<T>::put(v[i], inv, r);
@@ -691,8 +691,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) rows_sweep_kernel
                 float m = 0.f;
 #pragma unroll
                 for (int l = 0; l < NU; ++l) m = fmaxf(m, v[l]);
+                m = coded_scale<T>(m);
                 a.scale[row] = m;
-                inv = m > 0.f ? __fdividef(1.f, m) : 0.f;
+                inv = inv_scale(m);
             }
             unsigned rng = CODED_RNG_INIT((unsigned long long)row * NU, a.seed);
 #pragma unroll

@@ -66,8 +66,7 @@ template <> struct Lane<__nv_bfloat16> {
     // rows are stored in order, so the rounding stream advances once per row
     __device__ static void store(__nv_bfloat16 *p, X v, const float *sp, unsigned &rng)
     {
-        const float s = *sp;
-        const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+        const float inv = inv_scale(*sp);
         *reinterpret_cast<unsigned *>(p) = sr_pack_bf16x2(v.x * inv, v.y * inv, rng);
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
@@ -83,8 +82,7 @@ template <> struct Lane<__half> {
     }
     __device__ static void store(__half *p, X v, const float *sp, unsigned &rng)
     {
-        const float s = *sp;
-        const float inv = s > 0.f ? __fdividef(1.f, s) : 0.f;
+        const float inv = inv_scale(*sp);
         *reinterpret_cast<unsigned *>(p) = sr_pack_f16x2(v.x * inv, v.y * inv, rng);
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }

@@ -278,6 +278,17 @@ __device__ __forceinline__ unsigned sr_pack_bf16x2(float x, float y, unsigned &r
 #endif
 }
 
+// Line scales of the 16-bit codec.  coded_scale: the scale a refresh stores for a line
+// whose largest value is m; BF16 keeps at least 2^-64, so that a line left empty can
+// still take in mass from the sweeps that keep the scale (BF16 carries 8 significant
+// bits at any exponent: codes up to 2^64 x its largest value stay finite, and values
+// down to 2^-190 stay representable); FP16 has 5 exponent bits and keeps m itself.
+// inv_scale: 1 / s for encoding, 0 for s = 0 and for a subnormal s, whose reciprocal
+// would overflow (such a line holds nothing above 2^-126; its values encode as 0).
+template <typename T> __device__ __forceinline__ float coded_scale(float m) { return m; }
+template <> __device__ __forceinline__ float coded_scale<__nv_bfloat16>(float m) { return fmaxf(m, 0x1p-64f); }
+__device__ __forceinline__ float inv_scale(float s) { return s >= 0x1p-126f ? __fdividef(1.f, s) : 0.f; }
+
 // two non-negative FP32 values -> packed f16x2 (13 random bits below the FP16 mantissa)
 __device__ __forceinline__ unsigned pack_f16x2(float x, float y, unsigned rnd)
 {
