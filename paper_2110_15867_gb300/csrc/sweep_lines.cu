@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
         unsigned char *base = slot(k);
         if constexpr (FUSE_Y) {
             // every row of the tile belongs to one spatial cell
-            const LineCoefT<float> ky = args.cell_coef_y[row0 / args.rows_per_cell];
+            const LineCoefT<float> ky = args.cell_coef_y[fdiv(unsigned(row0), args.div_rpc)];
             if (row0 < args.rows && ky.nd >= 0) {
                 const bool bad = (ky.nd & 1) ? plane_columns<NU, true>(base, tid, to_lim2(ky, ky))
                                              : plane_columns<NU, false>(base, tid, to_lim2(ky, ky));
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kLineThreads + kProducer, 3)
             __syncwarp();
         }
         if (row0 + r0 < args.rows) {
-            const LineCoefT<float> kc = args.cell_coef[(row0 + r0) / args.rows_per_cell];
+            const LineCoefT<float> kc = args.cell_coef[fdiv(unsigned(row0 + r0), args.div_rpc)];
             if (kc.nd >= 0) {
                 float s0 = 1.f, s1 = 1.f;
                 if (sizeof(T) == 2) {
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
         const float sc = CODED && row0 + r < args.rows ? args.scale[row0 + r] : 1.f;
         bool from_wide = false; // 16-bit fused: the u_z rows come from the FP32 copy
         if constexpr (FUSE_Y) {
-            const LineCoefT<float> ky = args.cell_coef_y[row0 / args.rows_per_cell];
+            const LineCoefT<float> ky = args.cell_coef_y[fdiv(unsigned(row0), args.div_rpc)];
             if (row0 < args.rows && ky.nd >= 0) {
                 bool bad;
                 if constexpr (CODED) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
             __syncwarp();
         }
         if (row0 + r < args.rows) {
-            const LineCoefT<float> kc = args.cell_coef[(row0 + r) / args.rows_per_cell];
+            const LineCoefT<float> kc = args.cell_coef[fdiv(unsigned(row0 + r), args.div_rpc)];
             if (kc.nd >= 0) {
                 const bool neg = kc.nd & 1; // one orientation per spatial cell: warp-uniform
                 unsigned rng = CODED_RNG_INIT((unsigned long long)(row0 + r) * NU, args.seed);
@@ -565,9 +565,17 @@ __global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T 
     constexpr bool CODED = sizeof(T) == 2;
     const long long t = a.line0 + blockIdx.x * 256ll + threadIdx.x;
     if (t >= a.line0 + a.nlines) return;
-    const long long outer = t / a.n_inner, inner = t - outer * a.n_inner;
+    long long outer, cell;
+    if (a.line0 + a.nlines <= 0xffffffffll) { // every line index of the launch fits 32 bits
+        outer = fdiv(unsigned(t), a.div_inner);
+        cell = fdiv(unsigned(outer), a.div_opc);
+    } else {
+        outer = t / a.n_inner;
+        cell = outer / a.outer_per_cell;
+    }
+    const long long inner = t - outer * a.n_inner;
     const long long base = outer * L * a.n_inner + inner;
-    const LineCoefT<float> kc = a.cell_coef[outer / a.outer_per_cell];
+    const LineCoefT<float> kc = a.cell_coef[cell];
     const T *p = src + base;
     T *q = dst + base;
     if (kc.nd < 0) {
@@ -577,8 +585,9 @@ __global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T 
             for (int i = 0; i < L; ++i) q[i * a.n_inner] = p[i * a.n_inner];
         return;
     }
-    // 16-bit: the u_z line of cell i is zl + i Iz
-    const long long Iz = CODED ? a.n_inner / a.nuz : 0, zl = CODED ? outer * L * Iz + inner / a.nuz : 0;
+    // 16-bit: the u_z line of cell i is zl + i Iz (inner < n_inner < 2^32)
+    const long long Iz = CODED ? a.n_inner / a.nuz : 0;
+    const long long zl = CODED ? outer * L * Iz + fdiv(unsigned(inner), a.div_nuz) : 0;
     const bool neg = kc.nd & 1; // one orientation per spatial cell
     float v[L];
 #pragma unroll
@@ -620,11 +629,17 @@ template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst
     return cudaGetLastError();
 }
 
-cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &a, int dtype, cudaStream_t st)
+cudaError_t launch_reg_lines(const void *src, void *dst, const RegLineArgs &args, int dtype, cudaStream_t st)
 {
-    if (a.nlines <= 0) return cudaSuccess;
-    const long long blocks = (a.nlines + 255) / 256;
-    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (args.nlines <= 0) return cudaSuccess;
+    const long long blocks = (args.nlines + 255) / 256;
+    if (blocks > 0x7fffffffll || args.n_inner <= 0 || args.n_inner > 0xffffffffll || args.outer_per_cell <= 0 ||
+        args.outer_per_cell > 0xffffffffll)
+        return cudaErrorInvalidValue;
+    RegLineArgs a = args;
+    a.div_inner = make_fastdiv(unsigned(a.n_inner));
+    a.div_opc = make_fastdiv(unsigned(a.outer_per_cell));
+    a.div_nuz = make_fastdiv(unsigned(a.nuz > 0 ? a.nuz : 1));
     switch (dtype) {
     case 1: return launch_reg_t<float>(src, dst, a, unsigned(blocks), st);
     case 2: return launch_reg_t<__nv_bfloat16>(src, dst, a, unsigned(blocks), st);
@@ -671,7 +686,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) rows_sweep_kernel
     __syncwarp();
     if (lane < nrows) {
         const long long row = r0 + lane;
-        const LineCoefT<C> kc = static_cast<const LineCoefT<C> *>(a.cell_coef)[row / a.rows_per_cell];
+        const LineCoefT<C> kc = static_cast<const LineCoefT<C> *>(a.cell_coef)[fdiv(unsigned(row), a.div_rpc)];
         if (kc.nd >= 0) {
             const bool neg = kc.nd & 1; // one orientation per spatial cell
             unsigned char *mine = reinterpret_cast<unsigned char *>(sr + lane * PC);
@@ -739,10 +754,15 @@ template <typename T> static cudaError_t launch_rows_len(const void *src, void *
     }
 }
 
-cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &a, int dtype, cudaStream_t st)
+cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &args, int dtype, cudaStream_t st)
 {
-    if (a.nrows <= 0) return cudaSuccess;
-    if ((dtype == 2 || dtype == 3) && !a.scale) return cudaErrorInvalidValue;
+    if (args.nrows <= 0) return cudaSuccess;
+    if ((dtype == 2 || dtype == 3) && !args.scale) return cudaErrorInvalidValue;
+    // row indices (u_z lines) stay below 2^31 (checked at init)
+    if (args.row0 + args.nrows + 255 > 0xffffffffll || args.rows_per_cell <= 0 || args.rows_per_cell > 0xffffffffll)
+        return cudaErrorInvalidValue;
+    RowsArgs a = args;
+    a.div_rpc = make_fastdiv(unsigned(a.rows_per_cell));
     switch (dtype) {
     case 0: return launch_rows_len<double>(src, dst, a, st);
     case 1: return launch_rows_len<float>(src, dst, a, st);
@@ -793,15 +813,20 @@ bool line_sweep_supported(int nu, long long rows_per_cell)
     return (nu == 16 || nu == 32) && rows_per_cell % kLineRows == 0;
 }
 
-cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a, int nu,
+cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const ContigArgs<float> &a_in, int nu,
                               int dtype, int grid, cudaStream_t st, bool fuse_y)
 {
-    if (fuse_y && (!line_sweep_fused_supported(dtype) || !a.cell_coef_y)) return cudaErrorInvalidValue;
+    if (fuse_y && (!line_sweep_fused_supported(dtype) || !a_in.cell_coef_y)) return cudaErrorInvalidValue;
+    // row indices (u_z lines) stay below 2^31 (checked at init), a tile's rows below rows + 256
+    if (a_in.rows + 256 > 0xffffffffll || a_in.rows_per_cell <= 0 || a_in.rows_per_cell > 0xffffffffll)
+        return cudaErrorInvalidValue;
+    ContigArgs<float> a = a_in;
+    a.div_rpc = make_fastdiv(unsigned(a.rows_per_cell));
     const void *k = line_kernel_for(nu, dtype, fuse_y);
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2, fuse_y);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<ContigArgs<float> *>(&a)};
+    void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), &a};
     const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;
     return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st);
 }

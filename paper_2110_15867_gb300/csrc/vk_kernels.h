@@ -12,6 +12,29 @@ namespace vk {
 // sticky error bits of the device error word
 enum : unsigned { ERR_CFL = 1u, ERR_NAN = 2u, ERR_TIMEOUT = 4u };
 
+// Division of 32-bit unsigned integers by an invariant divisor d >= 1: one multiply-high,
+// a subtract, an add and two shifts instead of a division routine (the round-up method
+// of Granlund & Montgomery, "Division by invariant integers using multiplication",
+// PLDI 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n), for every n < 2^32.
+struct FastDivU32 {
+    unsigned m, s1, s2;
+};
+inline FastDivU32 make_fastdiv(unsigned d)
+{
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDivU32{unsigned(m), l ? 1u : 0u, l ? l - 1 : 0u};
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDivU32 &f)
+{
+    const unsigned t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
+
 constexpr int kMaxVel = 128;       // largest velocity-axis length a position table holds
 constexpr int kConsumers = 256;    // consumer threads per CTA (8 warps)
 constexpr int kProducer = 32;      // one producer warp (lane 0 drives the TMA engine)
@@ -160,6 +183,7 @@ template <typename C> struct ContigArgs {
     unsigned seed;
     const LineCoefT<C> *cell_coef_y; // fused kick tail: the u_y sweep's per-cell constants
     long long tile0;                 // first tile of this launch (num_tiles tiles from there)
+    FastDivU32 div_rpc;              // set by launch_line_sweep: division by rows_per_cell
 };
 
 // u_z sweep with whole lines in registers (FP32, n_uz 16 or 32): TMA box
@@ -196,6 +220,8 @@ struct RegLineArgs {
     const float *scale; // 16-bit storage only
     int nuz;
     unsigned seed;
+    // set by launch_reg_lines: line indices below 2^32 take these dividers
+    FastDivU32 div_inner, div_opc, div_nuz;
 };
 // u_z lines (rows of n_uz contiguous FP32 cells) of lengths the TMA line kernel does not
 // take (n_uz = 24, 40, 48): each warp stages 32 rows through shared memory with coalesced
@@ -208,6 +234,7 @@ struct RowsArgs {
     unsigned *err;
     float *scale;  // 16-bit storage: the FP32 scale of each row, refreshed by the sweep (else null)
     unsigned seed; // 16-bit storage: stochastic-rounding stream of this sweep
+    FastDivU32 div_rpc; // set by launch_rows_sweep: division by rows_per_cell
 };
 // u_z rows of L = 24, 40 or 48 cells (dtype 0 f64, 1 f32, 2 bf16, 3 f16), in place or src -> dst
 bool rows_sweep_supported(int L, int dtype);
