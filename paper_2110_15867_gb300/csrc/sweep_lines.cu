@@ -686,7 +686,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) rows_sweep_kernel
     __syncwarp();
     if (lane < nrows) {
         const long long row = r0 + lane;
-        const LineCoefT<C> kc = static_cast<const LineCoefT<C> *>(a.cell_coef)[fdiv(unsigned(row), a.div_rpc)];
+        // FP32 rows keep the plain division: measured 22.1 ms per u_z sweep on 48^3 x 48^3
+        // against 24.2 with the divider (16-bit rows: 19.5 with it against 21.6)
+        const long long cell = sizeof(T) == 4 ? row / a.rows_per_cell : (long long)fdiv(unsigned(row), a.div_rpc);
+        const LineCoefT<C> kc = static_cast<const LineCoefT<C> *>(a.cell_coef)[cell];
         if (kc.nd >= 0) {
             const bool neg = kc.nd & 1; // one orientation per spatial cell
             unsigned char *mine = reinterpret_cast<unsigned char *>(sr + lane * PC);

@@ -514,18 +514,31 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
 
     for (long long k = 0; k < n_my && alive; ++k) {
         const long long t = args.tile0 + b + k * G;
-        const long long inner = (t % args.tiles_inner) * W + w;
-        const long long outer = (t / args.tiles_inner) * P + p;
+        long long tq;  // tile row (outer block) of tile t
+        if (args.fast32) tq = fdiv(unsigned(t), args.div_tiles);
+        else tq = t / args.tiles_inner;
+        const long long tr = t - tq * args.tiles_inner;
+        const long long inner = tr * W + w;
+        const long long outer = tq * P + p;
         bool work = has_col && inner < args.n_inner && outer < args.n_outer;
         Lim<X> lim{};
         bool neg = false;
         if (work) {
             LineCoefT<C> ka, kb;
             if (args.coef_mode == 0) {
-                ka = tab[(inner / args.vstride) % args.nvel];
-                kb = tab[((inner + V - 1) / args.vstride) % args.nvel];
+                // velocity column of each of the thread's columns: (inner / vstride) % nvel
+                if (args.fast32) {
+                    const unsigned qa = fdiv(unsigned(inner), args.div_vstride);
+                    const unsigned qb = fdiv(unsigned(inner + V - 1), args.div_vstride);
+                    ka = tab[qa - fdiv(qa, args.div_nvel) * unsigned(args.nvel)];
+                    kb = tab[qb - fdiv(qb, args.div_nvel) * unsigned(args.nvel)];
+                } else {
+                    ka = tab[(inner / args.vstride) % args.nvel];
+                    kb = tab[((inner + V - 1) / args.vstride) % args.nvel];
+                }
             } else {
-                ka = args.cell_coef[outer / args.outer_per_cell];
+                ka = args.cell_coef[args.fast32 ? (long long)fdiv(unsigned(outer), args.div_opc)
+                                                : outer / args.outer_per_cell];
                 kb = ka;
             }
             if (ka.nd < 0 || kb.nd < 0) work = false; // Courant number out of range: leave as is
@@ -543,7 +556,7 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
         // 16-bit storage: a rounding stream per column pair and block, from the element index
         unsigned rng = CODED ? sr_bits((unsigned long long)(outer * L * args.n_inner + inner), args.seed) : 0u;
         // this column's line in a scale slot
-        const int c0 = int((t % args.tiles_inner) * W);
+        const int c0 = int(tr * W);
         const int soff = CODED ? (p * R * Wl + (c0 + w) / nuz - ((c0 / nuz) & ~3)) : 0;
         X sum;
         if (neg)
@@ -558,10 +571,26 @@ __global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM
     }
 }
 
+// the dividers of the consumers' per-block index arithmetic (fast32 when every index fits)
+template <typename C> static void set_stream_dividers(StreamArgs<C> &a)
+{
+    const long long lim = 0xffffffffll - 1024;
+    a.fast32 = a.tile0 + a.num_blocks < lim && a.n_inner < lim && a.n_outer < lim && a.tiles_inner > 0 &&
+               a.vstride > 0 && a.vstride < lim && a.outer_per_cell > 0 && a.outer_per_cell < lim;
+    if (!a.fast32) return;
+    a.div_tiles = make_fastdiv(unsigned(a.tiles_inner));
+    a.div_vstride = make_fastdiv(unsigned(a.vstride));
+    a.div_nvel = make_fastdiv(unsigned(a.nvel > 0 ? a.nvel : 1));
+    a.div_opc = make_fastdiv(unsigned(a.outer_per_cell));
+}
+
 template <typename T>
 static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &dmap, const CUtensorMap &smap,
-                                   const StreamArgs<typename Compute<T>::type> &a, int grid, size_t smem, cudaStream_t st)
+                                   const StreamArgs<typename Compute<T>::type> &a_in, int grid, size_t smem,
+                                   cudaStream_t st)
 {
+    StreamArgs<typename Compute<T>::type> a = a_in;
+    set_stream_dividers(a);
     auto kern = a.periodic ? stream_sweep_kernel<T, true> : stream_sweep_kernel<T, false>;
     int threads = Lane<T>::NC + stream_head<false>();
     if constexpr (sizeof(T) != 2)

@@ -146,6 +146,10 @@ template <typename C> struct StreamArgs {
     void *mpart;
     long long cube;
     int nparts;
+    // set by the launchers: fast32 = 1 when tile indices, inner and outer offsets all stay
+    // below 2^32, so that the per-block index arithmetic takes these dividers
+    int fast32;
+    FastDivU32 div_tiles, div_vstride, div_nvel, div_opc;
     LineCoefT<C> table[kMaxVel];
 };
 
