@@ -569,6 +569,13 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
 // ----------------------------------------------------------------------------
 // kernels
 // ----------------------------------------------------------------------------
+// n / d by the launch's invariant divider when every index fits 32 bits
+template <typename C>
+__device__ __forceinline__ long long adj_div(long long n, const AdjArgs<C> &a, const FastDivU32 &fd, long long d)
+{
+    return a.fast32 ? (long long)fdiv(unsigned(n), fd) : n / d;
+}
+
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
 template <typename T, bool PERIODIC, bool SMALL4, int LCT>
@@ -587,8 +594,14 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2
     long long cell = -1;
     C dnu = C(0);
     if (t < a.nlines) {
-        const long long outer = t / a.n_inner, inner = t - outer * a.n_inner;
-        const LineCoefT<C> kc = a.coef_mode == 0 ? a.table[(inner / a.vstride) % a.nvel] : a.cell_coef[outer / a.outer_per_cell];
+        const long long outer = adj_div(t, a, a.div_inner, a.n_inner), inner = t - outer * a.n_inner;
+        LineCoefT<C> kc;
+        if (a.coef_mode == 0) {
+            const long long q = adj_div(inner, a, a.div_vstride, a.vstride);
+            kc = a.table[q - adj_div(q, a, a.div_nvel, a.nvel) * a.nvel];
+        } else {
+            kc = a.cell_coef[adj_div(outer, a, a.div_opc, a.outer_per_cell)];
+        }
         const long long base = outer * a.L * a.n_inner + inner;
         const T *f = static_cast<const T *>(a.f_in) + base;
         const T *lin = static_cast<const T *>(a.lam_in) + base;
@@ -627,7 +640,7 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = neg ? -dLds : dLds;
         }
-        cell = a.dLdg ? t / a.lines_per_cell : -1;
+        cell = a.dLdg ? adj_div(t, a, a.div_lpc, a.lines_per_cell) : -1;
     }
     if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
@@ -666,7 +679,7 @@ __global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid
     long long cell = -1;
     C dnu = C(0);
     if (t < a.nlines) {
-        const LineCoefT<C> kc = a.cell_coef[t / a.outer_per_cell];
+        const LineCoefT<C> kc = a.cell_coef[adj_div(t, a, a.div_opc, a.outer_per_cell)];
         const uint4 *fp = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.f_in) + t * L);
         const uint4 *lp = reinterpret_cast<const uint4 *>(static_cast<const T *>(a.lam_in) + t * L);
         uint4 *op = reinterpret_cast<uint4 *>(static_cast<T *>(a.lam_out) + t * L);
@@ -682,7 +695,7 @@ __global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = (kc.nd & 1) ? -dLds : dLds;
         }
-        cell = a.dLdg ? t / a.lines_per_cell : -1;
+        cell = a.dLdg ? adj_div(t, a, a.div_lpc, a.lines_per_cell) : -1;
     }
     if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
@@ -723,7 +736,7 @@ __global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_staged_kernel(const
     long long cell = -1;
     C dnu = C(0);
     if (lane < nrows) {
-        const LineCoefT<C> kc = a.cell_coef[t / a.outer_per_cell];
+        const LineCoefT<C> kc = a.cell_coef[adj_div(t, a, a.div_opc, a.outer_per_cell)];
         if (kc.nd >= 0 && (kc.nd >> 1) == 0) {
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
@@ -749,7 +762,7 @@ __global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_staged_kernel(const
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = neg ? -dLds : dLds;
         }
-        cell = a.dLdg ? t / a.lines_per_cell : -1;
+        cell = a.dLdg ? adj_div(t, a, a.div_lpc, a.lines_per_cell) : -1;
     }
     __syncwarp();
     // lambda rows out (rows left unchanged by the forward pass through as loaded)
@@ -807,8 +820,19 @@ template <typename T, int L> static cudaError_t launch_rows(const AdjArgs<T> &a,
     return cudaGetLastError();
 }
 
-template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a, bool rows, cudaStream_t st)
+template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a_in, bool rows, cudaStream_t st)
 {
+    AdjArgs<T> a = a_in;
+    const long long lim = 0xffffffffll - 2 * kAdjBlock;
+    a.fast32 = a.nlines < lim && a.n_inner > 0 && a.n_inner < lim && a.vstride > 0 && a.vstride < lim &&
+               a.outer_per_cell > 0 && a.outer_per_cell < lim && a.lines_per_cell >= 0 && a.lines_per_cell < lim;
+    if (a.fast32) {
+        a.div_inner = make_fastdiv(unsigned(a.n_inner));
+        a.div_vstride = make_fastdiv(unsigned(a.vstride));
+        a.div_nvel = make_fastdiv(unsigned(a.nvel > 0 ? a.nvel : 1));
+        a.div_opc = make_fastdiv(unsigned(a.outer_per_cell));
+        a.div_lpc = make_fastdiv(unsigned(a.lines_per_cell > 0 ? a.lines_per_cell : 1));
+    }
     const long long blocks = (a.nlines + kAdjBlock - 1) / kAdjBlock;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;

@@ -287,6 +287,9 @@ template <typename C> struct AdjArgs {
     int perm_line;            // > 0 (z sweep): the Courant number changes sign in the middle of each u_z
                               // line of this length; a block's first half of threads takes the u_z < 0
                               // halves of its lines and the second half the rest (whole warps of one sign)
+    // set by the launchers: fast32 = 1 when line indices and divisors fit 32 bits
+    int fast32;
+    FastDivU32 div_inner, div_vstride, div_nvel, div_opc, div_lpc;
     LineCoefT<C> table[kMaxVel];
 };
 
