@@ -55,18 +55,24 @@ typedef struct vlasov_ctx vlasov_ctx; /* opaque, owned by the library */
 
 typedef struct {
     int nx, ny, nz;    /* spatial cells (each >= 4, <= 256)                    */
-    int nux, nuy, nuz; /* velocity cells (each >= 4, <= 256, multiple of 4)    */
+    int nux, nuy, nuz; /* velocity cells (each >= 4, <= 128, multiple of 4)    */
     double L;          /* box side                                              */
     double V;          /* velocity half-extent: -V <= u < V                     */
-    int dtype;         /* VLASOV_F64 / F32 (BF16 / F16 reserved for the codec)  */
+    int dtype;         /* VLASOV_F64 / F32 / BF16 / F16 (storage type of f)     */
 } vlasov_grid;
 
 /*
  * Create a context for the grid g and the caller's distribution function
  * f_dev (nx*ny*nz*nux*nuy*nuz elements of g->dtype, 16-byte aligned).
- * scale_dev must be NULL for F64/F32.  stream is a cudaStream_t (NULL = the
+ * scale_dev must be NULL for F64/F32.  BF16 / F16 storage (the 16-bit codec):
+ * f holds codes, value = code x the FP32 scale of its u_z line; scale_dev holds
+ * nx*ny*nz*nux*nuy floats (16-byte aligned, caller-owned), refreshed by every
+ * u_z sweep to the line's largest value (BF16: at least 2^-64); nuz must be 16
+ * or 32 with nux*nuy a multiple of 256, or 24, 40 or 48; arithmetic is FP32 and
+ * every encode rounds stochastically.  stream is a cudaStream_t (NULL = the
  * legacy default stream).  Allocates the library's scratch on the current
- * device.  On success *out receives the context.
+ * device.  On success *out receives the context.  Errors: VLASOV_EINVAL for a
+ * grid outside these limits or a misaligned / missing / unexpected pointer.
  */
 int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev,
                 void *stream);
