@@ -360,3 +360,105 @@ def test_step_conserves_mass_and_self_consistency():
     assert abs(m1 - m0) < 1e-13 * m0
     assert f.min() >= 0.0
     assert np.allclose(phi1, O.poisson(g, rho1 + bg, 0.55, 1.0), atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# the kicks of one step, Eq. (5): half steps, phi^n first, phi^{n+1} second
+# ---------------------------------------------------------------------------
+# Setup shared by the two pins below: 8 x 2 x 2 spatial cells with f and phi
+# uniform along y and z (every y and z line is uniform, so D_y, D_z, D_uy and D_uz
+# leave f unchanged bit for bit), 8^3 velocity cells with V = 4 (du = 1, u_j =
+# j - 7/2), dyadic data.  dt and a_half make every x-drift Courant number
+# u_j dt / (a_half^2 dx) a whole number of cells, so the drift of Eq. (3) is an
+# exact translation.  phi is zero except at cells i0 - 1 and i0 + 1 and is chosen
+# so that the periodic 4th-order gradient at i0 is a dyadic number: the kick
+# Courant number -g (dt / 2) / du there is a whole number N, and Eq. (4) moves that
+# cell's velocity cube by exactly N cells along u_x per kick.  The two outer
+# neighbours i0 -+ 2 of i0 + 4 carry no potential either, so that cell's kick is
+# the identity.
+
+def _kick_pin_setup(a_levels):
+    n, nu, V = (8, 2, 2), 8, 4.0
+    g = O.grid(n, nu, V=V)
+    rng = np.random.default_rng(21)
+    prof = np.zeros((nu, nu, nu))
+    # compact along u_x (j_x = 1, 2: room for shifts of up to 3 cells before the edge),
+    # multiples of 1/16 in [1/2, 2): every difference and sum of the exact shifts is exact
+    prof[1:3] = rng.integers(8, 32, size=(2, nu, nu)) / 16.0
+    f = np.empty(n + (nu, nu, nu))
+    for ix in range(n[0]):
+        f[ix] = a_levels[ix] * prof
+    return g, f, prof
+
+
+def _phi_with_gradient_at(n, i0, ghalf):
+    # phi along x only, nonzero at i0 -+ 1, such that the 4th-order central difference
+    # [8 (phi_{i+1} - phi_{i-1}) - (phi_{i+2} - phi_{i-2})] / (12 dx) at i0 equals ghalf
+    # (dx = 1/8, so 12 dx = 3/2 and the two values are +- 3 ghalf / 32)
+    phi = np.zeros(n)
+    phi[(i0 + 1) % n[0]] = 3.0 * ghalf / 32.0
+    phi[(i0 - 1) % n[0]] = -3.0 * ghalf / 32.0
+    return phi
+
+
+def test_step_kicks_are_half_steps_with_phi_n():
+    # Eq. (5) with an external potential: D_u(dt/2) D_x(dt) D_u(dt/2), both kicks with
+    # phi.  dt / a_half^2 = 2 makes the x-drift Courant numbers 16 u_j = 8 (2 j - 7):
+    # whole periods of the 8-cell line, so the drift is the identity.  With g = -1/4 at
+    # cell 2 each half kick has nu = -g (dt / 2) / du = 1: the cube moves by exactly
+    # 2 cells along u_x over the step (a kick of dt would move it by 4).  Cell 6 feels
+    # no force and must come back bit for bit.  a_full = 3 is unused here (an x drift
+    # at a_full would not be a whole-period translation).
+    g, f, prof = _kick_pin_setup([1.0] * 8)
+    n = (8, 2, 2)
+    phi = _phi_with_gradient_at(n, 2, -0.25)
+    dt, a_half, a_full = 8.0, 2.0, 3.0
+    assert O.gradient(g, phi, 0)[2, 0, 0] == -0.25
+    O.step(g, f, dt, a_half, a_full, phi)
+    want = np.zeros_like(prof)
+    want[3:5] = prof[1:3]
+    for iy in range(2):
+        for iz in range(2):
+            assert np.array_equal(f[2, iy, iz], want)
+            assert np.array_equal(f[6, iy, iz], prof)
+
+
+def test_step_second_kick_uses_post_drift_potential():
+    # Eq. (5), self-consistent: the first kick uses phi^n, the drift runs at a_half,
+    # the density rho_nu of the drifted f plus rho_bg gives phi^{n+1} through Eq. (2)
+    # at a_full, and the second kick uses phi^{n+1}.  dt / a_half^2 = 1 makes the x
+    # drift a translation by half the box (Courant numbers 8 u_j = 4 (2 j - 7)), so
+    # the drifted density differs from the initial one (the two halves of the box
+    # hold f at levels 1 and 3/2).  phi^n gives nu = 1 at cell 2 (g = -1/2, dt / 2
+    # = 2).  rho_bg is chosen so that phi^{n+1} = phi_T exactly when the density of
+    # the drifted f is used: Laplacian(phi_T) / (4 pi G a_full^2) minus that density.
+    # phi_T gives nu = 2 at cell 6.  Cell 2's cube, kicked by 1, lands on cell 6 and
+    # is kicked by 2: 3 cells in all.  phi^n for the second kick would give 1 + 0,
+    # the pre-drift density a phi^{n+1} whose nu at cell 6 is not 2, a kick of dt
+    # 2 + 4; each fails this check.
+    levels = [1.0] * 4 + [1.5] * 4
+    g, f, prof = _kick_pin_setup(levels)
+    n = (8, 2, 2)
+    dt, a_half, a_full, G4 = 4.0, 2.0, 0.75, 1.0
+    phi_n = _phi_with_gradient_at(n, 2, -0.5)
+    phi_T = _phi_with_gradient_at(n, 6, -1.0)
+    du3 = 1.0
+    # density of the drifted f: the initial density translated by 4 cells along x
+    # (each kick keeps every cell's mass: its velocity faces carry no flux)
+    rho0 = np.array([levels[ix] * prof.sum() * du3 for ix in range(8)])
+    rho_post = np.roll(rho0, 4)[:, None, None] * np.ones(n)
+    kx = 2 * np.pi * np.fft.fftfreq(8) * 8
+    lap = np.real(np.fft.ifftn(-(kx ** 2)[:, None, None] * np.fft.fftn(phi_T)))
+    rho_bg = lap / (G4 * a_full ** 2) - rho_post
+    phi_next, rho_nu = O.step(g, f, dt, a_half, a_full, phi_n, rho_bg=rho_bg, four_pi_G=G4,
+                              self_consistent=True)
+    assert np.allclose(rho_nu, rho_post, rtol=1e-14, atol=0)
+    assert np.abs(phi_next - phi_T).max() < 1e-14
+    want6 = np.zeros_like(prof)
+    want6[4:6] = levels[2] * prof[1:3]
+    for iy in range(2):
+        for iz in range(2):
+            assert np.abs(f[6, iy, iz] - want6).max() < 1e-12
+            # cell 2 holds cell 6's cube, which neither kick moves (no force at 6 from
+            # phi^n, none at 2 from phi_T)
+            assert np.abs(f[2, iy, iz] - levels[6] * prof).max() < 1e-12
