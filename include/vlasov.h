@@ -104,6 +104,34 @@ int vlasov_set_f(vlasov_ctx *ctx, void *f_dev, float *scale_dev);
 int vlasov_sweep(vlasov_ctx *ctx, int axis, double dt, double a, const float *phi_dev);
 
 /*
+ * The 16-bit storage codec, for getting a distribution function into and out of
+ * BF16 / FP16 storage (vlasov_init with VLASOV_BF16 or VLASOV_F16).  The paper
+ * keeps f in FP32 (Sec. 5.1); this storage and its codec are the library's own.
+ * Both calls work on nlines u_z lines of nuz values each (1 <= nuz <= 128), laid
+ * out one line after another (a whole grid is nx*ny*nz*nux*nuy lines of nuz; a
+ * slab of x-planes is a contiguous part of it); they need no context, allocate
+ * nothing and queue one kernel on stream (a cudaStream_t, NULL = legacy default).
+ *
+ * vlasov_encode: src_dev holds the values (src_dtype VLASOV_F64 or VLASOV_F32).
+ * For each line, with w_k = v_k rounded to FP32 (to nearest even):
+ *   scale_dev[line] = s = max(max_k w_k, 0), for BF16 codes at least 2^-64 (the
+ *                     floor the sweeps keep on every scale refresh),
+ *   codes_dev[line * nuz + k] = w_k / s (IEEE FP32 quotient) rounded to nearest
+ *                     even in code_dtype (VLASOV_BF16 or VLASOV_F16); 0 where s = 0.
+ * The values of a distribution function are non-negative, so codes lie in [0, 1].
+ * vlasov_decode: dst_dev[line * nuz + k] = code x scale, exact for
+ * dst_dtype = VLASOV_F64, rounded to nearest even for VLASOV_F32.
+ * Every pointer is a device pointer aligned to its element size; the caller owns
+ * all of them.  Errors (VLASOV_EINVAL for sizes, types, null or misaligned
+ * pointers; VLASOV_ECUDA for a failed launch) are returned with the message in
+ * vlasov_last_error(NULL).
+ */
+int vlasov_encode(long long nlines, int nuz, const void *src_dev, int src_dtype, void *codes_dev, int code_dtype,
+                  float *scale_dev, void *stream);
+int vlasov_decode(long long nlines, int nuz, const void *codes_dev, int code_dtype, const float *scale_dev,
+                  void *dst_dev, int dst_dtype, void *stream);
+
+/*
  * Kicks of vlasov_step (D_uz D_uy D_ux, Eq. 5) on FP32 storage with n_uy = n_uz
  * = 16 or 32 run D_uy and D_uz in one pass over f: each u_z tile of 256 rows
  * holds whole (cell, j_x) planes, whose columns are the u_y lines, so D_uy runs
@@ -246,11 +274,13 @@ int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nki
  * static device array built into the library, VLASOV_STATIC_MAX_CELLS spatial
  * cells in size (about 1.2 MB, held on every GPU that loads the library until
  * the process exits).  Grids with more spatial cells are rejected with
- * VLASOV_EINVAL.  The first call on a device looks up the array's device
- * address (once per device, with that device current); make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's contents: calls that may overlap on the GPU (different streams,
- * different host threads) race and must be serialised by the caller.
+ * VLASOV_EINVAL.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress), so the address stays right after a
+ * cudaDeviceReset; the first call on a device loads the library's kernels
+ * there, so make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents: calls that may overlap
+ * on the GPU (different streams, different host threads) race and must be
+ * serialised by the caller.
  *
  *   g        grid (dtype must be VLASOV_F32); f_dev as for vlasov_init
  *   axis     3, 4 or 5; dt, phi_dev as for vlasov_sweep

@@ -46,7 +46,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
-           "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host")
+           "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host", "vlasov_encode", "vlasov_decode")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -134,6 +134,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_host.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP,
                                    ctypes.c_double, _VP, _VP]
     L.vlasov_step_host.restype = ctypes.c_int
+    L.vlasov_encode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP]
+    L.vlasov_encode.restype = ctypes.c_int
+    L.vlasov_decode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]
+    L.vlasov_decode.restype = ctypes.c_int
     L.vlasov_last_error.argtypes = [_VP]
     L.vlasov_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -298,25 +302,66 @@ def _ptr(t):
     return None if t is None else t.data_ptr()
 
 
-def encode_lines(f, dtype):
-    """Storage of f for the 16-bit codec: one FP32 scale per u_z line (the line's
-    largest value; BF16 at least 2^-64, as the sweeps' refresh keeps it, so that an
-    empty line can take in mass) and the codes f / scale rounded to `dtype`
-    (torch.bfloat16 or torch.float16).  f: 6D torch tensor (any device); returns
-    (codes, scale)."""
-    import torch
-    scale = f.amax(dim=-1).to(torch.float32)
-    if dtype == torch.bfloat16:
-        scale = scale.clamp(min=2.0 ** -64)
-    inv = torch.where(scale > 0, 1.0 / scale.to(f.dtype), torch.zeros_like(scale, dtype=f.dtype))
-    codes = (f * inv[..., None]).to(dtype)
-    return codes.contiguous(), scale.contiguous()
+def vlasov_encode(nlines: int, nuz: int, src_ptr, src_dtype: int, codes_ptr, code_dtype: int, scale_ptr,
+                  stream: int):
+    return _check(None, load().vlasov_encode(nlines, nuz, src_ptr, src_dtype, codes_ptr, code_dtype, scale_ptr,
+                                             stream))
 
 
-def decode_lines(codes, scale):
-    """Values held by a 16-bit codec array (FP64, same device)."""
+def vlasov_decode(nlines: int, nuz: int, codes_ptr, code_dtype: int, scale_ptr, dst_ptr, dst_dtype: int,
+                  stream: int):
+    return _check(None, load().vlasov_decode(nlines, nuz, codes_ptr, code_dtype, scale_ptr, dst_ptr, dst_dtype,
+                                             stream))
+
+
+def _dtype_codes():
     import torch
-    return codes.to(torch.float64) * scale.to(torch.float64)[..., None]
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+
+
+def encode_lines(f, dtype, codes=None, scale=None):
+    """16-bit storage of the CUDA tensor f (FP64 or FP32, contiguous, last axis = the u_z
+    line) through vlasov_encode: returns (codes of `dtype`, torch.bfloat16 or
+    torch.float16, shaped like f; scale, float32, f.shape[:-1]).  codes / scale may be
+    given to be filled in place."""
+    import torch
+    kinds = _dtype_codes()
+    if not f.is_cuda or not f.is_contiguous() or kinds.get(f.dtype) not in (F64, F32):
+        raise ValueError("f must be a contiguous float64 or float32 CUDA tensor")
+    if kinds.get(dtype) not in (BF16, F16):
+        raise ValueError("dtype must be torch.bfloat16 or torch.float16")
+    if codes is None:
+        codes = torch.empty(f.shape, dtype=dtype, device=f.device)
+    if scale is None:
+        scale = torch.empty(f.shape[:-1], dtype=torch.float32, device=f.device)
+    if codes.dtype != dtype or tuple(codes.shape) != tuple(f.shape) or not codes.is_contiguous() or \
+            scale.dtype != torch.float32 or tuple(scale.shape) != tuple(f.shape[:-1]) or not scale.is_contiguous():
+        raise ValueError("codes / scale do not match f")
+    nuz = f.shape[-1]
+    with torch.cuda.device(f.device):
+        vlasov_encode(f.numel() // nuz, nuz, f.data_ptr(), kinds[f.dtype], codes.data_ptr(), kinds[dtype],
+                      scale.data_ptr(), torch.cuda.current_stream(f.device).cuda_stream)
+    return codes, scale
+
+
+def decode_lines(codes, scale, dtype=None):
+    """Values held by a 16-bit codec array (code x scale, through vlasov_decode): a CUDA
+    tensor of `dtype` (torch.float64, exact, by default; or torch.float32)."""
+    import torch
+    kinds = _dtype_codes()
+    dtype = torch.float64 if dtype is None else dtype
+    if not codes.is_cuda or not codes.is_contiguous() or kinds.get(codes.dtype) not in (BF16, F16):
+        raise ValueError("codes must be a contiguous bfloat16 or float16 CUDA tensor")
+    if scale.dtype != torch.float32 or tuple(scale.shape) != tuple(codes.shape[:-1]) or not scale.is_contiguous():
+        raise ValueError("scale must be a contiguous float32 tensor of shape codes.shape[:-1]")
+    if kinds.get(dtype) not in (F64, F32):
+        raise ValueError("dtype must be torch.float64 or torch.float32")
+    out = torch.empty(codes.shape, dtype=dtype, device=codes.device)
+    nuz = codes.shape[-1]
+    with torch.cuda.device(codes.device):
+        vlasov_decode(codes.numel() // nuz, nuz, codes.data_ptr(), kinds[codes.dtype], scale.data_ptr(),
+                      out.data_ptr(), kinds[dtype], torch.cuda.current_stream(codes.device).cuda_stream)
+    return out
 
 
 class Vlasov:

@@ -324,6 +324,12 @@ cudaError_t launch_moment_adjoint(const GridDims &g, const double *dLdrho, int d
                                   cudaStream_t st, int sm_count);
 // y += x (or y = x when assign), FP64, n values
 cudaError_t launch_add(long long n, const double *x, double *y, bool assign, cudaStream_t st);
+// 16-bit storage codec over nlines u_z lines of nuz values (codec.cu): src / dst FP64 or
+// FP32 (dtype 0 / 1), codes BF16 or FP16 (code_dtype 2 / 3), one FP32 scale per line
+cudaError_t launch_encode(long long nlines, int nuz, const void *src, int src_dtype, void *codes, int code_dtype,
+                          float *scale, cudaStream_t st, int sm_count);
+cudaError_t launch_decode(long long nlines, int nuz, const void *codes, int code_dtype, const float *scale, void *dst,
+                          int dst_dtype, cudaStream_t st, int sm_count);
 // mass = dx dy dz * sum rho (FP64, compensated) written to out (device)
 cudaError_t launch_mass(const GridDims &g, const double *rho, double *out, cudaStream_t st);
 

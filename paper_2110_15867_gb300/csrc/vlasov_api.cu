@@ -218,7 +218,9 @@ static CUtensorMapDataType tmap_type(int dtype)
     }
 }
 
-static int plan_axes(vlasov_ctx *c)
+// Plan the sweeps of the axes whose bits are set in mask (all six by default): tensor
+// maps, tile geometry and launch grids.
+static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return fail(c, VLASOV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -228,6 +230,7 @@ static int plan_axes(vlasov_ctx *c)
     const bool coded = c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16;
     // whole-line kernels (whole-cell shifts, u_z lines of other lengths): FP32 / FP64 only
     for (int ax = 0; ax < 6 && !coded; ++ax) {
+        if (!(mask >> ax & 1)) continue;
         AxisPlan &p = c->plan[ax];
         p.L = int(d6[ax]);
         long long I = 1, O = 1;
@@ -290,6 +293,7 @@ static int plan_axes(vlasov_ctx *c)
     const int V = stream_columns_per_thread(c->g.dtype); // columns per consumer thread
     const int cols = V * stream_consumers(c->g.dtype);
     for (int ax = 0; ax < 5; ++ax) {
+        if (!(mask >> ax & 1)) continue;
         AxisPlan &p = c->splan[ax];
         p.L = int(d6[ax]);
         long long I = 1, O = 1;
@@ -368,7 +372,8 @@ static int plan_axes(vlasov_ctx *c)
         c->splan_tpp[ax] = (p.n_outer % c->g.nx == 0 && opp % P == 0) ? (opp / P) * p.tiles_inner : 0;
     }
     // u_z: register lines when a line is 32, 64 or 128 bytes (FP32 / 16-bit, n_uz 16 or 32)
-    c->use_lines = c->g.dtype != VLASOV_F64 && line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
+    c->use_lines = (mask >> 5 & 1) && c->g.dtype != VLASOV_F64 &&
+                   line_sweep_supported(c->g.nuz, (long long)c->g.nux * c->g.nuy);
     if (c->use_lines) {
         const int nu = c->g.nuz, rpt = line_sweep_rows_per_tile();
         c->lrows = c->ncell * c->g.nux * c->g.nuy;
@@ -386,7 +391,8 @@ static int plan_axes(vlasov_ctx *c)
         const long long rpp = c->lrows / c->g.nx; // u_z rows per x-plane
         c->ltpp = rpp % rpt == 0 ? rpp / rpt : 0;
     }
-    c->can_fuse_kick = c->use_lines && line_sweep_fused_supported(c->g.dtype) && c->g.nuy == c->g.nuz;
+    c->can_fuse_kick = c->use_lines && (mask >> 4 & 1) && line_sweep_fused_supported(c->g.dtype) &&
+                       c->g.nuy == c->g.nuz;
     if (c->can_fuse_kick) {
         const int occ = occupancy_line_sweep(c->g.nuz, c->g.dtype, true);
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "fused kick CTA does not fit");
@@ -1539,21 +1545,15 @@ constexpr size_t kStaticHeader = 256;
 constexpr size_t kStaticBytes = kStaticHeader + (size_t)VLASOV_STATIC_MAX_CELLS * sizeof(LineCoefT<float>);
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-// Device address of g_static_scratch on device `dev` (looked up once per device).
-static cudaError_t static_scratch_address(int dev, unsigned char **out)
+// Device address of g_static_scratch in the current device's context.  It is looked up
+// on every call (a table lookup once the module is loaded): an address kept from an
+// earlier call would be stale after a cudaDeviceReset, which unloads the module.
+static cudaError_t static_scratch_address(unsigned char **out)
 {
-    constexpr int kMaxDevices = 64;
-    static std::mutex m;
-    static unsigned char *addr[kMaxDevices] = {};
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(m);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
@@ -1578,11 +1578,13 @@ extern "C" int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, 
                     "vlasov_sweep_velocity_static: %lld spatial cells exceed the static scratch (%d cells)", ncell,
                     VLASOV_STATIC_MAX_CELLS);
     if (ncell * g->nux * g->nuy >= (1ll << 31)) return fail(nullptr, VLASOV_EINVAL, "too many u_z lines for 32-bit TMA coordinates");
+    if (ncell * ((long long)g->nux * g->nuy * g->nuz) / g->nx >= (1ll << 32))
+        return fail(nullptr, VLASOV_EINVAL, "grid too large for 32-bit TMA extents");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     unsigned char *scratch = nullptr;
-    if (e == cudaSuccess) e = static_scratch_address(dev, &scratch);
+    if (e == cudaSuccess) e = static_scratch_address(&scratch);
     if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "static scratch lookup: %s", cudaGetErrorString(e));
 
     // A context on the stack: the plan and the launch helpers need no allocation.
@@ -1598,7 +1600,7 @@ extern "C" int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, 
     c.gd.V = g->V;
     e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "device query: %s", cudaGetErrorString(e));
-    int rc = plan_axes(&c);
+    int rc = plan_axes(&c, 1 << axis); // the swept axis only
     if (rc != VLASOV_OK) return fail(nullptr, rc, "%s", c.msg);
 
     unsigned *err = status_dev;
@@ -1614,5 +1616,62 @@ extern "C" int vlasov_sweep_velocity_static(const vlasov_grid *g, float *f_dev, 
     rc = prep_velocity(&c, phi_dev, dt, 1 << (axis - 3));
     if (rc == VLASOV_OK) rc = run_velocity(&c, axis);
     if (rc != VLASOV_OK) return fail(nullptr, rc, "%s", c.msg);
+    return VLASOV_OK;
+}
+
+// ----------------------------------------------------------------------------
+// 16-bit storage codec (vlasov_encode / vlasov_decode)
+// ----------------------------------------------------------------------------
+
+static int codec_args(long long nlines, int nuz, const void *vals, int vdtype, const void *codes, int cdtype,
+                      const float *scale, const char *who)
+{
+    if (nlines < 0 || nuz < 1 || nuz > kMaxVel)
+        return fail(nullptr, VLASOV_EINVAL, "%s: need nlines >= 0 and 1 <= nuz <= %d", who, kMaxVel);
+    if (vdtype != VLASOV_F64 && vdtype != VLASOV_F32)
+        return fail(nullptr, VLASOV_EINVAL, "%s: values must be VLASOV_F64 or VLASOV_F32", who);
+    if (cdtype != VLASOV_BF16 && cdtype != VLASOV_F16)
+        return fail(nullptr, VLASOV_EINVAL, "%s: codes must be VLASOV_BF16 or VLASOV_F16", who);
+    if (nlines == 0) return VLASOV_OK;
+    if (!vals || !codes || !scale) return fail(nullptr, VLASOV_EINVAL, "%s: null pointer", who);
+    const uintptr_t va = reinterpret_cast<uintptr_t>(vals), ca = reinterpret_cast<uintptr_t>(codes),
+                    sa = reinterpret_cast<uintptr_t>(scale);
+    if (va % (vdtype == VLASOV_F64 ? 8 : 4) || ca % 2 || sa % 4)
+        return fail(nullptr, VLASOV_EINVAL, "%s: a pointer is not aligned to its element size", who);
+    return VLASOV_OK;
+}
+
+static int current_sm_count(int *sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_encode(long long nlines, int nuz, const void *src_dev, int src_dtype, void *codes_dev,
+                             int code_dtype, float *scale_dev, void *stream)
+{
+    int rc = codec_args(nlines, nuz, src_dev, src_dtype, codes_dev, code_dtype, scale_dev, "vlasov_encode");
+    if (rc != VLASOV_OK || nlines == 0) return rc;
+    int sm = 0;
+    if ((rc = current_sm_count(&sm))) return rc;
+    const cudaError_t e = launch_encode(nlines, nuz, src_dev, src_dtype == VLASOV_F64 ? 0 : 1, codes_dev, code_dtype,
+                                        scale_dev, (cudaStream_t)stream, sm);
+    if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "encode launch: %s", cudaGetErrorString(e));
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_decode(long long nlines, int nuz, const void *codes_dev, int code_dtype, const float *scale_dev,
+                             void *dst_dev, int dst_dtype, void *stream)
+{
+    int rc = codec_args(nlines, nuz, dst_dev, dst_dtype, codes_dev, code_dtype, scale_dev, "vlasov_decode");
+    if (rc != VLASOV_OK || nlines == 0) return rc;
+    int sm = 0;
+    if ((rc = current_sm_count(&sm))) return rc;
+    const cudaError_t e = launch_decode(nlines, nuz, codes_dev, code_dtype, scale_dev, dst_dev,
+                                        dst_dtype == VLASOV_F64 ? 0 : 1, (cudaStream_t)stream, sm);
+    if (e != cudaSuccess) return fail(nullptr, VLASOV_ECUDA, "decode launch: %s", cudaGetErrorString(e));
     return VLASOV_OK;
 }

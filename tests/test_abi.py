@@ -60,3 +60,24 @@ def test_init_rejects_empty_and_degenerate_grids(field, value):
     with pytest.raises(B.VlasovError) as e:
         B.vlasov_init(g, 16, None, 0)
     assert e.value.code == B.EINVAL
+
+
+def test_codec_rejects_bad_arguments_without_touching_the_gpu():
+    # vlasov_encode / vlasov_decode check sizes, types and pointers on the host first;
+    # nothing to do (zero lines) returns at once
+    from paper_2110_15867_gb300 import binding as B
+    B.load(build_if_missing=True)
+    bad = [(4, 0, 16, B.F64, 16, B.BF16, 16), (4, 129, 16, B.F64, 16, B.BF16, 16),
+           (-1, 16, 16, B.F64, 16, B.BF16, 16), (4, 16, 16, B.BF16, 16, B.BF16, 16),
+           (4, 16, 16, B.F64, 16, B.F32, 16), (4, 16, None, B.F64, 16, B.BF16, 16),
+           (4, 16, 12, B.F64, 16, B.BF16, 16), (4, 16, 16, B.F32, 17, B.F16, 16),
+           (4, 16, 16, B.F32, 16, B.F16, 18)]
+    for nl, nuz, src, sdt, codes, cdt, scale in bad:
+        with pytest.raises(B.VlasovError) as e:
+            B.vlasov_encode(nl, nuz, src, sdt, codes, cdt, scale, 0)
+        assert e.value.code == B.EINVAL
+        with pytest.raises(B.VlasovError) as e:
+            B.vlasov_decode(nl, nuz, codes, cdt, scale, src, sdt, 0)
+        assert e.value.code == B.EINVAL
+    assert B.vlasov_encode(0, 16, None, B.F64, None, B.BF16, None, 0) == B.OK
+    assert B.vlasov_decode(0, 16, None, B.BF16, None, None, B.F32, 0) == B.OK

@@ -61,9 +61,8 @@ def test_large_run_50_self_consistent_steps(fmt):
         f = torch.empty((n, n, n, nu, nu, nu), dtype=torch.bfloat16, device="cuda")
         scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device="cuda")
         for ix in range(n):
-            c, s = B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], torch.bfloat16)
-            f[ix] = c
-            scale[ix] = s
+            B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], torch.bfloat16,
+                           codes=f[ix], scale=scale[ix])
     du = 2.0 * V / nu
     rho_bar = float(Fu.sum().item()) * du ** 3
     dc = torch.from_numpy(I.gaussian_field(n, cfg["cdm_rms"], seed=cfg["seed"] + 1)).cuda()
