@@ -36,15 +36,15 @@ if ROOT not in sys.path:
 METRIC = "6D cell-updates/s per sweep"
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-# ALU-bound roofline (the fused kick tail): min / max operations one cell update of
-# SL-MPP5 needs with 3-input min / max -- limited curvature 6 (min and max of four,
-# median with 0), MP clamp 6 (four bounds, max(fbar, A, B), min(., C, D)), positivity 2 --
-# against the ALU pipe: 152 SMs x 4 schedulers x 16 lanes per clock at 2070 MHz
-ALU_OPS_PER_UPDATE = 14
-ALU_PEAK_TOPS = 152 * 64 * 2.070e9 / 1e12
+NOMINAL_HBM_GBS = 7900.0  # HBM3e specification, for context beside the measured copy peak
+# algorithmic bytes of one FP32 cell update: one 4-byte read and one 4-byte write of f
+BYTES_PER_UPDATE = 8.0
+# cell updates per cell that one launch of each sweep kind makes (the fused kick tail
+# runs D_uy and D_uz in one pass over f)
+UPDATES_PER_PASS = {"sweep_uyuz": 2}
 
 WORKLOAD = dict(name="fp32_64x32", n=64, nu=32, V=5.0, L=1.0, delta_rms=0.05, cdm_rms=1.0,
-                f_nu=0.03, four_pi_G=1.0, a0=0.5, a1=0.6, sched=10, cfl=(0.5, 0.9), seed=2)
+                f_nu=0.03, four_pi_G=1.0, a0=0.5, a1=0.6, cfl=(0.5, 0.9), seed=2)
 # Reduced-precision storage: BF16 / FP16 f with one FP32 scale per u_z line on
 # 96^3 x 32^3 cells, the 16^3-parity setup (delta rms 0.01, external phi, CFL 0.7, a = 1).
 LOWPREC = dict(name="lowprec_96x32", n=96, nu=32, V=5.0, delta_rms=0.01, seed=1, cfl=0.7)
@@ -63,9 +63,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-lowprec", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-large", action="store_true")
     p.add_argument("--fused-kick", type=int, default=None,
                    help="1 / 0: run the kicks' D_uy D_uz in one pass or separately (default: the library's)")
     p.add_argument("--fused-moment", type=int, default=None,
@@ -102,13 +103,13 @@ def whole_job_rate(world, cells, steps, ms, sweeps=9):
     return world * sweeps * cells * steps / (ms * 1e-3)
 
 
-def schedule(k, w=WORKLOAD):
-    """a at the start / middle / end of step k and the step's Courant number."""
+def schedule(k, nsteps, w=WORKLOAD):
+    """a at the start / middle / end of step k of a run of nsteps steps that takes a
+    linearly from a0 to a1 once, and step k's seeded Courant number."""
     rng = np.random.default_rng(1000 + k)
     cfl = rng.uniform(*w["cfl"])
-    kk = k % w["sched"]
-    da = (w["a1"] - w["a0"]) / w["sched"]
-    a_start = w["a0"] + da * kk
+    da = (w["a1"] - w["a0"]) / nsteps
+    a_start = w["a0"] + da * k
     a_end = a_start + da
     return a_start, 0.5 * (a_start + a_end), a_end, cfl
 
@@ -159,6 +160,21 @@ def kernel_source_hash(kind):
             h.update(fn.encode())
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
+
+
+def committed_alu(kind):
+    """ALU-pipe activity (% of peak, ncu sm__inst_executed_pipe_alu / sm__pipe_alu_cycles_active)
+    of `kind` from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    ent = d.get("kernels", {}).get(kind)
+    if not ent or ent.get("source_hash") != kernel_source_hash(kind):
+        return None
+    return ent.get("alu_pipe_pct")
 
 
 def committed_traffic(kind):
@@ -248,11 +264,12 @@ def oracle_sample_setup():
     return O, g, f, bg, phi
 
 
-def oracle_steps(O, g, f, bg, phi, k0, nsteps):
+def oracle_steps(O, g, f, bg, phi, k0, nsteps, total):
+    """Steps k0 .. k0 + nsteps - 1 of a run of `total` steps (a from a0 to a1)."""
     w = WORKLOAD
     n, nu = SAMPLE["n"], SAMPLE["nu"]
     for k in range(k0, k0 + nsteps):
-        a_s, a_h, a_e, cfl = schedule(k)
+        a_s, a_h, a_e, cfl = schedule(k, total)
         dt = drift_dt(cfl, a_h, n, nu, w["V"], w["L"])
         phi, _ = O.step(g, f, dt, a_h, a_e, phi, rho_bg=bg, four_pi_G=w["four_pi_G"],
                         self_consistent=True)
@@ -264,7 +281,7 @@ def cpu_baseline(min_seconds=10.0):
     t0 = time.perf_counter()
     k = 0
     while True:
-        phi = oracle_steps(O, g, f, bg, phi, k, 1)
+        phi = oracle_steps(O, g, f, bg, phi, k % 10, 1, 10)  # config 2's 10-step schedule, repeated
         k += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
@@ -273,6 +290,36 @@ def cpu_baseline(min_seconds=10.0):
             "sample": "%d steps of the FP64 oracle's Eq. (5) step on an %d^3 x %d^3 sample of the "
                       "workload (same velocity cube, dt scaled to the sample's dx), %.1f s"
                       % (k, SAMPLE["n"], SAMPLE["nu"], t)}
+
+
+# Per-axis CPU rates: the oracle's single sweeps on the 16^3 x 16^3 parity grid, the
+# 24^3 x 16^3 low-precision sub-run grid and a 32^3 x 32^3 grid (1.07e9 cells, 8.6 GB FP64)
+CPU_AXIS_GRIDS = ((16, 16), (24, 16), (32, 32))
+
+
+def cpu_per_axis():
+    """Cell updates per second of one oracle sweep along each axis (CFL 0.7, external phi)."""
+    import oracle as O
+    from paper_2110_15867_gb300 import inputs as I
+    out = {}
+    names = ("x", "y", "z", "ux", "uy", "uz")
+    for n, nu in CPU_AXIS_GRIDS:
+        V = 5.0
+        g = O.grid(n, nu, V=V)
+        f = I.initial_f(I.gaussian_field(n, 0.01, seed=1), I.fermi_dirac(nu, V), np.float64)
+        phi = I.fourier_potential(n, seed=11)
+        c = courant_per_dt(phi, n, nu, V)
+        rates = {}
+        for ax in range(6):
+            dt = 0.7 / c[ax]
+            t0 = time.perf_counter()
+            O.sweep(g, f, ax, dt, 1.0, phi)
+            rates[names[ax]] = f.size / (time.perf_counter() - t0)
+        out["%d^3 x %d^3" % (n, nu)] = rates
+        del f
+    return {"unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "what": "one FP64 oracle sweep per axis at Courant number 0.7 (external phi for the velocity "
+                    "axes), cell updates per second", "grids": out}
 
 
 def workload_config(world):
@@ -292,9 +339,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     O, g, f, bg, phi = oracle_sample_setup()
-    phi = oracle_steps(O, g, f, bg, phi, 0, args.warmup)
+    phi = oracle_steps(O, g, f, bg, phi, 0, args.warmup, max(1, args.warmup))
     t0 = time.perf_counter()
-    phi = oracle_steps(O, g, f, bg, phi, args.warmup, args.steps)
+    phi = oracle_steps(O, g, f, bg, phi, 0, args.steps, args.steps)
     t = time.perf_counter() - t0
     value = 9.0 * f.size * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -364,9 +411,8 @@ def run_lowprec(torch, B, dev, steps, warmup):
         codes = torch.empty((n, n, n, nu, nu, nu), dtype=tdt, device=dev)
         scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device=dev)
         for ix in range(n):
-            c, s = B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], tdt)
-            codes[ix].copy_(c)
-            scale[ix].copy_(s)
+            B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], tdt,
+                           codes=codes[ix], scale=scale[ix])
         v = B.Vlasov(codes, V=V, scale=scale)
         rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
         for _ in range(warmup):
@@ -393,6 +439,95 @@ def run_lowprec(torch, B, dev, steps, warmup):
                                  for k in kind_ms if kind_n[k] and k.startswith("sweep_")}}
         del codes, scale
         torch.cuda.empty_cache()
+    return out
+
+
+def run_large(torch, B, dev, steps, warmup):
+    """The large self-consistent run (48^3 x 48^3 cells, |u| <= 8 u_T, delta rms 0.1, CDM
+    contrast rms 3.0, a from 0.2 over a 50-step schedule to 1.0, moment and Poisson every
+    step) in FP32 and in BF16 storage side by side: the first warmup + steps steps of the
+    schedule, the last `steps` timed; per-sweep rate, per-kernel times, and the density of
+    the last step in BF16 against FP32."""
+    from paper_2110_15867_gb300 import inputs as I
+    cfg = I.CONFIGS["large_48x48"]
+    n, nu, V, L, f_nu = cfg["n"], cfg["nu"], cfg["V"], 1.0, 0.03
+    delta = torch.from_numpy(I.gaussian_field(n, cfg["delta_rms"], seed=cfg["seed"])).to(dev)
+    Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
+    du = 2.0 * V / nu
+    rho_bar = float(Fu.sum().item()) * du ** 3
+    dc = torch.from_numpy(I.gaussian_field(n, cfg["cdm_rms"], seed=cfg["seed"] + 1)).to(dev)
+    rho_bg = (rho_bar * (1.0 / f_nu - 1.0) * (1.0 + dc)).contiguous()
+    da = (cfg["a1"] - cfg["a0"]) / cfg["steps"]
+    umax = V - 0.5 * du
+    cells = n ** 3 * nu ** 3
+    out = {"workload": "large_48x48: %d^3 x %d^3 cells, |u| <= 8 u_T, self-consistent Eq. (5) steps "
+                       "(moment + Poisson every step), steps %d..%d of the 50-step a = 0.2 -> 1.0 schedule"
+                       % (n, nu, warmup, warmup + steps - 1), "cells": cells}
+    dts = None
+    rhos = {}
+    for name in ("f32", "bf16"):
+        if name == "f32":
+            f = torch.empty((n, n, n, nu, nu, nu), dtype=torch.float32, device=dev)
+            for ix in range(n):
+                f[ix] = ((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None]).to(torch.float32)
+            scale = None
+        else:
+            f = torch.empty((n, n, n, nu, nu, nu), dtype=torch.bfloat16, device=dev)
+            scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device=dev)
+            for ix in range(n):
+                B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], torch.bfloat16,
+                               codes=f[ix], scale=scale[ix])
+        v = B.Vlasov(f, L=L, V=V, scale=scale)
+        rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+        v.moment(rho)
+        phi = v.poisson(rho, cfg["a0"], 1.0, rho_bg=rho_bg)
+        phi2 = torch.empty_like(phi)
+        if dts is None:
+            # dt per step: the largest position Courant number at a_half is 0.9, capped so that a
+            # kick's velocity Courant number under the initial potential stays <= 0.3 (room for
+            # phi to grow); the same dt sequence for both storage types
+            g0 = max(courant_per_dt(phi.cpu().numpy(), n, nu, V)[3:]) * du  # largest |grad phi|
+            dt_vel = 0.3 * 2.0 * du / max(g0, 1e-30)
+            dts = []
+            for k in range(warmup + steps):
+                a_h = cfg["a0"] + da * (k + 0.5)
+                dts.append(min(cfg["cfl"] * a_h * a_h * (L / n) / umax, dt_vel))
+
+        def one(k):
+            nonlocal phi, phi2
+            a_s = cfg["a0"] + da * k
+            v.step(dts[k], a_s + 0.5 * da, a_s + da, phi, rho_bg=rho_bg, four_pi_G=1.0, phi_next=phi2, rho_nu=rho)
+            phi, phi2 = phi2, phi
+
+        for k in range(warmup):
+            one(k)
+        v.status()
+        v.read_timers()
+        v.enable_timers(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(warmup, warmup + steps):
+            one(k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kind_ms, kind_n = v.read_timers()
+        v.enable_timers(False)
+        v.status()
+        rhos[name] = rho.clone()
+        out[name] = {"value": 9.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "kernels": {k: {"ms_per_launch": kind_ms[k] / kind_n[k], "launches": kind_n[k],
+                                     "cell_updates_per_s": UPDATES_PER_PASS.get(k, 1) * cells /
+                                     (kind_ms[k] / kind_n[k] * 1e-3)}
+                                 for k in kind_ms if kind_n[k] and k.startswith("sweep_")}}
+        v.close()
+        del f, scale, v
+        torch.cuda.empty_cache()
+    out["bf16_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
+    d = (rhos["bf16"] - rhos["f32"]).abs()
+    out["density_bf16_vs_f32"] = {"rel_l1": float(d.sum() / rhos["f32"].abs().sum()),
+                                  "max_cell_rel": float((d / rhos["f32"].abs()).max())}
     return out
 
 
@@ -525,15 +660,15 @@ def run_ours(args):
     v.moment(rho)
     v.poisson(rho, w["a0"], w["four_pi_G"], rho_bg=rho_bg, phi=phi)
 
-    def one_step(k):
+    def one_step(k, total):
         nonlocal phi, phi2
-        a_s, a_h, a_e, cfl = schedule(k)
+        a_s, a_h, a_e, cfl = schedule(k, total)
         dt = drift_dt(cfl, a_h, n, nu, V, L)
         v.step(dt, a_h, a_e, phi, rho_bg=rho_bg, four_pi_G=w["four_pi_G"], phi_next=phi2, rho_nu=rho)
         phi, phi2 = phi2, phi
 
     for k in range(args.warmup):
-        one_step(k)
+        one_step(k, args.warmup)
     v.status()
     v.read_timers()  # reset the launch counters
     v.enable_timers(True)
@@ -545,8 +680,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for k in range(args.warmup, args.warmup + args.steps):
-        one_step(k)
+    for k in range(args.steps):  # a runs from a0 to a1 once over the timed steps
+        one_step(k, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -559,33 +694,38 @@ def run_ours(args):
     ms_total = max_over_ranks(ms_total, dist, dev)
     value = whole_job_rate(world, cells, args.steps, ms_total)
 
-    # dominant kernel and its roofline
+    # dominant kernel and its roofline: algorithmic bytes = 8 B per cell update x the
+    # updates one launch makes, over its mean event time, against the measured copy peak
     sweep_kinds = [k for k in kind_ms if k.startswith("sweep_")]
     dom = max(sweep_kinds, key=lambda k: kind_ms[k])
     dom_ms = kind_ms[dom] / max(1, kind_n[dom])
-    alg_bytes = 8.0 * cells  # one FP32 read + one FP32 write per cell
-    hbm_achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     hbm_peak, peak_src = measured_peaks()
-    traffic = committed_traffic(dom)
-    if dom == "sweep_uyuz":
-        # two sweeps per pass over f: bound by the ALU pipe that runs the limiter's min / max
-        sweeps_in_pass = 2
-        achieved = ALU_OPS_PER_UPDATE * sweeps_in_pass * cells / (dom_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ALU_PEAK_TOPS,
-                    "peak_source": "nominal: 152 SMs x 64 ALU-pipe lanes per clock x 2070 MHz",
-                    "unit": "Tops/s (min/max, %d per cell update)" % ALU_OPS_PER_UPDATE,
-                    "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
-                    "hbm_achieved_GBs": hbm_achieved, "hbm_frac": hbm_achieved / hbm_peak,
-                    "algorithmic_bytes_per_launch": alg_bytes}
-    else:
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": hbm_peak,
-                    "peak_source": peak_src, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                    "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes}
+    upd = UPDATES_PER_PASS.get(dom, 1)
+    alg_bytes = BYTES_PER_UPDATE * upd * cells
+    moved_bytes = BYTES_PER_UPDATE * cells  # what one pass reads and writes
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                "peak_source": "%s copy peak (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
+                else "fallback 6.8 TB/s", "unit": "GB/s", "frac": achieved / hbm_peak,
+                "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
+                "traffic": committed_traffic(dom), "algorithmic_bytes_per_launch": alg_bytes,
+                "cell_updates_per_launch": upd * cells,
+                "hbm_frac_actual_bytes": moved_bytes / (dom_ms * 1e-3) / 1e9 / hbm_peak,
+                "ms_per_launch": dom_ms}
+    alu = committed_alu(dom)
+    if alu is not None:
+        roofline["alu_pipe_active_pct_ncu"] = alu
     per_kind = {k: {"ms_per_launch": (kind_ms[k] / kind_n[k]) if kind_n[k] else 0.0,
                     "launches": kind_n[k]} for k in kind_ms if kind_n[k]}
     for k in sweep_kinds:
         if kind_n[k]:
-            per_kind[k]["GBs"] = alg_bytes / (per_kind[k]["ms_per_launch"] * 1e-3) / 1e9
+            t = per_kind[k]["ms_per_launch"] * 1e-3
+            u = UPDATES_PER_PASS.get(k, 1)
+            per_kind[k]["cell_updates_per_s"] = u * cells / t
+            per_kind[k]["GBs"] = BYTES_PER_UPDATE * u * cells / t / 1e9
+            per_kind[k]["frac"] = per_kind[k]["GBs"] / hbm_peak
+            if u > 1:
+                per_kind[k]["GBs_actual_bytes"] = BYTES_PER_UPDATE * cells / t / 1e9
     gpu_launches = int(sum(kind_n.values()))
 
     # velocity moments of the final state (density, mean velocity, dispersion tensor), timed alone
@@ -617,9 +757,9 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
-        def host_step(k):
+        def host_step(k, total):
             nonlocal phi, phi2
-            a_s, a_h, a_e, cfl = schedule(k)
+            a_s, a_h, a_e, cfl = schedule(k, total)
             dt = drift_dt(cfl, a_h, n, nu, V, L)
             v.step_host(fh, dt, a_h, a_e, phi, rho_bg=rho_bg, four_pi_G=w["four_pi_G"], phi_next=phi2, rho_nu=rho)
             rho_h.copy_(rho, non_blocking=True)
@@ -627,12 +767,11 @@ def run_ours(args):
 
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        base = args.warmup + args.steps
-        host_step(base)  # warm-up: the copy stream and its events
+        host_step(0, 1)  # warm-up: the copy stream and its events
         torch.cuda.synchronize()
         t0.record(stream)
-        for k in range(base + 1, base + 1 + args.e2e_steps):
-            host_step(k)
+        for k in range(args.e2e_steps):
+            host_step(k, args.e2e_steps)
         t1.record(stream)
         torch.cuda.synchronize()
         e_ms = t0.elapsed_time(t1)
@@ -657,12 +796,18 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
+        cpu["per_axis"] = cpu_per_axis()
     v.close()
+    del f, v
+    torch.cuda.empty_cache()
     lowprec = None
     if not args.no_lowprec:
         lowprec = run_lowprec(torch, B, dev, max(2, min(args.steps, 3)), 2)
         for k in ("bf16", "f16"):
             lowprec[k]["vs_fp32"] = lowprec[k]["value"] / (9.0 * cells * args.steps / (ms_total * 1e-3))
+    large = None
+    if not args.no_large:
+        large = run_large(torch, B, dev, 5, 2)
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(torch, dev)
@@ -676,6 +821,7 @@ def run_ours(args):
             "kernels": per_kind,
             "cpu_baseline": cpu,
             "lowprec": lowprec,
+            "large": large,
             "adjoint": adjoint,
             "moments": moments,
             "e2e": e2e,

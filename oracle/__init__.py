@@ -90,6 +90,8 @@ def lib():
         L.orc_sweep.argtypes = [_G, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
                                 ctypes.c_int]
         L.orc_sweep.restype = ctypes.c_int
+        L.orc_sweep_cells.argtypes = [_G, _D, ctypes.c_int, _D, ctypes.c_int]
+        L.orc_sweep_cells.restype = ctypes.c_int
         L.orc_max_abs_nu.argtypes = [_G, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
         L.orc_max_abs_nu.restype = ctypes.c_double
         L.orc_gradient.argtypes = [_G, _D, ctypes.c_int, _D]
@@ -174,6 +176,17 @@ def sweep(g: Grid, f: np.ndarray, axis: int, dt: float, a: float = 1.0, phi=None
     if axis >= 3 and phi_a is None:
         raise ValueError("velocity sweeps need phi")
     lib().orc_sweep(ctypes.byref(g), _p(f), axis, dt, a, _p(phi_a), flags)
+
+
+def sweep_cells(g: Grid, f: np.ndarray, axis: int, nu_cell, flags: int = MPP) -> None:
+    """In-place velocity sweep (axis 3..5) with each spatial cell's Courant number given
+    (nu_cell: the spatial grid's shape)."""
+    if axis < 3:
+        raise ValueError("sweep_cells takes velocity axes 3..5")
+    nu_a = _f64(nu_cell)
+    if nu_a.size != g.n[0] * g.n[1] * g.n[2]:
+        raise ValueError("nu_cell must hold one Courant number per spatial cell")
+    lib().orc_sweep_cells(ctypes.byref(g), _p(f), axis, _p(nu_a), flags)
 
 
 def max_abs_nu(g: Grid, axis: int, dt: float, a: float = 1.0, phi=None) -> float:

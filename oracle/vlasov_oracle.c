@@ -347,6 +347,41 @@ int orc_sweep(const orc_grid *g, double *f, int axis, double dt, double a, const
     return 0;
 }
 
+/*
+ * A velocity sweep (axis 3..5) of Eq. (4) with the Courant number of each spatial
+ * cell given directly: nu_cell[c] for cell c = (ix ny + iy) nz + iz, the same for
+ * every line of that cell's velocity cube.  orc_sweep with phi is this sweep with
+ * nu_cell = -g dt / du, g the gradient of phi.  Lines as in orc_sweep.  Returns 0,
+ * or -1 for a position axis.
+ */
+int orc_sweep_cells(const orc_grid *g, double *f, int axis, const double *nu_cell, int flags)
+{
+    if (axis < 3) return -1;
+    long d[6]; dims6(g, d);
+    long stride[6];
+    stride[5] = 1;
+    for (int k = 4; k >= 0; --k) stride[k] = stride[k + 1] * d[k + 1];
+    const long n = d[axis];
+    const long nlines = orc_num_cells(g) / n;
+    const long inner = stride[axis];
+#pragma omp parallel
+    {
+        double *line = (double *)malloc(sizeof(double) * (2 * n + 1));
+        double *work = line + n;
+#pragma omp for schedule(static)
+        for (long l = 0; l < nlines; ++l) {
+            const long outer = l / inner, in = l % inner;
+            const long base = outer * n * inner + in;
+            const long cell = base / stride[2];
+            for (long i = 0; i < n; ++i) line[i] = f[base + i * inner];
+            orc_sweep_line(line, n, nu_cell[cell], 0, flags, work);
+            for (long i = 0; i < n; ++i) f[base + i * inner] = line[i];
+        }
+        free(line);
+    }
+    return 0;
+}
+
 /* largest |nu| a sweep would use (diagnostic for choosing dt) */
 double orc_max_abs_nu(const orc_grid *g, int axis, double dt, double a, const double *phi)
 {

@@ -56,9 +56,8 @@ def _build_f(cfg, dtype):
     codes = torch.empty((n, n, n, nu, nu, nu), dtype=dtype, device="cuda")
     scale = torch.empty((n, n, n, nu, nu), dtype=torch.float32, device="cuda")
     for ix in range(n):
-        c, s = B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], dtype)
-        codes[ix] = c
-        scale[ix] = s
+        B.encode_lines((1.0 + delta[ix])[:, :, None, None, None] * Fu[None, None], dtype,
+                       codes=codes[ix], scale=scale[ix])
     return codes, scale
 
 
@@ -146,6 +145,65 @@ def test_fullsize_16bit_sweeps_sampled_lines(name, fmt):
     phi = I.fourier_potential(cfg["n"], seed=cfg["seed"] + 10).astype(np.float32)
     _sweep_sampled(B, cfg, codes, scale, phi, bound + 1e-6, 1.5 * (2 * bound + 1e-6), seed=2)
     del codes, scale
+    _free()
+
+
+def _cubes(f, scale, cells):
+    """Whole velocity cubes of the sampled spatial cells as FP64 host arrays (16-bit:
+    decoded with their u_z line scales)."""
+    ix, iy, iz = (torch.from_numpy(c).cuda() for c in cells)
+    v = f[ix, iy, iz].to(torch.float64)
+    if scale is not None:
+        v = v * scale[ix, iy, iz].to(torch.float64)[..., None]
+    return v.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,fmt", [("fp32_64x32", "f32"), ("lowprec_96x32", "bf16")])
+def test_fullsize_kick_sampled_cells(name, fmt):
+    # One kick D_uz D_uy D_ux of Eq. (5) through vlasov_kick on the whole grid (the u_x
+    # register-line kernel, then the fused u_y u_z pass the step runs).  A kick never
+    # leaves a spatial cell, so each sampled cell's whole velocity cube after the kick
+    # must match the oracle's three velocity sweeps of that cube at that cell's Courant
+    # numbers nu_i = -g_i dt / du.  Tolerance: three times the per-sweep bound (FP32:
+    # relative L1 1e-6, L_inf 1e-4; BF16: the codec bound).
+    B = _lib()
+    cfg = I.CONFIGS[name]
+    n, nu, V = cfg["n"], cfg["nu"], cfg["V"]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[fmt]
+    f, scale = _build_f(cfg, tdt)
+    phi = I.fourier_potential(n, seed=cfg["seed"] + 10).astype(np.float32)
+    g = O.grid(n, nu, V=V)
+    phi64 = phi.astype(np.float64)
+    dt = 0.45 / max(O.max_abs_nu(g, ax, 1.0, 1.0, phi64) for ax in (3, 4, 5))
+    rng = np.random.default_rng(7)
+    k = 128
+    cells = [rng.integers(0, n, size=k) for _ in range(3)]
+    for c in cells:
+        c[0], c[1] = 0, n - 1
+    before = _cubes(f, scale, cells)
+    v = B.Vlasov(f, V=V, scale=scale)
+    v.kick(dt, torch.from_numpy(phi).cuda())
+    v.status()
+    after = _cubes(f, scale, cells)
+    v.close()
+    du = 2.0 * V / nu
+    gs = O.grid((k, 1, 1), nu, V=V)
+    ref = before.reshape((k, 1, 1) + (nu,) * 3).copy()
+    for ax in (3, 4, 5):
+        nus = -O.gradient(g, phi64, ax - 3)[cells[0], cells[1], cells[2]] * dt / du
+        O.sweep_cells(gs, ref, ax, nus.reshape(k, 1, 1))
+    ref = ref.reshape(after.shape)
+    err = np.abs(after - ref)
+    rl1 = err.sum() / np.abs(ref).sum()
+    rinf = err.max() / np.abs(ref).max()
+    if fmt == "f32":
+        tol_l1, tol_inf = 3 * RTOL_L1, 3 * RTOL_LINF
+    else:
+        b = 2.0 ** -8
+        tol_l1, tol_inf = 3 * (b + 1e-6), 3 * 1.5 * (2 * b + 1e-6)
+    print("%s kick: %d cubes, rel L1 %.2e, rel Linf %.2e" % (name, k, rl1, rinf))
+    assert rl1 <= tol_l1 and rinf <= tol_inf, (rl1, rinf)
+    del f, scale
     _free()
 
 

@@ -2,9 +2,12 @@
 
 Tolerances (per sweep, FP32 storage and arithmetic against the FP64 oracle on the
 same FP32-rounded input): relative L1 <= 1e-6, L_inf <= 1e-4 of max f.  Mass:
-FP64 storage conserves to <= 1e-13 relative; FP32 storage rounds every cell once
-per sweep, and on smooth data those roundings are correlated, so the drift is
-asserted at <= 1e-9 relative per sweep and its measured value is printed.
+FP64 storage conserves to <= 1e-13 relative.  FP32 storage rounds every cell once per
+sweep (at most 2^-24 of its value); the relative drift of the sum falls like the inverse
+square root of the number of cells when the roundings are independent, and on smooth
+data they are partly correlated.  The drift is asserted per shape at 10 times the
+largest value measured over the six axes on a GB300 (never looser than 1e-9), and the
+measured value is printed.
 """
 import math
 
@@ -56,6 +59,10 @@ SHAPES = [
     ((4, 4, 4), (8, 8, 48)),        # u_z rows of 48 (the 48^3 velocity grid's line length)
     ((4, 5, 4), (48, 48, 8)),       # u_x, u_y lines of 48 in registers; z blocks of 32 u_z lines
 ]
+# largest relative mass drift of one FP32 sweep over the six axes, measured per shape
+# (1.7e7, 4.0e5, 2.0e5, 2.0e5 and 1.8e5 cells)
+MASS_DRIFT_MEASURED = {SHAPES[0]: 7.7e-12, SHAPES[1]: 2.6e-10, SHAPES[2]: 5.9e-10, SHAPES[3]: 6.3e-10,
+                       SHAPES[4]: 1.5e-10}
 
 
 @pytest.mark.parametrize("n,nu", SHAPES)
@@ -78,7 +85,7 @@ def test_single_sweep_fp32(n, nu, axis):
     m0 = math.fsum(f0.astype(np.float64).ravel())
     m1 = math.fsum(out.astype(np.float64).ravel())
     print("axis %d mass drift %.3e (relative)" % (axis, (m1 - m0) / m0))
-    assert abs(m1 - m0) <= 1e-9 * m0
+    assert abs(m1 - m0) <= min(10 * MASS_DRIFT_MEASURED[(n, nu)], 1e-9) * m0
     assert out.min() >= 0.0
     v.close()
 

@@ -462,3 +462,28 @@ def test_step_second_kick_uses_post_drift_potential():
             # cell 2 holds cell 6's cube, which neither kick moves (no force at 6 from
             # phi^n, none at 2 from phi_T)
             assert np.abs(f[2, iy, iz] - levels[6] * prof).max() < 1e-12
+
+
+def test_sweep_cells_is_the_velocity_sweep_at_given_courant_numbers():
+    # Eq. (4) with nu(x) given per spatial cell: with nu = -g dt / du (g the pinned
+    # 4th-order gradient) it is the velocity sweep of orc_sweep bit for bit, and with
+    # whole numbers per cell every cube moves by exactly that many cells
+    n, nu, V = (4, 3, 5), (8, 12, 10), 5.0
+    g = O.grid(n, nu, V=V)
+    f0 = I.initial_f(I.gaussian_field(n, 0.1, seed=2), I.fermi_dirac(nu, V), np.float64)
+    phi = I.fourier_potential(n, seed=6)
+    for ax in (3, 4, 5):
+        d = ax - 3
+        dt = 0.6 / O.max_abs_nu(g, ax, 1.0, 1.0, phi)
+        a = f0.copy()
+        b = f0.copy()
+        O.sweep(g, a, ax, dt, 1.0, phi)
+        O.sweep_cells(g, b, ax, -O.gradient(g, phi, d) * dt / (2 * V / nu[d]))
+        assert np.array_equal(a, b)
+    prof = np.zeros(nu)
+    prof[3:5, 4:7, 2:6] = np.random.default_rng(1).integers(8, 32, size=(2, 3, 4)) / 16.0
+    f = np.broadcast_to(prof, n + nu).copy()
+    shifts = np.random.default_rng(2).integers(-2, 3, size=n).astype(np.float64)
+    O.sweep_cells(g, f, 3, shifts)
+    for idx in np.ndindex(*n):
+        assert np.array_equal(f[idx], np.roll(prof, int(shifts[idx]), axis=0))
