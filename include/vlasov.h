@@ -132,24 +132,31 @@ int vlasov_decode(long long nlines, int nuz, const void *codes_dev, int code_dty
                   void *dst_dev, int dst_dtype, void *stream);
 
 /*
- * Kicks of vlasov_step (D_uz D_uy D_ux, Eq. 5) on FP32 storage with n_uy = n_uz
- * = 16 or 32 run D_uy and D_uz in one pass over f: each u_z tile of 256 rows
- * holds whole (cell, j_x) planes, whose columns are the u_y lines, so D_uy runs
- * on the staged tile before D_uz (the arithmetic of the separate sweeps,
- * bit for bit; for BF16 / FP16 storage the D_uy result stays FP32 in shared
- * memory and only D_uz's is encoded).  On by default (FP32: 11 % faster than the
- * two sweeps at n_u = 32); on = 0 runs them separately.  FP64 storage and other
- * shapes always run the sweeps separately.
+ * How the kicks of vlasov_step and vlasov_kick (D_uz D_uy D_ux, Eq. 5) run.
+ *   mode 2 (the default): with n_ux = n_uy = n_uz = 16 or 32 (FP32, BF16 or FP16
+ *     storage) the whole kick runs in one pass over f: each spatial cell's velocity
+ *     cube goes through shared memory once and the three sweeps run on it there
+ *     (a kick never leaves the cell, Sec. 4.1.3).  The result equals the separate
+ *     sweeps bit for bit, for 16-bit storage too (the same rounding points and
+ *     stochastic-rounding streams: D_ux encodes with the line scales it kept, D_uy
+ *     stays FP32, D_uz refreshes the scales and encodes).  Other shapes fall back
+ *     to mode 1.
+ *   mode 1: D_ux alone, then D_uy and D_uz in one pass over f where n_uy = n_uz =
+ *     16 or 32: each u_z tile of 256 rows holds whole (cell, j_x) planes, whose
+ *     columns are the u_y lines, so D_uy runs on the staged tile before D_uz (FP32:
+ *     the separate sweeps bit for bit; 16-bit storage: D_uy's result stays FP32 in
+ *     shared memory and only D_uz's is encoded).
+ *   mode 0: three separate sweeps.
+ * FP64 storage always runs the sweeps separately.  Errors: VLASOV_EINVAL for
+ * another mode.
  */
-int vlasov_set_fused_kick(vlasov_ctx *ctx, int on);
+int vlasov_set_fused_kick(vlasov_ctx *ctx, int mode);
 
 /*
  * One kick of Eq. (5): D_uz D_uy D_ux (dt), D_ux first, with the acceleration
  * -grad phi (phi_dev: FP32 potential on the device, nx*ny*nz, as for
- * vlasov_sweep).  vlasov_step runs it with dt/2 before and after the drift.  The
- * u_y and u_z sweeps run as one pass where vlasov_set_fused_kick allows (FP32:
- * the separate sweeps bit for bit; 16-bit storage: D_uy's result stays FP32 in
- * shared memory and only D_uz's is encoded).  Same errors as vlasov_sweep.
+ * vlasov_sweep).  vlasov_step runs it with dt/2 before and after the drift; it runs
+ * as vlasov_set_fused_kick selects.  Same errors as vlasov_sweep.
  */
 int vlasov_kick(vlasov_ctx *ctx, double dt, const float *phi_dev);
 
@@ -257,7 +264,8 @@ int vlasov_step_host(vlasov_ctx *ctx, void *f_host, double dt, double a_half, do
 #define VLASOV_T_MOMENT_ADJ 17 /* moment adjoint                                      */
 #define VLASOV_T_SWEEP_UYUZ 18 /* fused kick tail D_uz D_uy (see vlasov_set_fused_kick) */
 #define VLASOV_T_MOMENTS 19    /* vlasov_moments                                      */
-#define VLASOV_T_KINDS 20
+#define VLASOV_T_KICK 20       /* one-pass kick D_uz D_uy D_ux (see vlasov_set_fused_kick) */
+#define VLASOV_T_KINDS 21
 int vlasov_enable_timers(vlasov_ctx *ctx, int on);
 int vlasov_read_timers(vlasov_ctx *ctx, double *ms, long long *launches, int nkinds);
 

@@ -54,7 +54,7 @@ STATIC_MAX_CELLS = 32768
 # timer kinds of vlasov_read_timers
 T_KINDS = ("sweep_x", "sweep_y", "sweep_z", "sweep_ux", "sweep_uy", "sweep_uz", "moment",
            "poisson", "coef", "mass", "adj_x", "adj_y", "adj_z", "adj_ux", "adj_uy", "adj_uz",
-           "grad_adj", "moment_adj", "sweep_uyuz", "moments")
+           "grad_adj", "moment_adj", "sweep_uyuz", "moments", "kick")
 
 
 def library_path() -> str:
@@ -226,8 +226,8 @@ def vlasov_moment_adjoint(ctx, dLdrho_ptr: int, lam_ptr: int, accumulate: bool =
     return _check(ctx, load().vlasov_moment_adjoint(ctx, dLdrho_ptr, lam_ptr, int(bool(accumulate))))
 
 
-def vlasov_set_fused_kick(ctx, on: bool):
-    return _check(ctx, load().vlasov_set_fused_kick(ctx, int(bool(on))))
+def vlasov_set_fused_kick(ctx, mode: int):
+    return _check(ctx, load().vlasov_set_fused_kick(ctx, int(mode)))
 
 
 def vlasov_set_fused_moment(ctx, on: bool):
@@ -579,9 +579,11 @@ class Vlasov:
         """f-sized scratch arrays step_adjoint may hold: 8, 4 or 0 (8 if they fit, else 4)."""
         _check(self.ctx, load().vlasov_set_adjoint_arrays(self.ctx, int(arrays)))
 
-    def set_fused_kick(self, on: bool = True):
-        """Run the kicks' D_uy and D_uz in one pass (FP32, n_uy = n_uz = 16 or 32)."""
-        vlasov_set_fused_kick(self.ctx, on)
+    def set_fused_kick(self, mode=2):
+        """How the kicks run: 2 (default) the whole kick in one pass over each velocity cube
+        (n_ux = n_uy = n_uz = 16 or 32), 1 (or True) D_ux then D_uy D_uz in one pass, 0 (or
+        False) three separate sweeps."""
+        vlasov_set_fused_kick(self.ctx, int(mode))
 
     def set_fused_moment(self, on: bool = True):
         """Let the step's x sweep sum the moment of its output (FP32 / FP64 storage)."""

@@ -199,6 +199,25 @@ int line_sweep_rows_per_tile();
 // fuse_y: D_uy on the tile's (cell, j_x) planes first (FP32, n_uy = n_uz)
 int occupancy_line_sweep(int nu, int dtype, bool fuse_y = false); // dtype: 1 f32, 2 bf16, 3 f16
 
+// ----------------------------------------------------------------------------
+// one kick D_uz D_uy D_ux in a single pass (kick_cube.cu): n_ux = n_uy = n_uz = 16 or 32,
+// FP32 / BF16 / FP16 storage.  fmap views f as rows of NU values (the u_z lines) with box
+// {NU, kick_cube_box_rows(NU)} and the 32/64/128-byte swizzle of the row size; smap (16-bit)
+// views the scales as [ncell NU][NU] with box {NU, NU / 2}.
+// ----------------------------------------------------------------------------
+struct KickArgs {
+    long long cell0, ncells; // the cubes of spatial cells [cell0, cell0 + ncells)
+    const LineCoefT<float> *coef_x, *coef_y, *coef_z;
+    unsigned *err;
+    unsigned seed_x, seed_z; // 16-bit: stochastic-rounding streams of the D_ux and D_uz encodes
+};
+bool kick_cube_supported(int nux, int nuy, int nuz, int dtype); // dtype 1 f32, 2 bf16, 3 f16
+int kick_cube_box_rows(int nu);
+size_t kick_cube_smem(int nu, int dtype);
+int occupancy_kick_cube(int nu, int dtype);
+cudaError_t launch_kick_cube(const CUtensorMap &fmap, const CUtensorMap &smap, const KickArgs &a, int nu, int dtype,
+                             int grid, cudaStream_t st);
+
 // host launchers (return cudaGetLastError() of the launch); tiles are loaded
 // through map and stored through dmap (the same map for an in-place sweep)
 cudaError_t launch_strided_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<float> &a, int grid,

@@ -118,8 +118,13 @@ struct vlasov_ctx {
     bool use_lines;
     CUtensorMap lmap;
     MapSpec lspec;
-    // kick tail D_uz D_uy fused in the u_z line kernel (FP32, n_uy = n_uz)
-    bool can_fuse_kick, fuse_kick;
+    // kick tail D_uz D_uy fused in the u_z line kernel (n_uy = n_uz)
+    bool can_fuse_kick;
+    int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
+    // the whole kick D_uz D_uy D_ux in one pass (n_ux = n_uy = n_uz = 16 or 32)
+    bool can_kick_cube;
+    CUtensorMap kmap, ksmap;
+    int kgrid;
     int lgrid_fused;
     long long lrows, ltiles;
     int lgrid;
@@ -391,6 +396,31 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
         const long long rpp = c->lrows / c->g.nx; // u_z rows per x-plane
         c->ltpp = rpp % rpt == 0 ? rpp / rpt : 0;
     }
+    c->can_kick_cube = (mask & 0x38) == 0x38 && kick_cube_supported(c->g.nux, c->g.nuy, c->g.nuz, c->g.dtype) &&
+                       c->ncell * c->g.nux * c->g.nuy < (1ll << 31);
+    if (c->can_kick_cube) {
+        // f as rows of nu values (u_z lines), a box of half a cube's rows (at most 256)
+        const int nu = c->g.nuz;
+        const size_t rowbytes = nu * es;
+        const CUtensorMapSwizzle sw = rowbytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                      : rowbytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                       : CU_TENSOR_MAP_SWIZZLE_32B;
+        const MapSpec ks = spec_rows(tmap_type(c->g.dtype), nu, c->ncell * nu * nu, es, kick_cube_box_rows(nu), sw);
+        CUresult r = encode_spec(&c->kmap, ks, c->f);
+        if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "kick tensor map failed (%d)", int(r));
+        if (coded) {
+            // the scales as [ncell nu][nu] (one row per j_x plane), half a cube per box
+            const MapSpec ss = spec_rows(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nu, c->ncell * nu, 4, nu / 2,
+                                         CU_TENSOR_MAP_SWIZZLE_NONE);
+            r = encode_spec(&c->ksmap, ss, c->scale);
+            if (r != CUDA_SUCCESS) return fail(c, VLASOV_ECUDA, "kick scale tensor map failed (%d)", int(r));
+        } else {
+            c->ksmap = c->kmap; // not read
+        }
+        const int occ = occupancy_kick_cube(nu, c->g.dtype);
+        if (occ <= 0) return fail(c, VLASOV_ECUDA, "one-pass kick CTA does not fit");
+        c->kgrid = int(c->ncell < (long long)occ * c->sm_count ? c->ncell : (long long)occ * c->sm_count);
+    }
     c->can_fuse_kick = c->use_lines && (mask >> 4 & 1) && line_sweep_fused_supported(c->g.dtype) &&
                        c->g.nuy == c->g.nuz;
     if (c->can_fuse_kick) {
@@ -456,7 +486,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->stream = (cudaStream_t)stream;
     c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
-    c->fuse_kick = true; // see vlasov_set_fused_kick
+    c->fuse_kick = 2; // see vlasov_set_fused_kick
     c->fuse_moment = true; // see vlasov_set_fused_moment
     c->slab_x0 = c->slab_x1 = 0;
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
@@ -954,20 +984,48 @@ static int run_kick_tail(vlasov_ctx *c)
     return VLASOV_OK;
 }
 
+// D_uz D_uy D_ux in one pass over each cell's velocity cube (constants in d_coef)
+static int run_kick_cube(vlasov_ctx *c)
+{
+    KickArgs A{};
+    A.seed_x = c->sweeps + 1; // the streams the separate u_x and fused u_y u_z kernels would draw
+    A.seed_z = c->sweeps + 3;
+    c->sweeps += 3;
+    A.coef_x = (const LineCoefT<float> *)c->d_coef[0];
+    A.coef_y = (const LineCoefT<float> *)c->d_coef[1];
+    A.coef_z = (const LineCoefT<float> *)c->d_coef[2];
+    A.err = c->d_err;
+    A.cell0 = 0;
+    A.ncells = c->ncell;
+    if (c->slab_x1 > c->slab_x0) {
+        const long long cpp = c->ncell / c->g.nx; // spatial cells per x-plane
+        A.cell0 = c->slab_x0 * cpp;
+        A.ncells = (c->slab_x1 - c->slab_x0) * cpp;
+    }
+    if (A.ncells <= 0) return VLASOV_OK;
+    PartTimer t(c, VLASOV_T_KICK, 1);
+    const int grid = int(A.ncells < c->kgrid ? A.ncells : c->kgrid);
+    const cudaError_t e = launch_kick_cube(c->kmap, c->ksmap, A, c->g.nuz, c->g.dtype, grid, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "one-pass kick launch");
+    return VLASOV_OK;
+}
+
 // one kick D_uz D_uy D_ux (constants already in d_coef), in place
 static int run_kick(vlasov_ctx *c)
 {
     int rc;
+    if (c->can_kick_cube && c->fuse_kick >= 2) return run_kick_cube(c);
     if ((rc = run_velocity(c, 3))) return rc;
-    if (c->can_fuse_kick && c->fuse_kick) return run_kick_tail(c);
+    if (c->can_fuse_kick && c->fuse_kick >= 1) return run_kick_tail(c);
     if ((rc = run_velocity(c, 4))) return rc;
     return run_velocity(c, 5);
 }
 
-extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int on)
+extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int mode)
 {
     if (!c) return VLASOV_EINVAL;
-    c->fuse_kick = on != 0;
+    if (mode < 0 || mode > 2) return fail(c, VLASOV_EINVAL, "vlasov_set_fused_kick: mode %d is not 0, 1 or 2", mode);
+    c->fuse_kick = mode;
     return VLASOV_OK;
 }
 
@@ -1031,11 +1089,14 @@ static double position_numax(const vlasov_ctx *c, int ax, double dt, double a)
 static int slab_count(const vlasov_ctx *c, double dt, double a_half)
 {
     if (coded(c)) return 0; // the 16-bit encodes draw per-sweep random streams
-    const bool fused = c->can_fuse_kick && c->fuse_kick;
+    const bool cube = c->can_kick_cube && c->fuse_kick >= 2; // whole cubes: any x-slab
+    const bool fused = c->can_fuse_kick && c->fuse_kick >= 1;
     const bool rows = rows_sweep_supported(int(c->g.nuz), c->g.dtype);
-    if (!rows && (!c->use_lines || c->ltpp <= 0)) return 0;
-    if ((!use_reg_lines(c, 3) && c->splan_tpp[3] <= 0) || (!fused && !use_reg_lines(c, 4) && c->splan_tpp[4] <= 0))
-        return 0;
+    if (!cube) {
+        if (!rows && (!c->use_lines || c->ltpp <= 0)) return 0;
+        if ((!use_reg_lines(c, 3) && c->splan_tpp[3] <= 0) || (!fused && !use_reg_lines(c, 4) && c->splan_tpp[4] <= 0))
+            return 0;
+    }
     for (int ax = 1; ax <= 2; ++ax)
         if (c->splan_tpp[ax] <= 0 || !(position_numax(c, ax, dt, a_half) < 1.0)) return 0;
     for (int sl = kMaxSlabs; sl >= 2; --sl)

@@ -1,8 +1,8 @@
 """vlasov_step_host (one Eq. (5) step of a host buffer, its x-slabs copied in and out on a
 second stream behind the cell-local sweeps) against upload + vlasov_step + download: the
 same kernels on the same tiles, so the same f, rho and phi^{n+1} bit for bit, for a
-self-consistent step (Poisson between the kicks) with the fused kick tail and fused moment
-on and off, on 16 and on 8 slabs of one x-plane, and for a step that falls back to
+self-consistent step (Poisson between the kicks) with the one-pass kick, the fused kick
+tail and the separate sweeps, the fused moment on and off, on 16 and on 8 slabs of one x-plane, and for a step that falls back to
 the three calls in sequence (a whole-cell shift in D_y / D_z)."""
 import numpy as np
 import pytest
@@ -25,8 +25,8 @@ def _run(B, f0, phi0, bg, dt, a_half, host, fused):
     n = f0.shape[:3]
     f = torch.from_numpy(f0).cuda()
     v = B.Vlasov(f, V=V)
-    v.set_fused_kick(fused)
-    v.set_fused_moment(fused)
+    v.set_fused_kick(int(fused))
+    v.set_fused_moment(bool(fused))
     phi = torch.from_numpy(phi0).cuda()
     phi1 = torch.empty_like(phi)
     rho = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -44,12 +44,12 @@ def _run(B, f0, phi0, bg, dt, a_half, host, fused):
     _, launches = v.read_timers()
     out = (fh.numpy().copy(), rho.cpu().numpy(), phi1.cpu().numpy())
     v.close()
-    return out, launches["sweep_ux"]
+    return out, launches["sweep_ux"] + launches["kick"]
 
 
 @pytest.mark.parametrize("n,nu,a_half", [((16, 8, 8), (16, 16, 16), 0.55), ((8, 4, 4), (32, 32, 32), 0.55),
                                          ((16, 8, 8), (16, 16, 16), 0.12)])
-@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("fused", [2, 1, 0])
 def test_step_host_is_upload_step_download(n, nu, a_half, fused):
     B = _lib()
     V = 5.0
@@ -66,7 +66,8 @@ def test_step_host_is_upload_step_download(n, nu, a_half, fused):
     got, ux_launches = _run(B, f0, phi0, bg, dt, a_half, True, fused)
     for r, o in zip(ref, got):
         assert np.array_equal(r, o)
-    # up to 16 slabs (one per x-plane here): each kick runs u_x once per slab; the fallback once
+    # up to 16 slabs (one per x-plane here): each kick runs u_x (or the one-pass kick) once per
+    # slab; the fallback once
     assert ux_launches == (2 if a_half < 0.5 else 2 * min(16, n[0]))
 
 
