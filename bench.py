@@ -137,8 +137,9 @@ def measured_peaks():
 _COMMON_SOURCES = ("vk_common.cuh", "vk_kernels.h")
 KERNEL_SOURCES = {
     "sweep_x": ("sweep_stream.cu",), "sweep_y": ("sweep_stream.cu",), "sweep_z": ("sweep_stream.cu",),
-    "sweep_ux": ("sweep_lines.cu",), "sweep_uy": ("sweep_lines.cu",),  # register lines (FP32, n_u 16 / 32)
-    "sweep_uz": ("sweep_lines.cu",), "sweep_uyuz": ("sweep_lines.cu",),
+    "sweep_ux": ("sweep_lines.cu", "vk_lines.cuh"), "sweep_uy": ("sweep_lines.cu", "vk_lines.cuh"),
+    "sweep_uz": ("sweep_lines.cu", "vk_lines.cuh"), "sweep_uyuz": ("sweep_lines.cu", "vk_lines.cuh"),
+    "kick": ("kick_cube.cu", "vk_lines.cuh"),
 }
 
 

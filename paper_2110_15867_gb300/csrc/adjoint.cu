@@ -32,23 +32,9 @@
 namespace vk {
 
 constexpr int kAdjBlock = 256;
-#ifndef VK_ADJ_UNROLL
-#define VK_ADJ_UNROLL 1 // interior faces per loop iteration of the column march
-#endif
-#ifndef VK_ADJ_MINB
-#define VK_ADJ_MINB 3 // resident blocks per SM the FP32 column march is compiled for
-#endif
-#ifndef VK_ADJ_LCT
-#define VK_ADJ_LCT 1 // FP32 lines of 16, 32, 64 cells: unrolled instances
-#endif
-#ifndef VK_ADJ_MINB_U
-#define VK_ADJ_MINB_U 3 // the same for its unrolled (compile-time length) instances
-#endif
-constexpr int kAdjUnroll = VK_ADJ_UNROLL;
-#ifndef VK_ADJ_REG_MAX
-#define VK_ADJ_REG_MAX 32 // lines up to this length (compile-time instances) are marched in registers
-#endif
-constexpr int kAdjRegMax = VK_ADJ_REG_MAX;
+constexpr int kAdjUnroll = 1;    // interior faces per loop iteration of the column march
+constexpr int kAdjMinBlocks = 3; // resident blocks per SM the FP32 column march is compiled for
+constexpr int kAdjRegMax = 32;   // FP32 lines up to this length (compile-time instances) march in registers
 
 template <typename C> struct AdjLim {
     C w[5];  // weights of fbar
@@ -579,9 +565,7 @@ __device__ __forceinline__ long long adj_div(long long n, const AdjArgs<C> &a, c
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
 template <typename T, bool PERIODIC, bool SMALL4, int LCT>
-__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2
-                                             : (LCT > 16 && LCT <= VK_ADJ_REG_MAX) ? 2
-                                             : (LCT > 0 ? VK_ADJ_MINB_U : VK_ADJ_MINB))
+__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 16 && LCT <= kAdjRegMax) ? 2 : kAdjMinBlocks)
     adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
@@ -848,19 +832,19 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a_in, bo
         }
     } else if (a.periodic && a.L == 4) {
         adjoint_lines_kernel<T, true, true, 0><<<grid, kAdjBlock, 0, st>>>(a);
-    } else if constexpr (std::is_same<T, float>::value && VK_ADJ_LCT) {
+    } else if constexpr (std::is_same<T, float>::value) {
         // FP32: unrolled walks for the common line lengths
         const bool p = a.periodic;
-#define VK_ADJ_LINES(LL)                                                                                              \
+#define ADJ_LINES(LL)                                                                                              \
     if (a.L == LL) {                                                                                                  \
         if (p) adjoint_lines_kernel<T, true, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                               \
         else adjoint_lines_kernel<T, false, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                                \
         return cudaGetLastError();                                                                                    \
     }
-        VK_ADJ_LINES(16)
-        VK_ADJ_LINES(32)
-        VK_ADJ_LINES(64)
-#undef VK_ADJ_LINES
+        ADJ_LINES(16)
+        ADJ_LINES(32)
+        ADJ_LINES(64)
+#undef ADJ_LINES
         if (p) adjoint_lines_kernel<T, true, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
         else adjoint_lines_kernel<T, false, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
     } else {

@@ -7,14 +7,12 @@
 // with the 64-/128-byte hardware swizzle: 16-byte chunk j of row r lands at
 // chunk j ^ ((r * rowbytes >> 7) & (rowbytes / 16 - 1)), so eight threads that
 // each read a 16-byte chunk of eight consecutive rows hit eight different bank
-// groups.  In the default kernel (line_sweep1_kernel) each of 256 consumer
-// threads owns one row of the tile, pulls it into registers, marches it fully
-// unrolled (the orientation is a warp-uniform branch: all 256 rows of a tile
-// share a spatial cell), and writes it back for the TMA store; the older kernel
-// (line_sweep_kernel, VK_LINE_SINGLE=0) holds rows t and t + 128 as one packed
-// FP32 pair.  This replaces the shared-memory transpose of sweep_contig.cu, the
-// GPU analogue of the paper's load-and-transpose (LAT, Sec. 4.3), for these
-// line lengths.
+// groups.  Each of 256 consumer threads (line_sweep1_kernel) owns one row of
+// the tile, pulls it into registers, marches it fully unrolled (the orientation
+// is a warp-uniform branch: all 256 rows of a tile share a spatial cell), and
+// writes it back for the TMA store.  This replaces the shared-memory transpose
+// of sweep_contig.cu, the GPU analogue of the paper's load-and-transpose (LAT,
+// Sec. 4.3), for these line lengths.
 //
 // Fused kick tail (FUSE_Y, n_uy = n_uz): a tile of 256 rows is 256 / n_uy
 // whole (cell, j_x) planes of n_uy rows (j_y) by n_uz columns (j_z), so the
@@ -29,8 +27,7 @@
 
 namespace vk {
 
-constexpr int kLineThreads = 128;           // consumer threads; 2 rows each
-constexpr int kLineRows = 2 * kLineThreads; // rows per tile
+constexpr int kLineRows = 256;              // rows per tile, one per consumer thread
 constexpr int kLineRing = 2;                // tile slots
 
 template <int NU, typename T> struct LineGeom {
@@ -41,193 +38,8 @@ template <int NU, typename T> struct LineGeom {
     __device__ static int off(int r, int j) { return r * rowbytes + 16 * (j ^ ((r * rowbytes >> 7) & (chunks - 1))); }
 };
 
-// Rows r0 and r1 of a swizzled tile: gather (back to front when NEG, the
-// mirror image of a negative Courant number), march, scatter.  16-bit codes are
-// decoded with the rows' scales s0 / s1 and re-encoded with new scales, the
-// largest updated value of each line (written back through s0 / s1).  Returns
-// true when a line sum is negative, NaN or infinite.
-template <int NU, bool NEG, typename T>
-__device__ __forceinline__ bool line_pair(unsigned char *base, int r0, int r1, const Lim<float2> &lim, float &s0,
-                                          float &s1, unsigned long long e0, unsigned long long e1, unsigned seed)
-{
-    unsigned g0 = CODED_RNG_INIT(e0, seed), g1 = CODED_RNG_INIT(e1, seed);
-    using G_ = LineGeom<NU, T>;
-    constexpr int PER = G_::per;
-    constexpr bool CODED = sizeof(T) == 2;
-    float2 v[NU];
-#pragma unroll
-    for (int j = 0; j < G_::chunks; ++j) {
-        float a[PER], c[PER];
-        Chunk<T>::get(base + G_::off(r0, j), s0, a);
-        Chunk<T>::get(base + G_::off(r1, j), s1, c);
-#pragma unroll
-        for (int q = 0; q < PER; ++q) v[NEG ? NU - 1 - (PER * j + q) : PER * j + q] = make_float2(a[q], c[q]);
-    }
-    const float2 sum = march_regs<NU, float2>(v, lim);
-    float i0 = 1.f, i1 = 1.f;
-    if (CODED) {
-        float m0 = 0.f, m1 = 0.f;
-#pragma unroll
-        for (int l = 0; l < NU; ++l) {
-            m0 = fmaxf(m0, v[l].x);
-            m1 = fmaxf(m1, v[l].y);
-        }
-        s0 = coded_scale<T>(m0);
-        s1 = coded_scale<T>(m1);
-        i0 = inv_scale(s0);
-        i1 = inv_scale(s1);
-    }
-#pragma unroll
-    for (int j = 0; j < G_::chunks; ++j) {
-        float a[PER], c[PER];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const float2 x = v[NEG ? NU - 1 - (PER * j + q) : PER * j + q];
-            a[q] = x.x;
-            c[q] = x.y;
-        }
-        Chunk<T>::put(base + G_::off(r0, j), i0, a, g0);
-        Chunk<T>::put(base + G_::off(r1, j), i1, c, g1);
-    }
-    return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
-}
-
-// D_uy on the tile's planes (FP32, n_uy = n_uz = NU).  Warp w later sweeps
-// rows 32w..32w+31 and 128+32w..128+32w+31 along u_z, which are whole planes
-// (NU = 16 or 32 divides 32): lanes 0-15 take the first block of rows, lanes
-// 16-31 the second, and each lane owns one packed pair of adjacent columns of
-// one plane, so a warp only touches its own rows.  Returns true when a line
-// sum is negative, NaN or infinite.
-template <int NU, bool NEG>
-__device__ __forceinline__ bool plane_columns(unsigned char *base, int tid, const Lim<float2> &lim)
-{
-    using G_ = LineGeom<NU, float>;
-    const int w = tid >> 5, l = tid & 31;
-    const int within = l & 15;
-    const int r_first = ((l >> 4) ? kLineThreads : 0) + 32 * w + (within / (NU / 2)) * NU; // first row of the plane
-    const int c = 2 * (within % (NU / 2));
-    float2 v[NU];
-#pragma unroll
-    for (int i = 0; i < NU; ++i)
-        v[NEG ? NU - 1 - i : i] =
-            *reinterpret_cast<const float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4);
-    const float2 sum = march_regs<NU, float2>(v, lim);
-#pragma unroll
-    for (int i = 0; i < NU; ++i)
-        *reinterpret_cast<float2 *>(base + G_::off(r_first + i, c / G_::per) + (c % G_::per) * 4) =
-            v[NEG ? NU - 1 - i : i];
-    return !(sum.x >= 0.f) || !(sum.y >= 0.f) || isinf(sum.x) || isinf(sum.y);
-}
-
-template <int NU, typename T, bool FUSE_Y>
-__global__ void __launch_bounds__(kLineThreads + kProducer, 3)
-    line_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
-                      const __grid_constant__ ContigArgs<float> args)
-{
-    constexpr int S = kLineRing;
-    constexpr unsigned slot_bytes = kLineRows * NU * sizeof(T);
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *done = full + S;
-    // swizzled boxes need a 1024-byte aligned destination
-    unsigned char *ring = smem + 128 + ((1024u - ((smem_u32(smem) + 128u) & 1023u)) & 1023u);
-    auto slot = [&](unsigned e) { return ring + slot_bytes * (e % S); };
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&done[s], kLineThreads);
-        }
-        fence_barrier_init();
-    }
-    __syncthreads();
-
-    const long long Gd = gridDim.x, b = blockIdx.x;
-    const unsigned n_my = unsigned((args.num_tiles > b) ? (args.num_tiles - b + Gd - 1) / Gd : 0);
-
-    if (threadIdx.x < kProducer) {
-        if (threadIdx.x != 0) return;
-        unsigned loaded = 0, retired = 0;
-        bool ok = true;
-        while (retired < n_my) {
-            bool progress = false;
-            while (retired < loaded && mbar_test_wait(&done[retired % S], (retired / S) & 1u)) {
-                tma_store_2d(&dmap, slot(retired), 0, int((args.tile0 + b + (long long)retired * Gd) * kLineRows));
-                bulk_commit();
-                ++retired;
-                progress = true;
-            }
-            if (loaded < n_my && loaded < retired + S) {
-                if (loaded >= unsigned(S)) bulk_wait_read_at_most(retired - 1u - (loaded - S));
-                const unsigned st = loaded % S;
-                mbar_arrive_expect_tx(&full[st], slot_bytes);
-                tma_load_2d(slot(loaded), &map, &full[st], 0, int((args.tile0 + b + (long long)loaded * Gd) * kLineRows));
-                ++loaded;
-                progress = true;
-            }
-            if (!progress && !mbar_wait_bounded(&done[retired % S], (retired / S) & 1u)) {
-                ok = false;
-                break;
-            }
-        }
-        bulk_wait_all();
-        if (!ok) {
-            atomicOr(args.err, ERR_TIMEOUT);
-            for (unsigned t = retired; t < loaded; ++t) mbar_wait_bounded(&full[t % S], (t / S) & 1u);
-        }
-        return;
-    }
-
-    const int tid = threadIdx.x - kProducer;
-    const int r0 = tid, r1 = tid + kLineThreads;
-    for (unsigned k = 0; k < n_my; ++k) {
-        const unsigned st = k % S;
-        // all lanes of a warp leave together (the fused pass synchronises the warp)
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (k / S) & 1u))) {
-            atomicOr(args.err, ERR_TIMEOUT);
-            break;
-        }
-        const long long row0 = (args.tile0 + b + (long long)k * Gd) * kLineRows;
-        unsigned char *base = slot(k);
-        if constexpr (FUSE_Y) {
-            // every row of the tile belongs to one spatial cell
-            const LineCoefT<float> ky = args.cell_coef_y[fdiv(unsigned(row0), args.div_rpc)];
-            if (row0 < args.rows && ky.nd >= 0) {
-                const bool bad = (ky.nd & 1) ? plane_columns<NU, true>(base, tid, to_lim2(ky, ky))
-                                             : plane_columns<NU, false>(base, tid, to_lim2(ky, ky));
-                if (bad) atomicOr(args.err, ERR_NAN);
-            }
-            __syncwarp();
-        }
-        if (row0 + r0 < args.rows) {
-            const LineCoefT<float> kc = args.cell_coef[fdiv(unsigned(row0 + r0), args.div_rpc)];
-            if (kc.nd >= 0) {
-                float s0 = 1.f, s1 = 1.f;
-                if (sizeof(T) == 2) {
-                    s0 = args.scale[row0 + r0];
-                    s1 = args.scale[row0 + r1];
-                }
-                // one orientation per spatial cell, so the branch is warp-uniform
-                const unsigned long long e0 = (unsigned long long)(row0 + r0) * NU, e1 = (unsigned long long)(row0 + r1) * NU;
-                const bool bad = (kc.nd & 1)
-                                     ? line_pair<NU, true, T>(base, r0, r1, to_lim2(kc, kc), s0, s1, e0, e1, args.seed)
-                                     : line_pair<NU, false, T>(base, r0, r1, to_lim2(kc, kc), s0, s1, e0, e1, args.seed);
-                if (sizeof(T) == 2) {
-                    args.scale[row0 + r0] = s0;
-                    args.scale[row0 + r1] = s1;
-                }
-                if (bad) atomicOr(args.err, ERR_NAN);
-            }
-        }
-        fence_proxy_async();
-        mbar_arrive(&done[st]);
-    }
-}
-
-// One row per consumer thread (256 consumer threads, the same tiles and tensor
-// map as the paired kernel): half the registers of a row pair, so twice the
-// warps per SM, at the price of unpacked FP32 arithmetic.  16-bit codes use
-// the same per-row rounding streams as the paired kernel (bit-identical).
+// One row per consumer thread: a tile of 256 rows, 256 consumer threads and one
+// producer warp.
 constexpr int kLine1Threads = kLineRows;
 
 // D_uy on the tile's planes for the one-row kernel (FP32, n_uy = n_uz = NU):
@@ -429,9 +241,6 @@ __global__ void __launch_bounds__(kLine1Threads + kProducer, 3)
 // order (the march always flows toward +index).  16-bit codes: cell i decodes with
 // the scale of its u_z line (line0 + i Iz, Iz = n_inner / nuz u_z lines per row of
 // the swept axis), which the sweep keeps, and encodes back with stochastic rounding.
-#ifndef VK_REG_LINES48
-#define VK_REG_LINES48 1 // 1: u_x / u_y lines of 48 cells in registers too (128 registers, 2 CTAs per SM)
-#endif
 
 template <int L, typename T>
 __global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T *__restrict__ src, T *dst,
@@ -490,7 +299,7 @@ __global__ void __launch_bounds__(256, L > 32 ? 2 : 3) reg_lines_kernel(const T 
     if (!(sum >= 0.f) || isinf(sum)) atomicOr(a.err, ERR_NAN);
 }
 
-bool reg_lines_supported(int L) { return L == 16 || L == 32 || (VK_REG_LINES48 && L == 48); }
+bool reg_lines_supported(int L) { return L == 16 || L == 32 || L == 48; }
 
 template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst, const RegLineArgs &a, unsigned blocks,
                                                       cudaStream_t st)
@@ -499,7 +308,7 @@ template <typename T> static cudaError_t launch_reg_t(const void *src, void *dst
     T *d = static_cast<T *>(dst);
     if (a.L == 32) reg_lines_kernel<32, T><<<blocks, 256, 0, st>>>(s, d, a);
     else if (a.L == 16) reg_lines_kernel<16, T><<<blocks, 256, 0, st>>>(s, d, a);
-    else if (VK_REG_LINES48 && a.L == 48) reg_lines_kernel<48, T><<<blocks, 256, 0, st>>>(s, d, a);
+    else if (a.L == 48) reg_lines_kernel<48, T><<<blocks, 256, 0, st>>>(s, d, a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -650,32 +459,20 @@ cudaError_t launch_rows_sweep(const void *src, void *dst, const RowsArgs &args, 
     }
 }
 
-#ifndef VK_LINE_SINGLE
-#define VK_LINE_SINGLE 1 // 1: u_z lines one row per thread (0: two rows as a packed pair)
-#endif
-
-template <typename T> static const void *line_kernel_ptr(int nu)
-{
-    return nu == 32 ? (const void *)line_sweep_kernel<32, T, false> : (const void *)line_sweep_kernel<16, T, false>;
-}
-
-static bool line_single(int, bool) { return VK_LINE_SINGLE; }
-
 static const void *line_kernel_for(int nu, int dtype, bool fuse_y)
 {
-    if (line_single(dtype, fuse_y)) {
-        if (fuse_y && dtype == 2)
-            return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, true>
-                            : (const void *)line_sweep1_kernel<16, __nv_bfloat16, true>;
-        if (fuse_y && dtype == 3)
-            return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, true> : (const void *)line_sweep1_kernel<16, __half, true>;
-        if (fuse_y) return nu == 32 ? (const void *)line_sweep1_kernel<32, float, true> : (const void *)line_sweep1_kernel<16, float, true>;
-        if (dtype == 2) return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, false> : (const void *)line_sweep1_kernel<16, __nv_bfloat16, false>;
-        if (dtype == 3) return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, false> : (const void *)line_sweep1_kernel<16, __half, false>;
-        return nu == 32 ? (const void *)line_sweep1_kernel<32, float, false> : (const void *)line_sweep1_kernel<16, float, false>;
-    }
-    if (fuse_y) return nu == 32 ? (const void *)line_sweep_kernel<32, float, true> : (const void *)line_sweep_kernel<16, float, true>;
-    return dtype == 2 ? line_kernel_ptr<__nv_bfloat16>(nu) : dtype == 3 ? line_kernel_ptr<__half>(nu) : line_kernel_ptr<float>(nu);
+    if (fuse_y && dtype == 2)
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, true>
+                        : (const void *)line_sweep1_kernel<16, __nv_bfloat16, true>;
+    if (fuse_y && dtype == 3)
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, true> : (const void *)line_sweep1_kernel<16, __half, true>;
+    if (fuse_y) return nu == 32 ? (const void *)line_sweep1_kernel<32, float, true> : (const void *)line_sweep1_kernel<16, float, true>;
+    if (dtype == 2)
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, __nv_bfloat16, false>
+                        : (const void *)line_sweep1_kernel<16, __nv_bfloat16, false>;
+    if (dtype == 3)
+        return nu == 32 ? (const void *)line_sweep1_kernel<32, __half, false> : (const void *)line_sweep1_kernel<16, __half, false>;
+    return nu == 32 ? (const void *)line_sweep1_kernel<32, float, false> : (const void *)line_sweep1_kernel<16, float, false>;
 }
 
 // the ring of tiles, plus the FP32 tile copy of the 16-bit fused pass
@@ -684,7 +481,7 @@ size_t line_sweep_smem(int nu, int es, bool fuse_y)
     return 128 + 1024 + (size_t)kLineRing * kLineRows * nu * es + (fuse_y && es == 2 ? (size_t)kLineRows * nu * 4 : 0);
 }
 
-bool line_sweep_fused_supported(int dtype) { return dtype == 1 || (VK_LINE_SINGLE && (dtype == 2 || dtype == 3)); }
+bool line_sweep_fused_supported(int dtype) { return dtype >= 1 && dtype <= 3; }
 
 bool line_sweep_supported(int nu, long long rows_per_cell)
 {
@@ -705,7 +502,7 @@ cudaError_t launch_line_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), &a};
-    const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;
+    const int threads = kLine1Threads + kProducer;
     return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st);
 }
 
@@ -715,7 +512,7 @@ int occupancy_line_sweep(int nu, int dtype, bool fuse_y)
     const size_t smem = line_sweep_smem(nu, dtype == 1 ? 4 : 2, fuse_y);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
-    const int threads = (line_single(dtype, fuse_y) ? kLine1Threads : kLineThreads) + kProducer;
+    const int threads = kLine1Threads + kProducer;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
     return n;
 }

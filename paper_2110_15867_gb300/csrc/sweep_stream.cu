@@ -26,12 +26,7 @@
 
 namespace vk {
 
-#ifndef VK_STREAM_MINB
-#define VK_STREAM_MINB 4 // resident CTAs per SM the streamed sweep is compiled for
-#endif
-#ifndef VK_STREAM_SINGLE
-#define VK_STREAM_SINGLE 0 // 1: FP32 columns one per thread (0: packed pairs)
-#endif
+constexpr int kStreamMinBlocks = 4; // resident CTAs per SM the streamed sweep is compiled for
 
 // Per-thread view of the storage of its column(s): load a row as the compute
 // vector X and store X back.  FP32 / FP64 store f itself.  BF16 / FP16 store
@@ -87,20 +82,6 @@ template <> struct Lane<__half> {
     }
     __device__ static bool bad(X s) { return Lane<float>::bad(s); }
 };
-
-// FP32 storage walked one column per thread (twice the consumer threads of the
-// packed pairs, the same 256-column blocks)
-struct F32Single {
-    float v;
-};
-template <> struct Lane<F32Single> {
-    using X = float;
-    static constexpr int V = 1, NC = 2 * kStreamConsumers;
-    __device__ static X load(const F32Single *p, const float *) { return p->v; }
-    __device__ static void store(F32Single *p, X v, const float *, unsigned &) { p->v = v; }
-    __device__ static bool bad(X s) { return !(s >= 0.f) || isinf(s); }
-};
-template <> struct Compute<F32Single> { using type = float; };
 
 template <typename C, typename X> struct PairLim;
 template <> struct PairLim<float, float> {
@@ -292,10 +273,6 @@ __device__ __forceinline__ float lane_row_sum(const float *row, int lane)
     const float4 a = q[lane], b = q[lane + 32];
     return ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
 }
-__device__ __forceinline__ float lane_row_sum(const F32Single *row, int lane)
-{
-    return lane_row_sum(reinterpret_cast<const float *>(row), lane);
-}
 __device__ __forceinline__ double lane_row_sum(const double *row, int lane)
 {
     const double2 *q = reinterpret_cast<const double2 *>(row);
@@ -323,7 +300,7 @@ template <typename A> __device__ __forceinline__ A rows4_warp_sum(A v0, A v1, A 
 template <bool MOMENT> __host__ __device__ constexpr int stream_head() { return kProducer + (MOMENT ? 32 : 0); }
 
 template <typename T, bool PERIODIC, bool MOMENT = false>
-__global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), VK_STREAM_MINB)
+__global__ void __launch_bounds__(Lane<T>::NC + stream_head<MOMENT>(), kStreamMinBlocks)
     stream_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                         const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ StreamArgs<typename Compute<T>::type> args)
@@ -607,7 +584,6 @@ static cudaError_t launch_stream_t(const CUtensorMap &map, const CUtensorMap &dm
 cudaError_t launch_stream_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StreamArgs<float> &a, int grid,
                               size_t smem, cudaStream_t st)
 {
-    if (VK_STREAM_SINGLE) return launch_stream_t<F32Single>(map, dmap, map, a, grid, smem, st);
     return launch_stream_t<float>(map, dmap, map, a, grid, smem, st);
 }
 
@@ -634,13 +610,13 @@ template <typename T> static const void *stream_ptr(int periodic)
     return periodic ? (const void *)stream_sweep_kernel<T, true> : (const void *)stream_sweep_kernel<T, false>;
 }
 
-int stream_columns_per_thread(int dtype) { return dtype == 0 || (dtype == 1 && VK_STREAM_SINGLE) ? 1 : 2; }
-int stream_consumers(int dtype) { return dtype == 1 && VK_STREAM_SINGLE ? Lane<F32Single>::NC : kStreamConsumers; }
+int stream_columns_per_thread(int dtype) { return dtype == 0 ? 1 : 2; }
+int stream_consumers(int) { return kStreamConsumers; }
 
 int occupancy_stream(int dtype, int periodic, size_t smem)
 {
     const void *k = dtype == 0 ? stream_ptr<double>(periodic)
-                    : dtype == 1 ? (VK_STREAM_SINGLE ? stream_ptr<F32Single>(periodic) : stream_ptr<float>(periodic))
+                    : dtype == 1 ? stream_ptr<float>(periodic)
                     : dtype == 2 ? stream_ptr<__nv_bfloat16>(periodic)
                                  : stream_ptr<__half>(periodic);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;

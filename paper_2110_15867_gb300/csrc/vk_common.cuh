@@ -227,9 +227,6 @@ __device__ __forceinline__ double mx2(double a, double b) { return fmax(a, b); }
 // per-sweep seed; the stream then advances with the 32-bit linear congruential
 // generator of Numerical Recipes (a = 1664525, c = 1013904223), whose upper 16
 // bits feed one value each.  A run is reproducible.
-#ifndef VK_SR
-#define VK_SR 1
-#endif
 
 __device__ __forceinline__ unsigned fmix32(unsigned h)
 {
@@ -253,29 +250,13 @@ __device__ __forceinline__ unsigned lcg_next(unsigned &x)
 }
 
 
-// two non-negative FP32 values -> packed bf16x2; rnd supplies 16 random bits per value
-__device__ __forceinline__ unsigned pack_bf16x2(float x, float y, unsigned rnd)
-{
-#if VK_SR
-    const unsigned a = (__float_as_uint(x) + (rnd & 0xffffu)) >> 16;
-    const unsigned b = (__float_as_uint(y) + (rnd >> 16)) >> 16;
-    return a | (b << 16);
-#else
-    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-    return *reinterpret_cast<const unsigned *>(&h);
-#endif
-}
-
-// The same from the stream directly: the upper 16 bits of two LCG steps, added below the
-// BF16 mantissa of x and of y; one byte permute packs the two upper halves.
+// Two non-negative FP32 values -> packed bf16x2 with stochastic rounding: the upper 16
+// bits of two LCG steps are added below the BF16 mantissa of x and of y, and one byte
+// permute packs the two upper halves.
 __device__ __forceinline__ unsigned sr_pack_bf16x2(float x, float y, unsigned &rng)
 {
-#if VK_SR
     const unsigned r1 = lcg_next(rng) >> 16, r2 = lcg_next(rng) >> 16;
     return __byte_perm(__float_as_uint(x) + r1, __float_as_uint(y) + r2, 0x7632);
-#else
-    return pack_bf16x2(x, y, 0u);
-#endif
 }
 
 // Line scales of the 16-bit codec.  coded_scale: the scale a refresh stores for a line
@@ -289,32 +270,16 @@ template <typename T> __device__ __forceinline__ float coded_scale(float m) { re
 template <> __device__ __forceinline__ float coded_scale<__nv_bfloat16>(float m) { return fmaxf(m, 0x1p-64f); }
 __device__ __forceinline__ float inv_scale(float s) { return s >= 0x1p-126f ? __fdividef(1.f, s) : 0.f; }
 
-// two non-negative FP32 values -> packed f16x2 (13 random bits below the FP16 mantissa)
-__device__ __forceinline__ unsigned pack_f16x2(float x, float y, unsigned rnd)
-{
-#if VK_SR
-    const float xr = __uint_as_float(__float_as_uint(x) + (rnd & 0x1fffu));
-    const float yr = __uint_as_float(__float_as_uint(y) + ((rnd >> 16) & 0x1fffu));
-    const __half2 h = __halves2half2(__float2half_rz(xr), __float2half_rz(yr));
-#else
-    const __half2 h = __floats2half2_rn(x, y);
-#endif
-    return *reinterpret_cast<const unsigned *>(&h);
-}
-
-// The same from the stream directly (13 of the upper 16 bits of two LCG steps); one
-// round-toward-zero conversion packs both (x in the lower half).
+// Two non-negative FP32 values -> packed f16x2 with stochastic rounding: 13 of the upper
+// 16 bits of two LCG steps are added below the FP16 mantissa (13 bits below FP32's), and
+// one round-toward-zero conversion packs both (x in the lower half).
 __device__ __forceinline__ unsigned sr_pack_f16x2(float x, float y, unsigned &rng)
 {
-#if VK_SR
     const unsigned r1 = (lcg_next(rng) >> 16) & 0x1fffu, r2 = (lcg_next(rng) >> 16) & 0x1fffu;
     const float xr = __uint_as_float(__float_as_uint(x) + r1), yr = __uint_as_float(__float_as_uint(y) + r2);
     unsigned out;
     asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yr), "f"(xr));
     return out;
-#else
-    return pack_f16x2(x, y, 0u);
-#endif
 }
 
 // ----------------------------------------------------------------------------
@@ -323,10 +288,6 @@ __device__ __forceinline__ unsigned sr_pack_f16x2(float x, float y, unsigned &rn
 // act per component)
 // ----------------------------------------------------------------------------
 
-#ifndef VK_PACKED
-#define VK_PACKED 1 // 1: float2 add/sub/mul/fma as one f32x2 instruction; 0: two FP32 instructions
-#endif
-#if VK_PACKED
 #define VK_F2_BINOP(name, op)                                                                        \
     __device__ __forceinline__ float2 name(float2 a, float2 b)                                        \
     {                                                                                                 \
@@ -352,15 +313,6 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return d;
 }
-#else
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
-{
-    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-#endif
 __device__ __forceinline__ float vadd(float a, float b) { return a + b; }
 __device__ __forceinline__ float vsub(float a, float b) { return a - b; }
 __device__ __forceinline__ float vmul(float a, float b) { return a * b; }

@@ -94,9 +94,6 @@ struct AxisPlan {
 } // namespace
 
 constexpr int kMaxSlabs = 16; // x-slabs of the pipelined host-buffer step
-#ifndef VK_REG_LINES
-#define VK_REG_LINES 1 // FP32 u_x / u_y sweeps of 16 or 32 cells: whole lines in registers (0: streamed)
-#endif
 
 struct vlasov_ctx {
     vlasov_grid g;
@@ -793,7 +790,7 @@ static int line_grid(const vlasov_ctx *, int grid, long long tiles) { return int
 // u_x / u_y on FP32 or 16-bit storage with lines of 16 or 32 cells: the register-line kernel
 static bool use_reg_lines(const vlasov_ctx *c, int ax)
 {
-    if (!VK_REG_LINES || c->g.dtype == VLASOV_F64 || (ax != 3 && ax != 4)) return false;
+    if (c->g.dtype == VLASOV_F64 || (ax != 3 && ax != 4)) return false;
     const int L = (&c->g.nux)[ax - 3];
     // FP32 u_x lines of 48 cells stream faster (48^3 x 48^3: 20.7 ms against 22.3 in registers;
     // u_y 23.8 streamed against 22.0, BF16 u_x 29.6 / 28.6 and u_y 33.7 / 27.8)
