@@ -76,6 +76,9 @@ def parse():
                    help="run the small profiling case instead of the benchmark: sweeps on a "
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
     p.add_argument("--axes", default="0,1,2,3,4,5", help="sweep axes of --profile-case")
+    p.add_argument("--profile-shape", default="64,8,8",
+                   help="spatial cells nx,ny,nz of --profile-case (32^3 velocity cells)")
+    p.add_argument("--streamed", action="store_true", help="--profile-case runs the streamed position sweeps")
     p.add_argument("--adjoint", action="store_true", help="--profile-case runs the adjoint sweeps")
     p.add_argument("--step", action="store_true", help="--profile-case runs one Eq. (5) step (fused kick tail)")
     return p.parse_args()
@@ -844,7 +847,7 @@ def run_profile_case(args):
     import torch
     from paper_2110_15867_gb300 import binding as B
     from paper_2110_15867_gb300 import inputs as I
-    n, nu, V = (64, 8, 8), 32, 5.0
+    n, nu, V = tuple(int(x) for x in args.profile_shape.split(",")), 32, 5.0
     axes = [int(a) for a in args.axes.split(",")]
     dev = torch.device("cuda", 0)
     delta = torch.from_numpy(I.gaussian_field(n, 0.05, seed=2)).to(dev)
@@ -869,6 +872,8 @@ def run_profile_case(args):
                 v.sweep_adjoint(f, lam, ax, 0.7 / cmax[ax], 1.0, phi, dLdg if ax >= 3 else None)
     else:
         v = B.Vlasov(f, V=V)
+        if args.streamed:
+            v.set_position_tiles(False)
         for _ in range(2):
             for ax in axes:
                 v.sweep(ax, 0.7 / cmax[ax], 1.0, phi)

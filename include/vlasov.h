@@ -161,6 +161,17 @@ int vlasov_set_fused_kick(vlasov_ctx *ctx, int mode);
 int vlasov_kick(vlasov_ctx *ctx, double dt, const float *phi_dev);
 
 /*
+ * Position sweeps (Eq. 3, |nu| < 1) on FP32 storage with lines of 16, 24, 32, 48
+ * or 64 cells and a multiple of 256 cells on the faster axes run with whole
+ * lines staged in shared memory: each tile of 256 lines x all their cells is
+ * loaded once, every line is marched in registers by one thread and the tile is
+ * stored once (the same arithmetic as the streamed sweep, bit for bit).  On by
+ * default; on = 0 runs the streamed sweep (chunks of rows moving down the line),
+ * which FP64 and 16-bit storage and other shapes always use.
+ */
+int vlasov_set_position_tiles(vlasov_ctx *ctx, int on);
+
+/*
  * The moment rho_nu that vlasov_step and vlasov_step_record_sc take after the
  * drift (Eq. 5, Sec. 4.1.3) is summed by the x sweep itself when that sweep is
  * streamed (|nu| < 1 in every velocity column) on FP32 or FP64 storage and the

@@ -46,7 +46,8 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_step_adjoint", "vlasov_step_record", "vlasov_step_adjoint_recorded",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
-           "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host", "vlasov_encode", "vlasov_decode")
+           "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host", "vlasov_encode", "vlasov_decode",
+           "vlasov_set_position_tiles")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -127,6 +128,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_moments.restype = ctypes.c_int
     L.vlasov_set_fused_kick.argtypes = [_VP, ctypes.c_int]
     L.vlasov_set_fused_kick.restype = ctypes.c_int
+    L.vlasov_set_position_tiles.argtypes = [_VP, ctypes.c_int]
+    L.vlasov_set_position_tiles.restype = ctypes.c_int
     L.vlasov_set_fused_moment.argtypes = [_VP, ctypes.c_int]
     L.vlasov_set_fused_moment.restype = ctypes.c_int
     L.vlasov_kick.argtypes = [_VP, ctypes.c_double, _VP]
@@ -584,6 +587,10 @@ class Vlasov:
         (n_ux = n_uy = n_uz = 16 or 32), 1 (or True) D_ux then D_uy D_uz in one pass, 0 (or
         False) three separate sweeps."""
         vlasov_set_fused_kick(self.ctx, int(mode))
+
+    def set_position_tiles(self, on: bool = True):
+        """Run the FP32 position sweeps on whole staged lines (the default) or streamed."""
+        _check(self.ctx, load().vlasov_set_position_tiles(self.ctx, int(bool(on))))
 
     def set_fused_moment(self, on: bool = True):
         """Let the step's x sweep sum the moment of its output (FP32 / FP64 storage)."""

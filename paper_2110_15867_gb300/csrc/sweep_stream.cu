@@ -195,17 +195,19 @@ __device__ __forceinline__ X march_stream(const Lim<X> &lim, unsigned e, unsigne
     } else {
         constexpr int LA = 3;
         // window c_{i-1} .. c_{i+3}, donor c_{i+1}, flux toward -index
+        // curvatures are summed in the marching order (toward -index), as every kernel
+        // that walks a line with a negative Courant number from its far end sums them
         const X s2 = LN::load(row_ptr(2), srow_ptr(2));
-        const X dmn = curv(p2, p1, s0); // d_{-1}
-        const X d0 = curv(p1, s0, s1);
-        const X d1 = curv(s0, s1, s2);
+        const X dmn = curv(s0, p1, p2); // d_{-1}
+        const X d0 = curv(s1, s0, p1);
+        const X d1 = curv(s2, s1, s0);
         X dm4a = dm4(d0, d1);           // limited curvature at face i+1/2
         X Fm;                            // mass moving left through face i-1/2
         if (PERIODIC) Fm = sl_mpp5_flux(lim, s2, s1, s0, p1, p2, dm4a, dm4(dmn, d0));
         else Fm = zero;
         X cm1 = p1, c0 = s0, cp1 = s1, cp2 = s2, d_1 = d1;
         auto face = [&](X cp3, T *dst, const float *dsc) {
-            const X d_2 = curv(cp1, cp2, cp3);
+            const X d_2 = curv(cp3, cp2, cp1);
             const X dm4b = dm4(d_1, d_2); // face i+3/2
             const X F = sl_mpp5_flux(lim, cp3, cp2, cp1, c0, cm1, dm4b, dm4a);
             const X out = vadd(c0, vsub(F, Fm));

@@ -1,0 +1,325 @@
+// sweep_tile.cu -- position sweeps D_x, D_y, D_z of Eq. (3) (periodic lines,
+// |nu| < 1) on FP32 storage with whole lines staged in shared memory.
+//
+// f is viewed as [O][L][I] (slower axes, the swept axis of L cells, the faster
+// axes) and the faster axes I are cut into tiles of 256 contiguous columns: a
+// tile holds every cell of 256 lines (L rows of 1 KB), loaded and stored by one
+// TMA box {32, 8, L} of the 4D view [O][L][I / 32][32] with the 128-byte swizzle,
+// so that 16-byte chunk j of the 128-byte unit u of a row lands at chunk
+// j ^ (u & 7).  A thread owns one column (one line of Eq. 3, whose Courant number
+// nu_j = u_j dt / (a^2 dx) depends only on the column's velocity index j) and
+// marches it fully unrolled in registers with a sliding five-cell window, reading
+// each row once and writing it back in place (SL-MPP5, the same code as every
+// other sweep).  Groups of 256 threads work on different tiles; a ring of
+// groups + 1 tile slots, filled and drained by one producer thread, keeps the
+// next tile loading while the groups march theirs.  The orientation of a line
+// is its sign of nu.  In the x and y sweeps it is the same for whole tiles; when
+// every tile a CTA takes has one sign, or the tiles can be taken sign by sign (all
+// tiles of u < 0 first, in runs long enough to keep DRAM pages whole), an SM runs
+// one unrolled march with a fixed direction at a time.  Otherwise, and in the z
+// sweep (n_uz = 32), where the sign flips in the middle of every u_z line, the march
+// takes its direction at run time (one body: two unrolled copies running side by
+// side would not fit the instruction cache); there warps take the 16 columns of one
+// sign of two u_z lines four units apart (no bank conflicts under the swizzle).  For the x sweep the group's
+// warps also add up every marched tile's rows into per-cell partials of rho_nu (the
+// moment of Eq. 5 is taken right after this sweep), in the order of the streamed
+// sweep's moment warp.
+#include "vk_common.cuh"
+
+namespace vk {
+
+namespace {
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *src, int c0, int c1, int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// thread groups (256 columns each) marching tiles at once; the ring holds one slot more
+template <int L> constexpr int tile_groups() { return L <= 48 ? 3 : 2; }
+template <int L> constexpr unsigned tile_bytes() { return unsigned(L) * 1024u; }
+// barriers (128 B), the velocity-column table, alignment to 1 KB, the ring
+constexpr size_t kTileHeader = 128 + kMaxVel * sizeof(LineCoefT<float>);
+template <int L> constexpr size_t tile_smem() { return kTileHeader + 1024 + size_t(tile_groups<L>() + 1) * tile_bytes<L>(); }
+
+// March the periodic line p[0], p[st], ..., p[(L - 1) st] (flow toward +index) in place;
+// st < 0 walks a line with a negative Courant number from its far end.  DIR = +1 / -1 fixes
+// the stride at compile time; DIR = 0 takes it at run time, one body for both
+// orientations: in the z sweep both run side by side on every SM, and two unrolled copies
+// would not fit the instruction cache.  Returns the sum of the new values.
+template <int L, int DIR>
+__device__ __forceinline__ float march_tile(float *p, int st_rt, const Lim<float> &lim)
+{
+    const int st = DIR == 0 ? st_rt : DIR * 256; // rows are 256 floats apart
+    auto cv = [](float x, float y, float z) { return curv(x, y, z); };
+    const float a = p[(L - 3) * st], b = p[(L - 2) * st], c = p[(L - 1) * st];
+    const float s0 = p[0], s1 = p[st];
+    const float dmm = cv(a, b, c), dm = cv(b, c, s0), d0 = cv(c, s0, s1);
+    float dm4m = dm4(dm, d0);
+    float Fm = sl_mpp5_flux(lim, a, b, c, s0, s1, dm4(dmm, dm), dm4m); // face -1/2, donor c_{-1}
+    float cm2 = b, cm1 = c, c0 = s0, cp1 = s1, dcur = d0, sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const float cp2 = i + 2 < L ? p[(i + 2) * st] : (i + 2 == L ? s0 : s1);
+        const float dn = cv(c0, cp1, cp2);
+        const float dm4p = dm4(dcur, dn);
+        const float F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
+        const float out = c0 + (Fm - F);
+        p[i * st] = out;
+        sum += out;
+        cm2 = cm1;
+        cm1 = c0;
+        c0 = cp1;
+        cp1 = cp2;
+        dcur = dn;
+        dm4m = dm4p;
+        Fm = F;
+    }
+    return sum;
+}
+
+// The logical 16-byte chunks lane and lane + 32 of a swizzled 1-KB row (chunk j of unit u
+// is stored at chunk j ^ (u & 7) of that unit), summed in the order the streamed x sweep
+// sums its unswizzled rows: the partial sums agree bit for bit.
+__device__ __forceinline__ float lane_row_sum1k(const float *row, int lane)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(row);
+    const int u = lane >> 3, j = lane & 7;
+    const float4 x = q[u * 8 + (j ^ u)], y = q[(u + 4) * 8 + (j ^ (u + 4))];
+    return ((x.x + x.y) + (x.z + x.w)) + ((y.x + y.y) + (y.z + y.w));
+}
+
+// rows v0..v3 of 32 lanes each -> lane l holds the total of row l >> 3 (a fixed butterfly)
+__device__ __forceinline__ float rows4_sum(float v0, float v1, float v2, float v3, int lane)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool hi = lane & 16, odd = lane & 8;
+    float k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+    k0 += __shfl_xor_sync(kAll, hi ? v0 : v2, 16);
+    k1 += __shfl_xor_sync(kAll, hi ? v1 : v3, 16);
+    float k = odd ? k1 : k0;
+    k += __shfl_xor_sync(kAll, odd ? k0 : k1, 8);
+    k += __shfl_xor_sync(kAll, k, 4);
+    k += __shfl_xor_sync(kAll, k, 2);
+    k += __shfl_xor_sync(kAll, k, 1);
+    return k;
+}
+
+// SIGNED: every tile has one sign of u (TileArgs::tile_sign), marched with a fixed direction
+template <int L, bool MOMENT, bool SIGNED>
+__global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
+    tile_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
+                      const __grid_constant__ TileArgs a)
+{
+    constexpr int NG = tile_groups<L>(), S = NG + 1, NT = NG * 256;
+    constexpr unsigned TB = tile_bytes<L>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem); // S: the slot holds its tile
+    uint64_t *done = full + S;                           // S: the tile's group is done with it
+    uint64_t *marched = done + S;                        // NG: every column of the group's tile is marched
+    LineCoefT<float> *tab = reinterpret_cast<LineCoefT<float> *>(smem + 128);
+    static_assert((2 * S + NG) * 8 <= 128, "barriers fit ahead of the table");
+    unsigned char *ring = smem + kTileHeader + ((1024u - ((smem_u32(smem) + unsigned(kTileHeader)) & 1023u)) & 1023u);
+    auto slot = [&](unsigned k) { return reinterpret_cast<float *>(ring + size_t(TB) * (k % S)); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], 256);
+        }
+        for (int g = 0; g < NG; ++g) mbar_init(&marched[g], 256);
+        fence_barrier_init();
+    }
+    for (int j = threadIdx.x; j < a.nvel; j += blockDim.x) tab[j] = a.table[j];
+    __syncthreads();
+
+    const long long G = gridDim.x, b = blockIdx.x;
+    const unsigned n_my = unsigned(a.num_tiles > b ? (a.num_tiles - b + G - 1) / G : 0);
+    auto coords = [&](unsigned k, int &u0, int &o) {
+        long long m = b + (long long)k * G, t;
+        if (a.sort_half > 0) {
+            // the tiles of u < 0 first, then those of u > 0: runs of sort_half tiles alternate
+            // in sign, and a CTA then meets one orientation at a time
+            const long long half = a.num_tiles / 2, pos = m >= half ? 1 : 0, mm = m - pos * half;
+            t = a.tile0 + (mm / a.sort_half) * 2 * a.sort_half + pos * a.sort_half + mm % a.sort_half;
+        } else {
+            t = a.tile0 + m;
+        }
+        const long long oq = t / a.tiles_inner;
+        u0 = int((t - oq * a.tiles_inner) * 8); // first 32-column unit of the tile
+        o = int(oq);
+    };
+
+    if (threadIdx.x >= NT) {
+        // producer: one thread drives the TMA engine
+        if (threadIdx.x != NT) return;
+        auto load = [&](unsigned k) {
+            int u0, o;
+            coords(k, u0, o);
+            mbar_arrive_expect_tx(&full[k % S], TB);
+            tma_load_4d(slot(k), &map, &full[k % S], 0, u0, 0, o);
+        };
+        unsigned loaded = 0;
+        for (; loaded < unsigned(S) && loaded < n_my; ++loaded) load(loaded);
+        bool ok = true;
+        for (unsigned k = 0; k < n_my; ++k) {
+            if (!mbar_wait_bounded(&done[k % S], (k / S) & 1u)) {
+                ok = false;
+                break;
+            }
+            int u0, o;
+            coords(k, u0, o);
+            tma_store_4d(&dmap, slot(k), 0, u0, 0, o);
+            bulk_commit();
+            if (loaded < n_my) {
+                bulk_wait_read_all(); // the slot is free once the store has read it
+                load(loaded++);
+            }
+        }
+        bulk_wait_all();
+        if (!ok) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            for (unsigned k = 0; k < loaded; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1u);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, w = tid >> 5, lane = tid & 31;
+    int unit, e; // the thread's column: 32-column unit of the tile and position in it
+    if (a.zperm) {
+        // z sweep, n_uz = 32: warps 0-3 take u_z < 0 (e < 16), warps 4-7 u_z > 0, each
+        // warp the same half of units w % 4 and w % 4 + 4
+        unit = (w & 3) + (lane < 16 ? 0 : 4);
+        e = (w >> 2) * 16 + (lane & 15);
+    } else {
+        unit = w;
+        e = lane;
+    }
+    // swizzled offset of the column inside a 1-KB row, in floats
+    const int coff = unit * 32 + (((e >> 2) ^ (unit & 7)) << 2) + (e & 3);
+    bool bad = false;
+    for (unsigned k = grp; k < n_my; k += NG) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[k % S], (k / S) & 1u))) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            return;
+        }
+        int u0, o;
+        coords(k, u0, o);
+        const long long inner = 32ll * (u0 + unit) + e;
+        const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
+        float *p = slot(k) + coff;
+        if (kc.nd >= 0) {
+            const Lim<float> lim = to_lim(kc);
+            // a negative Courant number is the mirror image: march the line from its far end
+            const bool neg = kc.nd & 1;
+            float sum;
+            if constexpr (!SIGNED) sum = march_tile<L, 0>(neg ? p + (L - 1) * 256 : p, neg ? -256 : 256, lim);
+            else if (neg) sum = march_tile<L, -1>(p + (L - 1) * 256, 0, lim); // one sign per tile
+            else sum = march_tile<L, 1>(p, 0, lim);
+            bad |= !(sum >= 0.f) || isinf(sum);
+        }
+        if constexpr (MOMENT) {
+            // x sweep: once the group's tile is marched, warp w adds up rows 4q .. 4q + 3 for
+            // q = w, w + 8, ...: row x of the tile whose first column is c0 adds to spatial
+            // cell x (n_inner / cube) + c0 / cube as its partial (c0 % cube) / 256, stored at
+            // mpart[((c0 / cube) nparts + part) L + x]
+            const unsigned j = k / NG; // the group's tile count: the phase of its barrier
+            mbar_arrive(&marched[grp]);
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&marched[grp], j & 1u))) {
+                atomicOr(a.err, ERR_TIMEOUT);
+                return;
+            }
+            const long long c0 = 32ll * u0;
+            float *base = static_cast<float *>(a.mpart) + ((c0 / a.cube) * a.nparts + (c0 % a.cube) / 256) * (long long)L;
+            const float *q = slot(k);
+#pragma unroll
+            for (int r = 4 * w; r < L; r += 32) {
+                const float tot = rows4_sum(lane_row_sum1k(q + r * 256, lane), lane_row_sum1k(q + (r + 1) * 256, lane),
+                                            lane_row_sum1k(q + (r + 2) * 256, lane),
+                                            lane_row_sum1k(q + (r + 3) * 256, lane), lane);
+                if ((lane & 7) == 0) base[r + (lane >> 3)] = tot;
+            }
+        }
+        fence_proxy_async();
+        mbar_arrive(&done[k % S]);
+    }
+    if (bad) atomicOr(a.err, ERR_NAN);
+}
+
+template <int L> const void *tile_kernel(bool moment, bool sign)
+{
+    if (sign) return moment ? (const void *)tile_sweep_kernel<L, true, true> : (const void *)tile_sweep_kernel<L, false, true>;
+    return moment ? (const void *)tile_sweep_kernel<L, true, false> : (const void *)tile_sweep_kernel<L, false, false>;
+}
+
+const void *tile_kernel_for(int L, bool moment, bool sign = true)
+{
+    switch (L) {
+    case 16: return tile_kernel<16>(moment, sign);
+    case 24: return tile_kernel<24>(moment, sign);
+    case 32: return tile_kernel<32>(moment, sign);
+    case 48: return tile_kernel<48>(moment, sign);
+    case 64: return tile_kernel<64>(moment, sign);
+    default: return nullptr;
+    }
+}
+
+size_t tile_smem_for(int L)
+{
+    switch (L) {
+    case 16: return tile_smem<16>();
+    case 24: return tile_smem<24>();
+    case 32: return tile_smem<32>();
+    case 48: return tile_smem<48>();
+    default: return tile_smem<64>();
+    }
+}
+
+int tile_threads_for(int L, bool) { return (L <= 48 ? 3 : 2) * 256 + kProducer; }
+
+} // namespace
+
+bool tile_sweep_supported(int L, long long n_inner) { return tile_kernel_for(L, false) && n_inner % 256 == 0; }
+
+int occupancy_tile_sweep(int L, bool moment)
+{
+    const void *k = tile_kernel_for(L, moment);
+    if (!k) return 0;
+    const size_t smem = tile_smem_for(L);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tile_threads_for(L, moment), smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const TileArgs &a, int grid,
+                              cudaStream_t st)
+{
+    if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
+    const bool moment = a.mpart != nullptr;
+    const void *k = tile_kernel_for(a.L, moment, a.tile_sign != 0);
+    if (!k || a.nvel <= 0 || a.nvel > kMaxVel || a.vstride <= 0 || a.tiles_inner <= 0) return cudaErrorInvalidValue;
+    if (moment && (a.cube % 256 || a.nparts <= 0)) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem_for(a.L);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    void *params[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<TileArgs *>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(tile_threads_for(a.L, moment)), params, smem, st);
+}
+
+} // namespace vk

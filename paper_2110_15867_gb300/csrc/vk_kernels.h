@@ -218,6 +218,34 @@ int occupancy_kick_cube(int nu, int dtype);
 cudaError_t launch_kick_cube(const CUtensorMap &fmap, const CUtensorMap &smap, const KickArgs &a, int nu, int dtype,
                              int grid, cudaStream_t st);
 
+// ----------------------------------------------------------------------------
+// position sweeps with whole lines staged per tile (sweep_tile.cu): FP32, periodic,
+// |nu| < 1, L = 16, 24, 32, 48 or 64 cells, n_inner a multiple of 256.  map views f as
+// [n_outer][L][n_inner / 32][32] with box {32, 8, L, 1} and the 128-byte swizzle.
+// ----------------------------------------------------------------------------
+struct TileArgs {
+    int L;
+    long long n_inner, n_outer, tiles_inner; // tiles_inner = n_inner / 256
+    long long tile0, num_tiles;              // tiles [tile0, tile0 + num_tiles), t = outer tiles_inner + block
+    long long vstride;                       // column j takes table[(inner / vstride) % nvel]
+    int nvel;
+    int zperm;                               // z sweep with n_uz = 32: warps grouped by the sign of u_z
+    long long sort_half;                     // > 0: runs of sort_half tiles alternate in the sign of u
+                                             // (num_tiles a multiple of 2 sort_half): taken sign by sign
+    int tile_sign;                           // 1: every column of a tile has one sign of u (else per column)
+    unsigned *err;
+    // x sweep with the moment: per-cell partial sums as in StreamArgs (null: no moment)
+    void *mpart;
+    long long cube;
+    int nparts;
+    LineCoefT<float> table[kMaxVel];
+};
+bool tile_sweep_supported(int L, long long n_inner);
+int occupancy_tile_sweep(int L, bool moment);
+// tiles are loaded through map and stored through dmap (the same map for an in-place sweep)
+cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const TileArgs &a, int grid,
+                              cudaStream_t st);
+
 // host launchers (return cudaGetLastError() of the launch); tiles are loaded
 // through map and stored through dmap (the same map for an in-place sweep)
 cudaError_t launch_strided_f32(const CUtensorMap &map, const CUtensorMap &dmap, const StridedArgs<float> &a, int grid,

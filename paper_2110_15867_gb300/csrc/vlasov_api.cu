@@ -41,16 +41,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 struct MapSpec {
     CUtensorMapDataType type;
     cuuint32_t rank;
-    cuuint64_t gdim[3];
-    cuuint64_t gstr[2];
-    cuuint32_t box[3];
+    cuuint64_t gdim[4];
+    cuuint64_t gstr[3];
+    cuuint32_t box[4];
     CUtensorMapSwizzle swz;
     CUtensorMapL2promotion promo;
 };
 
 CUresult encode_spec(CUtensorMap *m, const MapSpec &s, const void *base)
 {
-    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     return encode_fn()(m, s.type, s.rank, const_cast<void *>(base), s.gdim, s.gstr, s.box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, s.swz, s.promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
@@ -78,6 +78,20 @@ MapSpec spec_rows(CUtensorMapDataType type, long long L, long long rows, size_t 
     s.gstr[0] = (cuuint64_t)(L * es);
     s.box[0] = (cuuint32_t)L; s.box[1] = (cuuint32_t)R;
     s.swz = swz;
+    s.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+    return s;
+}
+
+// f as [O][L][I / 32][32] FP32 with box {32, 8, L, 1}: the tiles of the staged position sweeps
+MapSpec spec_tiles(long long I, long long L, long long O)
+{
+    MapSpec s{};
+    s.type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    s.rank = 4;
+    s.gdim[0] = 32; s.gdim[1] = (cuuint64_t)(I / 32); s.gdim[2] = (cuuint64_t)L; s.gdim[3] = (cuuint64_t)O;
+    s.gstr[0] = 128; s.gstr[1] = (cuuint64_t)(I * 4); s.gstr[2] = (cuuint64_t)(I * L * 4);
+    s.box[0] = 32; s.box[1] = 8; s.box[2] = (cuuint32_t)L; s.box[3] = 1;
+    s.swz = CU_TENSOR_MAP_SWIZZLE_128B;
     s.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
     return s;
 }
@@ -118,6 +132,12 @@ struct vlasov_ctx {
     // kick tail D_uz D_uy fused in the u_z line kernel (n_uy = n_uz)
     bool can_fuse_kick;
     int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
+    // position sweeps with whole lines staged per tile (FP32; see vlasov_set_position_tiles)
+    bool tile_ok[3], use_tiles;
+    CUtensorMap tmap[3];
+    MapSpec tspec[3];
+    int tgrid[3];
+    long long ttiles_inner[3], tn_outer[3];
     // the whole kick D_uz D_uy D_ux in one pass (n_ux = n_uy = n_uz = 16 or 32)
     bool can_kick_cube;
     CUtensorMap kmap, ksmap;
@@ -393,6 +413,23 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
         const long long rpp = c->lrows / c->g.nx; // u_z rows per x-plane
         c->ltpp = rpp % rpt == 0 ? rpp / rpt : 0;
     }
+    for (int ax = 0; ax < 3; ++ax) {
+        c->tile_ok[ax] = false;
+        if (!(mask >> ax & 1) || c->g.dtype != VLASOV_F32) continue;
+        long long I = 1, O = 1;
+        for (int k = ax + 1; k < 6; ++k) I *= d6[k];
+        for (int k = 0; k < ax; ++k) O *= d6[k];
+        if (!tile_sweep_supported(int(d6[ax]), I) || O > 0x7fffffffll || I / 32 > 0x7fffffffll) continue;
+        c->tspec[ax] = spec_tiles(I, d6[ax], O);
+        if (encode_spec(&c->tmap[ax], c->tspec[ax], c->f) != CUDA_SUCCESS) continue;
+        const int occ = occupancy_tile_sweep(int(d6[ax]), ax == 0);
+        if (occ <= 0) continue;
+        c->ttiles_inner[ax] = I / 256;
+        c->tn_outer[ax] = O;
+        const long long tiles = O * (I / 256);
+        c->tgrid[ax] = int(tiles < (long long)occ * c->sm_count ? tiles : (long long)occ * c->sm_count);
+        c->tile_ok[ax] = true;
+    }
     c->can_kick_cube = (mask & 0x38) == 0x38 && kick_cube_supported(c->g.nux, c->g.nuy, c->g.nuz, c->g.dtype) &&
                        c->ncell * c->g.nux * c->g.nuy < (1ll << 31);
     if (c->can_kick_cube) {
@@ -484,6 +521,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
     c->es = g->dtype == VLASOV_F64 ? 8 : (coded ? 2 : 4);
     c->ncell = ncell;
     c->fuse_kick = 2; // see vlasov_set_fused_kick
+    c->use_tiles = true; // see vlasov_set_position_tiles
     c->fuse_moment = true; // see vlasov_set_fused_moment
     c->slab_x0 = c->slab_x1 = 0;
     c->gd.n[0] = g->nx; c->gd.n[1] = g->ny; c->gd.n[2] = g->nz;
@@ -674,14 +712,12 @@ static int moment_parts(const vlasov_ctx *c) { return int(velocity_cube(c) / c->
 // moment warp sums chunks of 4 rows x W values (32 bytes a lane), which must lie
 // in one spatial cell's velocity cube (W | cube, one plane per block); the partial
 // sums need ncell x cube / W values.
-static bool fused_moment_ok(vlasov_ctx *c, int ax)
+// The per-cell partial sums of the fused moment (ncell x cube / W values of the storage
+// type, W = the 1-KB blocks of the x sweep), allocated on first use.
+static bool moment_buffer(vlasov_ctx *c)
 {
-    if (ax != 0 || !c->fuse_moment || coded(c)) return false;
-    const AxisPlan &sp = c->splan[0];
-    const long long cube = velocity_cube(c);
-    if (sp.P != 1 || c->splan_R[0] != 4 || (long long)sp.W * c->es != 1024 || cube % sp.W) return false;
     if (!c->d_mpart) {
-        if (cudaMalloc(&c->d_mpart, (size_t)c->es * c->ncell * moment_parts(c)) != cudaSuccess) {
+        if (cudaMalloc(&c->d_mpart, (size_t)c->es * c->ncell * (velocity_cube(c) * c->es / 1024)) != cudaSuccess) {
             cudaGetLastError();
             c->d_mpart = nullptr;
             c->fuse_moment = false; // no room: the separate moment kernel from here on
@@ -689,6 +725,15 @@ static bool fused_moment_ok(vlasov_ctx *c, int ax)
         }
     }
     return true;
+}
+
+static bool fused_moment_ok(vlasov_ctx *c, int ax)
+{
+    if (ax != 0 || !c->fuse_moment || coded(c)) return false;
+    const AxisPlan &sp = c->splan[0];
+    const long long cube = velocity_cube(c);
+    if (sp.P != 1 || c->splan_R[0] != 4 || (long long)sp.W * c->es != 1024 || cube % sp.W) return false;
+    return moment_buffer(c);
 }
 
 // position sweep from src to dst (NULL, NULL: c->f in place) with per-velocity-column
@@ -713,6 +758,61 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
     for (int j = 0; j < nvel; ++j) numax = fmax(numax, fabs((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx)));
     SweepMaps m;
     int rc;
+    if (numax < 1.0 && c->use_tiles && c->tile_ok[ax]) {
+        // no whole-cell shift: whole lines staged per tile
+        TileArgs A{};
+        A.L = (&c->g.nx)[ax];
+        A.n_inner = c->ttiles_inner[ax] * 256;
+        A.n_outer = c->tn_outer[ax];
+        A.tiles_inner = c->ttiles_inner[ax];
+        A.tile0 = 0;
+        A.num_tiles = A.n_outer * A.tiles_inner;
+        if (c->slab_x1 > c->slab_x0) {
+            const long long tpp = A.num_tiles / c->g.nx; // tiles per x-plane (y and z sweeps)
+            A.tile0 = c->slab_x0 * tpp;
+            A.num_tiles = (c->slab_x1 - c->slab_x0) * tpp;
+        }
+        A.vstride = vstride;
+        A.nvel = nvel;
+        A.zperm = ax == 2 && c->g.nuz == 32;
+        // tiles of one sign of u come in runs of vstride nvel / 2 columns when that is a whole
+        // number of tiles (u_j < 0 exactly for j < nvel / 2)
+        const long long run = vstride * nvel / 2;
+        const int grid = int(A.num_tiles < c->tgrid[ax] ? A.num_tiles : c->tgrid[ax]);
+        A.sort_half = 0;
+        A.tile_sign = 0;
+        if (!A.zperm && nvel % 2 == 0 && run % 256 == 0 && A.tiles_inner % (2 * (run / 256)) == 0 &&
+            A.num_tiles % (2 * (run / 256)) == 0) {
+            const long long half = run / 256; // tiles of one sign in a row
+            if (grid % (2 * half) == 0 || A.num_tiles <= grid) {
+                A.tile_sign = 1; // every CTA meets one sign only
+            } else if (half >= 16) {
+                A.tile_sign = 1; // runs of 16 KB or more per row: take the tiles sign by sign
+                A.sort_half = half;
+            }
+        }
+        A.err = c->d_err;
+        for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
+        const long long cube = velocity_cube(c);
+        const bool fm = rho_fused && ax == 0 && c->fuse_moment && cube % 256 == 0 && moment_buffer(c);
+        if (fm) { A.mpart = c->d_mpart; A.cube = cube; A.nparts = int(cube / 256); }
+        if ((rc = sweep_maps(c, c->tmap[ax], c->tspec[ax], src, dst, m))) return rc;
+        cudaError_t e;
+        {
+            PartTimer t(c, ax, 1);
+            e = launch_tile_sweep(m.in, m.out, A, grid, c->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
+        if (fm) {
+            const double du3 = (2.0 * c->g.V / c->g.nux) * (2.0 * c->g.V / c->g.nuy) * (2.0 * c->g.V / c->g.nuz);
+            PartTimer t(c, VLASOV_T_MOMENT, 1);
+            e = launch_moment_finish(c->d_mpart, 1, int(cube / 256), c->g.nx, c->ncell / c->g.nx, du3, rho_fused,
+                                     c->stream, c->sm_count);
+            if (e != cudaSuccess) return cuda_fail(c, e, "moment launch");
+            if (fused) *fused = true;
+        }
+        return VLASOV_OK;
+    }
     if (numax < 1.0) {
         // no whole-cell shift on any line: streamed sweep
         const AxisPlan &sp = c->splan[ax];
@@ -1032,6 +1132,13 @@ extern "C" int vlasov_kick(vlasov_ctx *c, double dt, const float *phi_dev)
     int rc = prep_velocity(c, phi_dev, dt, 7);
     if (rc) return rc;
     return run_kick(c);
+}
+
+extern "C" int vlasov_set_position_tiles(vlasov_ctx *c, int on)
+{
+    if (!c) return VLASOV_EINVAL;
+    c->use_tiles = on != 0;
+    return VLASOV_OK;
 }
 
 extern "C" int vlasov_set_fused_moment(vlasov_ctx *c, int on)
