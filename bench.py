@@ -570,17 +570,20 @@ def run_adjoint(torch, dev, reps=3):
         torch.cuda.synchronize()
         return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
 
+    nseg = (w["steps"] + w["K"] - 1) // w["K"]
+    taped = run.taped_segments(nseg, w["K"])  # the default: as many segments as half the free memory holds
     once()
     ts = [once() for _ in range(reps)]
     fw = float(np.median([t[0] for t in ts]))
     bw = float(np.median([t[1] for t in ts]))
-    # the same run with the last two segments recorded by the forward (one more segment of tape)
-    run.tape_segments = 2
-    once()
-    ts2 = [once() for _ in range(reps)]
-    fw2 = float(np.median([t[0] for t in ts2]))
-    bw2 = float(np.median([t[1] for t in ts2]))
+    # the same run with one taped segment (the backward runs the other segments again)
     run.tape_segments = 1
+    run.release_tape()
+    once()
+    ts1 = [once() for _ in range(reps)]
+    fw1 = float(np.median([t[0] for t in ts1]))
+    bw1 = float(np.median([t[1] for t in ts1]))
+    run.tape_segments = "auto"
     seg_gb = (8 * w["K"] + w["K"] - 1) * f0.size * 4 / 1e9
     run.v.read_timers()
     run.v.enable_timers(True)
@@ -631,8 +634,10 @@ def run_adjoint(torch, dev, reps=3):
     return {"workload": "%s: %d^3 x %d^3 cells FP32, %d steps, checkpoint every %d, external phi, "
                         "loss sum over 0<|n|<8 of |rho_hat|^2" % (w["name"], n, nu, w["steps"], w["K"]),
             "forward_ms": fw, "backward_ms": bw, "backward_over_forward": bw / fw,
-            "tape_2_segments": {"forward_ms": fw2, "backward_ms": bw2, "backward_over_forward": bw2 / fw2,
-                                "extra_tape_GB": seg_gb},
+            "taped_segments": taped, "segments": nseg, "tape_GB": taped * seg_gb,
+            "one_taped_segment": {"forward_ms": fw1, "backward_ms": bw1, "backward_over_forward": bw1 / fw1,
+                                  "tape_GB": seg_gb,
+                                  "what": "the backward runs the other segments again from their checkpoints"},
             "adjoint_sweeps": per, "gradients_finite": ok,
             "self_consistent": {"what": "the same run with phi^{n+1} from the post-drift moment plus a "
                                         "background (Poisson every step); gradients for f0, phi0, rho_bg",

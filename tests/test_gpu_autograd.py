@@ -157,10 +157,11 @@ def test_run_fp32_gradient_close_to_fp64():
         assert np.isfinite(g32[k]).all() and rel <= 3 * sens + 1e-6
 
 
-@pytest.mark.parametrize("tape_segments", [2, 3])
+@pytest.mark.parametrize("tape_segments", [2, 3, "auto"])
 def test_more_taped_segments_give_the_same_gradients(tape_segments):
-    # the forward records the last tape_segments segments directly; the backward runs the
-    # others again: the same sweeps on the same inputs, so lambda is bit for bit and
+    # the forward records the last tape_segments segments directly ("auto": as many as half the
+    # free memory holds, here all 4); the backward runs the others again: the same sweeps on
+    # the same inputs, so lambda is bit for bit and
     # dL/dphi (per-cell sums by FP64 atomics at this velocity size) agrees to rounding
     A, _ = _mods()
     n, nu = (8, 8, 8), (8, 8, 8)

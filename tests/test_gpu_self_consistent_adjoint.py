@@ -69,7 +69,8 @@ def test_step_adjoint_sc_matches_oracle_fp64():
     v.close()
 
 
-def test_run_sc_gradient_matches_oracle_chain():
+@pytest.mark.parametrize("tape_segments", [1, "auto"])
+def test_run_sc_gradient_matches_oracle_chain(tape_segments):
     A, B = _mods()
     n, nu = (6, 6, 6), (8, 8, 8)
     g, f0, bg, phi0 = _setup(n, nu, np.float64)
@@ -94,7 +95,8 @@ def test_run_sc_gradient_matches_oracle_chain():
         lam_phi = dphi
         dbg_ref += dbg
 
-    run = A.Run(f0.shape, torch.float64, L=1.0, V=V)
+    # one taped segment (the backward runs the others again) or all of them (nothing again)
+    run = A.Run(f0.shape, torch.float64, L=1.0, V=V, tape_segments=tape_segments)
     ft = torch.from_numpy(f0).cuda().requires_grad_()
     pt = torch.from_numpy(phi0).cuda().requires_grad_()
     bt = torch.from_numpy(bg).cuda().requires_grad_()
