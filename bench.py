@@ -139,7 +139,8 @@ def measured_peaks():
 # one of them changes)
 _COMMON_SOURCES = ("vk_common.cuh", "vk_kernels.h")
 KERNEL_SOURCES = {
-    "sweep_x": ("sweep_stream.cu",), "sweep_y": ("sweep_stream.cu",), "sweep_z": ("sweep_stream.cu",),
+    # FP32 position sweeps of 16-64 cells: whole lines staged per tile
+    "sweep_x": ("sweep_tile.cu",), "sweep_y": ("sweep_tile.cu",), "sweep_z": ("sweep_tile.cu",),
     "sweep_ux": ("sweep_lines.cu", "vk_lines.cuh"), "sweep_uy": ("sweep_lines.cu", "vk_lines.cuh"),
     "sweep_uz": ("sweep_lines.cu", "vk_lines.cuh"), "sweep_uyuz": ("sweep_lines.cu", "vk_lines.cuh"),
     "kick": ("kick_cube.cu", "vk_lines.cuh"),
