@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--profile-shape", default="64,8,8",
                    help="spatial cells nx,ny,nz of --profile-case (32^3 velocity cells)")
     p.add_argument("--streamed", action="store_true", help="--profile-case runs the streamed position sweeps")
+    p.add_argument("--profile-dtype", default="f32", choices=["f32", "bf16", "f16"],
+                   help="storage of --profile-case's sweeps (16-bit: codes with a scale per u_z line)")
     p.add_argument("--adjoint", action="store_true", help="--profile-case runs the adjoint sweeps")
     p.add_argument("--step", action="store_true", help="--profile-case runs one Eq. (5) step (fused kick tail)")
     return p.parse_args()
@@ -859,6 +861,9 @@ def run_profile_case(args):
     delta = torch.from_numpy(I.gaussian_field(n, 0.05, seed=2)).to(dev)
     Fu = torch.from_numpy(I.fermi_dirac(nu, V)).to(dev)
     f = ((1 + delta)[:, :, :, None, None, None] * Fu[None, None, None]).float().contiguous()
+    scale = None
+    if args.profile_dtype != "f32":
+        f, scale = B.encode_lines(f, {"bf16": torch.bfloat16, "f16": torch.float16}[args.profile_dtype])
     phi_np = I.fourier_potential(n, seed=3)
     phi = torch.from_numpy(phi_np.astype(np.float32)).to(dev)
     cmax = courant_per_dt(phi_np, n, nu, V)
@@ -877,7 +882,7 @@ def run_profile_case(args):
             for ax in axes:
                 v.sweep_adjoint(f, lam, ax, 0.7 / cmax[ax], 1.0, phi, dLdg if ax >= 3 else None)
     else:
-        v = B.Vlasov(f, V=V)
+        v = B.Vlasov(f, V=V, scale=scale)
         if args.streamed:
             v.set_position_tiles(False)
         for _ in range(2):

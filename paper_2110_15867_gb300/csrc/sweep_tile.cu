@@ -10,9 +10,9 @@
 // nu_j = u_j dt / (a^2 dx) depends only on the column's velocity index j) and
 // marches it fully unrolled in registers with a sliding five-cell window, reading
 // each row once and writing it back in place (SL-MPP5, the same code as every
-// other sweep).  Groups of 256 threads work on different tiles; a ring of
-// groups + 1 tile slots, filled and drained by one producer thread, keeps the
-// next tile loading while the groups march theirs.  The orientation of a line
+// other sweep).  Groups of 256 threads work on different tiles; a ring of at
+// least groups + 1 tile slots (up to 192 KB), filled and drained by one producer
+// thread, keeps the next tiles loading while the groups march theirs.  The orientation of a line
 // is its sign of nu.  In the x and y sweeps it is the same for whole tiles; when
 // every tile a CTA takes has one sign, or the tiles can be taken sign by sign (all
 // tiles of u < 0 first, in runs long enough to keep DRAM pages whole), an SM runs
@@ -24,7 +24,7 @@
 // warps also add up every marched tile's rows into per-cell partials of rho_nu (the
 // moment of Eq. 5 is taken right after this sweep), in the order of the streamed
 // sweep's moment warp.
-#include "vk_common.cuh"
+#include "vk_lines.cuh"
 
 namespace vk {
 
@@ -52,34 +52,43 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void 
 // thread groups (256 columns each) marching tiles at once; the ring holds one slot more
 template <int L> constexpr int tile_groups() { return L <= 48 ? 3 : 2; }
 template <int L> constexpr unsigned tile_bytes() { return unsigned(L) * 1024u; }
-// barriers (128 B), the velocity-column table, alignment to 1 KB, the ring
-constexpr size_t kTileHeader = 128 + kMaxVel * sizeof(LineCoefT<float>);
-template <int L> constexpr size_t tile_smem() { return kTileHeader + 1024 + size_t(tile_groups<L>() + 1) * tile_bytes<L>(); }
+// ring slots: one more than the groups, more for short lines (up to 192 KB of tiles), so
+// that several tile loads are in flight while the groups march
+template <int L> constexpr int tile_slots()
+{
+    return (196608 / tile_bytes<L>() > 12 ? 12 : int(196608 / tile_bytes<L>())) > tile_groups<L>() + 1
+               ? (196608 / tile_bytes<L>() > 12 ? 12 : int(196608 / tile_bytes<L>()))
+               : tile_groups<L>() + 1;
+}
+// barriers (256 B), the velocity-column table, alignment to 1 KB, the ring
+constexpr size_t kTileHeader = 256 + kMaxVel * sizeof(LineCoefT<float>);
+template <int L> constexpr size_t tile_smem() { return kTileHeader + 1024 + size_t(tile_slots<L>()) * tile_bytes<L>(); }
 
 // March the periodic line p[0], p[st], ..., p[(L - 1) st] (flow toward +index) in place;
 // st < 0 walks a line with a negative Courant number from its far end.  DIR = +1 / -1 fixes
 // the stride at compile time; DIR = 0 takes it at run time, one body for both
 // orientations: in the z sweep both run side by side on every SM, and two unrolled copies
 // would not fit the instruction cache.  Returns the sum of the new values.
+// Faces marched per loop iteration: lines up to 32 cells unroll completely; longer lines
+// in blocks of 8 faces, so that the code of a march stays inside the instruction cache.
+template <int L> constexpr int march_unroll() { return L <= 32 ? L : 8; }
+
 template <int L, int DIR>
 __device__ __forceinline__ float march_tile(float *p, int st_rt, const Lim<float> &lim)
 {
     const int st = DIR == 0 ? st_rt : DIR * 256; // rows are 256 floats apart
-    auto cv = [](float x, float y, float z) { return curv(x, y, z); };
     const float a = p[(L - 3) * st], b = p[(L - 2) * st], c = p[(L - 1) * st];
     const float s0 = p[0], s1 = p[st];
-    const float dmm = cv(a, b, c), dm = cv(b, c, s0), d0 = cv(c, s0, s1);
+    const float dmm = curv(a, b, c), dm = curv(b, c, s0), d0 = curv(c, s0, s1);
     float dm4m = dm4(dm, d0);
     float Fm = sl_mpp5_flux(lim, a, b, c, s0, s1, dm4(dmm, dm), dm4m); // face -1/2, donor c_{-1}
     float cm2 = b, cm1 = c, c0 = s0, cp1 = s1, dcur = d0, sum = 0.f;
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-        const float cp2 = i + 2 < L ? p[(i + 2) * st] : (i + 2 == L ? s0 : s1);
-        const float dn = cv(c0, cp1, cp2);
+    auto face = [&](float cp2, float *dst) {
+        const float dn = curv(c0, cp1, cp2);
         const float dm4p = dm4(dcur, dn);
         const float F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
         const float out = c0 + (Fm - F);
-        p[i * st] = out;
+        *dst = out;
         sum += out;
         cm2 = cm1;
         cm1 = c0;
@@ -88,7 +97,11 @@ __device__ __forceinline__ float march_tile(float *p, int st_rt, const Lim<float
         dcur = dn;
         dm4m = dm4p;
         Fm = F;
-    }
+    };
+#pragma unroll march_unroll<L>()
+    for (int i = 0; i < L - 2; ++i) face(p[(i + 2) * st], p + i * st);
+    face(s0, p + (L - 2) * st); // the last two faces take the first two cells' old values
+    face(s1, p + (L - 1) * st);
     return sum;
 }
 
@@ -125,14 +138,14 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     tile_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                       const __grid_constant__ TileArgs a)
 {
-    constexpr int NG = tile_groups<L>(), S = NG + 1, NT = NG * 256;
+    constexpr int NG = tile_groups<L>(), S = tile_slots<L>(), NT = NG * 256;
     constexpr unsigned TB = tile_bytes<L>();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem); // S: the slot holds its tile
     uint64_t *done = full + S;                           // S: the tile's group is done with it
     uint64_t *marched = done + S;                        // NG: every column of the group's tile is marched
-    LineCoefT<float> *tab = reinterpret_cast<LineCoefT<float> *>(smem + 128);
-    static_assert((2 * S + NG) * 8 <= 128, "barriers fit ahead of the table");
+    LineCoefT<float> *tab = reinterpret_cast<LineCoefT<float> *>(smem + 256);
+    static_assert((2 * S + NG) * 8 <= 256, "barriers fit ahead of the table");
     unsigned char *ring = smem + kTileHeader + ((1024u - ((smem_u32(smem) + unsigned(kTileHeader)) & 1023u)) & 1023u);
     auto slot = [&](unsigned k) { return reinterpret_cast<float *>(ring + size_t(TB) * (k % S)); };
 
@@ -261,6 +274,204 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     if (bad) atomicOr(a.err, ERR_NAN);
 }
 
+// ----------------------------------------------------------------------------
+// 16-bit storage (BF16 / FP16 codes, one FP32 scale per u_z line of 32 cells)
+// ----------------------------------------------------------------------------
+// The same tiles, 512-byte rows of codes (no swizzle) plus the tile's scales (box
+// {8 u_z lines, L rows}); a position sweep keeps every scale.  Each value decodes as
+// code x scale, the line is marched in FP32 and every value is encoded back with
+// stochastic rounding (one stream per column and sweep, one draw per value in march
+// order).  z sweep: warp w takes the columns of one sign of units 2 (w % 4) and
+// 2 (w % 4) + 1 (adjacent 64-byte units fall on disjoint banks).
+template <int L> constexpr unsigned tile16_codes() { return unsigned(L) * 512u; }
+template <int L> constexpr unsigned tile16_slot() { return (tile16_codes<L>() + unsigned(L) * 32u + 127u) & ~127u; }
+template <int L> constexpr int tile16_slots()
+{
+    return (196608 / tile16_slot<L>() > 12 ? 12 : int(196608 / tile16_slot<L>())) > tile_groups<L>() + 1
+               ? (196608 / tile16_slot<L>() > 12 ? 12 : int(196608 / tile16_slot<L>()))
+               : tile_groups<L>() + 1;
+}
+template <int L> constexpr size_t tile16_smem() { return kTileHeader + 1024 + size_t(tile16_slots<L>()) * tile16_slot<L>(); }
+
+template <int L, int DIR, typename T>
+__device__ __forceinline__ float march_tile16(T *p, const float *sp, int st_rt, const Lim<float> &lim, unsigned rng)
+{
+    const int st = DIR == 0 ? st_rt : DIR * 256; // rows are 256 codes apart
+    const int ss = DIR == 0 ? (st_rt > 0 ? 8 : -8) : DIR * 8; // and 8 scales
+    auto get = [&](int i) { return RegCodec<T>::get(p[i * st], sp[i * ss]); };
+    const float a = get(L - 3), b = get(L - 2), c = get(L - 1);
+    const float s0 = get(0), s1 = get(1);
+    const float dmm = curv(a, b, c), dm = curv(b, c, s0), d0 = curv(c, s0, s1);
+    float dm4m = dm4(dm, d0);
+    float Fm = sl_mpp5_flux(lim, a, b, c, s0, s1, dm4(dmm, dm), dm4m);
+    float cm2 = b, cm1 = c, c0 = s0, cp1 = s1, dcur = d0, sum = 0.f;
+    auto face = [&](float cp2, int i) {
+        const float dn = curv(c0, cp1, cp2);
+        const float dm4p = dm4(dcur, dn);
+        const float F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
+        const float out = c0 + (Fm - F);
+        p[i * st] = RegCodec<T>::put(out, inv_scale(sp[i * ss]), lcg_next(rng) >> 16);
+        sum += out;
+        cm2 = cm1;
+        cm1 = c0;
+        c0 = cp1;
+        cp1 = cp2;
+        dcur = dn;
+        dm4m = dm4p;
+        Fm = F;
+    };
+#pragma unroll march_unroll<L>()
+    for (int i = 0; i < L - 2; ++i) face(get(i + 2), i);
+    face(s0, L - 2);
+    face(s1, L - 1);
+    return sum;
+}
+
+template <int L, typename T, bool SIGNED>
+__global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
+    tile_sweep16_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
+                        const __grid_constant__ TileArgs a)
+{
+    constexpr int NG = tile_groups<L>(), S = tile16_slots<L>(), NT = NG * 256;
+    constexpr unsigned CB = tile16_codes<L>(), SB = tile16_slot<L>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *done = full + S;
+    LineCoefT<float> *tab = reinterpret_cast<LineCoefT<float> *>(smem + 256);
+    static_assert(2 * S * 8 <= 256, "barriers fit ahead of the table");
+    unsigned char *ring = smem + kTileHeader + ((1024u - ((smem_u32(smem) + unsigned(kTileHeader)) & 1023u)) & 1023u);
+    auto slot = [&](unsigned k) { return reinterpret_cast<T *>(ring + size_t(SB) * (k % S)); };
+    auto sslot = [&](unsigned k) { return reinterpret_cast<float *>(ring + size_t(SB) * (k % S) + CB); };
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&done[q], 256);
+        }
+        fence_barrier_init();
+    }
+    for (int j = threadIdx.x; j < a.nvel; j += blockDim.x) tab[j] = a.table[j];
+    __syncthreads();
+
+    const long long G = gridDim.x, b = blockIdx.x;
+    const unsigned n_my = unsigned(a.num_tiles > b ? (a.num_tiles - b + G - 1) / G : 0);
+    auto coords = [&](unsigned k, int &u0, int &o) {
+        long long m = b + (long long)k * G, t;
+        if (a.sort_half > 0) {
+            const long long half = a.num_tiles / 2, pos = m >= half ? 1 : 0, mm = m - pos * half;
+            t = a.tile0 + (mm / a.sort_half) * 2 * a.sort_half + pos * a.sort_half + mm % a.sort_half;
+        } else {
+            t = a.tile0 + m;
+        }
+        const long long oq = t / a.tiles_inner;
+        u0 = int((t - oq * a.tiles_inner) * 8);
+        o = int(oq);
+    };
+
+    if (threadIdx.x >= NT) {
+        if (threadIdx.x != NT) return;
+        auto load = [&](unsigned k) {
+            int u0, o;
+            coords(k, u0, o);
+            mbar_arrive_expect_tx(&full[k % S], CB + unsigned(L) * 32u);
+            tma_load_4d(slot(k), &map, &full[k % S], 0, u0, 0, o);
+            tma_load_3d(sslot(k), &smap, &full[k % S], u0, 0, o);
+        };
+        unsigned loaded = 0;
+        for (; loaded < unsigned(S) && loaded < n_my; ++loaded) load(loaded);
+        bool ok = true;
+        for (unsigned k = 0; k < n_my; ++k) {
+            if (!mbar_wait_bounded(&done[k % S], (k / S) & 1u)) {
+                ok = false;
+                break;
+            }
+            int u0, o;
+            coords(k, u0, o);
+            tma_store_4d(&map, slot(k), 0, u0, 0, o); // the scales stay as they are
+            bulk_commit();
+            if (loaded < n_my) {
+                bulk_wait_read_all();
+                load(loaded++);
+            }
+        }
+        bulk_wait_all();
+        if (!ok) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            for (unsigned k = 0; k < loaded; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1u);
+        }
+        return;
+    }
+
+    const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, w = tid >> 5, lane = tid & 31;
+    int unit, e;
+    if (a.zperm) {
+        unit = ((w & 3) << 1) + (lane >> 4);
+        e = (w >> 2) * 16 + (lane & 15);
+    } else {
+        unit = w;
+        e = lane;
+    }
+    bool bad = false;
+    for (unsigned k = grp; k < n_my; k += NG) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[k % S], (k / S) & 1u))) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            return;
+        }
+        int u0, o;
+        coords(k, u0, o);
+        const long long inner = 32ll * (u0 + unit) + e;
+        const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
+        T *p = slot(k) + unit * 32 + e;
+        const float *sp = sslot(k) + unit;
+        if (kc.nd >= 0) {
+            const Lim<float> lim = to_lim(kc);
+            const bool neg = kc.nd & 1;
+            // the column's stream, from the index of its first cell
+            const unsigned rng = sr_bits((unsigned long long)((long long)o * L * a.n_inner + inner), a.seed);
+            float sum;
+            if constexpr (!SIGNED)
+                sum = march_tile16<L, 0, T>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * 8 : sp, neg ? -256 : 256,
+                                            lim, rng);
+            else if (neg) sum = march_tile16<L, -1, T>(p + (L - 1) * 256, sp + (L - 1) * 8, 0, lim, rng);
+            else sum = march_tile16<L, 1, T>(p, sp, 0, lim, rng);
+            bad |= !(sum >= 0.f) || isinf(sum);
+        }
+        fence_proxy_async();
+        mbar_arrive(&done[k % S]);
+    }
+    if (bad) atomicOr(a.err, ERR_NAN);
+}
+
+template <int L, typename T> const void *tile16_kernel(bool sign)
+{
+    return sign ? (const void *)tile_sweep16_kernel<L, T, true> : (const void *)tile_sweep16_kernel<L, T, false>;
+}
+
+template <typename T> const void *tile16_kernel_for(int L, bool sign)
+{
+    switch (L) {
+    case 16: return tile16_kernel<16, T>(sign);
+    case 24: return tile16_kernel<24, T>(sign);
+    case 32: return tile16_kernel<32, T>(sign);
+    case 48: return tile16_kernel<48, T>(sign);
+    case 64: return tile16_kernel<64, T>(sign);
+    case 96: return tile16_kernel<96, T>(sign);
+    default: return nullptr;
+    }
+}
+
+size_t tile16_smem_for(int L)
+{
+    switch (L) {
+    case 16: return tile16_smem<16>();
+    case 24: return tile16_smem<24>();
+    case 32: return tile16_smem<32>();
+    case 48: return tile16_smem<48>();
+    case 64: return tile16_smem<64>();
+    default: return tile16_smem<96>();
+    }
+}
+
 template <int L> const void *tile_kernel(bool moment, bool sign)
 {
     if (sign) return moment ? (const void *)tile_sweep_kernel<L, true, true> : (const void *)tile_sweep_kernel<L, false, true>;
@@ -292,33 +503,46 @@ size_t tile_smem_for(int L)
 
 int tile_threads_for(int L, bool) { return (L <= 48 ? 3 : 2) * 256 + kProducer; }
 
+const void *tile_kernel_any(int L, int dtype, bool moment, bool sign)
+{
+    if (dtype == 2) return moment ? nullptr : tile16_kernel_for<__nv_bfloat16>(L, sign);
+    if (dtype == 3) return moment ? nullptr : tile16_kernel_for<__half>(L, sign);
+    return tile_kernel_for(L, moment, sign);
+}
+
 } // namespace
 
-bool tile_sweep_supported(int L, long long n_inner) { return tile_kernel_for(L, false) && n_inner % 256 == 0; }
-
-int occupancy_tile_sweep(int L, bool moment)
+bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz)
 {
-    const void *k = tile_kernel_for(L, moment);
+    if (n_inner % 256 != 0 || !tile_kernel_any(L, dtype, false, true)) return false;
+    return dtype == 1 || ((dtype == 2 || dtype == 3) && nuz == 32);
+}
+
+int occupancy_tile_sweep(int L, int dtype, bool moment)
+{
+    const void *k = tile_kernel_any(L, dtype, moment, true);
     if (!k) return 0;
-    const size_t smem = tile_smem_for(L);
+    const size_t smem = dtype == 1 ? tile_smem_for(L) : tile16_smem_for(L);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tile_threads_for(L, moment), smem) != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const TileArgs &a, int grid,
-                              cudaStream_t st)
+cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const CUtensorMap &smap,
+                              const TileArgs &a, int dtype, int grid, cudaStream_t st)
 {
     if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
     const bool moment = a.mpart != nullptr;
-    const void *k = tile_kernel_for(a.L, moment, a.tile_sign != 0);
+    const void *k = tile_kernel_any(a.L, dtype, moment, a.tile_sign != 0);
     if (!k || a.nvel <= 0 || a.nvel > kMaxVel || a.vstride <= 0 || a.tiles_inner <= 0) return cudaErrorInvalidValue;
-    if (moment && (a.cube % 256 || a.nparts <= 0)) return cudaErrorInvalidValue;
-    const size_t smem = tile_smem_for(a.L);
+    if (moment && (dtype != 1 || a.cube % 256 || a.nparts <= 0)) return cudaErrorInvalidValue;
+    const size_t smem = dtype == 1 ? tile_smem_for(a.L) : tile16_smem_for(a.L);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    void *params[] = {const_cast<CUtensorMap *>(&map), const_cast<CUtensorMap *>(&dmap), const_cast<TileArgs *>(&a)};
+    // FP32: (map, dmap, args); 16-bit: in place (map, smap, args)
+    void *params[] = {const_cast<CUtensorMap *>(&map),
+                      const_cast<CUtensorMap *>(dtype == 1 ? &dmap : &smap), const_cast<TileArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(grid), dim3(tile_threads_for(a.L, moment)), params, smem, st);
 }
 

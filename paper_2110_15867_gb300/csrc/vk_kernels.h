@@ -233,6 +233,7 @@ struct TileArgs {
     long long sort_half;                     // > 0: runs of sort_half tiles alternate in the sign of u
                                              // (num_tiles a multiple of 2 sort_half): taken sign by sign
     int tile_sign;                           // 1: every column of a tile has one sign of u (else per column)
+    unsigned seed;                           // 16-bit storage: the stochastic-rounding streams of this sweep
     unsigned *err;
     // x sweep with the moment: per-cell partial sums as in StreamArgs (null: no moment)
     void *mpart;
@@ -240,11 +241,14 @@ struct TileArgs {
     int nparts;
     LineCoefT<float> table[kMaxVel];
 };
-bool tile_sweep_supported(int L, long long n_inner);
-int occupancy_tile_sweep(int L, bool moment);
-// tiles are loaded through map and stored through dmap (the same map for an in-place sweep)
-cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const TileArgs &a, int grid,
-                              cudaStream_t st);
+// dtype 1 (FP32), 2 (BF16), 3 (FP16; n_uz = 32, one scale per 32-code unit, L up to 96)
+bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz);
+int occupancy_tile_sweep(int L, int dtype, bool moment);
+// FP32: tiles loaded through map and stored through dmap (the same map in place).  16-bit:
+// in place through map (codes, box {32, 8, L, 1}, no swizzle) with the scales through smap
+// ([n_outer][L][n_inner / 32] floats, box {8, L, 1})
+cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const CUtensorMap &smap,
+                              const TileArgs &a, int dtype, int grid, cudaStream_t st);
 
 // host launchers (return cudaGetLastError() of the launch); tiles are loaded
 // through map and stored through dmap (the same map for an in-place sweep)

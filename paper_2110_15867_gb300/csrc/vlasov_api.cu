@@ -132,9 +132,9 @@ struct vlasov_ctx {
     // kick tail D_uz D_uy fused in the u_z line kernel (n_uy = n_uz)
     bool can_fuse_kick;
     int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
-    // position sweeps with whole lines staged per tile (FP32; see vlasov_set_position_tiles)
+    // position sweeps with whole lines staged per tile (see vlasov_set_position_tiles)
     bool tile_ok[3], use_tiles;
-    CUtensorMap tmap[3];
+    CUtensorMap tmap[3], tsmap[3]; // tsmap: 16-bit storage, the scales of a tile
     MapSpec tspec[3];
     int tgrid[3];
     long long ttiles_inner[3], tn_outer[3];
@@ -415,14 +415,31 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
     }
     for (int ax = 0; ax < 3; ++ax) {
         c->tile_ok[ax] = false;
-        if (!(mask >> ax & 1) || c->g.dtype != VLASOV_F32) continue;
+        if (!(mask >> ax & 1) || c->g.dtype == VLASOV_F64) continue;
         long long I = 1, O = 1;
         for (int k = ax + 1; k < 6; ++k) I *= d6[k];
         for (int k = 0; k < ax; ++k) O *= d6[k];
-        if (!tile_sweep_supported(int(d6[ax]), I) || O > 0x7fffffffll || I / 32 > 0x7fffffffll) continue;
+        if (!tile_sweep_supported(int(d6[ax]), I, c->g.dtype, int(c->g.nuz)) || O > 0x7fffffffll ||
+            I / 32 > 0x7fffffffll)
+            continue;
         c->tspec[ax] = spec_tiles(I, d6[ax], O);
+        if (coded) {
+            // codes: 512-byte rows of 32-code units, no swizzle; scales: one per 32-code unit
+            c->tspec[ax].type = tmap_type(c->g.dtype);
+            c->tspec[ax].gstr[0] = 64; c->tspec[ax].gstr[1] = (cuuint64_t)(I * 2); c->tspec[ax].gstr[2] = (cuuint64_t)(I * d6[ax] * 2);
+            c->tspec[ax].swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+            MapSpec ss{};
+            ss.type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+            ss.rank = 3;
+            ss.gdim[0] = (cuuint64_t)(I / 32); ss.gdim[1] = (cuuint64_t)d6[ax]; ss.gdim[2] = (cuuint64_t)O;
+            ss.gstr[0] = (cuuint64_t)(I / 32 * 4); ss.gstr[1] = (cuuint64_t)(I / 32 * d6[ax] * 4);
+            ss.box[0] = 8; ss.box[1] = (cuuint32_t)d6[ax]; ss.box[2] = 1;
+            ss.swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+            ss.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+            if (encode_spec(&c->tsmap[ax], ss, c->scale) != CUDA_SUCCESS) continue;
+        }
         if (encode_spec(&c->tmap[ax], c->tspec[ax], c->f) != CUDA_SUCCESS) continue;
-        const int occ = occupancy_tile_sweep(int(d6[ax]), ax == 0);
+        const int occ = occupancy_tile_sweep(int(d6[ax]), c->g.dtype, ax == 0 && !coded);
         if (occ <= 0) continue;
         c->ttiles_inner[ax] = I / 256;
         c->tn_outer[ax] = O;
@@ -792,15 +809,17 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
             }
         }
         A.err = c->d_err;
+        A.seed = c->sweeps;
         for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
         const long long cube = velocity_cube(c);
-        const bool fm = rho_fused && ax == 0 && c->fuse_moment && cube % 256 == 0 && moment_buffer(c);
+        const bool fm = rho_fused && ax == 0 && !coded(c) && c->fuse_moment && cube % 256 == 0 && moment_buffer(c);
         if (fm) { A.mpart = c->d_mpart; A.cube = cube; A.nparts = int(cube / 256); }
-        if ((rc = sweep_maps(c, c->tmap[ax], c->tspec[ax], src, dst, m))) return rc;
+        if (coded(c)) m.in = m.out = c->tmap[ax]; // 16-bit sweeps run in place (checked above)
+        else if ((rc = sweep_maps(c, c->tmap[ax], c->tspec[ax], src, dst, m))) return rc;
         cudaError_t e;
         {
             PartTimer t(c, ax, 1);
-            e = launch_tile_sweep(m.in, m.out, A, grid, c->stream);
+            e = launch_tile_sweep(m.in, m.out, c->tsmap[ax], A, c->g.dtype, grid, c->stream);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "position sweep launch");
         if (fm) {

@@ -77,3 +77,38 @@ def test_tile_step_and_fused_moment_are_bitwise_the_streamed_ones(n, nu):
     for k in ("sweep_x", "sweep_y", "sweep_z"):
         assert out[True][2][k] == 2 and out[False][2][k] == 2
     assert out[True][2]["moment"] == 2  # the partial sums of the tile x sweep, added per cell
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_tile_sweeps_against_the_oracle(fmt):
+    # BF16 / FP16 storage with n_uz = 32 runs the staged tiles too (decode, FP32 march,
+    # stochastic-rounding encode per value with the kept line scales).  Its random streams
+    # differ from the streamed sweep's, so both are held to the codec bound of the parity
+    # tests against the FP64 oracle's sweep of the same decoded input: relative L1 <=
+    # 2^-8 (BF16) / 2^-11 (FP16) + 1e-6, L_inf <= 1.5 x twice that, per sweep and axis.
+    B = _lib()
+    V = 5.0
+    bound = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[fmt]
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[fmt]
+    n, nu = (32, 16, 16), (16, 16, 32)
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=8), I.fermi_dirac(nu, V), np.float64)
+    g = O.grid(n, nu, V=V)
+    codes0, scale0 = B.encode_lines(torch.from_numpy(f0).cuda(), tdt)
+    for ax in range(3):
+        dt = 0.8 / O.max_abs_nu(g, ax, 1.0, 0.9)
+        ref = B.decode_lines(codes0, scale0).cpu().numpy()
+        O.sweep(g, ref, ax, dt, 0.9)
+        for tiles in (True, False):
+            codes, scale = codes0.clone(), scale0.clone()
+            v = B.Vlasov(codes, V=V, scale=scale)
+            v.set_position_tiles(tiles)
+            v.sweep(ax, dt, 0.9)
+            v.status()
+            out = B.decode_lines(codes, scale).cpu().numpy()
+            v.close()
+            err = np.abs(out - ref)
+            rl1 = err.sum() / np.abs(ref).sum()
+            rinf = err.max() / np.abs(ref).max()
+            print("%s axis %d %s: rel L1 %.2e, rel Linf %.2e" % (fmt, ax, "tiles" if tiles else "streamed", rl1, rinf))
+            assert rl1 <= bound + 1e-6 and rinf <= 1.5 * (2 * bound + 1e-6)
+            assert torch.equal(scale, scale0)  # a position sweep keeps the line scales
