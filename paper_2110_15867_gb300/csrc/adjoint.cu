@@ -17,9 +17,9 @@
 //
 // One thread per line.  Strided axes (x, y, z, u_x, u_y): neighbouring threads
 // own neighbouring columns, so every row access of a warp is one coalesced
-// segment.  u_z: a line is one contiguous row; for n_uz = 8, 16, 32 the thread
-// loads the row with 16-byte vector loads into registers and the march runs
-// on compile-time indices.  A negative Courant number is the mirror image of a
+// segment.  u_z: a line is one contiguous row; for n_uz = 8, 16, 32 the row
+// reaches the thread's registers through 16-byte vector loads (32: staged per
+// warp through shared memory) and the march runs on compile-time indices.  A negative Courant number is the mirror image of a
 // positive one: the line is walked from its far end (negated stride).
 //
 // For a velocity sweep dL/dnu of every line is summed over its spatial cell
@@ -155,8 +155,16 @@ __device__ __forceinline__ C face_adjoint(const AdjLim<C> &k, C cm2, C cm1, C c0
 // ----------------------------------------------------------------------------
 // the march over one line (local frame: flow toward +index)
 // ----------------------------------------------------------------------------
-// minmod of (4 d0 - d1, 4 d1 - d0, d0, d1) with its partials ka = dr/dd0 and
-// kb = dr/dd1 (the selected argument's; 0 where the minmod is 0)
+// minmod of (4 d0 - d1, 4 d1 - d0, d0, d1)
+template <typename C> __device__ __forceinline__ C dm4_val(C d0, C d1)
+{
+    const C a = C(4) * d0 - d1, b = C(4) * d1 - d0;
+    const C lo = mn2(mn3(a, b, d0), d1), hi = mx2(mx3(a, b, d0), d1);
+    return mn2(mx2(lo, C(0)), hi);
+}
+
+// the same with its partials ka = dr/dd0 and kb = dr/dd1 (the selected
+// argument's; 0 where the minmod is 0)
 template <typename C> __device__ __forceinline__ C dm4_coef(C d0, C d1, C &ka, C &kb)
 {
     const C a = C(4) * d0 - d1, b = C(4) * d1 - d0;
@@ -180,13 +188,21 @@ template <typename C> __device__ __forceinline__ C dm4_coef(C d0, C d1, C &ka, C
 // every face that uses it and is scattered once (curvature j - 1 after face
 // j, dm4 at j - 1/2 at face j).  The adjoint is linear, so on a periodic line
 // the contributions of the wrap-around faces can be scattered when they come.
+//
+// On a velocity line, a plain face (v = fbar, s v inside [0, c0]) with no
+// curvature adjoint pending (nothing from the faces before it) only scatters
+// gbar s w_m: it skips the source selection and the dm4 partials, which the
+// other faces recompute from the curvatures in the window.  On the smooth
+// velocity profiles every face is plain; position lines, limited at about
+// half of their faces, take the general path at every face (the two bodies
+// side by side made the unrolled position walks slower).
 template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     Acc &acc;
     const AdjLim<C> &k;
     int n;
     C cw[5], ow[5], lo[3]; // c and running dL/dc of cells j-2..j+2; original lambda of cells j..j+2
     C dm, d0;              // curvatures of cells j-1, j
-    C qm, qam, qbm;        // dm4 at j-1/2 and its partials with respect to (dm, d0)
+    C qm;                  // dm4 at j-1/2 (of dm, d0)
     C gq;                  // adjoint of qm from face j-1 (where it was the downwind dm4)
     C gdm, gd0;            // adjoints of dm, d0 collected so far
     C pA, pB, p0, p1;      // periodic: partial sums of cells n-2, n-1 (faces 0, 1) and 0, 1 (faces up to 3)
@@ -223,7 +239,7 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         ow[4] = lo[2];
         dm = cw[0] - C(2) * cw[1] + cw[2];
         d0 = cw[1] - C(2) * cw[2] + cw[3];
-        qm = dm4_coef(dm, d0, qam, qbm);
+        qm = dm4_val(dm, d0);
         gq = gdm = gd0 = C(0);
         pA = pB = p0 = p1 = C(0);
         dLds = osum = C(0);
@@ -238,8 +254,7 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         const C gbar = lo[1] - lo[0]; // dL/dF of this face
         // forward
         const C dp = c0 - C(2) * cp1 + cp2;
-        C qap, qbp;
-        const C qp = dm4_coef(d0, dp, qap, qbp);
+        const C qp = dm4_val(d0, dp);
         const C fbar = k.w[0] * cm2 + k.w[1] * cm1 + k.w[2] * c0 + k.w[3] * cp1 + k.w[4] * cp2;
         const C dlm = c0 - cm1;
         const C ful = c0 + k.alpha * dlm;
@@ -250,40 +265,51 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         const C sv = k.s * v;
         // reverse: F = clamp(s v, 0, c0)
         const bool inr = sv >= C(0) && sv <= c0;
-        const C gv = inr ? k.s * gbar : C(0);
-        const C gpp = sv > c0 ? gbar : C(0);
-        // v's source, first match in the order fbar, c0, cp1, f_MD, f_UL, f_LC
         const bool isf = v == fbar;
-        const bool e0 = !isf && v == c0;
-        const bool e1 = !isf && !e0 && v == cp1;
-        const bool em = !isf && !e0 && !e1 && v == fmd;
-        const bool eu = !isf && !e0 && !e1 && !em && v == ful;
-        const bool el = !isf && !e0 && !e1 && !em && !eu;
-        const C k0 = isf ? k.w[0] : C(0);
-        const C k4 = isf ? k.w[4] : C(0);
-        const C k1 = isf ? k.w[1] : eu ? -k.alpha : el ? C(-0.5) : C(0);
-        const C k2 = isf ? k.w[2] : e0 ? C(1) : em ? C(0.5) : eu ? C(1) + k.alpha : el ? C(1.5) : C(0);
-        const C k3 = isf ? k.w[3] : e1 ? C(1) : em ? C(0.5) : C(0);
-        // dL/ds: velocity sweeps only (a position sweep's s does not depend on phi)
-        const C ks = PERIODIC ? C(0)
-                     : isf    ? (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2)
-                     : eu     ? k.dalpha * dlm
-                              : C(0);
-        ow[0] += gv * k0;
-        ow[1] += gv * k1;
-        ow[2] += gv * k2 + gpp;
-        ow[3] += gv * k3;
-        ow[4] += gv * k4;
-        if (!PERIODIC) dLds += gv * ks + (inr ? v * gbar : C(0));
-        // dm4 at j - 1/2 is complete: scatter to the curvatures of cells j-1, j
-        const C gqm = gq + (el ? C(4.0 / 3.0) * gv : C(0));
-        gdm += gqm * qam;
-        gd0 += gqm * qbm;
-        gq = em ? C(-0.5) * gv : C(0);
-        // the curvature of cell j - 1 is complete: scatter to cells j-2, j-1, j
-        ow[0] += gdm;
-        ow[1] -= C(2) * gdm;
-        ow[2] += gdm;
+        // d fbar / ds (velocity sweeps only: a position sweep's s does not depend on phi)
+        const C dfs = PERIODIC ? C(0) : (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2);
+        if (!PERIODIC && isf && inr && gq == C(0) && gdm == C(0)) {
+            // plain face: F = s fbar
+            const C gv = k.s * gbar;
+            ow[0] += gv * k.w[0];
+            ow[1] += gv * k.w[1];
+            ow[2] += gv * k.w[2];
+            ow[3] += gv * k.w[3];
+            ow[4] += gv * k.w[4];
+            if (!PERIODIC) dLds += gv * dfs + v * gbar;
+        } else {
+            C qam, qbm;
+            dm4_coef(dm, d0, qam, qbm); // partials of qm
+            const C gv = inr ? k.s * gbar : C(0);
+            const C gpp = sv > c0 ? gbar : C(0);
+            // v's source, first match in the order fbar, c0, cp1, f_MD, f_UL, f_LC
+            const bool e0 = !isf && v == c0;
+            const bool e1 = !isf && !e0 && v == cp1;
+            const bool em = !isf && !e0 && !e1 && v == fmd;
+            const bool eu = !isf && !e0 && !e1 && !em && v == ful;
+            const bool el = !isf && !e0 && !e1 && !em && !eu;
+            const C k0 = isf ? k.w[0] : C(0);
+            const C k4 = isf ? k.w[4] : C(0);
+            const C k1 = isf ? k.w[1] : eu ? -k.alpha : el ? C(-0.5) : C(0);
+            const C k2 = isf ? k.w[2] : e0 ? C(1) : em ? C(0.5) : eu ? C(1) + k.alpha : el ? C(1.5) : C(0);
+            const C k3 = isf ? k.w[3] : e1 ? C(1) : em ? C(0.5) : C(0);
+            const C ks = PERIODIC ? C(0) : isf ? dfs : eu ? k.dalpha * dlm : C(0);
+            ow[0] += gv * k0;
+            ow[1] += gv * k1;
+            ow[2] += gv * k2 + gpp;
+            ow[3] += gv * k3;
+            ow[4] += gv * k4;
+            if (!PERIODIC) dLds += gv * ks + (inr ? v * gbar : C(0));
+            // dm4 at j - 1/2 is complete: scatter to the curvatures of cells j-1, j
+            const C gqm = gq + (el ? C(4.0 / 3.0) * gv : C(0));
+            gdm += gqm * qam;
+            gd0 += gqm * qbm;
+            gq = em ? C(-0.5) * gv : C(0);
+            // the curvature of cell j - 1 is complete: scatter to cells j-2, j-1, j
+            ow[0] += gdm;
+            ow[1] -= C(2) * gdm;
+            ow[2] += gdm;
+        }
         // cell j - 2 leaves, cell j + 3 enters
         const int mo = j - 2, mi = j + 3;
         C lnew, cnew, init;
@@ -327,8 +353,6 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         dm = d0;
         d0 = dp;
         qm = qp;
-        qam = qap;
-        qbm = qbp;
         gdm = gd0;
         gd0 = C(0);
     }
@@ -337,6 +361,8 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     // curvatures of cells J, J+1 and qm the downwind dm4 of face J
     __device__ __forceinline__ void end()
     {
+        C qam, qbm;
+        dm4_coef(dm, d0, qam, qbm);
         gdm += gq * qam;
         gd0 += gq * qbm;
         ow[0] += gdm;
