@@ -77,7 +77,8 @@ def parse():
                         "(64, 8, 8) x 32^3 FP32 grid (537 MB, larger than L2), twice per axis")
     p.add_argument("--axes", default="0,1,2,3,4,5", help="sweep axes of --profile-case")
     p.add_argument("--profile-shape", default="64,8,8",
-                   help="spatial cells nx,ny,nz of --profile-case (32^3 velocity cells)")
+                   help="spatial cells nx,ny,nz of --profile-case")
+    p.add_argument("--profile-nu", type=int, default=32, help="velocity cells per axis of --profile-case")
     p.add_argument("--streamed", action="store_true", help="--profile-case runs the streamed position sweeps")
     p.add_argument("--profile-dtype", default="f32", choices=["f32", "bf16", "f16"],
                    help="storage of --profile-case's sweeps (16-bit: codes with a scale per u_z line)")
@@ -851,11 +852,11 @@ def run_ours(args):
 
 def run_profile_case(args):
     """Each requested sweep (or, with --adjoint, its adjoint) twice plus the moment on a
-    (64, 8, 8) x 32^3 FP32 grid (1.34e8 cells, 537 MB)."""
+    small FP32 grid (default (64, 8, 8) x 32^3: 1.34e8 cells, 537 MB)."""
     import torch
     from paper_2110_15867_gb300 import binding as B
     from paper_2110_15867_gb300 import inputs as I
-    n, nu, V = tuple(int(x) for x in args.profile_shape.split(",")), 32, 5.0
+    n, nu, V = tuple(int(x) for x in args.profile_shape.split(",")), args.profile_nu, 5.0
     axes = [int(a) for a in args.axes.split(",")]
     dev = torch.device("cuda", 0)
     delta = torch.from_numpy(I.gaussian_field(n, 0.05, seed=2)).to(dev)

@@ -189,20 +189,23 @@ template <typename C> __device__ __forceinline__ C dm4_coef(C d0, C d1, C &ka, C
 // j, dm4 at j - 1/2 at face j).  The adjoint is linear, so on a periodic line
 // the contributions of the wrap-around faces can be scattered when they come.
 //
-// On a velocity line, a plain face (v = fbar, s v inside [0, c0]) with no
-// curvature adjoint pending (nothing from the faces before it) only scatters
-// gbar s w_m: it skips the source selection and the dm4 partials, which the
-// other faces recompute from the curvatures in the window.  On the smooth
-// velocity profiles every face is plain; position lines, limited at about
-// half of their faces, take the general path at every face (the two bodies
-// side by side made the unrolled position walks slower).
+// On a velocity line, a plain face (fbar between c0 and f_MP = median(c0,
+// cp1, f_UL), so that the constraint keeps it, and s fbar inside [0, c0])
+// with no curvature adjoint pending from the faces before it only scatters
+// gbar s w_m: it skips the limited curvatures, f_MD, f_LC, the clamp and the
+// source selection; the other faces compute the dm4 at their upwind face with
+// its partials from the curvatures in the window.  On the smooth velocity
+// profiles every face is plain.  Position lines, limited at about half of
+// their faces, take the general path at every face (two bodies side by side
+// made the unrolled position walks slower) and keep each dm4 with its partials
+// for the next face.
 template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     Acc &acc;
     const AdjLim<C> &k;
     int n;
     C cw[5], ow[5], lo[3]; // c and running dL/dc of cells j-2..j+2; original lambda of cells j..j+2
     C dm, d0;              // curvatures of cells j-1, j
-    C qm;                  // dm4 at j-1/2 (of dm, d0)
+    C qm, pqa, pqb;        // periodic: dm4 at j-1/2 and its partials with respect to (dm, d0)
     C gq;                  // adjoint of qm from face j-1 (where it was the downwind dm4)
     C gdm, gd0;            // adjoints of dm, d0 collected so far
     C pA, pB, p0, p1;      // periodic: partial sums of cells n-2, n-1 (faces 0, 1) and 0, 1 (faces up to 3)
@@ -239,7 +242,8 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         ow[4] = lo[2];
         dm = cw[0] - C(2) * cw[1] + cw[2];
         d0 = cw[1] - C(2) * cw[2] + cw[3];
-        qm = dm4_val(dm, d0);
+        qm = pqa = pqb = C(0);
+        if (PERIODIC) qm = dm4_coef(dm, d0, pqa, pqb);
         gq = gdm = gd0 = C(0);
         pA = pB = p0 = p1 = C(0);
         dLds = osum = C(0);
@@ -254,21 +258,23 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         const C gbar = lo[1] - lo[0]; // dL/dF of this face
         // forward
         const C dp = c0 - C(2) * cp1 + cp2;
-        const C qp = dm4_val(d0, dp);
+        C qpa = C(0), qpb = C(0);
+        C qp = PERIODIC ? dm4_coef(d0, dp, qpa, qpb) : C(0);
         const C fbar = k.w[0] * cm2 + k.w[1] * cm1 + k.w[2] * c0 + k.w[3] * cp1 + k.w[4] * cp2;
         const C dlm = c0 - cm1;
         const C ful = c0 + k.alpha * dlm;
-        const C fmd = C(0.5) * (c0 + cp1 - qp);
-        const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * qm;
-        // clamp(fbar, max(A, B), min(C, D)) as min(max(fbar, A, B), C, D)
-        const C v = mn3(mx3(fbar, mn3(c0, cp1, fmd), mn3(c0, ful, flc)), mx3(c0, cp1, fmd), mx3(c0, ful, flc));
-        const C sv = k.s * v;
-        // reverse: F = clamp(s v, 0, c0)
-        const bool inr = sv >= C(0) && sv <= c0;
-        const bool isf = v == fbar;
         // d fbar / ds (velocity sweeps only: a position sweep's s does not depend on phi)
         const C dfs = PERIODIC ? C(0) : (k.ws[0] * cm2 + k.ws[1] * cm1 + k.ws[2] * c0 + k.ws[3] * cp1 + k.ws[4] * cp2);
-        if (!PERIODIC && isf && inr && gq == C(0) && gdm == C(0)) {
+        bool plain = false;
+        if constexpr (!PERIODIC) {
+            // fbar between c0 and f_MP = median(c0, cp1, f_UL) lies inside [fmin, fmax]:
+            // the constraint keeps it (v = fbar) without the limited curvatures
+            const C fmp = mx3(mn2(c0, cp1), mn2(c0, ful), mn2(cp1, ful));
+            const C sf = k.s * fbar;
+            plain = fbar >= mn2(c0, fmp) && fbar <= mx2(c0, fmp) && sf >= C(0) && sf <= c0 && gq == C(0) &&
+                    gdm == C(0);
+        }
+        if (plain) {
             // plain face: F = s fbar
             const C gv = k.s * gbar;
             ow[0] += gv * k.w[0];
@@ -276,10 +282,21 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
             ow[2] += gv * k.w[2];
             ow[3] += gv * k.w[3];
             ow[4] += gv * k.w[4];
-            if (!PERIODIC) dLds += gv * dfs + v * gbar;
+            dLds += gv * dfs + fbar * gbar;
         } else {
-            C qam, qbm;
-            dm4_coef(dm, d0, qam, qbm); // partials of qm
+            C qam = pqa, qbm = pqb, qmv = qm;
+            if (!PERIODIC) {
+                qmv = dm4_coef(dm, d0, qam, qbm); // dm4 at j - 1/2 and its partials
+                qp = dm4_val(d0, dp);
+            }
+            const C fmd = C(0.5) * (c0 + cp1 - qp);
+            const C flc = c0 + C(0.5) * dlm + C(4.0 / 3.0) * qmv;
+            // clamp(fbar, max(A, B), min(C, D)) as min(max(fbar, A, B), C, D)
+            const C v = mn3(mx3(fbar, mn3(c0, cp1, fmd), mn3(c0, ful, flc)), mx3(c0, cp1, fmd), mx3(c0, ful, flc));
+            const C sv = k.s * v;
+            // reverse: F = clamp(s v, 0, c0)
+            const bool inr = sv >= C(0) && sv <= c0;
+            const bool isf = v == fbar;
             const C gv = inr ? k.s * gbar : C(0);
             const C gpp = sv > c0 ? gbar : C(0);
             // v's source, first match in the order fbar, c0, cp1, f_MD, f_UL, f_LC
@@ -353,6 +370,8 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
         dm = d0;
         d0 = dp;
         qm = qp;
+        pqa = qpa;
+        pqb = qpb;
         gdm = gd0;
         gd0 = C(0);
     }
@@ -361,8 +380,8 @@ template <bool PERIODIC, typename C, typename Acc> struct AdjMarch {
     // curvatures of cells J, J+1 and qm the downwind dm4 of face J
     __device__ __forceinline__ void end()
     {
-        C qam, qbm;
-        dm4_coef(dm, d0, qam, qbm);
+        C qam = pqa, qbm = pqb;
+        if (!PERIODIC) dm4_coef(dm, d0, qam, qbm);
         gdm += gq * qam;
         gd0 += gq * qbm;
         ow[0] += gdm;
@@ -655,18 +674,28 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 16 && L
     if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
 
-// u_z lines of L = 8, 16, 32 cells: one row per thread through 16-byte vector loads
-template <typename T, bool NEG, int L>
-__device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint4 *op, const AdjLim<T> &lim, T &dLds, T &osum)
+// u_z lines of L = 8, 16, 32 cells: one row per thread through 16-byte vector
+// loads.  One march body for both signs of the Courant number (two unrolled
+// bodies side by side overflowed the instruction cache): a negative one
+// reverses the row in registers on the way in and out.
+template <typename T, int L>
+__device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint4 *op, bool neg, const AdjLim<T> &lim,
+                                          T &dLds, T &osum)
 {
     constexpr int per = 16 / int(sizeof(T)); // elements per 16-byte chunk
-    RegLine<T, L, NEG> acc;
+    T cv[L], lv[L];
 #pragma unroll
     for (int q = 0; q < L / per; ++q) {
         const uint4 u = __ldg(fp + q), w = __ldg(lp + q);
         const T *pu = reinterpret_cast<const T *>(&u), *pw = reinterpret_cast<const T *>(&w);
 #pragma unroll
-        for (int e = 0; e < per; ++e) { acc.cv[q * per + e] = pu[e]; acc.lv[q * per + e] = pw[e]; }
+        for (int e = 0; e < per; ++e) { cv[q * per + e] = pu[e]; lv[q * per + e] = pw[e]; }
+    }
+    RegLine<T, L, false> acc;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        acc.cv[i] = neg ? cv[L - 1 - i] : cv[i];
+        acc.lv[i] = neg ? lv[L - 1 - i] : lv[i];
     }
     march_adjoint<false, L, T>(acc, lim, L, dLds, osum);
 #pragma unroll
@@ -674,7 +703,10 @@ __device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint
         uint4 u;
         T *pu = reinterpret_cast<T *>(&u);
 #pragma unroll
-        for (int e = 0; e < per; ++e) pu[e] = acc.lv[q * per + e];
+        for (int e = 0; e < per; ++e) {
+            const int i = q * per + e;
+            pu[e] = neg ? acc.lv[L - 1 - i] : acc.lv[i];
+        }
         op[q] = u;
     }
 }
@@ -700,8 +732,7 @@ __global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid
         } else {
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
-            if (kc.nd & 1) rows_line<T, true, L>(fp, lp, op, lim, dLds, osum);
-            else rows_line<T, false, L>(fp, lp, op, lim, dLds, osum);
+            rows_line<T, L>(fp, lp, op, kc.nd & 1, lim, dLds, osum);
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = (kc.nd & 1) ? -dLds : dLds;
         }
@@ -751,24 +782,32 @@ __global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_staged_kernel(const
             const AdjLim<C> lim = make_adj_lim(kc);
             C dLds, osum;
             const bool neg = kc.nd & 1;
-            auto run = [&](auto negc) {
-                constexpr bool NEG = decltype(negc)::value;
-                RegLine<T, L, NEG> acc;
+            // one march body for both signs: a negative row is reversed on the way in and out
+            float cv[L], lv[L];
 #pragma unroll
-                for (int q = 0; q < CH; ++q) {
-                    const float4 u = *reinterpret_cast<const float4 *>(sf + lane * P + 4 * q);
-                    const float4 v = *reinterpret_cast<const float4 *>(sl + lane * P + 4 * q);
-                    acc.cv[4 * q] = u.x; acc.cv[4 * q + 1] = u.y; acc.cv[4 * q + 2] = u.z; acc.cv[4 * q + 3] = u.w;
-                    acc.lv[4 * q] = v.x; acc.lv[4 * q + 1] = v.y; acc.lv[4 * q + 2] = v.z; acc.lv[4 * q + 3] = v.w;
+            for (int q = 0; q < CH; ++q) {
+                const float4 u = *reinterpret_cast<const float4 *>(sf + lane * P + 4 * q);
+                const float4 v = *reinterpret_cast<const float4 *>(sl + lane * P + 4 * q);
+                cv[4 * q] = u.x; cv[4 * q + 1] = u.y; cv[4 * q + 2] = u.z; cv[4 * q + 3] = u.w;
+                lv[4 * q] = v.x; lv[4 * q + 1] = v.y; lv[4 * q + 2] = v.z; lv[4 * q + 3] = v.w;
+            }
+            RegLine<T, L, false> acc;
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                acc.cv[i] = neg ? cv[L - 1 - i] : cv[i];
+                acc.lv[i] = neg ? lv[L - 1 - i] : lv[i];
+            }
+            march_adjoint<false, L, T>(acc, lim, L, dLds, osum);
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = 4 * q + e;
+                    o[e] = neg ? acc.lv[L - 1 - i] : acc.lv[i];
                 }
-                march_adjoint<false, L, T>(acc, lim, L, dLds, osum);
-#pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    *reinterpret_cast<float4 *>(sl + lane * P + 4 * q) =
-                        make_float4(acc.lv[4 * q], acc.lv[4 * q + 1], acc.lv[4 * q + 2], acc.lv[4 * q + 3]);
-            };
-            if (neg) run(std::true_type{});
-            else run(std::false_type{});
+                *reinterpret_cast<float4 *>(sl + lane * P + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
+            }
             if (!isfinite(osum)) atomicOr(a.err, ERR_NAN);
             dnu = neg ? -dLds : dLds;
         }

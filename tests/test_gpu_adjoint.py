@@ -115,6 +115,67 @@ def test_sweep_adjoint(n, nu, axis, dtype):
     v.close()
 
 
+def _rough_velocity_f(n, nu, dtype, seed=7):
+    # the Fermi-Dirac profile times positive white noise, with a tenth of the cells
+    # nearly emptied: velocity lines whose constraint acts at many faces (and whose
+    # positivity clamp acts on the nearly empty donors), unlike the smooth profiles.
+    # No exact zeros: equal neighbours would tie the limiter's selections, where the
+    # oracle's min / max and the kernel may credit different (equal) arguments
+    rng = np.random.default_rng(seed)
+    f = I.initial_f(I.gaussian_field(n, 0.01, seed=seed), I.fermi_dirac(nu, 5.0), np.float64)
+    f *= 0.2 + rng.random(f.shape)
+    f[rng.random(f.shape) < 0.1] *= 1e-3
+    return f.astype(dtype)
+
+
+def _general_path_fraction(f, axis, s):
+    # share of the faces of the velocity lines along `axis` (fractional Courant number
+    # s, flow toward +index) where fbar is not between c0 and f_MP = median(c0, cp1,
+    # f_UL), i.e. where the adjoint cannot take the plain-face path
+    c = np.moveaxis(f.astype(np.float64), axis, -1)
+    pad = np.zeros(c.shape[:-1] + (3,))
+    e = np.concatenate([pad, c, pad], -1)
+    m = c.shape[-1]
+    cm2, cm1, c0, cp1, cp2 = (e[..., 3 + o:3 + o + m] for o in (-2, -1, 0, 1, 2))
+    # weights of the mean flux over the departure interval, in powers of s
+    W = np.array([[2, -13, 47, 27, -3]]) / 60.0
+    w = (W[0] + np.array([0, -1 / 24, 5 / 8, -5 / 8, 1 / 24]) * s + np.array([-1 / 24, 1 / 4, -1 / 3, 1 / 12, 1 / 24]) * s ** 2
+         + np.array([0, 1 / 24, -1 / 8, 1 / 8, -1 / 24]) * s ** 3 + np.array([1 / 120, -1 / 30, 1 / 20, -1 / 30, 1 / 120]) * s ** 4)
+    fbar = w[0] * cm2 + w[1] * cm1 + w[2] * c0 + w[3] * cp1 + w[4] * cp2
+    ful = c0 + (1 - s) / s * (c0 - cm1)
+    fmp = np.median(np.stack([c0, cp1, ful]), axis=0)
+    between = (fbar >= np.minimum(c0, fmp)) & (fbar <= np.maximum(c0, fmp))
+    return 1.0 - between[..., :m - 1].mean()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("n,nu", [((4, 4, 4), (16, 16, 16)), ((4, 5, 6), (8, 20, 32))])
+@pytest.mark.parametrize("axis", [3, 4, 5])
+def test_sweep_adjoint_rough_velocity_lines(n, nu, axis, dtype):
+    # On smooth velocity profiles every face of a velocity adjoint is plain (fbar kept,
+    # no curvature adjoint pending); rough lines run its general path at many faces and
+    # the hand-over between the two, which must agree with the oracle as well
+    B = _lib()
+    f0 = _rough_velocity_f(n, nu, dtype)
+    phi = I.fourier_potential(n, seed=11).astype(np.float32)
+    lam0 = np.random.default_rng(21).standard_normal(f0.shape).astype(dtype)
+    assert _general_path_fraction(f0, axis, 0.5) > 0.5  # (smooth profiles: about 0.13)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_for(g, axis, phi, 0.8)
+    lam_ref = lam0.astype(np.float64)
+    dLdg_ref = O.sweep_adjoint(g, f0.astype(np.float64), lam_ref, axis, dt, 1.0, phi.astype(np.float64))
+    dev = torch.device("cuda")
+    lam = torch.from_numpy(lam0).to(dev)
+    dLdg = torch.zeros(n, dtype=torch.float64, device=dev)
+    v = B.Vlasov(torch.zeros(f0.shape, dtype=lam.dtype, device=dev), L=1.0, V=5.0)
+    v.sweep_adjoint(torch.from_numpy(f0).to(dev), lam, axis, dt, 1.0, torch.from_numpy(phi).to(dev), dLdg)
+    v.status()
+    fp64 = dtype == np.float64
+    _compare(lam.cpu().numpy(), lam_ref, fp64, "rough axis %d lambda" % axis)
+    _compare_field(dLdg.cpu().numpy(), dLdg_ref, fp64, "rough axis %d dL/dg" % axis)
+    v.close()
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_sweep_adjoint_whole_cell_shift(axis, dtype):
