@@ -762,13 +762,21 @@ def run_ours(args):
     del um, s2
 
     # end to end through the C ABI with host buffers: vlasov_step_host reads f from pinned
-    # host memory, steps and writes it back (x-slabs copied on a second stream behind the
-    # cell-local sweeps); rho comes back too
+    # host memory, steps and writes it back (x-slabs copied in and out on streams of their
+    # own behind the cell-local sweeps; a step's uploads run beside the previous step's
+    # downloads); rho comes back too
     e2e = None
     if not args.no_e2e:
         fh = torch.empty(f.shape, dtype=f.dtype, pin_memory=True)
         fh.copy_(f)
-        rho_h = torch.empty(rho.shape, dtype=rho.dtype, pin_memory=True)
+        # each step's rho is read back on a side stream into one of two buffers, so that the
+        # read (queued behind the slab downloads on the copy engine) does not hold up the
+        # next step; the step after next writes the same rho buffer once that read is done
+        rho_d = [rho, torch.empty_like(rho)]
+        rho_h = [torch.empty(rho.shape, dtype=rho.dtype, pin_memory=True) for _ in range(2)]
+        side = torch.cuda.Stream(device=dev)
+        stepped = [torch.cuda.Event() for _ in range(2)]
+        read = [torch.cuda.Event() for _ in range(2)]
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -777,17 +785,28 @@ def run_ours(args):
             nonlocal phi, phi2
             a_s, a_h, a_e, cfl = schedule(k, total)
             dt = drift_dt(cfl, a_h, n, nu, V, L)
-            v.step_host(fh, dt, a_h, a_e, phi, rho_bg=rho_bg, four_pi_G=w["four_pi_G"], phi_next=phi2, rho_nu=rho)
-            rho_h.copy_(rho, non_blocking=True)
+            b = k % 2
+            if k >= 2:
+                stream.wait_event(read[b])
+            v.step_host(fh, dt, a_h, a_e, phi, rho_bg=rho_bg, four_pi_G=w["four_pi_G"], phi_next=phi2,
+                        rho_nu=rho_d[b])
+            stepped[b].record(stream)
+            side.wait_event(stepped[b])
+            with torch.cuda.stream(side):
+                rho_h[b].copy_(rho_d[b], non_blocking=True)
+            read[b].record(side)
             phi, phi2 = phi2, phi
 
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        host_step(0, 1)  # warm-up: the copy stream and its events
+        host_step(0, 1)  # warm-up: the copy streams and their events
         torch.cuda.synchronize()
         t0.record(stream)
         for k in range(args.e2e_steps):
             host_step(k, args.e2e_steps)
+        v.host_wait()  # the last step's downloads inside the timed region
+        for b in range(2):
+            stream.wait_event(read[b])  # and the last reads of rho
         t1.record(stream)
         torch.cuda.synchronize()
         e_ms = t0.elapsed_time(t1)

@@ -250,12 +250,31 @@ int vlasov_download(vlasov_ctx *ctx, void *f_host);
  * is done; only D_x, the moment and the Poisson solve wait for the whole grid.
  * Without pinned host memory the copies do not overlap.  Falls back to the
  * three calls in sequence for 16-bit storage, a whole-cell shift in D_z or D_y,
- * or a grid whose tiles do not fall on x-planes.  f_host must stay valid until
- * the context stream reaches the end of the step (vlasov_status synchronises).
+ * or a grid whose tiles do not fall on x-planes.
+ *
+ * Ordering.  The uploads run on a stream of the library's own after the work
+ * queued on the context stream before the call; the downloads on another, and
+ * the call returns with them queued, not waited for.  The next vlasov_step_host
+ * on the same slabs starts each slab's upload once the download of that slab is
+ * done, and nothing else (so one step's downloads and the next step's uploads
+ * share the link, one direction each); every other call of this library on the
+ * context, and vlasov_host_wait, first makes the context stream wait for all of
+ * them.  Work the caller queues on the stream itself after vlasov_step_host that
+ * reads the host buffer or reads or writes f on the device comes after
+ * vlasov_host_wait (or vlasov_status, which synchronises); other work (reading
+ * rho_nu or phi^{n+1}, say) need not.  f_host must stay valid until then.
  */
 int vlasov_step_host(vlasov_ctx *ctx, void *f_host, double dt, double a_half, double a_full,
                      const float *phi_n_dev, const double *rho_bg_dev, double four_pi_G, float *phi_next_dev,
                      double *rho_nu_dev);
+
+/*
+ * Make the context stream wait for the downloads of the last vlasov_step_host
+ * (a no-op when none are outstanding).  Queues the wait and returns; the
+ * paper has no counterpart (it keeps f in memory).  VLASOV_EINVAL for a null
+ * context.
+ */
+int vlasov_host_wait(vlasov_ctx *ctx);
 
 /*
  * Per-part timers (the paper times each part of a step, Sec. 5.1).  While

@@ -47,7 +47,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
            "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host", "vlasov_encode", "vlasov_decode",
-           "vlasov_set_position_tiles")
+           "vlasov_set_position_tiles", "vlasov_host_wait")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -137,6 +137,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_host.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP,
                                    ctypes.c_double, _VP, _VP]
     L.vlasov_step_host.restype = ctypes.c_int
+    L.vlasov_host_wait.argtypes = [_VP]
+    L.vlasov_host_wait.restype = ctypes.c_int
     L.vlasov_encode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP]
     L.vlasov_encode.restype = ctypes.c_int
     L.vlasov_decode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]
@@ -568,7 +570,9 @@ class Vlasov:
     def step_host(self, f_host, dt: float, a_half: float, a_full: float, phi_n, rho_bg=None,
                   four_pi_G: float = 1.0, phi_next=None, rho_nu=None):
         """One Eq. (5) step of the host tensor f_host (like f, ideally pinned), in place:
-        its x-slabs are copied in and out on a second stream behind the cell-local sweeps."""
+        its x-slabs are copied in on a second stream and out on a third behind the
+        cell-local sweeps.  The downloads may still run when the call returns: the next
+        step_host overlaps its uploads with them; host_wait (or status) orders later work."""
         if f_host.is_cuda or tuple(f_host.shape) != self.shape or f_host.dtype != self.f.dtype \
                 or not f_host.is_contiguous():
             raise ValueError("f_host must be a contiguous host tensor like f")
@@ -577,6 +581,13 @@ class Vlasov:
             self.ctx, f_host.data_ptr(), dt, a_half, a_full, _ptr(self._field(phi_n, self.torch.float32)),
             _ptr(self._field(rho_bg, self.torch.float64)), four_pi_G,
             _ptr(self._field(phi_next, self.torch.float32)), _ptr(self._field(rho_nu, self.torch.float64))))
+
+    def host_wait(self):
+        """Queue on the stream the wait for the downloads of the last step_host (they run on
+        a stream of their own; the next step_host waits per slab, every other call waits for
+        all of them first)."""
+        self._sync_stream()
+        _check(self.ctx, load().vlasov_host_wait(self.ctx))
 
     def set_adjoint_arrays(self, arrays: int):
         """f-sized scratch arrays step_adjoint may hold: 8, 4 or 0 (8 if they fit, else 4)."""

@@ -165,9 +165,17 @@ struct vlasov_ctx {
     int slab_x0, slab_x1;
     long long splan_tpp[5]; // tiles per x-plane of the streamed sweeps (0: a block spans planes)
     long long ltpp;         // the same for the u_z line kernel
-    cudaStream_t copy_stream;
+    cudaStream_t copy_stream;                // uploads
+    cudaStream_t down_stream;                // downloads
     cudaEvent_t slab_ev[2 * kMaxSlabs + 2];
+    cudaEvent_t down_ev[kMaxSlabs + 1];      // after each slab's download; [kMaxSlabs]: after the last
     bool slab_ev_ok;
+    // downloads of the last vlasov_step_host that the context stream has not been made
+    // to wait for (0: none), and their slab size: the next vlasov_step_host with the
+    // same slabs orders each upload after the download of its own slab only; any other
+    // call queues the wait for all of them first (settle)
+    int pending_slabs;
+    size_t pending_slab_bytes;
     int adj_arrays; // f-sized scratch arrays vlasov_step_adjoint may use: 8, 4 or 0 (8 if they fit, else 4)
     char msg[256];
     unsigned sweeps; // sweeps queued so far: the stochastic-rounding seed of the next one
@@ -228,6 +236,21 @@ static int cuda_fail(vlasov_ctx *c, cudaError_t e, const char *where)
     do {                                                                                                    \
         cudaError_t e_ = (call);                                                                            \
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);                                          \
+    } while (0)
+
+// queue on the context stream the wait for the downloads of the last vlasov_step_host
+static int settle(vlasov_ctx *c)
+{
+    if (c->pending_slabs) {
+        c->pending_slabs = 0;
+        VK_CUDA(c, cudaStreamWaitEvent(c->stream, c->down_ev[kMaxSlabs], 0));
+    }
+    return VLASOV_OK;
+}
+
+#define VK_SETTLE(ctx)                                                                                      \
+    do {                                                                                                    \
+        if (int rc_ = settle(ctx)) return rc_;                                                              \
     } while (0)
 
 static CUtensorMapDataType tmap_type(int dtype)
@@ -497,9 +520,12 @@ static void free_scratch(vlasov_ctx *c)
     cudaFree(c->d_sc);
     cudaFree(c->d_part);
     cudaFree(c->d_mpart);
-    if (c->slab_ev_ok)
+    if (c->slab_ev_ok) {
         for (auto e : c->slab_ev) cudaEventDestroy(e);
+        for (auto e : c->down_ev) cudaEventDestroy(e);
+    }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->down_stream) cudaStreamDestroy(c->down_stream);
 }
 
 extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, float *scale_dev, void *stream)
@@ -590,6 +616,7 @@ extern "C" int vlasov_init(vlasov_ctx **out, const vlasov_grid *g, void *f_dev, 
 extern "C" void vlasov_destroy(vlasov_ctx *c)
 {
     if (!c) return;
+    settle(c);
     cudaStreamSynchronize(c->stream);
     free_scratch(c);
     for (auto &p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -602,6 +629,7 @@ static size_t f_bytes(const vlasov_ctx *c) { return (size_t)c->ncell * c->g.nux 
 extern "C" int vlasov_upload(vlasov_ctx *c, const void *f_host)
 {
     if (!c || !f_host) return c ? fail(c, VLASOV_EINVAL, "vlasov_upload: null host buffer") : VLASOV_EINVAL;
+    VK_SETTLE(c);
     const size_t bytes = (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es;
     VK_CUDA(c, cudaMemcpyAsync(c->f, f_host, bytes, cudaMemcpyHostToDevice, c->stream));
     return VLASOV_OK;
@@ -610,6 +638,7 @@ extern "C" int vlasov_upload(vlasov_ctx *c, const void *f_host)
 extern "C" int vlasov_download(vlasov_ctx *c, void *f_host)
 {
     if (!c || !f_host) return c ? fail(c, VLASOV_EINVAL, "vlasov_download: null host buffer") : VLASOV_EINVAL;
+    VK_SETTLE(c);
     const size_t bytes = (size_t)c->ncell * c->g.nux * c->g.nuy * c->g.nuz * c->es;
     VK_CUDA(c, cudaMemcpyAsync(f_host, c->f, bytes, cudaMemcpyDeviceToHost, c->stream));
     return VLASOV_OK;
@@ -625,6 +654,7 @@ extern "C" int vlasov_enable_timers(vlasov_ctx *c, int on)
 extern "C" int vlasov_read_timers(vlasov_ctx *c, double *ms, long long *launches, int nkinds)
 {
     if (!c || nkinds < 0) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     VK_CUDA(c, cudaStreamSynchronize(c->stream));
     for (auto &p : c->pending) {
         float t = 0.f;
@@ -651,6 +681,7 @@ extern "C" int vlasov_set_stream(vlasov_ctx *c, void *stream)
 extern "C" int vlasov_set_f(vlasov_ctx *c, void *f_dev, float *scale_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (!f_dev || reinterpret_cast<uintptr_t>(f_dev) % 16) return fail(c, VLASOV_EINVAL, "vlasov_set_f: f_dev must be 16-byte aligned");
     const bool coded = c->g.dtype == VLASOV_BF16 || c->g.dtype == VLASOV_F16;
     if (coded != (scale_dev != nullptr) || (scale_dev && reinterpret_cast<uintptr_t>(scale_dev) % 16))
@@ -1025,6 +1056,7 @@ static int prep_velocity(vlasov_ctx *c, const float *phi, double dt, int mask)
 extern "C" int vlasov_sweep(vlasov_ctx *c, int axis, double dt, double a, const float *phi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (axis < 0 || axis > 5) return fail(c, VLASOV_EINVAL, "axis %d outside 0..5", axis);
     if (axis < 3) return run_position(c, axis, dt, a);
     int rc = prep_velocity(c, phi_dev, dt, 1 << (axis - 3));
@@ -1035,6 +1067,7 @@ extern "C" int vlasov_sweep(vlasov_ctx *c, int axis, double dt, double a, const 
 extern "C" int vlasov_moment(vlasov_ctx *c, double *rho_dev, double *mass_host)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (!rho_dev) return fail(c, VLASOV_EINVAL, "rho_dev is NULL");
     cudaError_t e;
     {
@@ -1060,6 +1093,7 @@ extern "C" int vlasov_moment(vlasov_ctx *c, double *rho_dev, double *mass_host)
 extern "C" int vlasov_moments(vlasov_ctx *c, double *rho_dev, double *umean_dev, double *sigma2_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (!rho_dev && !umean_dev && !sigma2_dev) return fail(c, VLASOV_EINVAL, "vlasov_moments: no output");
     PartTimer t(c, VLASOV_T_MOMENTS, 1);
     const cudaError_t e = launch_moments(c->gd, c->f, c->scale, c->g.dtype, rho_dev, umean_dev, sigma2_dev, c->stream,
@@ -1072,6 +1106,7 @@ extern "C" int vlasov_poisson(vlasov_ctx *c, const double *rho_dev, const double
                               double four_pi_G, float *phi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (!rho_dev || !phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_poisson: null rho or phi");
     if (!isfinite(a) || !isfinite(four_pi_G)) return fail(c, VLASOV_EINVAL, "vlasov_poisson: a and four_pi_G must be finite");
     PartTimer t(c, VLASOV_T_POISSON, 9);
@@ -1148,6 +1183,7 @@ extern "C" int vlasov_set_fused_kick(vlasov_ctx *c, int mode)
 extern "C" int vlasov_kick(vlasov_ctx *c, double dt, const float *phi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = prep_velocity(c, phi_dev, dt, 7);
     if (rc) return rc;
     return run_kick(c);
@@ -1171,6 +1207,7 @@ extern "C" int vlasov_step(vlasov_ctx *c, double dt, double a_half, double a_ful
                            const double *rho_bg_dev, double four_pi_G, float *phi_next_dev, double *rho_nu_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (!phi_n_dev) return fail(c, VLASOV_EINVAL, "vlasov_step: phi_n_dev is NULL");
     int rc;
     // kick D_uz D_uy D_ux (dt/2), D_ux first
@@ -1243,29 +1280,52 @@ extern "C" int vlasov_step_host(vlasov_ctx *c, void *f_host, double dt, double a
         if ((rc = vlasov_step(c, dt, a_half, a_full, phi_n_dev, rho_bg_dev, four_pi_G, phi_next_dev, rho_nu_dev))) return rc;
         return vlasov_download(c, f_host);
     }
-    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        c->copy_stream = nullptr;
-        return fail(c, VLASOV_ECUDA, "vlasov_step_host: copy stream");
+    for (cudaStream_t *st : {&c->copy_stream, &c->down_stream}) {
+        if (!*st && cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) {
+            *st = nullptr;
+            return fail(c, VLASOV_ECUDA, "vlasov_step_host: copy stream");
+        }
     }
     if (!c->slab_ev_ok) {
         for (auto &e : c->slab_ev) VK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : c->down_ev) VK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->slab_ev_ok = true;
     }
     cudaEvent_t *up = c->slab_ev, *ready = c->slab_ev + kMaxSlabs;
-    cudaEvent_t start = c->slab_ev[2 * kMaxSlabs], copied = c->slab_ev[2 * kMaxSlabs + 1];
+    cudaEvent_t start = c->slab_ev[2 * kMaxSlabs];
     const int planes = c->g.nx / S;
     const size_t plane_bytes = f_bytes(c) / c->g.nx, slab_bytes = plane_bytes * planes;
     unsigned char *fd = static_cast<unsigned char *>(c->f), *fh = static_cast<unsigned char *>(f_host);
     auto on_slab = [&](int sl) { c->slab_x0 = sl * planes; c->slab_x1 = (sl + 1) * planes; };
     auto all = [&]() { c->slab_x0 = c->slab_x1 = 0; };
+    // Downloads of the previous call still in flight on the same slabs: each upload
+    // waits for the download of its own slab only (the device slab it overwrites, the
+    // host slab it reads), so this step's uploads run beside the previous step's
+    // downloads, one direction each.  Otherwise the context stream waits for them all.
+    // (The context stream reaches D_x only after every upload, so the later library
+    // calls of this step, which wait for all of those downloads, wait for nothing.)
+    const bool chain = c->pending_slabs == S && c->pending_slab_bytes == slab_bytes;
+    if (!chain) VK_SETTLE(c);
     struct Reset { // whatever way this function returns, later calls see the whole grid
         vlasov_ctx *c;
-        ~Reset() { c->slab_x0 = c->slab_x1 = 0; }
-    } reset{c};
-    // the upload starts once earlier work on f (queued on the context's stream) is done
-    VK_CUDA(c, cudaEventRecord(start, c->stream));
-    VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, start, 0));
+        bool done;
+        ~Reset()
+        {
+            c->slab_x0 = c->slab_x1 = 0;
+            if (!done) settle(c); // an early return: later work waits for the previous downloads
+        }
+    } reset{c, false};
+    // The uploads start once earlier work on f (queued on the context's stream) is done.
+    // Chained, the library's own earlier work on each slab is behind that slab's
+    // download, and the caller's work on f after the previous call would have come
+    // after vlasov_host_wait (which ends the chain): the stream's tail (a read of rho,
+    // say, queued behind the downloads on the copy engine) does not hold them up.
+    if (!chain) {
+        VK_CUDA(c, cudaEventRecord(start, c->stream));
+        VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, start, 0));
+    }
     for (int sl = 0; sl < S; ++sl) {
+        if (chain) VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->down_ev[sl], 0));
         VK_CUDA(c, cudaMemcpyAsync(fd + sl * slab_bytes, fh + sl * slab_bytes, slab_bytes, cudaMemcpyHostToDevice,
                                    c->copy_stream));
         VK_CUDA(c, cudaEventRecord(up[sl], c->copy_stream));
@@ -1289,27 +1349,47 @@ extern "C" int vlasov_step_host(vlasov_ctx *c, void *f_host, double dt, double a
         if ((rc = vlasov_poisson(c, rho, rho_bg_dev, a_full, four_pi_G, phi_next_dev))) return rc;
         if ((rc = prep_velocity(c, phi_next_dev, 0.5 * dt, 7))) return rc;
     }
-    // second kick one slab at a time, each slab's download behind it
+    // the previous downloads are behind every upload, so behind D_x: waiting for them
+    // here costs nothing, and frees their events for this step's downloads
+    VK_SETTLE(c);
+    // second kick one slab at a time, each slab's download behind it on the download stream
+    int queued = 0;
     for (int sl = 0; sl < S && !rc; ++sl) {
         on_slab(sl);
         if (!(rc = run_kick(c))) {
             VK_CUDA(c, cudaEventRecord(ready[sl], c->stream));
-            VK_CUDA(c, cudaStreamWaitEvent(c->copy_stream, ready[sl], 0));
+            VK_CUDA(c, cudaStreamWaitEvent(c->down_stream, ready[sl], 0));
             VK_CUDA(c, cudaMemcpyAsync(fh + sl * slab_bytes, fd + sl * slab_bytes, slab_bytes, cudaMemcpyDeviceToHost,
-                                       c->copy_stream));
+                                       c->down_stream));
+            VK_CUDA(c, cudaEventRecord(c->down_ev[sl], c->down_stream));
+            ++queued;
         }
     }
     all();
-    if (rc) return rc;
-    // later work on the context's stream waits for the downloads
-    VK_CUDA(c, cudaEventRecord(copied, c->copy_stream));
-    VK_CUDA(c, cudaStreamWaitEvent(c->stream, copied, 0));
+    VK_CUDA(c, cudaEventRecord(c->down_ev[kMaxSlabs], c->down_stream));
+    if (rc || queued != S) {
+        // later work waits for whatever was queued
+        VK_CUDA(c, cudaStreamWaitEvent(c->stream, c->down_ev[kMaxSlabs], 0));
+        return rc;
+    }
+    // later calls wait for the downloads (settle); the next vlasov_step_host per slab
+    c->pending_slabs = S;
+    c->pending_slab_bytes = slab_bytes;
+    reset.done = true;
+    return VLASOV_OK;
+}
+
+extern "C" int vlasov_host_wait(vlasov_ctx *c)
+{
+    if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     return VLASOV_OK;
 }
 
 extern "C" int vlasov_status(vlasov_ctx *c)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     unsigned bits = 0;
     VK_CUDA(c, cudaStreamSynchronize(c->stream));
     VK_CUDA(c, cudaMemcpy(&bits, c->d_err, sizeof bits, cudaMemcpyDeviceToHost));
@@ -1445,6 +1525,7 @@ extern "C" int vlasov_sweep_adjoint(vlasov_ctx *c, const void *f_in_dev, void *l
                                     const float *phi_dev, double *dLdg_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (axis < 0 || axis > 5) return fail(c, VLASOV_EINVAL, "axis %d outside 0..5", axis);
     int rc = check_adjoint_args(c, f_in_dev, lam_dev, "vlasov_sweep_adjoint");
     if (rc) return rc;
@@ -1455,6 +1536,7 @@ extern "C" int vlasov_sweep_adjoint(vlasov_ctx *c, const void *f_in_dev, void *l
 extern "C" int vlasov_moment_adjoint(vlasov_ctx *c, const double *dLdrho_dev, void *lam_dev, int accumulate)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     if (c->g.dtype != VLASOV_F32 && c->g.dtype != VLASOV_F64)
         return fail(c, VLASOV_EINVAL, "vlasov_moment_adjoint: FP32 or FP64 storage only");
     if (!dLdrho_dev || !lam_dev || reinterpret_cast<uintptr_t>(lam_dev) % 16)
@@ -1483,6 +1565,7 @@ extern "C" int vlasov_step_record(vlasov_ctx *c, const void *f_n_dev, void *cons
                                   double a_half, const float *phi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = check_records(c, rec_dev, "vlasov_step_record");
     if (!rc) rc = check_adjoint_args(c, f_n_dev, rec_dev[0], "vlasov_step_record");
     if (rc) return rc;
@@ -1504,6 +1587,7 @@ extern "C" int vlasov_step_adjoint_recorded(vlasov_ctx *c, const void *f_n_dev, 
                                             double dt, double a_half, const float *phi_dev, double *dLdphi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint_recorded");
     if (!rc) rc = check_records(c, const_cast<void *const *>(rec_dev), "vlasov_step_adjoint_recorded");
     if (rc) return rc;
@@ -1583,6 +1667,7 @@ extern "C" int vlasov_step_adjoint(vlasov_ctx *c, const void *f_n_dev, void *lam
                                    const float *phi_dev, double *dLdphi_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint");
     if (rc) return rc;
     if (!phi_dev) return fail(c, VLASOV_EINVAL, "vlasov_step_adjoint: phi_dev is NULL");
@@ -1616,6 +1701,7 @@ extern "C" int vlasov_step_record_sc(vlasov_ctx *c, const void *f_n_dev, void *c
                                      double *rho_nu_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = check_records(c, rec_dev, "vlasov_step_record_sc");
     if (!rc) rc = check_adjoint_args(c, f_n_dev, rec_dev[0], "vlasov_step_record_sc");
     if (rc) return rc;
@@ -1667,6 +1753,7 @@ extern "C" int vlasov_step_adjoint_recorded_sc(vlasov_ctx *c, const void *f_n_de
                                                double *dLdrho_bg_dev)
 {
     if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
     int rc = check_adjoint_args(c, f_n_dev, lam_dev, "vlasov_step_adjoint_recorded_sc");
     if (!rc) rc = check_records(c, const_cast<void *const *>(rec_dev), "vlasov_step_adjoint_recorded_sc");
     if (rc) return rc;

@@ -89,3 +89,64 @@ def test_step_host_fp64_falls_back_to_the_three_calls():
     for r, o in zip(ref, got):
         assert np.array_equal(r, o)
     assert ux_launches == 2
+
+
+def _steps(B, f0, phi0, bg, dt, plan):
+    """Run `plan` (a sequence of "host", "host2" (a second host buffer holding the same
+    state), "moment" (a library call between steps) and "dev" (upload, vlasov_step,
+    download)) on a fresh context; returns the host state, rho and phi after the last step."""
+    V = 5.0
+    n = f0.shape[:3]
+    f = torch.zeros(f0.shape, dtype=torch.float32, device="cuda")
+    v = B.Vlasov(f, V=V)
+    phi = [torch.from_numpy(phi0).cuda(), torch.empty(n, dtype=torch.float32, device="cuda")]
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    bgt = torch.from_numpy(bg).cuda()
+    fh = torch.from_numpy(f0.copy()).pin_memory()
+    fh2 = torch.empty_like(fh).pin_memory()
+    cur = fh
+    for k, what in enumerate(plan):
+        p_n, p_next = phi[k % 2], phi[(k + 1) % 2]
+        if what == "host2":
+            v.host_wait()
+            torch.cuda.synchronize()
+            other = fh2 if cur is fh else fh
+            other.copy_(cur)
+            cur = other
+        if what in ("host", "host2"):
+            v.step_host(cur, dt, 0.55, 0.6, p_n, rho_bg=bgt, phi_next=p_next, rho_nu=rho)
+        elif what == "moment":
+            v.step_host(cur, dt, 0.55, 0.6, p_n, rho_bg=bgt, phi_next=p_next, rho_nu=rho)
+            v.moment(torch.empty(n, dtype=torch.float64, device="cuda"))
+        else:
+            v.upload(cur)
+            v.step(dt, 0.55, 0.6, p_n, rho_bg=bgt, phi_next=p_next, rho_nu=rho)
+            v.download(cur)
+    v.host_wait()
+    v.status()
+    out = (cur.numpy().copy(), rho.cpu().numpy(), phi[len(plan) % 2].cpu().numpy())
+    v.close()
+    return out
+
+
+@pytest.mark.parametrize("plan", [("host", "host", "host", "host"), ("host", "moment", "host", "host"),
+                                  ("host", "host2", "host", "dev", "host")])
+def test_consecutive_step_host_calls(plan):
+    # Back-to-back vlasov_step_host calls start each slab's upload once the previous call's
+    # download of that slab is done (the downloads run on a stream of their own); another
+    # library call between two of them, a second host buffer, or device steps in between
+    # must see the finished downloads.  Every plan equals the same number of device steps.
+    B = _lib()
+    V = 5.0
+    n, nu = (16, 8, 8), (16, 16, 16)
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=27), I.fermi_dirac(nu, V), np.float32)
+    phi0 = I.fourier_potential(n, seed=37).astype(np.float32)
+    bg = 3.0 * (1.0 + I.gaussian_field(n, 0.5, seed=28))
+    g = O.grid(n, nu, V=V)
+    p64 = phi0.astype(np.float64)
+    dt = min([1.4 / O.max_abs_nu(g, ax, 1.0, 1.0, p64) for ax in (3, 4, 5)] +
+             [0.7 / O.max_abs_nu(g, ax, 1.0, 0.55, p64) for ax in (0, 1, 2)])
+    ref = _steps(B, f0, phi0, bg, dt, ("dev",) * len(plan))
+    got = _steps(B, f0, phi0, bg, dt, plan)
+    for r, o in zip(ref, got):
+        assert np.array_equal(r, o)
