@@ -10,8 +10,9 @@ Where the forward sits within FP32 rounding of a limiter switch the two sides ma
 different branches (and over a step the FP32 forward states drift from the FP64 ones
 by rounding, so more faces sit near a switch); each such face moves a few entries by
 O(|lambda|).  For one sweep at most 2e-4 of the entries may be off by more than 1e-3
-of max |lambda| and the others must agree to FP32 rounding (relative L1 <= 1e-6 over
-them).  Over a step the later adjoint sweeps spread each flip over its neighbours, so
+of max |lambda| and the others, leaving out the cells within 3 of an off entry along
+the swept axis (the stencil of the flipped face), must agree to FP32 rounding (relative
+L1 <= 1e-6 over them).  Over a step the later adjoint sweeps spread each flip over its neighbours, so
 there the bound is at most 2e-4 of the entries off by 1e-3 and relative L1 <= 1e-3
 overall.  The measured values are printed.
 """
@@ -51,7 +52,7 @@ def _dt_step(g, phi, cfl, a=1.0):
     return cfl / m
 
 
-def _compare(gpu, ref, fp64, what="", step=False):
+def _compare(gpu, ref, fp64, what="", step=False, axis=None):
     gpu = np.asarray(gpu, dtype=np.float64)
     err = np.abs(gpu - ref)
     scale = np.abs(ref).max()
@@ -59,7 +60,14 @@ def _compare(gpu, ref, fp64, what="", step=False):
     rinf = err.max() / scale
     off = err > 1e-3 * scale
     bad = np.count_nonzero(off) / err.size
-    rl1_on = err[~off].sum() / np.abs(ref[~off]).sum()
+    # a limiter branch that flips at one face moves the adjoint of the cells of that
+    # face's stencil (up to 3 cells away along the swept axis) by amounts that can stay
+    # below the off-branch threshold: the on-branch set leaves those cells out
+    near = off.copy()
+    if axis is not None:
+        for k in range(1, 4):
+            near |= np.roll(off, k, axis) | np.roll(off, -k, axis)
+    rl1_on = err[~near].sum() / np.abs(ref[~near]).sum()
     print("%s rel L1 %.2e  rel Linf %.2e  off-branch fraction %.2e  rel L1 on-branch %.2e"
           % (what, rl1, rinf, bad, rl1_on))
     if fp64:
@@ -85,6 +93,7 @@ SHAPES = [
     ((16, 16, 16), (16, 16, 16)),   # u_z lines of 16 in registers
     ((6, 5, 7), (8, 20, 12)),       # ragged; u_z lines of 12 through the column march
     ((4, 5, 8), (4, 8, 32)),        # periodic lines of 4 and 5; u_x lines of 4; u_z rows of 32
+    ((32, 32, 16), (8, 8, 8)),      # FP32 position lines of 32 and 16 through staged tiles
 ]
 
 
@@ -108,7 +117,7 @@ def test_sweep_adjoint(n, nu, axis, dtype):
     v.sweep_adjoint(f_in, lam, axis, dt, a, torch.from_numpy(phi).to(dev), dLdg)
     v.status()
     fp64 = dtype == np.float64
-    _compare(lam.cpu().numpy(), lam_ref, fp64, "axis %d lambda" % axis)
+    _compare(lam.cpu().numpy(), lam_ref, fp64, "axis %d lambda" % axis, axis=axis)
     if axis >= 3:
         _compare_field(dLdg.cpu().numpy(), dLdg_ref, fp64, "axis %d dL/dg" % axis)
     assert torch.equal(f_in.cpu(), torch.from_numpy(f0))  # the sweep input is read only
@@ -171,7 +180,7 @@ def test_sweep_adjoint_rough_velocity_lines(n, nu, axis, dtype):
     v.sweep_adjoint(torch.from_numpy(f0).to(dev), lam, axis, dt, 1.0, torch.from_numpy(phi).to(dev), dLdg)
     v.status()
     fp64 = dtype == np.float64
-    _compare(lam.cpu().numpy(), lam_ref, fp64, "rough axis %d lambda" % axis)
+    _compare(lam.cpu().numpy(), lam_ref, fp64, "rough axis %d lambda" % axis, axis=axis)
     _compare_field(dLdg.cpu().numpy(), dLdg_ref, fp64, "rough axis %d dL/dg" % axis)
     v.close()
 
@@ -192,7 +201,7 @@ def test_sweep_adjoint_whole_cell_shift(axis, dtype):
     v = B.Vlasov(torch.zeros_like(f_in), V=5.0)
     v.sweep_adjoint(f_in, lam, axis, dt, 1.0)
     v.status()
-    _compare(lam.cpu().numpy(), lam_ref, dtype == np.float64, "axis %d shift lambda" % axis)
+    _compare(lam.cpu().numpy(), lam_ref, dtype == np.float64, "axis %d shift lambda" % axis, axis=axis)
     v.close()
 
 
