@@ -889,8 +889,8 @@ def run_profile_case(args):
     cmax = courant_per_dt(phi_np, n, nu, V)
     rho = torch.empty(n, dtype=torch.float64, device=dev)
     if args.step:
-        # one Eq. (5) step: the kicks run D_ux and the fused D_uy D_uz pass
-        v = B.Vlasov(f, V=V)
+        # one Eq. (5) step: the one-pass kicks and the three drift sweeps
+        v = B.Vlasov(f, V=V, scale=scale)
         dt = 0.7 / max(max(cmax[:3]), 0.5 * max(cmax[3:]))
         for _ in range(2):
             v.step(dt, 1.0, 1.0, phi, rho_nu=rho)  # the x sweep sums the moment
