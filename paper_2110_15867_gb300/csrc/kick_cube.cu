@@ -49,7 +49,9 @@ template <int NU, typename T> struct Cube {
     static constexpr int pitch = NU + 1;            // FP32 plane buffer: floats per row
     static constexpr int plane_floats = NU * pitch; // NU = 16: the two planes of a warp fall on complementary banks
     static constexpr unsigned plane_bytes = coded ? unsigned(warps * planes_per_warp * plane_floats) * 4u : 0u;
-    static constexpr size_t smem = 128 + 1024 + 3 * size_t(half_bytes) + 3 * size_t(scale_bytes) + plane_bytes;
+    // 16-bit: per warp, the inverse scales of the rows its D_ux lines cross (32)
+    static constexpr unsigned inv_bytes = coded ? unsigned(warps) * 32u * 4u : 0u;
+    static constexpr size_t smem = 128 + 1024 + 3 * size_t(half_bytes) + 3 * size_t(scale_bytes) + plane_bytes + inv_bytes;
     // swizzled byte offset of 16-byte chunk j of row r / of element c of row r
     __device__ static int off(int r, int j) { return r * rowbytes + 16 * (j ^ ((r * rowbytes >> 7) & (chunks - 1))); }
     __device__ static int eoff(int r, int c) { return off(r, c / per) + (c % per) * es; }
@@ -59,8 +61,8 @@ template <int NU, typename T> struct Cube {
 // index of the line's first element in f (16-bit stochastic-rounding stream).
 // Returns true when the line sum is negative, NaN or infinite.
 template <int NU, typename T, bool NEG>
-__device__ __forceinline__ bool cube_ux(unsigned char *const (&h)[2], const float *const (&s)[2], int jy, int jz,
-                                        const Lim<float> &lim, unsigned long long e0, unsigned seed)
+__device__ __forceinline__ bool cube_ux(unsigned char *const (&h)[2], const float *const (&s)[2], const float *inv_jx,
+                                        int jy, int jz, const Lim<float> &lim, unsigned long long e0, unsigned seed)
 {
     using G = Cube<NU, T>;
     constexpr int HP = NU / 2; // planes per half
@@ -79,7 +81,7 @@ __device__ __forceinline__ bool cube_ux(unsigned char *const (&h)[2], const floa
         float inv = 1.f;
         unsigned rb = 0u;
         if (G::coded) {
-            inv = inv_scale(s[jx / HP][r]); // u_x keeps the scales
+            inv = inv_jx[jx]; // u_x keeps the scales
             rb = lcg_next(rng) >> 16;
         }
         *reinterpret_cast<T *>(h[jx / HP] + G::eoff(r, jz)) = RegCodec<T>::put(v[NEG ? NU - 1 - jx : jx], inv, rb);
@@ -171,6 +173,8 @@ __global__ void __launch_bounds__(Cube<NU, T>::threads + kProducer, NU == 32 ? 1
         return reinterpret_cast<float *>(bufs + 3 * size_t(G::half_bytes) + size_t(G::scale_bytes) * (j % 3));
     };
     float *planes = reinterpret_cast<float *>(bufs + 3 * size_t(G::half_bytes) + 3 * size_t(G::scale_bytes));
+    float *invs = reinterpret_cast<float *>(bufs + 3 * size_t(G::half_bytes) + 3 * size_t(G::scale_bytes) +
+                                            G::plane_bytes); // 16-bit: 32 per warp
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < 3; ++q) {
@@ -251,8 +255,18 @@ __global__ void __launch_bounds__(Cube<NU, T>::threads + kProducer, NU == 32 ? 1
             for (int q = 0; q < 2; ++q) {
                 const int line = q * NT + t, jy = line / NU, jz = line % NU;
                 const unsigned long long e0 = e_cube + (unsigned long long)line;
-                bad |= (kx.nd & 1) ? cube_ux<NU, T, true>(h, sc, jy, jz, lim, e0, a.seed_x)
-                                   : cube_ux<NU, T, false>(h, sc, jy, jz, lim, e0, a.seed_x);
+                // 16-bit: the warp's lines cross NU rows per j_y (32 / NU values of j_y): each
+                // lane forms the inverse scale of one of them once, for the whole warp
+                float *wi = invs + w * 32;
+                if constexpr (G::coded) {
+                    __syncwarp();
+                    const int jy_l = (q * NT + w * 32) / NU + lane / NU, jx = lane % NU;
+                    wi[lane] = inv_scale(sc[jx / (NU / 2)][(jx % (NU / 2)) * NU + jy_l]);
+                    __syncwarp();
+                }
+                const float *inv_jx = wi + (lane / NU) * NU;
+                bad |= (kx.nd & 1) ? cube_ux<NU, T, true>(h, sc, inv_jx, jy, jz, lim, e0, a.seed_x)
+                                   : cube_ux<NU, T, false>(h, sc, inv_jx, jy, jz, lim, e0, a.seed_x);
             }
         }
         // every D_ux line crosses every plane: all of them finish before D_uy

@@ -291,13 +291,21 @@ template <int L> constexpr int tile16_slots()
                ? (196608 / tile16_slot<L>() > 12 ? 12 : int(196608 / tile16_slot<L>()))
                : tile_groups<L>() + 1;
 }
-template <int L> constexpr size_t tile16_smem() { return kTileHeader + 1024 + size_t(tile16_slots<L>()) * tile16_slot<L>(); }
+// after the ring: per consumer warp, the inverse scales of the (up to two) u_z lines its
+// columns belong to, one per row, formed once per tile instead of once per value
+template <int L> constexpr size_t tile16_inv_bytes() { return size_t(tile_groups<L>()) * 8 * 2 * L * sizeof(float); }
+template <int L> constexpr size_t tile16_smem()
+{
+    return kTileHeader + 1024 + size_t(tile16_slots<L>()) * tile16_slot<L>() + tile16_inv_bytes<L>();
+}
 
 template <int L, int DIR, typename T>
-__device__ __forceinline__ float march_tile16(T *p, const float *sp, int st_rt, const Lim<float> &lim, unsigned rng)
+__device__ __forceinline__ float march_tile16(T *p, const float *sp, const float *ip, int st_rt, const Lim<float> &lim,
+                                              unsigned rng)
 {
     const int st = DIR == 0 ? st_rt : DIR * 256; // rows are 256 codes apart
     const int ss = DIR == 0 ? (st_rt > 0 ? 8 : -8) : DIR * 8; // and 8 scales
+    const int is = DIR == 0 ? (st_rt > 0 ? 1 : -1) : DIR;     // and 1 inverse scale
     auto get = [&](int i) { return RegCodec<T>::get(p[i * st], sp[i * ss]); };
     const float a = get(L - 3), b = get(L - 2), c = get(L - 1);
     const float s0 = get(0), s1 = get(1);
@@ -310,7 +318,7 @@ __device__ __forceinline__ float march_tile16(T *p, const float *sp, int st_rt, 
         const float dm4p = dm4(dcur, dn);
         const float F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
         const float out = c0 + (Fm - F);
-        p[i * st] = RegCodec<T>::put(out, inv_scale(sp[i * ss]), lcg_next(rng) >> 16);
+        p[i * st] = RegCodec<T>::put(out, ip[i * is], lcg_next(rng) >> 16);
         sum += out;
         cm2 = cm1;
         cm1 = c0;
@@ -342,6 +350,8 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     unsigned char *ring = smem + kTileHeader + ((1024u - ((smem_u32(smem) + unsigned(kTileHeader)) & 1023u)) & 1023u);
     auto slot = [&](unsigned k) { return reinterpret_cast<T *>(ring + size_t(SB) * (k % S)); };
     auto sslot = [&](unsigned k) { return reinterpret_cast<float *>(ring + size_t(SB) * (k % S) + CB); };
+    float *winv = reinterpret_cast<float *>(ring + size_t(SB) * S);
+    static_assert(tile16_smem<L>() <= 227 * 1024, "the tiles and inverse scales fit shared memory");
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
@@ -411,6 +421,10 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         unit = w;
         e = lane;
     }
+    // this warp's inverse scales: [h][row] for its units u_first + h (two under zperm)
+    float *wi = winv + (grp * 8 + w) * 2 * L;
+    const int u_first = a.zperm ? ((w & 3) << 1) : w, nunits = a.zperm ? 2 : 1;
+    const float *ip_col = wi + (unit - u_first) * L;
     bool bad = false;
     for (unsigned k = grp; k < n_my; k += NG) {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[k % S], (k / S) & 1u))) {
@@ -423,6 +437,12 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
         T *p = slot(k) + unit * 32 + e;
         const float *sp = sslot(k) + unit;
+        __syncwarp(); // every lane is done with the previous tile's inverses
+        for (int idx = lane; idx < nunits * L; idx += 32) {
+            const int h = idx / L, r = idx - h * L;
+            wi[idx] = inv_scale(sslot(k)[r * 8 + u_first + h]);
+        }
+        __syncwarp();
         if (kc.nd >= 0) {
             const Lim<float> lim = to_lim(kc);
             const bool neg = kc.nd & 1;
@@ -430,10 +450,11 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
             const unsigned rng = sr_bits((unsigned long long)((long long)o * L * a.n_inner + inner), a.seed);
             float sum;
             if constexpr (!SIGNED)
-                sum = march_tile16<L, 0, T>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * 8 : sp, neg ? -256 : 256,
-                                            lim, rng);
-            else if (neg) sum = march_tile16<L, -1, T>(p + (L - 1) * 256, sp + (L - 1) * 8, 0, lim, rng);
-            else sum = march_tile16<L, 1, T>(p, sp, 0, lim, rng);
+                sum = march_tile16<L, 0, T>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * 8 : sp,
+                                            neg ? ip_col + (L - 1) : ip_col, neg ? -256 : 256, lim, rng);
+            else if (neg)
+                sum = march_tile16<L, -1, T>(p + (L - 1) * 256, sp + (L - 1) * 8, ip_col + (L - 1), 0, lim, rng);
+            else sum = march_tile16<L, 1, T>(p, sp, ip_col, 0, lim, rng);
             bad |= !(sum >= 0.f) || isinf(sum);
         }
         fence_proxy_async();
