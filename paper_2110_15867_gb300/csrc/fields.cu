@@ -315,8 +315,8 @@ template <> struct Vec16<__nv_bfloat16> {
         const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            o[2 * q] = __uint_as_float(w[q] << 16) * sc;
-            o[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u) * sc;
+            o[2 * q] = __fmul_rn(__uint_as_float(w[q] << 16), sc);
+            o[2 * q + 1] = __fmul_rn(__uint_as_float(w[q] & 0xffff0000u), sc);
         }
     }
 };
@@ -328,8 +328,8 @@ template <> struct Vec16<__half> {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
-            o[2 * q] = h.x * sc;
-            o[2 * q + 1] = h.y * sc;
+            o[2 * q] = __fmul_rn(h.x, sc);
+            o[2 * q + 1] = __fmul_rn(h.y, sc);
         }
     }
 };

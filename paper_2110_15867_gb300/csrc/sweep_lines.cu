@@ -80,7 +80,7 @@ __device__ __forceinline__ bool plane_column1_coded(const unsigned char *base, u
     for (int i = 0; i < NU; ++i) {
         const float s = __shfl_sync(0xffffffffu, s_own, j0 + i);
         const T code = *reinterpret_cast<const T *>(base + GT::off(r_first + i, c / GT::per) + (c % GT::per) * 2);
-        v[NEG ? NU - 1 - i : i] = float(code) * s;
+        v[NEG ? NU - 1 - i : i] = __fmul_rn(float(code), s);
     }
     const float sum = march_regs<NU, float>(v, lim);
 #pragma unroll

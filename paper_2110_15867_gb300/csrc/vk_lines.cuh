@@ -29,8 +29,8 @@ template <> struct Chunk<__nv_bfloat16> {
         const unsigned w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            o[2 * q] = __uint_as_float(w[q] << 16) * s;
-            o[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u) * s;
+            o[2 * q] = __fmul_rn(__uint_as_float(w[q] << 16), s);
+            o[2 * q + 1] = __fmul_rn(__uint_as_float(w[q] & 0xffff0000u), s);
         }
     }
     // rng: stochastic-rounding stream of the line
@@ -50,8 +50,8 @@ template <> struct Chunk<__half> {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
-            o[2 * q] = f.x * s;
-            o[2 * q + 1] = f.y * s;
+            o[2 * q] = __fmul_rn(f.x, s);
+            o[2 * q + 1] = __fmul_rn(f.y, s);
         }
     }
     __device__ static void put(unsigned char *p, float inv, const float (&o)[8], unsigned &rng)
@@ -115,14 +115,18 @@ __device__ __forceinline__ X march_regs(X (&v)[NU], const Lim<X> &lim)
 
 
 // A single value of a line (strided access): decode with the scale of its u_z line,
-// encode with one stochastic-rounding draw (16 random bits; v >= 0).
+// encode with one stochastic-rounding draw (16 random bits; v >= 0).  Every decode is
+// a rounded product (__fmul_rn): a plain product may be contracted into the first sum
+// that uses it, depending on the code around it, and the kernels that share a
+// rounding point (the one-pass kick, the fused tail, the separate sweeps) must agree
+// bit for bit.
 template <typename T> struct RegCodec;
 template <> struct RegCodec<float> {
     __device__ static float get(float c, float) { return c; }
     __device__ static float put(float v, float, unsigned) { return v; }
 };
 template <> struct RegCodec<__nv_bfloat16> {
-    __device__ static float get(__nv_bfloat16 c, float s) { return __bfloat162float(c) * s; }
+    __device__ static float get(__nv_bfloat16 c, float s) { return __fmul_rn(__bfloat162float(c), s); }
     __device__ static __nv_bfloat16 put(float v, float inv, unsigned r16)
     {
         const unsigned b = (__float_as_uint(v * inv) + r16) >> 16; // stochastic rounding (v >= 0)
@@ -130,7 +134,7 @@ template <> struct RegCodec<__nv_bfloat16> {
     }
 };
 template <> struct RegCodec<__half> {
-    __device__ static float get(__half c, float s) { return __half2float(c) * s; }
+    __device__ static float get(__half c, float s) { return __fmul_rn(__half2float(c), s); }
     __device__ static __half put(float v, float inv, unsigned r16)
     {
         return __float2half_rz(__uint_as_float(__float_as_uint(v * inv) + (r16 & 0x1fffu)));
