@@ -16,11 +16,12 @@
 // is its sign of nu.  In the x and y sweeps it is the same for whole tiles; when
 // every tile a CTA takes has one sign, or the tiles can be taken sign by sign (all
 // tiles of u < 0 first, in runs long enough to keep DRAM pages whole), an SM runs
-// one unrolled march with a fixed direction at a time.  Otherwise, and in the z
-// sweep (n_uz = 32), where the sign flips in the middle of every u_z line, the march
-// takes its direction at run time (one body: two unrolled copies running side by
-// side would not fit the instruction cache); there warps take the 16 columns of one
-// sign of two u_z lines four units apart (no bank conflicts under the swizzle).  For the x sweep the group's
+// one unrolled march with a fixed direction at a time.  In the z sweep (n_uz = 32),
+// where the sign flips in the middle of every u_z line, warps take the 16 columns of
+// one sign of two u_z lines four units apart (no bank conflicts under the swizzle) and
+// each warp marches with a fixed direction: both bodies run side by side on an SM,
+// which fits the instruction cache once lines of more than 32 cells march in blocks of
+// 8 faces.  Otherwise the march takes its direction at run time.  For the x sweep the group's
 // warps also add up every marched tile's rows into per-cell partials of rho_nu (the
 // moment of Eq. 5 is taken right after this sweep), in the order of the streamed
 // sweep's moment warp.
@@ -67,8 +68,8 @@ template <int L> constexpr size_t tile_smem() { return kTileHeader + 1024 + size
 // March the periodic line p[0], p[st], ..., p[(L - 1) st] (flow toward +index) in place;
 // st < 0 walks a line with a negative Courant number from its far end.  DIR = +1 / -1 fixes
 // the stride at compile time; DIR = 0 takes it at run time, one body for both
-// orientations: in the z sweep both run side by side on every SM, and two unrolled copies
-// would not fit the instruction cache.  Returns the sum of the new values.
+// orientations (for tiles whose CTAs meet both signs of u and cannot take them sign by
+// sign).  Returns the sum of the new values.
 // Faces marched per loop iteration: lines up to 32 cells unroll completely; longer lines
 // in blocks of 8 faces, so that the code of a march stays inside the instruction cache.
 template <int L> constexpr int march_unroll() { return L <= 32 ? L : 8; }

@@ -839,6 +839,9 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
                 A.sort_half = half;
             }
         }
+        // z sweep: each warp's columns have one sign of u_z, so the march takes a fixed
+        // direction per warp (both bodies, marched in blocks of 8 faces, fit the cache)
+        if (A.zperm) A.tile_sign = 1;
         A.err = c->d_err;
         A.seed = c->sweeps;
         for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
