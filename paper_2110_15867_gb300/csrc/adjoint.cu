@@ -562,7 +562,10 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
     __shared__ double s_sum[kAdjBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (part) {
-        const double s = warp_sum_d((double)dnu);
+        // FP32 storage: the lines' values are FP32; the warp sums them in FP32 (FP64 adds
+        // run at a small fraction of the FP32 rate on this part), the block and the cell
+        // in FP64, in a fixed order
+        const double s = sizeof(C) == 4 ? (double)warp_sum<C>(dnu) : warp_sum_d((double)dnu);
         if (lane == 0) s_sum[warp] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
