@@ -13,15 +13,13 @@
 // other sweep).  Groups of 256 threads work on different tiles; a ring of at
 // least groups + 1 tile slots (up to 192 KB), filled and drained by one producer
 // thread, keeps the next tiles loading while the groups march theirs.  The orientation of a line
-// is its sign of nu.  In the x and y sweeps it is the same for whole tiles; when
-// every tile a CTA takes has one sign, or the tiles can be taken sign by sign (all
-// tiles of u < 0 first, in runs long enough to keep DRAM pages whole), an SM runs
-// one unrolled march with a fixed direction at a time.  In the z sweep (n_uz = 32),
-// where the sign flips in the middle of every u_z line, warps take the 16 columns of
-// one sign of two u_z lines four units apart (no bank conflicts under the swizzle) and
-// each warp marches with a fixed direction: both bodies run side by side on an SM,
-// which fits the instruction cache once lines of more than 32 cells march in blocks of
-// 8 faces.  Otherwise the march takes its direction at run time.  For the x sweep the group's
+// is its sign of nu.  In the x and y sweeps it is the same for whole tiles, which
+// march with a fixed direction; in the z sweep (n_uz = 32), where the sign flips in
+// the middle of every u_z line, warps take the 16 columns of one sign of two u_z
+// lines four units apart (no bank conflicts under the swizzle) and each warp marches
+// with a fixed direction.  Both bodies run side by side on an SM, which fits the
+// instruction cache once lines of more than 32 cells march in blocks of 8 faces.
+// Tiles that mix signs take the direction per column at run time.  For the x sweep the group's
 // warps also add up every marched tile's rows into per-cell partials of rho_nu (the
 // moment of Eq. 5 is taken right after this sweep), in the order of the streamed
 // sweep's moment warp.
@@ -133,7 +131,7 @@ __device__ __forceinline__ float rows4_sum(float v0, float v1, float v2, float v
     return k;
 }
 
-// SIGNED: every tile has one sign of u (TileArgs::tile_sign), marched with a fixed direction
+// SIGNED: every warp's columns have one sign of u (TileArgs::tile_sign), marched with a fixed direction
 template <int L, bool MOMENT, bool SIGNED>
 __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     tile_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
@@ -164,15 +162,7 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     const long long G = gridDim.x, b = blockIdx.x;
     const unsigned n_my = unsigned(a.num_tiles > b ? (a.num_tiles - b + G - 1) / G : 0);
     auto coords = [&](unsigned k, int &u0, int &o) {
-        long long m = b + (long long)k * G, t;
-        if (a.sort_half > 0) {
-            // the tiles of u < 0 first, then those of u > 0: runs of sort_half tiles alternate
-            // in sign, and a CTA then meets one orientation at a time
-            const long long half = a.num_tiles / 2, pos = m >= half ? 1 : 0, mm = m - pos * half;
-            t = a.tile0 + (mm / a.sort_half) * 2 * a.sort_half + pos * a.sort_half + mm % a.sort_half;
-        } else {
-            t = a.tile0 + m;
-        }
+        const long long t = a.tile0 + b + (long long)k * G;
         const long long oq = t / a.tiles_inner;
         u0 = int((t - oq * a.tiles_inner) * 8); // first 32-column unit of the tile
         o = int(oq);
@@ -367,13 +357,7 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     const long long G = gridDim.x, b = blockIdx.x;
     const unsigned n_my = unsigned(a.num_tiles > b ? (a.num_tiles - b + G - 1) / G : 0);
     auto coords = [&](unsigned k, int &u0, int &o) {
-        long long m = b + (long long)k * G, t;
-        if (a.sort_half > 0) {
-            const long long half = a.num_tiles / 2, pos = m >= half ? 1 : 0, mm = m - pos * half;
-            t = a.tile0 + (mm / a.sort_half) * 2 * a.sort_half + pos * a.sort_half + mm % a.sort_half;
-        } else {
-            t = a.tile0 + m;
-        }
+        const long long t = a.tile0 + b + (long long)k * G;
         const long long oq = t / a.tiles_inner;
         u0 = int((t - oq * a.tiles_inner) * 8);
         o = int(oq);

@@ -230,8 +230,6 @@ struct TileArgs {
     long long vstride;                       // column j takes table[(inner / vstride) % nvel]
     int nvel;
     int zperm;                               // z sweep with n_uz = 32: warps grouped by the sign of u_z
-    long long sort_half;                     // > 0: runs of sort_half tiles alternate in the sign of u
-                                             // (num_tiles a multiple of 2 sort_half): taken sign by sign
     int tile_sign;                           // 1: every column of a tile has one sign of u (else per column)
     unsigned seed;                           // 16-bit storage: the stochastic-rounding streams of this sweep
     unsigned *err;

@@ -823,25 +823,15 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
         A.vstride = vstride;
         A.nvel = nvel;
         A.zperm = ax == 2 && c->g.nuz == 32;
-        // tiles of one sign of u come in runs of vstride nvel / 2 columns when that is a whole
-        // number of tiles (u_j < 0 exactly for j < nvel / 2)
+        // Tiles have one sign of u when its runs (vstride nvel / 2 columns: u_j < 0 exactly for
+        // j < nvel / 2) are whole tiles; the march then takes a fixed direction per tile (D_x,
+        // D_y: every thread of a tile the same), as it does per warp in the z sweep, whose
+        // warps hold the columns of one sign of u_z.  Both unrolled bodies run side by side on
+        // an SM (lines of more than 32 cells march in blocks of 8 faces, which fit the
+        // instruction cache).  Otherwise the direction is taken per column at run time.
         const long long run = vstride * nvel / 2;
         const int grid = int(A.num_tiles < c->tgrid[ax] ? A.num_tiles : c->tgrid[ax]);
-        A.sort_half = 0;
-        A.tile_sign = 0;
-        if (!A.zperm && nvel % 2 == 0 && run % 256 == 0 && A.tiles_inner % (2 * (run / 256)) == 0 &&
-            A.num_tiles % (2 * (run / 256)) == 0) {
-            const long long half = run / 256; // tiles of one sign in a row
-            if (grid % (2 * half) == 0 || A.num_tiles <= grid) {
-                A.tile_sign = 1; // every CTA meets one sign only
-            } else if (half >= 16) {
-                A.tile_sign = 1; // runs of 16 KB or more per row: take the tiles sign by sign
-                A.sort_half = half;
-            }
-        }
-        // z sweep: each warp's columns have one sign of u_z, so the march takes a fixed
-        // direction per warp (both bodies, marched in blocks of 8 faces, fit the cache)
-        if (A.zperm) A.tile_sign = 1;
+        A.tile_sign = A.zperm || (nvel % 2 == 0 && run % 256 == 0);
         A.err = c->d_err;
         A.seed = c->sweeps;
         for (int j = 0; j < nvel; ++j) A.table[j] = make_line_coef<float>((-c->g.V + (j + 0.5) * du) * dt / (a * a * dx));
