@@ -131,6 +131,7 @@ struct vlasov_ctx {
     MapSpec lspec;
     // kick tail D_uz D_uy fused in the u_z line kernel (n_uy = n_uz)
     bool can_fuse_kick;
+    bool can_plane_tail; // the kick tail over staged (cell, j_x) planes (FP32, n_uy = n_uz = 48)
     int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
     // position sweeps with whole lines staged per tile (see vlasov_set_position_tiles)
     bool tile_ok[3], use_tiles;
@@ -502,6 +503,8 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
         if (occ <= 0) return fail(c, VLASOV_ECUDA, "fused kick CTA does not fit");
         c->lgrid_fused = int(c->ltiles < (long long)occ * c->sm_count ? c->ltiles : (long long)occ * c->sm_count);
     }
+    c->can_plane_tail = !c->can_fuse_kick && (mask >> 4 & 1) && (mask >> 5 & 1) &&
+                        plane_tail_supported(c->g.nuy, c->g.nuz, c->g.nux, c->g.dtype);
     return VLASOV_OK;
 }
 
@@ -1129,6 +1132,29 @@ static int run_kick_tail(vlasov_ctx *c)
 }
 
 // D_uz D_uy D_ux in one pass over each cell's velocity cube (constants in d_coef)
+// D_uz D_uy (constants in d_coef[1], d_coef[2]) in one pass over staged planes
+static int run_plane_tail(vlasov_ctx *c)
+{
+    c->sweeps += 2;
+    PlaneTailArgs A{};
+    A.nux = c->g.nux;
+    A.plane0 = 0;
+    A.nplanes = c->ncell * c->g.nux;
+    if (c->slab_x1 > c->slab_x0) {
+        const long long cpp = c->ncell / c->g.nx; // spatial cells per x-plane
+        A.plane0 = c->slab_x0 * cpp * c->g.nux;
+        A.nplanes = (c->slab_x1 - c->slab_x0) * cpp * c->g.nux;
+    }
+    A.coef_y = (const LineCoefT<float> *)c->d_coef[1];
+    A.coef_z = (const LineCoefT<float> *)c->d_coef[2];
+    A.err = c->d_err;
+    if (A.nplanes <= 0) return VLASOV_OK;
+    PartTimer t(c, VLASOV_T_SWEEP_UYUZ, 1);
+    const cudaError_t e = launch_plane_tail(static_cast<float *>(c->f), A, c->g.nuz, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kick tail launch");
+    return VLASOV_OK;
+}
+
 static int run_kick_cube(vlasov_ctx *c)
 {
     KickArgs A{};
@@ -1161,6 +1187,7 @@ static int run_kick(vlasov_ctx *c)
     if (c->can_kick_cube && c->fuse_kick >= 2) return run_kick_cube(c);
     if ((rc = run_velocity(c, 3))) return rc;
     if (c->can_fuse_kick && c->fuse_kick >= 1) return run_kick_tail(c);
+    if (c->can_plane_tail && c->fuse_kick >= 1) return run_plane_tail(c);
     if ((rc = run_velocity(c, 4))) return rc;
     return run_velocity(c, 5);
 }

@@ -1,6 +1,7 @@
 """The fused kicks against the separate sweeps.  Mode 2 runs the whole kick D_uz D_uy D_ux
 in one pass over each velocity cube (n_ux = n_uy = n_uz = 16 or 32), mode 1 runs D_ux and
-then D_uy D_uz in one pass of the u_z line kernel, mode 0 three separate sweeps.  The
+then D_uy D_uz in one pass (of the u_z line kernel for n_uz = 16, 32; over staged (cell,
+j_x) planes for n_uy = n_uz = 48, FP32), mode 0 three separate sweeps.  The
 arithmetic of every line is the same, so whole FP32 steps must agree bit for bit, with both
 orientations of the Courant number present (the potential's gradient changes sign across
 the box), for n_u = 16 and 32 and a velocity grid the one-pass kick does not take.  16-bit
@@ -25,7 +26,7 @@ def _lib():
 
 
 @pytest.mark.parametrize("n,nu", [((8, 8, 8), (16, 16, 16)), ((4, 6, 4), (32, 32, 32)), ((6, 4, 4), (8, 32, 32)),
-                                  ((5, 4, 7), (32, 32, 32))])
+                                  ((5, 4, 7), (32, 32, 32)), ((4, 5, 4), (48, 48, 48)), ((4, 4, 4), (8, 48, 48))])
 def test_fused_kicks_are_bitwise_the_separate_sweeps(n, nu):
     B = _lib()
     V = 5.0
@@ -50,8 +51,8 @@ def test_fused_kicks_are_bitwise_the_separate_sweeps(n, nu):
         v.close()
     assert np.array_equal(out[2][0], out[0][0])
     assert np.array_equal(out[1][0], out[0][0])
-    cube = nu[0] == nu[1] == nu[2]
-    tail = nu[1] == nu[2]
+    cube = nu[0] == nu[1] == nu[2] and nu[2] in (16, 32)  # the one-pass kick
+    tail = nu[1] == nu[2]  # the fused tail: u_z lines of a TMA tile (16, 32) or staged planes (48)
     print("one-pass kick launches:", out[2][1]["kick"], "fused tail launches:", out[1][1]["sweep_uyuz"])
     assert out[2][1]["kick"] == (6 if cube else 0)
     if cube:
