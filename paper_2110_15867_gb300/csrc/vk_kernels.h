@@ -244,7 +244,7 @@ struct TileArgs {
     long long vstride;                       // column j takes table[(inner / vstride) % nvel]
     int nvel;
     int zperm;                               // z sweep with n_uz = 32: warps grouped by the sign of u_z
-    int tile_sign;                           // 1: every column of a tile has one sign of u (else per column)
+    int tile_sign;                           // 1: every warp's columns have one sign of u (else per column)
     unsigned seed;                           // 16-bit storage: the stochastic-rounding streams of this sweep
     unsigned *err;
     // x sweep with the moment: per-cell partial sums as in StreamArgs (null: no moment)
