@@ -430,7 +430,18 @@ cudaError_t launch_moments(const GridDims &g, const void *f, const float *scale,
 {
     const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
     const long long need = (ncell + 7) / 8; // 8 warps (cells) per block
-    const long long blocks = need < (long long)sm_count * 8 ? need : (long long)sm_count * 8;
+    // one wave of resident blocks: each warp strides over the cells, so a second, partial
+    // wave would leave most of the SMs idle for its whole length
+    const void *kern = dtype == 0 ? (const void *)moments_kernel<double>
+                       : dtype == 1 ? (const void *)moments_kernel<float>
+                       : dtype == 2 ? (const void *)moments_kernel<__nv_bfloat16>
+                                    : (const void *)moments_kernel<__half>;
+    int per_sm = 0;
+    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (oe != cudaSuccess) return oe;
+    if (per_sm < 1) per_sm = 1;
+    const long long wave = (long long)sm_count * per_sm;
+    const long long blocks = need < wave ? need : wave;
     switch (dtype) {
     case 0: moments_kernel<double><<<int(blocks), 256, 0, st>>>(g, (const double *)f, nullptr, rho, umean, sigma2); break;
     case 1: moments_kernel<float><<<int(blocks), 256, 0, st>>>(g, (const float *)f, nullptr, rho, umean, sigma2); break;
