@@ -2,8 +2,9 @@
 second stream behind the cell-local sweeps) against upload + vlasov_step + download: the
 same kernels on the same tiles, so the same f, rho and phi^{n+1} bit for bit, for a
 self-consistent step (Poisson between the kicks) with the one-pass kick, the fused kick
-tail and the separate sweeps, the fused moment on and off, on 16 and on 8 slabs of one x-plane, and for a step that falls back to
-the three calls in sequence (a whole-cell shift in D_y / D_z)."""
+tail (on u_z line tiles, or on staged planes for 48^3 velocity cubes) and the separate
+sweeps, the fused moment on and off, on 16 and on 8 slabs of one x-plane, and for a step
+that falls back to the three calls in sequence (a whole-cell shift in D_y / D_z)."""
 import numpy as np
 import pytest
 
@@ -48,7 +49,7 @@ def _run(B, f0, phi0, bg, dt, a_half, host, fused):
 
 
 @pytest.mark.parametrize("n,nu,a_half", [((16, 8, 8), (16, 16, 16), 0.55), ((8, 4, 4), (32, 32, 32), 0.55),
-                                         ((16, 8, 8), (16, 16, 16), 0.12)])
+                                         ((16, 8, 8), (16, 16, 16), 0.12), ((8, 4, 4), (48, 48, 48), 0.55)])
 @pytest.mark.parametrize("fused", [2, 1, 0])
 def test_step_host_is_upload_step_download(n, nu, a_half, fused):
     B = _lib()
