@@ -8,8 +8,9 @@
 // different banks), 48 threads per plane march its columns (D_uy), then its rows
 // (D_uz), and the block writes the planes back: f is read and written once for the
 // two sweeps instead of twice.  Each line is marched in shared memory through a
-// window of five cells in registers (march_strided), the arithmetic of march_regs in
-// the same order, so the result equals the separate u_y and u_z sweeps bit for bit.
+// window of five cells in registers (march_strided, one body for both sweeps, faces in
+// blocks of 8), the arithmetic of march_regs in the same order, so the result equals the
+// separate u_y and u_z sweeps bit for bit.
 // The stride of a line (its axis and the sign of its Courant number) is a run-time
 // value: one march body for both axes and signs (four compile-time bodies measured
 // slower: 43.9 against 41.0 ms on the 48^3 x 48^3 run).
@@ -34,7 +35,8 @@ template <int NU> __device__ __forceinline__ float march_strided(float *p, int s
     float db = curv(0.f, c0, cp1);  // curvature of cell 0
     float dm4m = dm4(c0, db);       // face -1/2: the ghost cell -1 has curvature 0 - 0 + c_0
     float Fprev = 0.f, sum = 0.f;
-#pragma unroll
+    // blocks of 8 faces: a fully unrolled 48-face body per sweep missed in the instruction cache
+#pragma unroll 8
     for (int i = 0; i < NU; ++i) {
         float F = 0.f, dm4p = 0.f, dc = 0.f;
         if (i + 1 < NU) {
@@ -80,22 +82,20 @@ __global__ void __launch_bounds__(kPlanesPerBlock * NU) plane_tail_kernel(float 
     const int q = threadIdx.x / NU, l = threadIdx.x - q * NU;
     float *plane = plane_s + q * NU * P;
     bool bad = false;
-    const LineCoefT<float> ky = a.coef_y[cell];
-    if (p0 + q < pend && ky.nd >= 0) {
-        // D_uy: column l, rows 0 .. NU-1 (from the far end when the Courant number is negative)
-        const bool neg = ky.nd & 1;
-        const float sum = march_strided<NU>(plane + (neg ? (NU - 1) * P : 0) + l, neg ? -P : P, to_lim(ky));
-        bad |= !(sum >= 0.f) || isinf(sum);
+    // D_uy (column l, rows 0 .. NU-1), then D_uz (row l): one march body for both
+#pragma unroll 1
+    for (int ax = 0; ax < 2; ++ax) {
+        const LineCoefT<float> k = ax == 0 ? a.coef_y[cell] : a.coef_z[cell];
+        if (p0 + q < pend && k.nd >= 0) {
+            // from the far end when the Courant number is negative
+            const bool neg = k.nd & 1;
+            const int step = ax == 0 ? P : 1;
+            float *first = plane + (ax == 0 ? l : l * P) + (neg ? (NU - 1) * step : 0);
+            const float sum = march_strided<NU>(first, neg ? -step : step, to_lim(k));
+            bad |= !(sum >= 0.f) || isinf(sum);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    const LineCoefT<float> kz = a.coef_z[cell];
-    if (p0 + q < pend && kz.nd >= 0) {
-        // D_uz: row l
-        const bool neg = kz.nd & 1;
-        const float sum = march_strided<NU>(plane + l * P + (neg ? NU - 1 : 0), neg ? -1 : 1, to_lim(kz));
-        bad |= !(sum >= 0.f) || isinf(sum);
-    }
-    __syncthreads();
     for (int k = threadIdx.x; k < kPlanesPerBlock * Q; k += blockDim.x) {
         const int qq = k / Q, e = 4 * (k - qq * Q), row = e / NU, col = e - row * NU;
         if (p0 + qq < pend) {
