@@ -274,28 +274,35 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
 // stochastic rounding (one stream per column and sweep, one draw per value in march
 // order).  z sweep: warp w takes the columns of one sign of units 2 (w % 4) and
 // 2 (w % 4) + 1 (adjacent 64-byte units fall on disjoint banks).
+// n_uz = 48: a tile's 256 columns fall on 6 or 7 u_z lines, starting anywhere in one; its
+// scale box starts at the line index rounded down to a multiple of 4 (the 16-byte rule of
+// TMA) and spans 12 lines.  n_uz = 32: the 8 lines of the tile exactly.
+template <int NZ> constexpr int tile16_scale_lines() { return NZ == 32 ? 8 : 12; }
 template <int L> constexpr unsigned tile16_codes() { return unsigned(L) * 512u; }
-template <int L> constexpr unsigned tile16_slot() { return (tile16_codes<L>() + unsigned(L) * 32u + 127u) & ~127u; }
-template <int L> constexpr int tile16_slots()
+template <int L, int NZ = 32> constexpr unsigned tile16_slot()
 {
-    return (196608 / tile16_slot<L>() > 12 ? 12 : int(196608 / tile16_slot<L>())) > tile_groups<L>() + 1
-               ? (196608 / tile16_slot<L>() > 12 ? 12 : int(196608 / tile16_slot<L>()))
+    return (tile16_codes<L>() + unsigned(L) * 4u * unsigned(tile16_scale_lines<NZ>()) + 127u) & ~127u;
+}
+template <int L, int NZ = 32> constexpr int tile16_slots()
+{
+    return (196608 / tile16_slot<L, NZ>() > 12 ? 12 : int(196608 / tile16_slot<L, NZ>())) > tile_groups<L>() + 1
+               ? (196608 / tile16_slot<L, NZ>() > 12 ? 12 : int(196608 / tile16_slot<L, NZ>()))
                : tile_groups<L>() + 1;
 }
 // after the ring: per consumer warp, the inverse scales of the (up to two) u_z lines its
 // columns belong to, one per row, formed once per tile instead of once per value
 template <int L> constexpr size_t tile16_inv_bytes() { return size_t(tile_groups<L>()) * 8 * 2 * L * sizeof(float); }
-template <int L> constexpr size_t tile16_smem()
+template <int L, int NZ = 32> constexpr size_t tile16_smem()
 {
-    return kTileHeader + 1024 + size_t(tile16_slots<L>()) * tile16_slot<L>() + tile16_inv_bytes<L>();
+    return kTileHeader + 1024 + size_t(tile16_slots<L, NZ>()) * tile16_slot<L, NZ>() + tile16_inv_bytes<L>();
 }
 
-template <int L, int DIR, typename T>
+template <int L, int DIR, typename T, int SX = 8>
 __device__ __forceinline__ float march_tile16(T *p, const float *sp, const float *ip, int st_rt, const Lim<float> &lim,
                                               unsigned rng)
 {
-    const int st = DIR == 0 ? st_rt : DIR * 256; // rows are 256 codes apart
-    const int ss = DIR == 0 ? (st_rt > 0 ? 8 : -8) : DIR * 8; // and 8 scales
+    const int st = DIR == 0 ? st_rt : DIR * 256;                // rows are 256 codes apart
+    const int ss = DIR == 0 ? (st_rt > 0 ? SX : -SX) : DIR * SX; // and SX scales
     const int is = DIR == 0 ? (st_rt > 0 ? 1 : -1) : DIR;     // and 1 inverse scale
     auto get = [&](int i) { return RegCodec<T>::get(p[i * st], sp[i * ss]); };
     const float a = get(L - 3), b = get(L - 2), c = get(L - 1);
@@ -326,13 +333,13 @@ __device__ __forceinline__ float march_tile16(T *p, const float *sp, const float
     return sum;
 }
 
-template <int L, typename T, bool SIGNED>
+template <int L, typename T, bool SIGNED, int NZ = 32>
 __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     tile_sweep16_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ TileArgs a)
 {
-    constexpr int NG = tile_groups<L>(), S = tile16_slots<L>(), NT = NG * 256;
-    constexpr unsigned CB = tile16_codes<L>(), SB = tile16_slot<L>();
+    constexpr int NG = tile_groups<L>(), S = tile16_slots<L, NZ>(), NT = NG * 256, SX = tile16_scale_lines<NZ>();
+    constexpr unsigned CB = tile16_codes<L>(), SB = tile16_slot<L, NZ>();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *done = full + S;
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     auto slot = [&](unsigned k) { return reinterpret_cast<T *>(ring + size_t(SB) * (k % S)); };
     auto sslot = [&](unsigned k) { return reinterpret_cast<float *>(ring + size_t(SB) * (k % S) + CB); };
     float *winv = reinterpret_cast<float *>(ring + size_t(SB) * S);
-    static_assert(tile16_smem<L>() <= 227 * 1024, "the tiles and inverse scales fit shared memory");
+    static_assert(tile16_smem<L, NZ>() <= 227 * 1024, "the tiles and inverse scales fit shared memory");
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
@@ -362,15 +369,17 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         u0 = int((t - oq * a.tiles_inner) * 8);
         o = int(oq);
     };
+    // first u_z line of the tile's scale box (n_uz = 32: its first line exactly)
+    auto line0 = [&](int u0) { return NZ == 32 ? u0 : int(32ll * u0 / NZ / 4 * 4); };
 
     if (threadIdx.x >= NT) {
         if (threadIdx.x != NT) return;
         auto load = [&](unsigned k) {
             int u0, o;
             coords(k, u0, o);
-            mbar_arrive_expect_tx(&full[k % S], CB + unsigned(L) * 32u);
+            mbar_arrive_expect_tx(&full[k % S], CB + unsigned(L) * 4u * unsigned(SX));
             tma_load_4d(slot(k), &map, &full[k % S], 0, u0, 0, o);
-            tma_load_3d(sslot(k), &smap, &full[k % S], u0, 0, o);
+            tma_load_3d(sslot(k), &smap, &full[k % S], line0(u0), 0, o);
         };
         unsigned loaded = 0;
         for (; loaded < unsigned(S) && loaded < n_my; ++loaded) load(loaded);
@@ -406,10 +415,8 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         unit = w;
         e = lane;
     }
-    // this warp's inverse scales: [h][row] for its units u_first + h (two under zperm)
+    // this warp's inverse scales: [h][row] for the (up to two) u_z lines of its columns
     float *wi = winv + (grp * 8 + w) * 2 * L;
-    const int u_first = a.zperm ? ((w & 3) << 1) : w, nunits = a.zperm ? 2 : 1;
-    const float *ip_col = wi + (unit - u_first) * L;
     bool bad = false;
     for (unsigned k = grp; k < n_my; k += NG) {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[k % S], (k / S) & 1u))) {
@@ -421,11 +428,26 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         const long long inner = 32ll * (u0 + unit) + e;
         const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
         T *p = slot(k) + unit * 32 + e;
-        const float *sp = sslot(k) + unit;
+        // the scale box column of this thread's u_z line, the warp's first such column and
+        // how many the warp spans (n_uz = 32: units are lines, two under zperm)
+        int col, first, nlines;
+        if constexpr (NZ == 32) {
+            col = unit;
+            first = a.zperm ? ((w & 3) << 1) : w;
+            nlines = a.zperm ? 2 : 1;
+        } else {
+            // (no zperm: the warp's 32 columns are contiguous, on one or two lines)
+            const long long x0 = line0(u0), c0 = 32ll * (u0 + w);
+            col = int(inner / NZ - x0);
+            first = int(c0 / NZ - x0);
+            nlines = int((c0 + 31) / NZ - c0 / NZ) + 1;
+        }
+        const float *sp = sslot(k) + col;
+        const float *ip_col = wi + (col - first) * L;
         __syncwarp(); // every lane is done with the previous tile's inverses
-        for (int idx = lane; idx < nunits * L; idx += 32) {
+        for (int idx = lane; idx < nlines * L; idx += 32) {
             const int h = idx / L, r = idx - h * L;
-            wi[idx] = inv_scale(sslot(k)[r * 8 + u_first + h]);
+            wi[idx] = inv_scale(sslot(k)[r * SX + first + h]);
         }
         __syncwarp();
         if (kc.nd >= 0) {
@@ -435,11 +457,11 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
             const unsigned rng = sr_bits((unsigned long long)((long long)o * L * a.n_inner + inner), a.seed);
             float sum;
             if constexpr (!SIGNED)
-                sum = march_tile16<L, 0, T>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * 8 : sp,
-                                            neg ? ip_col + (L - 1) : ip_col, neg ? -256 : 256, lim, rng);
+                sum = march_tile16<L, 0, T, SX>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * SX : sp,
+                                                neg ? ip_col + (L - 1) : ip_col, neg ? -256 : 256, lim, rng);
             else if (neg)
-                sum = march_tile16<L, -1, T>(p + (L - 1) * 256, sp + (L - 1) * 8, ip_col + (L - 1), 0, lim, rng);
-            else sum = march_tile16<L, 1, T>(p, sp, ip_col, 0, lim, rng);
+                sum = march_tile16<L, -1, T, SX>(p + (L - 1) * 256, sp + (L - 1) * SX, ip_col + (L - 1), 0, lim, rng);
+            else sum = march_tile16<L, 1, T, SX>(p, sp, ip_col, 0, lim, rng);
             bad |= !(sum >= 0.f) || isinf(sum);
         }
         fence_proxy_async();
@@ -448,13 +470,15 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     if (bad) atomicOr(a.err, ERR_NAN);
 }
 
-template <int L, typename T> const void *tile16_kernel(bool sign)
+template <int L, typename T, int NZ = 32> const void *tile16_kernel(bool sign)
 {
-    return sign ? (const void *)tile_sweep16_kernel<L, T, true> : (const void *)tile_sweep16_kernel<L, T, false>;
+    return sign ? (const void *)tile_sweep16_kernel<L, T, true, NZ> : (const void *)tile_sweep16_kernel<L, T, false, NZ>;
 }
 
-template <typename T> const void *tile16_kernel_for(int L, bool sign)
+template <typename T> const void *tile16_kernel_for(int L, bool sign, int nuz)
 {
+    if (nuz == 48) return L == 48 ? tile16_kernel<48, T, 48>(sign) : nullptr;
+    if (nuz != 32) return nullptr;
     switch (L) {
     case 16: return tile16_kernel<16, T>(sign);
     case 24: return tile16_kernel<24, T>(sign);
@@ -466,8 +490,9 @@ template <typename T> const void *tile16_kernel_for(int L, bool sign)
     }
 }
 
-size_t tile16_smem_for(int L)
+size_t tile16_smem_for(int L, int nuz)
 {
+    if (nuz == 48) return tile16_smem<48, 48>();
     switch (L) {
     case 16: return tile16_smem<16>();
     case 24: return tile16_smem<24>();
@@ -509,10 +534,10 @@ size_t tile_smem_for(int L)
 
 int tile_threads_for(int L, bool) { return (L <= 48 ? 3 : 2) * 256 + kProducer; }
 
-const void *tile_kernel_any(int L, int dtype, bool moment, bool sign)
+const void *tile_kernel_any(int L, int dtype, bool moment, bool sign, int nuz)
 {
-    if (dtype == 2) return moment ? nullptr : tile16_kernel_for<__nv_bfloat16>(L, sign);
-    if (dtype == 3) return moment ? nullptr : tile16_kernel_for<__half>(L, sign);
+    if (dtype == 2) return moment ? nullptr : tile16_kernel_for<__nv_bfloat16>(L, sign, nuz);
+    if (dtype == 3) return moment ? nullptr : tile16_kernel_for<__half>(L, sign, nuz);
     return tile_kernel_for(L, moment, sign);
 }
 
@@ -520,15 +545,15 @@ const void *tile_kernel_any(int L, int dtype, bool moment, bool sign)
 
 bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz)
 {
-    if (n_inner % 256 != 0 || !tile_kernel_any(L, dtype, false, true)) return false;
-    return dtype == 1 || ((dtype == 2 || dtype == 3) && nuz == 32);
+    if (n_inner % 256 != 0 || !tile_kernel_any(L, dtype, false, true, nuz)) return false;
+    return dtype == 1 || ((dtype == 2 || dtype == 3) && n_inner % nuz == 0);
 }
 
-int occupancy_tile_sweep(int L, int dtype, bool moment)
+int occupancy_tile_sweep(int L, int dtype, bool moment, int nuz)
 {
-    const void *k = tile_kernel_any(L, dtype, moment, true);
+    const void *k = tile_kernel_any(L, dtype, moment, true, nuz);
     if (!k) return 0;
-    const size_t smem = dtype == 1 ? tile_smem_for(L) : tile16_smem_for(L);
+    const size_t smem = dtype == 1 ? tile_smem_for(L) : tile16_smem_for(L, nuz);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tile_threads_for(L, moment), smem) != cudaSuccess) return 0;
@@ -540,10 +565,11 @@ cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
 {
     if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
     const bool moment = a.mpart != nullptr;
-    const void *k = tile_kernel_any(a.L, dtype, moment, a.tile_sign != 0);
+    const void *k = tile_kernel_any(a.L, dtype, moment, a.tile_sign != 0, a.nuz);
     if (!k || a.nvel <= 0 || a.nvel > kMaxVel || a.vstride <= 0 || a.tiles_inner <= 0) return cudaErrorInvalidValue;
     if (moment && (dtype != 1 || a.cube % 256 || a.nparts <= 0)) return cudaErrorInvalidValue;
-    const size_t smem = dtype == 1 ? tile_smem_for(a.L) : tile16_smem_for(a.L);
+    if (dtype != 1 && (a.zperm && a.nuz != 32)) return cudaErrorInvalidValue;
+    const size_t smem = dtype == 1 ? tile_smem_for(a.L) : tile16_smem_for(a.L, a.nuz);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // FP32: (map, dmap, args); 16-bit: in place (map, smap, args)

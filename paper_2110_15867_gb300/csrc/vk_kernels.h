@@ -243,6 +243,7 @@ struct TileArgs {
     long long tile0, num_tiles;              // tiles [tile0, tile0 + num_tiles), t = outer tiles_inner + block
     long long vstride;                       // column j takes table[(inner / vstride) % nvel]
     int nvel;
+    int nuz;                                 // 16-bit storage: n_uz (32 or 48), the length of a scale's line
     int zperm;                               // z sweep with n_uz = 32: warps grouped by the sign of u_z
     int tile_sign;                           // 1: every warp's columns have one sign of u (else per column)
     unsigned seed;                           // 16-bit storage: the stochastic-rounding streams of this sweep
@@ -253,12 +254,13 @@ struct TileArgs {
     int nparts;
     LineCoefT<float> table[kMaxVel];
 };
-// dtype 1 (FP32), 2 (BF16), 3 (FP16; n_uz = 32, one scale per 32-code unit, L up to 96)
+// dtype 1 (FP32), 2 (BF16), 3 (FP16; n_uz = 32 with L up to 96, or n_uz = 48 with L = 48;
+// one scale per u_z line)
 bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz);
-int occupancy_tile_sweep(int L, int dtype, bool moment);
+int occupancy_tile_sweep(int L, int dtype, bool moment, int nuz);
 // FP32: tiles loaded through map and stored through dmap (the same map in place).  16-bit:
 // in place through map (codes, box {32, 8, L, 1}, no swizzle) with the scales through smap
-// ([n_outer][L][n_inner / 32] floats, box {8, L, 1})
+// ([n_outer][L][n_inner / n_uz] floats, box {8, L, 1} for n_uz = 32, {12, L, 1} for 48)
 cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, const CUtensorMap &smap,
                               const TileArgs &a, int dtype, int grid, cudaStream_t st);
 

@@ -448,22 +448,25 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
             continue;
         c->tspec[ax] = spec_tiles(I, d6[ax], O);
         if (coded) {
-            // codes: 512-byte rows of 32-code units, no swizzle; scales: one per 32-code unit
+            // codes: 512-byte rows of 32-code units, no swizzle; scales: one per u_z line, a
+            // tile's 8 lines (n_uz = 32) or the 12 from its first line rounded down to a
+            // multiple of 4 (n_uz = 48: the 6 or 7 lines of its 256 columns)
+            const long long nl = I / c->g.nuz;
             c->tspec[ax].type = tmap_type(c->g.dtype);
             c->tspec[ax].gstr[0] = 64; c->tspec[ax].gstr[1] = (cuuint64_t)(I * 2); c->tspec[ax].gstr[2] = (cuuint64_t)(I * d6[ax] * 2);
             c->tspec[ax].swz = CU_TENSOR_MAP_SWIZZLE_NONE;
             MapSpec ss{};
             ss.type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
             ss.rank = 3;
-            ss.gdim[0] = (cuuint64_t)(I / 32); ss.gdim[1] = (cuuint64_t)d6[ax]; ss.gdim[2] = (cuuint64_t)O;
-            ss.gstr[0] = (cuuint64_t)(I / 32 * 4); ss.gstr[1] = (cuuint64_t)(I / 32 * d6[ax] * 4);
-            ss.box[0] = 8; ss.box[1] = (cuuint32_t)d6[ax]; ss.box[2] = 1;
+            ss.gdim[0] = (cuuint64_t)nl; ss.gdim[1] = (cuuint64_t)d6[ax]; ss.gdim[2] = (cuuint64_t)O;
+            ss.gstr[0] = (cuuint64_t)(nl * 4); ss.gstr[1] = (cuuint64_t)(nl * d6[ax] * 4);
+            ss.box[0] = c->g.nuz == 32 ? 8 : 12; ss.box[1] = (cuuint32_t)d6[ax]; ss.box[2] = 1;
             ss.swz = CU_TENSOR_MAP_SWIZZLE_NONE;
             ss.promo = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
             if (encode_spec(&c->tsmap[ax], ss, c->scale) != CUDA_SUCCESS) continue;
         }
         if (encode_spec(&c->tmap[ax], c->tspec[ax], c->f) != CUDA_SUCCESS) continue;
-        const int occ = occupancy_tile_sweep(int(d6[ax]), c->g.dtype, ax == 0 && !coded);
+        const int occ = occupancy_tile_sweep(int(d6[ax]), c->g.dtype, ax == 0 && !coded, int(c->g.nuz));
         if (occ <= 0) continue;
         c->ttiles_inner[ax] = I / 256;
         c->tn_outer[ax] = O;
@@ -825,6 +828,7 @@ static int run_position(vlasov_ctx *c, int ax, double dt, double a, const void *
         }
         A.vstride = vstride;
         A.nvel = nvel;
+        A.nuz = int(c->g.nuz);
         A.zperm = ax == 2 && c->g.nuz == 32;
         // Tiles have one sign of u when its runs (vstride nvel / 2 columns: u_j < 0 exactly for
         // j < nvel / 2) are whole tiles; the march then takes a fixed direction per tile (D_x,

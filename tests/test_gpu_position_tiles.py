@@ -112,3 +112,39 @@ def test_16bit_tile_sweeps_against_the_oracle(fmt):
             print("%s axis %d %s: rel L1 %.2e, rel Linf %.2e" % (fmt, ax, "tiles" if tiles else "streamed", rl1, rinf))
             assert rl1 <= bound + 1e-6 and rinf <= 1.5 * (2 * bound + 1e-6)
             assert torch.equal(scale, scale0)  # a position sweep keeps the line scales
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_tile_sweeps_with_48_cell_lines(fmt):
+    # n_uz = 48: a tile's 256 columns fall on 6 or 7 u_z lines, starting inside one, so each
+    # column finds its own line's scale in a box of 12 read from the line index rounded down
+    # to a multiple of 4; a warp's 32 columns span one or two lines.  One 48-cell position
+    # axis at a time (the staged tiles take L = 48), against the FP64 oracle with the codec
+    # bound, tiles and streamed sweep alike.
+    B = _lib()
+    V = 5.0
+    bound = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[fmt]
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[fmt]
+    nu = (8, 8, 48)
+    for ax in range(3):
+        n = tuple(48 if k == ax else 4 for k in range(3))
+        f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=9 + ax), I.fermi_dirac(nu, V), np.float64)
+        g = O.grid(n, nu, V=V)
+        codes0, scale0 = B.encode_lines(torch.from_numpy(f0).cuda(), tdt)
+        dt = 0.8 / O.max_abs_nu(g, ax, 1.0, 0.9)
+        ref = B.decode_lines(codes0, scale0).cpu().numpy()
+        O.sweep(g, ref, ax, dt, 0.9)
+        for tiles in (True, False):
+            codes, scale = codes0.clone(), scale0.clone()
+            v = B.Vlasov(codes, V=V, scale=scale)
+            v.set_position_tiles(tiles)
+            v.sweep(ax, dt, 0.9)
+            v.status()
+            out = B.decode_lines(codes, scale).cpu().numpy()
+            v.close()
+            err = np.abs(out - ref)
+            rl1 = err.sum() / np.abs(ref).sum()
+            rinf = err.max() / np.abs(ref).max()
+            print("%s n_uz 48 axis %d %s: rel L1 %.2e, rel Linf %.2e" % (fmt, ax, "tiles" if tiles else "streamed", rl1, rinf))
+            assert rl1 <= bound + 1e-6 and rinf <= 1.5 * (2 * bound + 1e-6)
+            assert torch.equal(scale, scale0)
