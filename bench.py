@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-lowprec", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-large", action="store_true")

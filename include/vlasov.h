@@ -163,13 +163,17 @@ int vlasov_set_fused_kick(vlasov_ctx *ctx, int mode);
 int vlasov_kick(vlasov_ctx *ctx, double dt, const float *phi_dev);
 
 /*
- * Position sweeps (Eq. 3, |nu| < 1) on FP32 storage with lines of 16, 24, 32, 48
- * or 64 cells and a multiple of 256 cells on the faster axes run with whole
+ * Staged tiles.  Position sweeps (Eq. 3, |nu| < 1) with lines of 16, 24, 32, 48 or
+ * 64 cells (FP32) or of 16-96 cells with n_uz = 32 and of 48 cells with n_uz = 48
+ * (BF16 / FP16), and a multiple of 256 cells on the faster axes, run with whole
  * lines staged in shared memory: each tile of 256 lines x all their cells is
- * loaded once, every line is marched in registers by one thread and the tile is
- * stored once (the same arithmetic as the streamed sweep, bit for bit).  On by
- * default; on = 0 runs the streamed sweep (chunks of rows moving down the line),
- * which FP64 and 16-bit storage and other shapes always use.
+ * loaded once, every line is marched by one thread and the tile is stored once.
+ * The u_x sweep (Eq. 4) with n_ux = 48 (FP32; 16-bit with n_uz = 48) and n_uy n_uz
+ * a multiple of 256 runs on the same tiles of [cell][u_x][u_y u_z] when the kick
+ * does not take the one-pass kernel.  FP32 results equal the streamed and
+ * register-line sweeps bit for bit; 16-bit results draw their own rounding
+ * streams.  On by default; on = 0 runs the streamed / register-line sweeps, which
+ * FP64 storage and other shapes always use.
  */
 int vlasov_set_position_tiles(vlasov_ctx *ctx, int on);
 

@@ -25,40 +25,6 @@ constexpr int kPlanesPerBlock = 4;
 template <int NU> constexpr int plane_pitch() { return NU + 1; }
 template <int NU> constexpr size_t plane_smem() { return size_t(kPlanesPerBlock) * NU * plane_pitch<NU>() * sizeof(float); }
 
-// The zero-flux line p[0], p[st], ..., p[(NU - 1) st] (forward local frame) advanced in
-// place: march_regs with the line read a window ahead and each cell written at its own
-// face (never read again).  Returns the sum of the new values.
-template <int NU> __device__ __forceinline__ float march_strided(float *p, int st, const Lim<float> &lim)
-{
-    static_assert(NU >= 4, "lines of at least 4 cells");
-    float cm2 = 0.f, cm1 = 0.f, c0 = p[0], cp1 = p[st], cp2 = p[2 * st];
-    float db = curv(0.f, c0, cp1);  // curvature of cell 0
-    float dm4m = dm4(c0, db);       // face -1/2: the ghost cell -1 has curvature 0 - 0 + c_0
-    float Fprev = 0.f, sum = 0.f;
-    // blocks of 8 faces: a fully unrolled 48-face body per sweep missed in the instruction cache
-#pragma unroll 8
-    for (int i = 0; i < NU; ++i) {
-        float F = 0.f, dm4p = 0.f, dc = 0.f;
-        if (i + 1 < NU) {
-            dc = curv(c0, cp1, cp2); // curvature of cell i + 1
-            dm4p = dm4(db, dc);
-            F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
-        }
-        const float out = vadd(c0, vsub(Fprev, F));
-        p[i * st] = out;
-        sum = vadd(sum, out);
-        Fprev = F;
-        dm4m = dm4p;
-        db = dc;
-        cm2 = cm1;
-        cm1 = c0;
-        c0 = cp1;
-        cp1 = cp2;
-        cp2 = i + 3 < NU ? p[(i + 3) * st] : 0.f;
-    }
-    return sum;
-}
-
 template <int NU>
 __global__ void __launch_bounds__(kPlanesPerBlock * NU) plane_tail_kernel(float *__restrict__ f, const __grid_constant__ PlaneTailArgs a)
 {

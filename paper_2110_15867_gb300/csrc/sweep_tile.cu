@@ -23,6 +23,9 @@
 // warps also add up every marched tile's rows into per-cell partials of rho_nu (the
 // moment of Eq. 5 is taken right after this sweep), in the order of the streamed
 // sweep's moment warp.
+// The same tiles serve the u_x sweep of Eq. (4) (ZF): f viewed as [cell][u_x][u_y u_z],
+// zero-flux lines, one Courant number per tile (the cell's), marched through a window of
+// five cells (march_strided, the arithmetic of the other velocity sweeps).
 #include "vk_lines.cuh"
 
 namespace vk {
@@ -131,8 +134,9 @@ __device__ __forceinline__ float rows4_sum(float v0, float v1, float v2, float v
     return k;
 }
 
-// SIGNED: every warp's columns have one sign of u (TileArgs::tile_sign), marched with a fixed direction
-template <int L, bool MOMENT, bool SIGNED>
+// SIGNED: every warp's columns have one sign of u (TileArgs::tile_sign), marched with a fixed direction.
+// ZF: a u_x sweep (zero-flux lines, the tile's cell's coefficients)
+template <int L, bool MOMENT, bool SIGNED, bool ZF = false>
 __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     tile_sweep_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
                       const __grid_constant__ TileArgs a)
@@ -225,14 +229,15 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         int u0, o;
         coords(k, u0, o);
         const long long inner = 32ll * (u0 + unit) + e;
-        const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
+        const LineCoefT<float> kc = ZF ? a.cell_coef[o] : tab[(inner / a.vstride) % a.nvel];
         float *p = slot(k) + coff;
         if (kc.nd >= 0) {
             const Lim<float> lim = to_lim(kc);
             // a negative Courant number is the mirror image: march the line from its far end
             const bool neg = kc.nd & 1;
             float sum;
-            if constexpr (!SIGNED) sum = march_tile<L, 0>(neg ? p + (L - 1) * 256 : p, neg ? -256 : 256, lim);
+            if constexpr (ZF) sum = march_strided<L>(neg ? p + (L - 1) * 256 : p, neg ? -256 : 256, lim);
+            else if constexpr (!SIGNED) sum = march_tile<L, 0>(neg ? p + (L - 1) * 256 : p, neg ? -256 : 256, lim);
             else if (neg) sum = march_tile<L, -1>(p + (L - 1) * 256, 0, lim); // one sign per tile
             else sum = march_tile<L, 1>(p, 0, lim);
             bad |= !(sum >= 0.f) || isinf(sum);
@@ -333,7 +338,44 @@ __device__ __forceinline__ float march_tile16(T *p, const float *sp, const float
     return sum;
 }
 
-template <int L, typename T, bool SIGNED, int NZ = 32>
+// march_strided on codes: a value is decoded (the scale of its row) as it enters the
+// window and a new value encoded (the inverse scale of its row, one stochastic-rounding
+// draw per cell in walk order) at its own face.  st, ss, is: the strides between rows of
+// codes, scales and inverse scales (negative for a line walked from its far end).
+template <int L, typename T>
+__device__ __forceinline__ float march_tile16_zf(T *p, int st, const float *sp, int ss, const float *ip, int is,
+                                                 const Lim<float> &lim, unsigned rng)
+{
+    static_assert(L >= 4, "lines of at least 4 cells");
+    auto get = [&](int i) { return RegCodec<T>::get(p[i * st], sp[i * ss]); };
+    float cm2 = 0.f, cm1 = 0.f, c0 = get(0), cp1 = get(1), cp2 = get(2);
+    float db = curv(0.f, c0, cp1); // curvature of cell 0
+    float dm4m = dm4(c0, db);      // face -1/2: the ghost cell -1 has curvature 0 - 0 + c_0
+    float Fprev = 0.f, sum = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < L; ++i) {
+        float F = 0.f, dm4p = 0.f, dc = 0.f;
+        if (i + 1 < L) {
+            dc = curv(c0, cp1, cp2); // curvature of cell i + 1
+            dm4p = dm4(db, dc);
+            F = sl_mpp5_flux(lim, cm2, cm1, c0, cp1, cp2, dm4m, dm4p);
+        }
+        const float out = vadd(c0, vsub(Fprev, F));
+        p[i * st] = RegCodec<T>::put(out, ip[i * is], lcg_next(rng) >> 16);
+        sum = vadd(sum, out);
+        Fprev = F;
+        dm4m = dm4p;
+        db = dc;
+        cm2 = cm1;
+        cm1 = c0;
+        c0 = cp1;
+        cp1 = cp2;
+        cp2 = i + 3 < L ? get(i + 3) : 0.f;
+    }
+    return sum;
+}
+
+template <int L, typename T, bool SIGNED, int NZ = 32, bool ZF = false>
 __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
     tile_sweep16_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
                         const __grid_constant__ TileArgs a)
@@ -426,7 +468,7 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
         int u0, o;
         coords(k, u0, o);
         const long long inner = 32ll * (u0 + unit) + e;
-        const LineCoefT<float> kc = tab[(inner / a.vstride) % a.nvel];
+        const LineCoefT<float> kc = ZF ? a.cell_coef[o] : tab[(inner / a.vstride) % a.nvel];
         T *p = slot(k) + unit * 32 + e;
         // the scale box column of this thread's u_z line, the warp's first such column and
         // how many the warp spans (n_uz = 32: units are lines, two under zperm)
@@ -456,7 +498,10 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
             // the column's stream, from the index of its first cell
             const unsigned rng = sr_bits((unsigned long long)((long long)o * L * a.n_inner + inner), a.seed);
             float sum;
-            if constexpr (!SIGNED)
+            if constexpr (ZF)
+                sum = march_tile16_zf<L, T>(neg ? p + (L - 1) * 256 : p, neg ? -256 : 256, neg ? sp + (L - 1) * SX : sp,
+                                            neg ? -SX : SX, neg ? ip_col + (L - 1) : ip_col, neg ? -1 : 1, lim, rng);
+            else if constexpr (!SIGNED)
                 sum = march_tile16<L, 0, T, SX>(neg ? p + (L - 1) * 256 : p, neg ? sp + (L - 1) * SX : sp,
                                                 neg ? ip_col + (L - 1) : ip_col, neg ? -256 : 256, lim, rng);
             else if (neg)
@@ -534,6 +579,17 @@ size_t tile_smem_for(int L)
 
 int tile_threads_for(int L, bool) { return (L <= 48 ? 3 : 2) * 256 + kProducer; }
 
+// u_x sweeps (zero-flux lines, one direction per tile): lines of 48 cells
+const void *tile_kernel_zf(int L, int dtype, int nuz)
+{
+    if (L != 48) return nullptr;
+    if (dtype == 1) return (const void *)tile_sweep_kernel<48, false, true, true>;
+    if (nuz != 48) return nullptr;
+    if (dtype == 2) return (const void *)tile_sweep16_kernel<48, __nv_bfloat16, true, 48, true>;
+    if (dtype == 3) return (const void *)tile_sweep16_kernel<48, __half, true, 48, true>;
+    return nullptr;
+}
+
 const void *tile_kernel_any(int L, int dtype, bool moment, bool sign, int nuz)
 {
     if (dtype == 2) return moment ? nullptr : tile16_kernel_for<__nv_bfloat16>(L, sign, nuz);
@@ -547,6 +603,11 @@ bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz)
 {
     if (n_inner % 256 != 0 || !tile_kernel_any(L, dtype, false, true, nuz)) return false;
     return dtype == 1 || ((dtype == 2 || dtype == 3) && n_inner % nuz == 0);
+}
+
+bool tile_sweep_zf_supported(int L, long long n_inner, int dtype, int nuz)
+{
+    return n_inner % 256 == 0 && n_inner % nuz == 0 && tile_kernel_zf(L, dtype, nuz) != nullptr;
 }
 
 int occupancy_tile_sweep(int L, int dtype, bool moment, int nuz)
@@ -564,9 +625,10 @@ cudaError_t launch_tile_sweep(const CUtensorMap &map, const CUtensorMap &dmap, c
                               const TileArgs &a, int dtype, int grid, cudaStream_t st)
 {
     if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
-    const bool moment = a.mpart != nullptr;
-    const void *k = tile_kernel_any(a.L, dtype, moment, a.tile_sign != 0, a.nuz);
-    if (!k || a.nvel <= 0 || a.nvel > kMaxVel || a.vstride <= 0 || a.tiles_inner <= 0) return cudaErrorInvalidValue;
+    const bool moment = a.mpart != nullptr, zf = a.cell_coef != nullptr;
+    const void *k = zf ? tile_kernel_zf(a.L, dtype, a.nuz) : tile_kernel_any(a.L, dtype, moment, a.tile_sign != 0, a.nuz);
+    if (!k || (!zf && (a.nvel <= 0 || a.vstride <= 0)) || a.nvel > kMaxVel || a.tiles_inner <= 0 || (zf && moment))
+        return cudaErrorInvalidValue;
     if (moment && (dtype != 1 || a.cube % 256 || a.nparts <= 0)) return cudaErrorInvalidValue;
     if (dtype != 1 && (a.zperm && a.nuz != 32)) return cudaErrorInvalidValue;
     const size_t smem = dtype == 1 ? tile_smem_for(a.L) : tile16_smem_for(a.L, a.nuz);

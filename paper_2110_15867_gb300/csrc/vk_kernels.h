@@ -248,6 +248,9 @@ struct TileArgs {
     int tile_sign;                           // 1: every warp's columns have one sign of u (else per column)
     unsigned seed;                           // 16-bit storage: the stochastic-rounding streams of this sweep
     unsigned *err;
+    // u_x sweep (zero-flux lines): the Courant numbers per outer index (a cell); null for
+    // the position sweeps, which take table[] per column
+    const LineCoefT<float> *cell_coef;
     // x sweep with the moment: per-cell partial sums as in StreamArgs (null: no moment)
     void *mpart;
     long long cube;
@@ -257,6 +260,8 @@ struct TileArgs {
 // dtype 1 (FP32), 2 (BF16), 3 (FP16; n_uz = 32 with L up to 96, or n_uz = 48 with L = 48;
 // one scale per u_z line)
 bool tile_sweep_supported(int L, long long n_inner, int dtype, int nuz);
+// the u_x sweep on the same tiles ([cell][u_x][u_y u_z]): lines of 48 cells (16-bit: n_uz = 48)
+bool tile_sweep_zf_supported(int L, long long n_inner, int dtype, int nuz);
 int occupancy_tile_sweep(int L, int dtype, bool moment, int nuz);
 // FP32: tiles loaded through map and stored through dmap (the same map in place).  16-bit:
 // in place through map (codes, box {32, 8, L, 1}, no swizzle) with the scales through smap

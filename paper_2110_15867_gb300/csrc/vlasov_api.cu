@@ -134,11 +134,12 @@ struct vlasov_ctx {
     bool can_plane_tail; // the kick tail over staged (cell, j_x) planes (FP32, n_uy = n_uz = 48)
     int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
     // position sweeps with whole lines staged per tile (see vlasov_set_position_tiles)
-    bool tile_ok[3], use_tiles;
-    CUtensorMap tmap[3], tsmap[3]; // tsmap: 16-bit storage, the scales of a tile
-    MapSpec tspec[3];
-    int tgrid[3];
-    long long ttiles_inner[3], tn_outer[3];
+    // staged tiles of the x, y, z sweeps and (index 3) of the u_x sweep
+    bool tile_ok[4], use_tiles;
+    CUtensorMap tmap[4], tsmap[4]; // tsmap: 16-bit storage, the scales of a tile
+    MapSpec tspec[4];
+    int tgrid[4];
+    long long ttiles_inner[4], tn_outer[4];
     // the whole kick D_uz D_uy D_ux in one pass (n_ux = n_uy = n_uz = 16 or 32)
     bool can_kick_cube;
     CUtensorMap kmap, ksmap;
@@ -437,15 +438,17 @@ static int plan_axes(vlasov_ctx *c, int mask = 0x3f)
         const long long rpp = c->lrows / c->g.nx; // u_z rows per x-plane
         c->ltpp = rpp % rpt == 0 ? rpp / rpt : 0;
     }
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int ax = 0; ax < 4; ++ax) {
         c->tile_ok[ax] = false;
         if (!(mask >> ax & 1) || c->g.dtype == VLASOV_F64) continue;
         long long I = 1, O = 1;
         for (int k = ax + 1; k < 6; ++k) I *= d6[k];
         for (int k = 0; k < ax; ++k) O *= d6[k];
-        if (!tile_sweep_supported(int(d6[ax]), I, c->g.dtype, int(c->g.nuz)) || O > 0x7fffffffll ||
-            I / 32 > 0x7fffffffll)
-            continue;
+        // u_x: [cell][u_x][u_y u_z], zero-flux lines of 48 (lines of 16 and 32 take the
+        // one-pass kick or the register lines)
+        const bool ok = ax == 3 ? tile_sweep_zf_supported(int(d6[ax]), I, c->g.dtype, int(c->g.nuz))
+                                : tile_sweep_supported(int(d6[ax]), I, c->g.dtype, int(c->g.nuz));
+        if (!ok || O > 0x7fffffffll || I / 32 > 0x7fffffffll) continue;
         c->tspec[ax] = spec_tiles(I, d6[ax], O);
         if (coded) {
             // codes: 512-byte rows of 32-code units, no swizzle; scales: one per u_z line, a
@@ -948,6 +951,41 @@ static bool use_reg_lines(const vlasov_ctx *c, int ax)
     return reg_lines_supported(L);
 }
 
+// the u_x sweep on staged tiles of [cell][u_x][u_y u_z] (zero-flux lines; each tile's
+// columns take the coefficients of its cell)
+static int run_tile_ux(vlasov_ctx *c, const void *src, void *dst)
+{
+    TileArgs A{};
+    A.L = int(c->g.nux);
+    A.n_inner = c->ttiles_inner[3] * 256;
+    A.n_outer = c->tn_outer[3];
+    A.tiles_inner = c->ttiles_inner[3];
+    A.tile0 = 0;
+    A.num_tiles = A.n_outer * A.tiles_inner;
+    if (c->slab_x1 > c->slab_x0) {
+        const long long tpp = A.num_tiles / c->g.nx; // tiles per x-plane
+        A.tile0 = c->slab_x0 * tpp;
+        A.num_tiles = (c->slab_x1 - c->slab_x0) * tpp;
+    }
+    if (A.num_tiles <= 0) return VLASOV_OK;
+    A.vstride = 1;
+    A.nvel = 0;
+    A.nuz = int(c->g.nuz);
+    A.tile_sign = 1;
+    A.err = c->d_err;
+    A.seed = c->sweeps;
+    A.cell_coef = (const LineCoefT<float> *)c->d_coef[0];
+    SweepMaps m;
+    int rc;
+    if (coded(c)) m.in = m.out = c->tmap[3]; // in place (checked by the caller)
+    else if ((rc = sweep_maps(c, c->tmap[3], c->tspec[3], src, dst, m))) return rc;
+    const int grid = int(A.num_tiles < c->tgrid[3] ? A.num_tiles : c->tgrid[3]);
+    PartTimer t(c, 3, 1);
+    const cudaError_t e = launch_tile_sweep(m.in, m.out, c->tsmap[3], A, c->g.dtype, grid, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "u_x tile sweep launch");
+    return VLASOV_OK;
+}
+
 // velocity sweep from src to dst (NULL, NULL: c->f in place) with the per-cell
 // constants already in d_coef[ax - 3]
 static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *dst = nullptr)
@@ -956,6 +994,7 @@ static int run_velocity(vlasov_ctx *c, int ax, const void *src = nullptr, void *
     if (!src) src = c->f;
     if (!dst) dst = c->f;
     if (coded(c) && (src != c->f || dst != c->f)) return fail(c, VLASOV_EINVAL, "16-bit storage sweeps in place only");
+    if (ax == 3 && c->use_tiles && c->tile_ok[3]) return run_tile_ux(c, src, dst);
     const AxisPlan &p = c->plan[ax];
     const void *coef = c->d_coef[ax - 3];
     SweepMaps m;

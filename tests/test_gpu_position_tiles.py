@@ -6,6 +6,9 @@ walks the line from its far end: the same operations), so single FP32 sweeps and
 Eq. (5) steps must agree bit for bit, the moment the tile x sweep sums must equal the
 streamed one's, and the launch counters must show which kernel ran.  Shapes: line
 lengths 16, 24, 32, 48 and 64, n_uz = 32 (the z sweep's sign-grouped warps) and 16.
+The u_x sweep of Eq. (4) with lines of 48 (zero-flux, the Courant number of each cell)
+runs on the same tiles of [cell][u_x][u_y u_z]: bit for bit the streamed sweep in FP32,
+within the codec bound of the oracle in BF16 / FP16.
 """
 import numpy as np
 import pytest
@@ -148,3 +151,63 @@ def test_16bit_tile_sweeps_with_48_cell_lines(fmt):
             print("%s n_uz 48 axis %d %s: rel L1 %.2e, rel Linf %.2e" % (fmt, ax, "tiles" if tiles else "streamed", rl1, rinf))
             assert rl1 <= bound + 1e-6 and rinf <= 1.5 * (2 * bound + 1e-6)
             assert torch.equal(scale, scale0)
+
+
+@pytest.mark.parametrize("n,nu", [((4, 4, 4), (48, 48, 48)), ((4, 5, 4), (48, 8, 32))])
+def test_ux_tile_sweep_is_bitwise_the_streamed_sweep(n, nu):
+    B = _lib()
+    V = 5.0
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=11), I.fermi_dirac(nu, V), np.float32)
+    phi_np = I.fourier_potential(n, seed=12)
+    g = O.grid(n, nu, V=V)
+    dt = 0.8 / O.max_abs_nu(g, 3, 1.0, 1.0, phi_np)
+    phi = torch.from_numpy(phi_np.astype(np.float32)).cuda()
+    out = {}
+    for tiles in (True, False):
+        f = torch.from_numpy(f0).cuda()
+        v = B.Vlasov(f, V=V)
+        v.set_position_tiles(tiles)
+        v.sweep(3, dt, 1.0, phi)
+        v.sweep(3, -0.6 * dt, 1.0, phi)
+        v.status()
+        out[tiles] = f.cpu().numpy()
+        v.close()
+    assert np.array_equal(out[True], out[False])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_ux_tile_sweep_against_the_oracle(fmt):
+    # n_ux = n_uz = 48: the u_x tiles take each column's own u_z line scale per row, as
+    # the position tiles do; held to the codec bound against the FP64 oracle's sweep of
+    # the decoded input, like the register-line sweep (whose random streams differ: the
+    # codes of the two must not be equal, which shows that two kernels ran)
+    B = _lib()
+    V = 5.0
+    bound = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[fmt]
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[fmt]
+    n, nu = (4, 4, 4), (48, 16, 48)
+    f0 = I.initial_f(I.gaussian_field(n, 0.05, seed=13), I.fermi_dirac(nu, V), np.float64)
+    phi_np = I.fourier_potential(n, seed=14)
+    g = O.grid(n, nu, V=V)
+    dt = 0.8 / O.max_abs_nu(g, 3, 1.0, 1.0, phi_np)
+    phi = torch.from_numpy(phi_np.astype(np.float32)).cuda()
+    codes0, scale0 = B.encode_lines(torch.from_numpy(f0).cuda(), tdt)
+    ref = B.decode_lines(codes0, scale0).cpu().numpy()
+    O.sweep(g, ref, 3, dt, 1.0, phi_np)
+    got = {}
+    for tiles in (True, False):
+        codes, scale = codes0.clone(), scale0.clone()
+        v = B.Vlasov(codes, V=V, scale=scale)
+        v.set_position_tiles(tiles)
+        v.sweep(3, dt, 1.0, phi)
+        v.status()
+        out = B.decode_lines(codes, scale).cpu().numpy()
+        v.close()
+        err = np.abs(out - ref)
+        rl1 = err.sum() / np.abs(ref).sum()
+        rinf = err.max() / np.abs(ref).max()
+        print("%s u_x %s: rel L1 %.2e, rel Linf %.2e" % (fmt, "tiles" if tiles else "lines", rl1, rinf))
+        assert rl1 <= bound + 1e-6 and rinf <= 1.5 * (2 * bound + 1e-6)
+        assert torch.equal(scale, scale0)  # the u_x sweep keeps the line scales
+        got[tiles] = codes
+    assert not torch.equal(got[True], got[False])
