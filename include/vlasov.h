@@ -145,9 +145,10 @@ int vlasov_decode(long long nlines, int nuz, const void *codes_dev, int code_dty
  *     16 or 32: each u_z tile of 256 rows holds whole (cell, j_x) planes, whose
  *     columns are the u_y lines, so D_uy runs on the staged tile before D_uz (FP32:
  *     the separate sweeps bit for bit; 16-bit storage: D_uy's result stays FP32 in
- *     shared memory and only D_uz's is encoded); and for FP32 with n_uy = n_uz = 48
- *     (n_ux a multiple of 4), over four staged (cell, j_x) planes per block (the
- *     separate sweeps bit for bit).
+ *     shared memory and only D_uz's is encoded); and with n_uy = n_uz = 48 (n_ux a
+ *     multiple of 4), over four staged (cell, j_x) planes per block (FP32: the
+ *     separate sweeps bit for bit; 16-bit: decoded as staged, encoded once after
+ *     D_uz with refreshed line scales).
  *   mode 0: three separate sweeps.
  * FP64 storage always runs the sweeps separately.  Errors: VLASOV_EINVAL for
  * another mode.

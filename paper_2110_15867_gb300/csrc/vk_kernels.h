@@ -219,18 +219,20 @@ cudaError_t launch_kick_cube(const CUtensorMap &fmap, const CUtensorMap &smap, c
                              int grid, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
-// the kick tail D_uz D_uy in one pass over (cell, j_x) planes (plane_tail.cu): FP32,
-// n_uy = n_uz = 48, n_ux a multiple of 4; planes [plane0, plane0 + nplanes) with plane p
-// in spatial cell p / nux, both multiples of 4
+// the kick tail D_uz D_uy in one pass over (cell, j_x) planes (plane_tail.cu): FP32 or
+// 16-bit codes (dtype 1, 2, 3), n_uy = n_uz = 48, n_ux a multiple of 4; planes [plane0,
+// plane0 + nplanes) with plane p in spatial cell p / nux, both multiples of 4
 // ----------------------------------------------------------------------------
 struct PlaneTailArgs {
     long long plane0, nplanes;
     long long nux;
     const LineCoefT<float> *coef_y, *coef_z;
     unsigned *err;
+    float *scale;  // 16-bit storage: one scale per u_z line (row of a plane), refreshed
+    unsigned seed; // 16-bit storage: the stochastic-rounding streams of the D_uz encode
 };
 bool plane_tail_supported(int nuy, int nuz, int nux, int dtype);
-cudaError_t launch_plane_tail(float *f, const PlaneTailArgs &a, int nu, cudaStream_t st);
+cudaError_t launch_plane_tail(void *f, const PlaneTailArgs &a, int nu, int dtype, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // position sweeps with whole lines staged per tile (sweep_tile.cu): FP32, periodic,

@@ -131,7 +131,7 @@ struct vlasov_ctx {
     MapSpec lspec;
     // kick tail D_uz D_uy fused in the u_z line kernel (n_uy = n_uz)
     bool can_fuse_kick;
-    bool can_plane_tail; // the kick tail over staged (cell, j_x) planes (FP32, n_uy = n_uz = 48)
+    bool can_plane_tail; // the kick tail over staged (cell, j_x) planes (n_uy = n_uz = 48)
     int fuse_kick; // vlasov_set_fused_kick: 0 separate sweeps, 1 fused tail, 2 whole kick in one pass
     // position sweeps with whole lines staged per tile (see vlasov_set_position_tiles)
     // staged tiles of the x, y, z sweeps and (index 3) of the u_x sweep
@@ -940,13 +940,15 @@ static void line_slab(const vlasov_ctx *c, ContigArgs<float> &A)
 
 static int line_grid(const vlasov_ctx *, int grid, long long tiles) { return int(tiles < grid ? tiles : grid); }
 
-// u_x / u_y on FP32 or 16-bit storage with lines of 16 or 32 cells: the register-line kernel
+// u_x / u_y on FP32 or 16-bit storage with lines of 16, 32 or 48 cells: the register-line
+// kernel, unless the u_x staged tiles take the sweep (run_tile_ux)
 static bool use_reg_lines(const vlasov_ctx *c, int ax)
 {
     if (c->g.dtype == VLASOV_F64 || (ax != 3 && ax != 4)) return false;
     const int L = (&c->g.nux)[ax - 3];
     // FP32 u_x lines of 48 cells stream faster (48^3 x 48^3: 20.7 ms against 22.3 in registers;
-    // u_y 23.8 streamed against 22.0, BF16 u_x 29.6 / 28.6 and u_y 33.7 / 27.8)
+    // u_y 23.8 streamed against 22.0, BF16 u_x 29.6 / 28.6 and u_y 33.7 / 27.8; on staged
+    // tiles u_x takes 16.6 ms in FP32 and 21.8 ms in BF16)
     if (L == 48 && ax == 3 && c->g.dtype == VLASOV_F32) return false;
     return reg_lines_supported(L);
 }
@@ -1191,9 +1193,11 @@ static int run_plane_tail(vlasov_ctx *c)
     A.coef_y = (const LineCoefT<float> *)c->d_coef[1];
     A.coef_z = (const LineCoefT<float> *)c->d_coef[2];
     A.err = c->d_err;
+    A.scale = c->scale;
+    A.seed = c->sweeps; // the stochastic-rounding stream of the D_uz encode (16-bit storage)
     if (A.nplanes <= 0) return VLASOV_OK;
     PartTimer t(c, VLASOV_T_SWEEP_UYUZ, 1);
-    const cudaError_t e = launch_plane_tail(static_cast<float *>(c->f), A, c->g.nuz, c->stream);
+    const cudaError_t e = launch_plane_tail(c->f, A, c->g.nuz, c->g.dtype, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "kick tail launch");
     return VLASOV_OK;
 }
