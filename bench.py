@@ -171,6 +171,18 @@ def kernel_source_hash(kind):
     return h.hexdigest()[:16]
 
 
+def step_bandwidth(kind_n, sweep_kinds, cells, steps, ms_per_step, hbm_peak):
+    """The step on the bandwidth basis: every launch of a sweep kind (the one-pass kick
+    included) reads and writes f once, BYTES_PER_UPDATE per cell, whatever the updates it
+    makes; those bytes per step over the step time, against the measured and nominal peaks."""
+    passes = sum(kind_n.get(k, 0) for k in sweep_kinds) / steps
+    b = passes * BYTES_PER_UPDATE * cells
+    gbs = b / (ms_per_step * 1e-3) / 1e9
+    return {"passes_per_step": passes, "bytes_per_step": b, "GBs": gbs, "frac_of_measured": gbs / hbm_peak,
+            "frac_of_nominal_7900": gbs / NOMINAL_HBM_GBS,
+            "what": "bytes the f-wide passes of a step read and write (8 B per cell and pass) over the step time"}
+
+
 def committed_alu(kind):
     """ALU-pipe activity (% of peak, ncu sm__inst_executed_pipe_alu / sm__pipe_alu_cycles_active)
     of `kind` from the committed ncu summary, if it is current."""
@@ -743,6 +755,7 @@ def run_ours(args):
             if u > 1:
                 per_kind[k]["GBs_actual_bytes"] = BYTES_PER_UPDATE * cells / t / 1e9
     gpu_launches = int(sum(kind_n.values()))
+    step_hbm = step_bandwidth(kind_n, sweep_kinds, cells, args.steps, ms_total / args.steps, hbm_peak)
 
     # velocity moments of the final state (density, mean velocity, dispersion tensor), timed alone
     um = torch.empty((3, n, n, n), dtype=torch.float64, device=dev)
@@ -853,6 +866,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(world),
             "roofline": roofline,
+            "step_hbm": step_hbm,
             "kernels": per_kind,
             "cpu_baseline": cpu,
             "lowprec": lowprec,

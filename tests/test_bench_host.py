@@ -68,3 +68,15 @@ def test_source_hash_ignores_comments_only():
         h = bench.kernel_source_hash(kind)
         assert isinstance(h, str) and len(h) == 16
     assert bench.kernel_source_hash("no_such_kernel") is None
+
+
+def test_step_bandwidth_counts_one_pass_per_sweep_launch():
+    # two one-pass kicks and three position sweeps per step: five passes of 8 B per cell,
+    # whatever the updates a pass makes
+    kind_n = {"kick": 6, "sweep_x": 3, "sweep_y": 3, "sweep_z": 3, "moment": 3, "poisson": 27}
+    kinds = ["kick", "sweep_x", "sweep_y", "sweep_z"]
+    r = bench.step_bandwidth(kind_n, kinds, cells=1000, steps=3, ms_per_step=1.0, hbm_peak=100.0)
+    assert r["passes_per_step"] == 5
+    assert r["bytes_per_step"] == 5 * bench.BYTES_PER_UPDATE * 1000
+    assert abs(r["GBs"] - 5 * 8 * 1000 / 1e-3 / 1e9) < 1e-12
+    assert abs(r["frac_of_measured"] - r["GBs"] / 100.0) < 1e-15
