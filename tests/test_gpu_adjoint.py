@@ -343,3 +343,37 @@ def test_dLdphi_is_reproducible_when_cells_fill_blocks():
         runs.append((lam.cpu().numpy(), dphi.cpu().numpy()))
         v.close()
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_step_record_with_48_cell_velocity_lines():
+    # n_u = 48: the recorded step runs D_ux on the staged tiles of [cell][u_x][u_y u_z] out
+    # of place (each sweep reads one array and writes the next); its result equals the
+    # in-place step (which takes the fused staged-plane tail) bit for bit, and the recorded
+    # adjoint of that step runs on the recorded inputs (finite, and the same as the
+    # adjoint that records into the library's own arrays)
+    B = _lib()
+    n, nu = (4, 4, 4), (48, 48, 48)
+    f0, phi, lam0 = _setup(n, nu)
+    g = O.grid(n, nu, V=5.0)
+    dt = _dt_step(g, phi, 0.8)
+    phi_t = torch.from_numpy(phi).cuda()
+    f = torch.from_numpy(f0).cuda()
+    v = B.Vlasov(f, V=5.0)
+    f_n = f.clone()
+    rec = [torch.empty_like(f) for _ in range(8)]
+    f_next = torch.empty_like(f)
+    v.step_record(f_n, rec, dt, 1.0, phi_t, f_next)
+    v.step(dt, 1.0, 1.0, phi_t)
+    v.status()
+    assert torch.equal(f_next, f)
+    lam = torch.from_numpy(lam0).cuda()
+    dphi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    v.step_adjoint_recorded(f_n, rec, lam, dt, 1.0, phi_t, dphi)
+    lam2 = torch.from_numpy(lam0).cuda()
+    dphi2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    v.step_adjoint(f_n, lam2, dt, 1.0, phi_t, dphi2)
+    v.status()
+    assert torch.isfinite(lam).all() and torch.isfinite(dphi).all()
+    assert torch.equal(lam, lam2)
+    assert (dphi - dphi2).abs().max() <= 1e-12 * dphi.abs().max()
+    v.close()
