@@ -31,7 +31,13 @@
 
 namespace vk {
 
-constexpr int kAdjBlock = 256;
+constexpr int kAdjBlock = 256;    // threads (lines) per block: position lines, u_z rows of 32
+// velocity lines and u_z rows of up to 16 cells: blocks of two warps, four times as many
+// resident (the warps of a block wait for each other at the per-cell reduction of dL/dnu;
+// on 32^3 x 16^3: u_x 0.374 -> 0.359 ms, u_z 0.362 -> 0.335 ms against 256 threads, 0.361 /
+// 0.341 with 128; position lines are slower in smaller blocks: 0.556 -> 0.584 ms with 128)
+constexpr int kAdjVelBlock = 64;
+template <bool PERIODIC> constexpr int adj_block() { return PERIODIC ? kAdjBlock : kAdjVelBlock; }
 constexpr int kAdjUnroll = 1;    // interior faces per loop iteration of the column march
 constexpr int kAdjMinBlocks = 3; // resident blocks per SM the FP32 column march is compiled for
 constexpr int kAdjRegMax = 32;   // FP32 lines up to this length (compile-time instances) march in registers
@@ -555,11 +561,11 @@ __device__ __forceinline__ double warp_sum_d(double v) { return warp_sum<double>
 // cell sums in registers; the block then merges runs of equal cells.  With
 // part non-null every block lies in one cell: the block's sum goes to
 // part[blockIdx.x] (summed per cell in a fixed order by a second kernel).
-template <typename C>
+template <int BT, typename C>
 __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, double fac, double *part)
 {
-    __shared__ long long s_cell[kAdjBlock / 32];
-    __shared__ double s_sum[kAdjBlock / 32];
+    __shared__ long long s_cell[BT / 32];
+    __shared__ double s_sum[BT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (part) {
         // FP32 storage: the lines' values are FP32; the warp sums them in FP32 (FP64 adds
@@ -570,7 +576,7 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
         __syncthreads();
         if (threadIdx.x == 0) {
             double acc = 0.0;
-            for (int q = 0; q < kAdjBlock / 32; ++q) acc += s_sum[q];
+            for (int q = 0; q < BT / 32; ++q) acc += s_sum[q];
             part[blockIdx.x] = acc;
         }
         return;
@@ -588,7 +594,7 @@ __device__ __forceinline__ void reduce_dnu(long long cell, C dnu, double *dLdg, 
     if (threadIdx.x == 0) {
         long long cur = -1;
         double acc = 0.0;
-        for (int q = 0; q < kAdjBlock / 32; ++q) {
+        for (int q = 0; q < BT / 32; ++q) {
             if (s_cell[q] != cur) {
                 if (cur >= 0 && acc != 0.0) atomicAdd(dLdg + cur, acc * fac);
                 cur = s_cell[q];
@@ -613,15 +619,18 @@ __device__ __forceinline__ long long adj_div(long long n, const AdjArgs<C> &a, c
 // Any axis: f viewed as [O][L][I]; thread t owns the line (outer = t / I,
 // inner = t % I).  SMALL4: periodic lines of 4 cells.
 template <typename T, bool PERIODIC, bool SMALL4, int LCT>
-__global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 16 && LCT <= kAdjRegMax) ? 2 : kAdjMinBlocks)
+__global__ void __launch_bounds__(adj_block<PERIODIC>(),
+                                  (sizeof(T) == 8 ? 2 : (LCT > 16 && LCT <= kAdjRegMax) ? 2 : kAdjMinBlocks) *
+                                      (kAdjBlock / adj_block<PERIODIC>()))
     adjoint_lines_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
-    long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    constexpr int BT = adj_block<PERIODIC>();
+    long long t = blockIdx.x * (long long)BT + threadIdx.x;
     if (a.perm_line > 0) {
-        // lines of the block's u_z rows, negative halves first (the host checks Lz | kAdjBlock)
-        const int h = a.perm_line / 2, tt = threadIdx.x % (kAdjBlock / 2);
-        t = blockIdx.x * (long long)kAdjBlock + (tt / h) * a.perm_line + (threadIdx.x >= kAdjBlock / 2 ? h : 0) + tt % h;
+        // lines of the block's u_z rows, negative halves first (the host checks Lz | BT)
+        const int h = a.perm_line / 2, tt = threadIdx.x % (BT / 2);
+        t = blockIdx.x * (long long)BT + (tt / h) * a.perm_line + (threadIdx.x >= BT / 2 ? h : 0) + tt % h;
     }
     long long cell = -1;
     C dnu = C(0);
@@ -674,7 +683,7 @@ __global__ void __launch_bounds__(kAdjBlock, sizeof(T) == 8 ? 2 : (LCT > 16 && L
         }
         cell = a.dLdg ? adj_div(t, a, a.div_lpc, a.lines_per_cell) : -1;
     }
-    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
+    if (a.dLdg) reduce_dnu<BT>(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
 
 // u_z lines of L = 8, 16, 32 cells: one row per thread through 16-byte vector
@@ -716,11 +725,11 @@ __device__ __forceinline__ void rows_line(const uint4 *fp, const uint4 *lp, uint
 
 // u_z rows of 8 or 16 cells: each thread loads its own row with 16-byte loads.
 template <typename T, int L>
-__global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
+__global__ void __launch_bounds__(kAdjVelBlock, 3 * kAdjBlock / kAdjVelBlock) adjoint_rows_kernel(const __grid_constant__ AdjArgs<T> a)
 {
     using C = T;
-    constexpr int per = 16 / int(sizeof(T));
-    const long long t = blockIdx.x * (long long)kAdjBlock + threadIdx.x;
+    constexpr int per = 16 / int(sizeof(T)), BT = kAdjVelBlock;
+    const long long t = blockIdx.x * (long long)BT + threadIdx.x;
     long long cell = -1;
     C dnu = C(0);
     if (t < a.nlines) {
@@ -741,7 +750,7 @@ __global__ void __launch_bounds__(kAdjBlock, 3) adjoint_rows_kernel(const __grid
         }
         cell = a.dLdg ? adj_div(t, a, a.div_lpc, a.lines_per_cell) : -1;
     }
-    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
+    if (a.dLdg) reduce_dnu<BT>(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
 
 // u_z rows of 32 cells: a warp's 32 rows are 32 L contiguous elements; it stages
@@ -823,7 +832,7 @@ __global__ void __launch_bounds__(kAdjBlock, 2) adjoint_rows_staged_kernel(const
         const int row = k / CH, col = 4 * (k % CH);
         if (row < nrows) go[k] = *reinterpret_cast<const uint4 *>(sl + row * P + col);
     }
-    if (a.dLdg) reduce_dnu(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
+    if (a.dLdg) reduce_dnu<kAdjBlock>(cell, dnu, a.dLdg, a.dnu_dg, a.block_part);
 }
 
 // dLdg[c] += fac * sum of part over the blocks of cell c, in block order
@@ -859,10 +868,11 @@ __global__ void gradient_adjoint_kernel(GridDims g, const double *__restrict__ d
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
-template <typename T, int L> static cudaError_t launch_rows(const AdjArgs<T> &a, dim3 grid, cudaStream_t st)
+template <typename T, int L> static cudaError_t launch_rows(const AdjArgs<T> &a, cudaStream_t st)
 {
+    const dim3 grid((unsigned)((a.nlines + adjoint_block(5, true, L) - 1) / adjoint_block(5, true, L)));
     if constexpr (L <= 16) {
-        adjoint_rows_kernel<T, L><<<grid, kAdjBlock, 0, st>>>(a);
+        adjoint_rows_kernel<T, L><<<grid, kAdjVelBlock, 0, st>>>(a);
     } else {
         const cudaError_t e = cudaFuncSetAttribute(adjoint_rows_staged_kernel<T, L>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(rows_smem<L>()));
@@ -885,7 +895,8 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a_in, bo
         a.div_opc = make_fastdiv(unsigned(a.outer_per_cell));
         a.div_lpc = make_fastdiv(unsigned(a.lines_per_cell > 0 ? a.lines_per_cell : 1));
     }
-    const long long blocks = (a.nlines + kAdjBlock - 1) / kAdjBlock;
+    const int bt = adjoint_block(a.periodic ? 0 : 3, rows, a.L);
+    const long long blocks = (a.nlines + bt - 1) / bt;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)blocks);
@@ -893,31 +904,31 @@ template <typename T> static cudaError_t launch_adj_t(const AdjArgs<T> &a_in, bo
         // FP32 only: a row of 32 doubles (twice, with lambda) would not stay in registers
         if constexpr (!std::is_same<T, float>::value) return cudaErrorInvalidValue;
         else switch (a.L) {
-        case 8: return launch_rows<T, 8>(a, grid, st);
-        case 16: return launch_rows<T, 16>(a, grid, st);
-        case 32: return launch_rows<T, 32>(a, grid, st);
+        case 8: return launch_rows<T, 8>(a, st);
+        case 16: return launch_rows<T, 16>(a, st);
+        case 32: return launch_rows<T, 32>(a, st);
         default: return cudaErrorInvalidValue;
         }
     } else if (a.periodic && a.L == 4) {
-        adjoint_lines_kernel<T, true, true, 0><<<grid, kAdjBlock, 0, st>>>(a);
+        adjoint_lines_kernel<T, true, true, 0><<<grid, bt, 0, st>>>(a);
     } else if constexpr (std::is_same<T, float>::value) {
         // FP32: unrolled walks for the common line lengths
         const bool p = a.periodic;
 #define ADJ_LINES(LL)                                                                                              \
     if (a.L == LL) {                                                                                                  \
-        if (p) adjoint_lines_kernel<T, true, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                               \
-        else adjoint_lines_kernel<T, false, false, LL><<<grid, kAdjBlock, 0, st>>>(a);                                \
+        if (p) adjoint_lines_kernel<T, true, false, LL><<<grid, bt, 0, st>>>(a);                               \
+        else adjoint_lines_kernel<T, false, false, LL><<<grid, bt, 0, st>>>(a);                                \
         return cudaGetLastError();                                                                                    \
     }
         ADJ_LINES(16)
         ADJ_LINES(32)
         ADJ_LINES(64)
 #undef ADJ_LINES
-        if (p) adjoint_lines_kernel<T, true, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
-        else adjoint_lines_kernel<T, false, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
+        if (p) adjoint_lines_kernel<T, true, false, 0><<<grid, bt, 0, st>>>(a);
+        else adjoint_lines_kernel<T, false, false, 0><<<grid, bt, 0, st>>>(a);
     } else {
-        if (a.periodic) adjoint_lines_kernel<T, true, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
-        else adjoint_lines_kernel<T, false, false, 0><<<grid, kAdjBlock, 0, st>>>(a);
+        if (a.periodic) adjoint_lines_kernel<T, true, false, 0><<<grid, bt, 0, st>>>(a);
+        else adjoint_lines_kernel<T, false, false, 0><<<grid, bt, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -931,7 +942,11 @@ cudaError_t launch_cell_sum(long long ncell, int blocks_per_cell, const double *
     return cudaGetLastError();
 }
 
-int adjoint_block_threads() { return kAdjBlock; }
+int adjoint_block(int axis, bool rows, int L)
+{
+    if (axis < 3) return kAdjBlock;
+    return rows && L > 16 ? kAdjBlock : kAdjVelBlock;
+}
 
 bool adjoint_rows_supported(int L, int dtype) { return dtype == 1 && (L == 8 || L == 16 || L == 32); }
 

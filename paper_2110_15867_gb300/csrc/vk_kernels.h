@@ -369,7 +369,8 @@ template <typename C> struct AdjArgs {
 bool adjoint_rows_supported(int L, int dtype);
 cudaError_t launch_adjoint_f32(const AdjArgs<float> &a, bool rows, cudaStream_t st);
 cudaError_t launch_adjoint_f64(const AdjArgs<double> &a, bool rows, cudaStream_t st);
-int adjoint_block_threads(); // lines (threads) per block of the adjoint kernels
+// lines (threads) per block of the adjoint kernel of axis (rows: the u_z row kernels; L: line length)
+int adjoint_block(int axis, bool rows, int L);
 // dLdg[c] += fac * sum_q part[c * blocks_per_cell + q] in order
 cudaError_t launch_cell_sum(long long ncell, int blocks_per_cell, const double *part, double fac, double *dLdg,
                             cudaStream_t st);

@@ -1522,7 +1522,7 @@ static int run_adjoint_t(vlasov_ctx *c, const void *f_in, void *lam, int ax, dou
             shifted = shifted || fabs(nu) >= 1.0;
         }
         // z: group each block's threads by the sign of u_z (whole u_z lines per block)
-        const int bt = adjoint_block_threads(), nuz = int(c->g.nuz);
+        const int bt = adjoint_block(ax, false, int(d6[ax])), nuz = int(c->g.nuz);
         if (ax == 2 && nuz % 2 == 0 && bt % nuz == 0 && I % bt == 0) A.perm_line = nuz;
         if (shifted) {
             // lambda is read N cells on: write the result to scratch, then copy back
@@ -1545,7 +1545,7 @@ static int run_adjoint_t(vlasov_ctx *c, const void *f_in, void *lam, int ax, dou
     if (rows) A.outer_per_cell = A.lines_per_cell; // one row per line: cell = row / rows per cell
     // when a cell's lines fill whole blocks, each block writes its sum and a second pass adds
     // them per cell in a fixed order (reproducible); otherwise FP64 atomics
-    const int bt = adjoint_block_threads();
+    const int bt = adjoint_block(ax, rows, A.L);
     const bool det = A.dLdg && A.lines_per_cell % bt == 0;
     if (det) {
         const size_t nblk = (size_t)(A.nlines / bt);
