@@ -659,15 +659,26 @@ __global__ void __launch_bounds__(adj_block<PERIODIC>(),
             C dLds, osum;
             if constexpr (!SMALL4 && LCT > 0 && LCT <= kAdjRegMax) {
                 // short line: every load first (in walk order; lambda rotated by a
-                // periodic whole-cell shift), the march on registers, then every store
+                // periodic whole-cell shift, read straight when there is none: the
+                // rotated index costs the position adjoints 0.556 against 0.526 ms),
+                // the march on registers, then every store
                 const int shift = PERIODIC ? (kc.nd >> 1) % LCT : 0;
                 RegLine<T, LCT, false> acc;
+                const T *fp = f + off, *lp = lin + off;
+                if (shift == 0) {
 #pragma unroll
-                for (int i = 0; i < LCT; ++i) {
-                    int r = i + shift;
-                    if (r >= LCT) r -= LCT;
-                    acc.cv[i] = f[off + i * st];
-                    acc.lv[i] = lin[off + r * st];
+                    for (int i = 0; i < LCT; ++i) {
+                        acc.cv[i] = fp[i * st];
+                        acc.lv[i] = lp[i * st];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < LCT; ++i) {
+                        int r = i + shift;
+                        if (r >= LCT) r -= LCT;
+                        acc.cv[i] = fp[i * st];
+                        acc.lv[i] = lp[r * st];
+                    }
                 }
                 march_adjoint<PERIODIC, LCT, C>(acc, lim, LCT, dLds, osum);
 #pragma unroll
