@@ -271,10 +271,10 @@ __global__ void __launch_bounds__(tile_groups<L>() * 256 + kProducer, 1)
 }
 
 // ----------------------------------------------------------------------------
-// 16-bit storage (BF16 / FP16 codes, one FP32 scale per u_z line of 32 cells)
+// 16-bit storage (BF16 / FP16 codes, one FP32 scale per u_z line of 32 or 48 cells)
 // ----------------------------------------------------------------------------
 // The same tiles, 512-byte rows of codes (no swizzle) plus the tile's scales (box
-// {8 u_z lines, L rows}); a position sweep keeps every scale.  Each value decodes as
+// {8 u_z lines, L rows} for n_uz = 32); a position sweep and a u_x sweep keep every scale.  Each value decodes as
 // code x scale, the line is marched in FP32 and every value is encoded back with
 // stochastic rounding (one stream per column and sweep, one draw per value in march
 // order).  z sweep: warp w takes the columns of one sign of units 2 (w % 4) and
