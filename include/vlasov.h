@@ -284,6 +284,17 @@ int vlasov_step_host(vlasov_ctx *ctx, void *f_host, double dt, double a_half, do
 int vlasov_host_wait(vlasov_ctx *ctx);
 
 /*
+ * Failure-path self-test (no counterpart in the paper).  Queues one kernel whose
+ * thread waits, with the library's bounded device wait (the wait of every TMA
+ * kernel for a copy or a peer; 2 s at most), for an mbarrier phase that nothing
+ * completes: the wait runs out, the kernel records the timeout in the context's
+ * error word and returns, with nothing left in flight.  The next vlasov_status
+ * returns VLASOV_ETIMEOUT and clears the word; the context stays usable.  No fault,
+ * trap or endless loop is involved.  VLASOV_EINVAL for a null context.
+ */
+int vlasov_selftest_wait(vlasov_ctx *ctx);
+
+/*
  * Per-part timers (the paper times each part of a step, Sec. 5.1).  While
  * enabled, every kernel the library queues is bracketed by two CUDA events on
  * the context stream.  vlasov_read_timers synchronises the stream and, for each

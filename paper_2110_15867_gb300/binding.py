@@ -47,7 +47,7 @@ SYMBOLS = ("vlasov_init", "vlasov_destroy", "vlasov_set_stream", "vlasov_sweep",
            "vlasov_moment_adjoint", "vlasov_set_fused_kick", "vlasov_moments",
            "vlasov_step_record_sc", "vlasov_step_adjoint_recorded_sc", "vlasov_set_adjoint_arrays",
            "vlasov_set_fused_moment", "vlasov_kick", "vlasov_step_host", "vlasov_encode", "vlasov_decode",
-           "vlasov_set_position_tiles", "vlasov_host_wait")
+           "vlasov_set_position_tiles", "vlasov_host_wait", "vlasov_selftest_wait")
 
 # spatial cells the allocation-free velocity sweep can hold (its static scratch)
 STATIC_MAX_CELLS = 32768
@@ -139,6 +139,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.vlasov_step_host.restype = ctypes.c_int
     L.vlasov_host_wait.argtypes = [_VP]
     L.vlasov_host_wait.restype = ctypes.c_int
+    L.vlasov_selftest_wait.argtypes = [_VP]
+    L.vlasov_selftest_wait.restype = ctypes.c_int
     L.vlasov_encode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP]
     L.vlasov_encode.restype = ctypes.c_int
     L.vlasov_decode.argtypes = [ctypes.c_longlong, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]
@@ -588,6 +590,12 @@ class Vlasov:
         all of them first)."""
         self._sync_stream()
         _check(self.ctx, load().vlasov_host_wait(self.ctx))
+
+    def selftest_wait(self):
+        """Queue the failure-path self-test: a kernel whose bounded device wait runs out;
+        the next status() raises ETIMEOUT and the context stays usable."""
+        self._sync_stream()
+        _check(self.ctx, load().vlasov_selftest_wait(self.ctx))
 
     def set_adjoint_arrays(self, arrays: int):
         """f-sized scratch arrays step_adjoint may hold: 8, 4 or 0 (8 if they fit, else 4)."""

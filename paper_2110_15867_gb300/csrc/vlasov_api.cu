@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include "../../include/vlasov.h"
+#include "vk_common.cuh"
 #include "vk_kernels.h"
 
 using namespace vk;
@@ -1450,6 +1451,30 @@ extern "C" int vlasov_host_wait(vlasov_ctx *c)
 {
     if (!c) return VLASOV_EINVAL;
     VK_SETTLE(c);
+    return VLASOV_OK;
+}
+
+namespace {
+// One thread waits, with the bounded wait of the TMA kernels, for an mbarrier phase that
+// no thread completes (one arrival expected, none made): the wait runs out at its limit,
+// the thread records ERR_TIMEOUT and the kernel returns.
+__global__ void wait_selftest_kernel(unsigned *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    if (!mbar_wait_bounded(&bar, 0)) atomicOr(err, ERR_TIMEOUT);
+}
+} // namespace
+
+extern "C" int vlasov_selftest_wait(vlasov_ctx *c)
+{
+    if (!c) return VLASOV_EINVAL;
+    VK_SETTLE(c);
+    wait_selftest_kernel<<<1, 32, 0, c->stream>>>(c->d_err);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "wait self-test launch");
     return VLASOV_OK;
 }
 
